@@ -1,0 +1,304 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself:
+brute force, library routines, closed forms, invariants and the paper's own
+design statement (Sec. III.A: adjacent channels cross over near -6 dB)."""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.signal
+import scipy.special
+
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+rng = np.random.default_rng(7)
+
+
+def crandn(*shape):
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+# ---------------------------------------------------------------- DFT / FFT
+@pytest.mark.parametrize("n", [1, 2, 4, 8, 16, 32, 64])
+def test_fft_matches_bruteforce_dft(n):
+    x = crandn(n)
+    # brute force written independently here: explicit double loop
+    ref = np.array([sum(x[p] * np.exp(-2j * np.pi * ((c * p) % n) / n) for p in range(n))
+                    for c in range(n)])
+    scale = np.linalg.norm(ref) + 1e-300
+    assert np.linalg.norm(oracle.dft(x) - ref) / scale < 1e-13
+    assert np.linalg.norm(oracle.fft(x) - ref) / scale < 1e-13
+
+
+@pytest.mark.parametrize("n", [128, 1024, 4096, 16384])
+def test_fft_matches_library_fft(n):
+    x = crandn(n)
+    ref = np.fft.fft(x)
+    assert np.linalg.norm(oracle.fft(x) - ref) / np.linalg.norm(ref) < 1e-13
+
+
+def test_fft_unit_impulse_and_dc():
+    n = 64
+    e = np.zeros(n, complex); e[3] = 1.0
+    c = np.arange(n)
+    assert np.allclose(oracle.fft(e), np.exp(-2j * np.pi * 3 * c / n), atol=1e-14)
+    assert np.allclose(oracle.fft(np.ones(n)), n * (c == 0), atol=1e-12)
+
+
+# ---------------------------------------------------------------- windows
+@pytest.mark.parametrize("m", [1, 2, 7, 64, 257])
+def test_windows_match_scipy(m):
+    sw = scipy.signal.windows
+    assert np.allclose(oracle.window("rect", m), np.ones(m), atol=0)
+    assert np.allclose(oracle.window("hann", m), sw.hann(m, sym=True), atol=1e-15)
+    assert np.allclose(oracle.window("hamming", m), sw.hamming(m, sym=True), atol=1e-15)
+    assert np.allclose(oracle.window("blackman", m), sw.blackman(m, sym=True), atol=1e-15)
+    for beta in (0.0, 5.0, 9.0):
+        assert np.allclose(oracle.window("kaiser", m, beta), sw.kaiser(m, beta, sym=True),
+                           rtol=1e-13, atol=1e-15)
+
+
+@pytest.mark.parametrize("x", [0.0, 0.5, 1.0, 3.0, 9.0, 20.0, 40.0])
+def test_bessel_i0_matches_library(x):
+    assert oracle.bessel_i0(x) == pytest.approx(float(scipy.special.i0(x)), rel=1e-14)
+
+
+def test_window_closed_form_points():
+    m = 65
+    assert oracle.window("hann", m)[0] == pytest.approx(0.0, abs=1e-16)
+    assert oracle.window("hann", m)[32] == pytest.approx(1.0, abs=1e-15)
+    assert oracle.window("hamming", m)[0] == pytest.approx(0.08, abs=1e-15)
+    assert oracle.window("blackman", m)[32] == pytest.approx(1.0, abs=1e-15)
+    assert oracle.window("kaiser", m, 9.0)[0] == pytest.approx(1.0 / scipy.special.i0(9.0),
+                                                               rel=1e-13)
+
+
+def test_lowpass_is_normalised_windowed_sinc():
+    m, fc = 256, 1.0 / 128
+    h = oracle.lowpass("hamming", m, fc)
+    j = np.arange(m)
+    ref = scipy.signal.windows.hamming(m) * np.sinc(2 * fc * (j - (m - 1) / 2))
+    ref /= ref.sum()
+    assert np.allclose(h, ref, rtol=1e-13, atol=1e-18)
+    assert h.sum() == pytest.approx(1.0, abs=1e-14)
+    # scipy.signal.firwin builds the same windowed sinc (cutoff in Nyquist units)
+    fw = scipy.signal.firwin(m, 2 * fc, window="hamming", scale=False)
+    assert np.allclose(h, fw / fw.sum(), rtol=1e-12, atol=1e-18)
+
+
+def test_square_window_is_moving_average():
+    """Sec. III.B: the demodulator's anti-alias filter is a square-window moving average."""
+    h = oracle.lowpass("rect", 500, 0.0)
+    assert np.allclose(h, 1.0 / 500, rtol=1e-15)
+
+
+def test_prototype_fp32_rounding():
+    h64, h32 = oracle.pfb_prototype(64, 4, "hann")
+    assert h32.dtype == np.float32
+    assert np.array_equal(h32, h64.astype(np.float32))
+    assert h64.sum() == pytest.approx(1.0, abs=1e-14)
+
+
+# ------------------------------------------------ paper: -6 dB cross-over
+def _resp(h, f):
+    j = np.arange(len(h))
+    return abs(np.sum(h * np.exp(-2j * np.pi * f * j)))
+
+
+def test_paper_adjacent_channel_crossover_6db():
+    """Sec. III.A / Fig. 3: the sinc cut-off is placed so that adjacent
+    channels cross over at about -6 dB.  Fixture cites the paper's parameters."""
+    with open(os.path.join(GOLDEN, "paper_pfb_crossover.json")) as f:
+        g = json.load(f)
+    for case in g["cases"]:
+        n, taps, win = case["n_chan"], case["taps"], case["window"]
+        h64, _ = oracle.pfb_prototype(n, taps, win, case.get("beta", 0.0))
+        ratio = _resp(h64, 0.5 / n) / _resp(h64, 0.0)
+        db = 20 * np.log10(ratio)
+        assert abs(db - g["crossover_db"]) < g["tolerance_db"], (case, db)
+
+
+# ---------------------------------------------------------- integer rules
+def test_freq_to_word_exact_values():
+    fs = 200e6
+    assert oracle.freq_to_word(0.0, fs) == 0
+    assert oracle.freq_to_word(fs / 4, fs) == 2 ** 62
+    assert oracle.freq_to_word(-fs / 4, fs) == 2 ** 64 - 2 ** 62
+    assert oracle.freq_to_word(-fs / 2, fs) == 2 ** 63
+    for c in (1, 5, 63):
+        assert oracle.freq_to_word(c * fs / 64, fs) == (c << 58)
+    # a 40 kHz tone: the rule scales the FP64 quotient f/fs (relative error
+    # <= 2^-53), so the word is within one unit of the exact rational value
+    from fractions import Fraction
+    exact = Fraction(40_000, 200_000_000) * 2 ** 64
+    assert abs(oracle.freq_to_word(40e3, fs) - round(exact)) <= 1
+
+
+def test_word_to_bin_rule():
+    from fractions import Fraction
+    r = np.random.default_rng(1)
+    for n in (2, 64, 4096, 16384):
+        words = [int(w) for w in r.integers(0, 2 ** 64, 200, dtype=np.uint64)]
+        words += [(c << (64 - int(np.log2(n)))) for c in range(0, n, max(1, n // 16))]
+        # exact ties: half a bin above centre rounds up
+        words += [((3 << 1) + 1) << (63 - int(np.log2(n))) & (2 ** 64 - 1)]
+        for w in words:
+            q = Fraction(w * n, 2 ** 64)
+            ref = int((q + Fraction(1, 2)).__floor__()) % n   # round half up
+            assert oracle.word_to_bin(w, n) == ref
+
+
+def test_nco_phase_is_product_mod_2_64():
+    for w, m in [(3, 5), (2 ** 63 + 12345, 2 ** 40 + 7), (2 ** 64 - 1, 2 ** 64 - 1)]:
+        assert oracle.nco_phase(w, m) == (w * m) % 2 ** 64
+
+
+# ------------------------------------------------------------- PFB pins
+def _tone(n, c0, N, A, th):
+    m = np.arange(n)
+    return A * np.exp(1j * (2 * np.pi * ((c0 * m) % N) / N + th))
+
+
+@pytest.mark.parametrize("N,T,win,beta", [(8, 4, "hann", 0.0), (16, 3, "kaiser", 9.0),
+                                          (32, 8, "hamming", 0.0)])
+def test_pfb_equals_filtered_mixed_stream(N, T, win, beta):
+    """Library-routine pin: each PFB channel c is the stream mixed down by
+    exp(-2*pi*i*c*m/N), convolved with the time-reversed prototype
+    (scipy.signal.lfilter) and sampled every N samples."""
+    h64, h32 = oracle.pfb_prototype(N, T, win, beta)
+    h = h32.astype(np.float64)
+    n = N * 23
+    x = crandn(n) * 100
+    y = oracle.pfb(x, N, T, h)["full"]
+    m = np.arange(n)
+    for c in range(N):
+        z = x * np.exp(-2j * np.pi * ((c * m) % N) / N)
+        conv = scipy.signal.lfilter(h[::-1], [1.0], z)
+        ref = conv[N - 1::N][: y.shape[0]]
+        assert np.allclose(y[:, c], ref, rtol=1e-12, atol=1e-10)
+
+
+def test_pfb_bin_centred_tone_closed_form():
+    """A pure tone at bin c0 (FP64, unquantised) gives, after T-1 warm-up frames,
+    y_k[c] = A e^{i th} DFT(P)[c - c0] with P[p] = sum_t h[tN+p]; so y_k[c0] =
+    A e^{i th} sum(h)."""
+    N, T, c0, A, th = 64, 4, 13, 1234.5, 0.7
+    _, h32 = oracle.pfb_prototype(N, T, "hann")
+    h = h32.astype(np.float64)
+    x = _tone(N * 40, c0, N, A, th)
+    y = oracle.pfb(x, N, T, h)["full"]
+    P = h.reshape(T, N).sum(axis=0)
+    leak = np.fft.fft(P)
+    for k in range(T - 1, y.shape[0]):
+        # the tone's phase at the frame origin (k+1)N - M is a multiple of 2*pi
+        ref = A * np.exp(1j * th) * leak[(np.arange(N) - c0) % N]
+        assert np.allclose(y[k], ref, rtol=1e-12, atol=1e-9 * A)
+    assert abs(y[T - 1, c0] - A * np.exp(1j * th) * h.sum()) < 1e-10 * A
+
+
+def test_pfb_parseval_linearity_shift():
+    N, T = 32, 4
+    _, h32 = oracle.pfb_prototype(N, T, "kaiser", 9.0)
+    h = h32.astype(np.float64)
+    n = N * 30
+    x1, x2 = crandn(n), crandn(n)
+    r1 = oracle.pfb(x1, N, T, h, want_v=True)
+    # Parseval on every frame
+    lhs = np.sum(abs(r1["full"]) ** 2, axis=1)
+    rhs = N * np.sum(abs(r1["v"]) ** 2, axis=1)
+    assert np.allclose(lhs, rhs, rtol=1e-12)
+    # linearity
+    a, b = 0.3 - 1.1j, 2.5
+    r12 = oracle.pfb(a * x1 + b * x2, N, T, h)["full"]
+    r2 = oracle.pfb(x2, N, T, h)["full"]
+    assert np.allclose(r12, a * r1["full"] + b * r2, rtol=1e-12, atol=1e-12)
+    # a shift by N samples shifts the output by one frame
+    xs = np.concatenate([np.zeros(N, complex), x1[:-N]])
+    rs = oracle.pfb(xs, N, T, h)["full"]
+    assert np.allclose(rs[1:], r1["full"][:-1], rtol=1e-12, atol=1e-12)
+
+
+def test_pfb_int16_matches_f64_and_slices():
+    N, T = 16, 4
+    _, h32 = oracle.pfb_prototype(N, T, "hann")
+    h = h32.astype(np.float64)
+    r = np.random.default_rng(3)
+    xi = r.integers(-8192, 8192, size=(N * 50, 2)).astype(np.int16)
+    xc = xi[:, 0].astype(float) + 1j * xi[:, 1]
+    bins = [0, 5, 15]
+    a = oracle.pfb(xi, N, T, h, bins=bins)
+    b = oracle.pfb(xc, N, T, h, bins=bins)
+    assert np.array_equal(a["full"], b["full"])
+    assert np.array_equal(a["tones"], b["tones"])
+    assert np.array_equal(a["tones"], b["full"][:, bins].T)
+    s = oracle.pfb(xi, N, T, h, k_begin=7, k_end=31, bins=bins)
+    assert np.array_equal(s["full"], a["full"][7:31])
+    assert np.array_equal(s["tones"], a["tones"][:, 7:31])
+
+
+# ----------------------------------------------------------- demod pins
+def _word_tone(n, w, A, th):
+    m = np.arange(n, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        ph = (m * np.uint64(w)).view(np.int64).astype(float) * (np.pi / 2 ** 63)
+    return A * np.exp(1j * (ph + th))
+
+
+def test_demod_own_tone_is_constant():
+    L, D = 64, 16
+    w = int(np.random.default_rng(5).integers(0, 2 ** 63)) * 2 + 1
+    h = oracle.lowpass("blackman", L, 0.05)
+    x = _word_tone(D * 40, w, 321.0, -0.4)
+    out = oracle.demod(x, L, D, h, [w])[0]
+    k0 = L // D - 1
+    assert np.allclose(out[k0:], 321.0 * np.exp(-0.4j), rtol=1e-12)
+
+
+def test_demod_moving_average_dirichlet():
+    """Square window, D = L: an off tone at delta cycles/sample gives the
+    Dirichlet kernel (1/L) sum_n e^{2 pi i delta (b+n)}."""
+    L = D = 50
+    fs = 1.0
+    w_t = oracle.freq_to_word(0.1, fs)
+    w_x = oracle.freq_to_word(0.1 + 0.013, fs)
+    delta = ((w_x - w_t) % 2 ** 64) / 2 ** 64
+    h = oracle.lowpass("rect", L, 0.0)
+    x = _word_tone(D * 12, w_x, 10.0, 0.0)
+    out = oracle.demod(x, L, D, h, [w_t])[0]
+    for k in range(1, 12):
+        b = (k + 1) * D - L
+        n = np.arange(L)
+        # x e^{-i phi_t} = 10 e^{i (phi_x - phi_t)} and phi_x - phi_t = 2 pi delta m exactly
+        ref = 10.0 / L * np.exp(1j * np.pi * delta * (2 * b + L - 1)) \
+            * np.sin(np.pi * delta * L) / np.sin(np.pi * delta)
+        assert abs(out[k] - ref) < 1e-11 * 10
+
+
+@pytest.mark.parametrize("N,T,win", [(16, 4, "hann"), (64, 4, "kaiser")])
+def test_demod_equals_pfb_channel_for_bin_centred_tones(N, T, win):
+    """With word c*2^64/N, L = N*T, D = N and the same taps, demodulation is
+    the PFB's channel c: b_k is a multiple of N so the mixer phases agree."""
+    beta = 9.0 if win == "kaiser" else 0.0
+    h64, _ = oracle.pfb_prototype(N, T, win, beta)
+    n = N * 25
+    x = crandn(n) * 50
+    y = oracle.pfb(x, N, T, h64)["full"]
+    for c in (0, 1, N // 2, N - 1):
+        w = (c << (64 - int(np.log2(N)))) % 2 ** 64
+        d = oracle.demod(x, N * T, N, h64, [w])[0]
+        assert np.allclose(d, y[:, c], rtol=1e-12, atol=1e-10)
+
+
+def test_demod_int16_matches_f64():
+    L, D = 40, 8
+    r = np.random.default_rng(11)
+    xi = r.integers(-8192, 8192, size=(D * 30, 2)).astype(np.int16)
+    xc = xi[:, 0].astype(float) + 1j * xi[:, 1]
+    h = oracle.lowpass("hann", L, 0.02)
+    ws = [int(v) for v in r.integers(0, 2 ** 64, 3, dtype=np.uint64)]
+    a = oracle.demod(xi, L, D, h, ws)
+    b = oracle.demod(xc, L, D, h, ws)
+    assert np.array_equal(a, b)
+    s = oracle.demod(xi, L, D, h, ws, k_begin=4, k_end=20)
+    assert np.array_equal(s, a[:, 4:20])
