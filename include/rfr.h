@@ -1,0 +1,234 @@
+/*
+ * rfr.h -- C ABI of the GB300 readout DSP library.
+ *
+ * The library turns a software radio's complex int16 ADC stream into
+ * per-tone baseband timestreams, in the two forms of arXiv:1812.02200:
+ *   - a critically sampled polyphase filter bank (PFB, Sec. III.A): a windowed
+ *     polyphase FIR over N channels x T taps, an N-point FFT per frame, and
+ *     the full spectrum and/or a gather of the bins that hold the tones;
+ *   - direct multi-tone demodulation (Sec. III.B): a per-tone NCO mix, a
+ *     low-pass FIR and decimation by D.
+ *
+ * Conventions shared by every call:
+ *   - Samples are complex int16, I then Q interleaved (4 bytes per sample),
+ *     as the radio delivers them (Sec. II.A).
+ *   - Outputs are complex64 (float re, float im).
+ *   - The stream starts at sample 0 with zero history.  Frame k is computed
+ *     from the W samples that end at sample (k+1)*hop - 1 (W = N*T, hop = N
+ *     for the PFB; W = L, hop = D for demodulation); samples before 0 are 0.
+ *   - The PFB output of channel c is y_k[c] = sum_p v_k[p] exp(-2*pi*i*c*p/N),
+ *     natural bin order, no 1/N factor (the taps sum to 1 instead).
+ *   - A tone is an NCO word w: a uint64 phase increment per sample in units
+ *     of 2*pi/2^64.  Its phase at absolute sample m is w*m mod 2^64 (exact
+ *     integer arithmetic); the mixer is exp(-i*phase).
+ *   - Device pointers are plain CUDA device (or managed) addresses; "stream"
+ *     is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *   - Every call returns an rfr_status; nothing is thrown across the ABI.
+ *     rfr_last_error() gives a message for the last failure of a plan.
+ *
+ * Thread safety: a plan is used by one host thread at a time.  Different
+ * plans are independent.
+ */
+#ifndef RFR_H
+#define RFR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rfr_plan rfr_plan;   /* opaque, owned by the library */
+
+typedef enum {
+    RFR_OK = 0,
+    RFR_E_INVALID = -1,     /* bad argument or plan parameters */
+    RFR_E_NOMEM = -2,       /* device or host allocation failed */
+    RFR_E_CUDA = -3,        /* a CUDA call failed (message in rfr_last_error) */
+    RFR_E_TIMEOUT = -4,     /* a bounded device-side wait gave up */
+    RFR_E_SHORT = -5,       /* output capacity too small; nothing consumed */
+    RFR_E_BUSY = -6,        /* resource in use (e.g. server slot pool full) */
+    RFR_E_UNSUPPORTED = -7  /* valid request this build does not implement */
+} rfr_status;
+
+typedef enum {
+    RFR_WIN_RECT = 0,       /* square window: the paper's moving average (Sec. III.B) */
+    RFR_WIN_HANN = 1,
+    RFR_WIN_HAMMING = 2,    /* the paper's PFB window (Sec. III.A) */
+    RFR_WIN_BLACKMAN = 3,
+    RFR_WIN_KAISER = 4      /* uses beta */
+} rfr_window_kind;
+
+/* Low-pass prototype h[j] = w[j] * sinc(2*cutoff*(j - (W-1)/2)), normalised
+ * to sum 1 in FP64 (DC gain 1), where w is the symmetric window of length W.
+ * cutoff is in cycles per sample.  PFB: cutoff 0 selects 1/(2N), which puts
+ * the cross-over of adjacent channels near -6 dB (Sec. III.A, Fig. 3).
+ * Demodulation: cutoff 0 drops the sinc factor (pure window; with
+ * RFR_WIN_RECT the moving average of Sec. III.B). */
+typedef struct {
+    int32_t kind;           /* rfr_window_kind */
+    double beta;            /* Kaiser shape parameter; ignored otherwise */
+    double cutoff;          /* cycles/sample, >= 0 */
+} rfr_window;
+
+/* Readout tones: NCO words (host memory; copied by rfr_plan_create). */
+typedef struct {
+    const uint64_t* words;
+    int32_t count;
+} rfr_tones;
+
+enum { RFR_OUT_FULL = 1, RFR_OUT_TONES = 2 };
+enum { RFR_MODE_PFB = 1, RFR_MODE_DEMOD = 2 };
+
+/* Caller-owned output buffers of one push (device memory).
+ *   full : complex64 [frames][full_ld], channel c of frame f at
+ *          full[(frame_offset + f) * full_ld + c]   (PFB with RFR_OUT_FULL)
+ *   tones: complex64 [count][tones_ld], tone s of frame f at
+ *          tones[s * tones_ld + frame_offset + f]  (PFB with RFR_OUT_TONES,
+ *          and always for demodulation)
+ * full_cap / tones_cap are the capacities in frames of each row range; a push
+ * that would write past frame_offset + cap fails with RFR_E_SHORT before any
+ * work is enqueued.  frames is written by the call (frames produced). */
+typedef struct {
+    void* full;
+    int64_t full_ld;
+    int64_t full_cap;
+    void* tones;
+    int64_t tones_ld;
+    int64_t tones_cap;
+    int64_t frame_offset;
+    int64_t frames;
+} rfr_output;
+
+typedef struct {
+    int32_t mode;           /* RFR_MODE_PFB or RFR_MODE_DEMOD */
+    int32_t channels;       /* N (PFB) or 0 */
+    int32_t taps;           /* T per channel (PFB) or L (demodulation) */
+    int32_t decimation;     /* hop: N (PFB) or D */
+    int32_t n_tones;
+    uint32_t out_flags;
+    int64_t samples_consumed;   /* stream position (samples pushed so far) */
+    int64_t frames_produced;
+    int64_t frames_pending;     /* produced by rfr_push, not yet pulled */
+    double tap_scale;           /* demodulation: power-of-two tap scale used by the
+                                   split-FP16 tensor-core path (diagnostic) */
+} rfr_plan_info;
+
+/*
+ * rfr_plan_create -- build a plan (Sec. III.A for channels > 0, Sec. III.B
+ * for channels == 0).
+ *   channels   N > 0: PFB with N channels, N a power of two, 16 <= N <= 16384.
+ *              0: direct demodulation.
+ *   taps       PFB: T taps per channel, 1 <= T <= 16 (prototype length N*T).
+ *              Demodulation: filter length L, 1 <= L <= 16384.
+ *   window     prototype window and cut-off (see rfr_window).
+ *   tones      NCO words of the readout tones (0 <= count <= 65536).  PFB:
+ *              tone s is read from bin rfr_word_to_bin(words[s], N).
+ *   decimation PFB: must equal N (critically sampled).  Demodulation: D >= 1
+ *              and D a multiple of 32 for the tensor-core path.
+ *   out_flags  PFB: any non-empty combination of RFR_OUT_FULL, RFR_OUT_TONES
+ *              (RFR_OUT_TONES needs count > 0).  Demodulation: RFR_OUT_TONES.
+ * Allocates the plan's device tables and stream state on the current device.
+ * Errors: RFR_E_INVALID (parameters), RFR_E_NOMEM, RFR_E_CUDA.
+ */
+rfr_status rfr_plan_create(rfr_plan** plan, int32_t channels, int32_t taps,
+                           const rfr_window* window, const rfr_tones* tones,
+                           int32_t decimation, uint32_t out_flags);
+
+/* Frees everything the plan owns (waits for its outstanding work). */
+void rfr_plan_destroy(rfr_plan* plan);
+
+rfr_status rfr_plan_get_info(const rfr_plan* plan, rfr_plan_info* info);
+
+/* Number of frames a push of n_samples would produce now. */
+rfr_status rfr_frames_for(const rfr_plan* plan, int64_t n_samples, int64_t* frames);
+
+/*
+ * rfr_push_into -- process the next n_samples of the stream (device buffer
+ * iq, [n_samples][2] int16) asynchronously on `stream`, writing the frames
+ * that complete into the caller's buffers `out` (device).  Filter history,
+ * the partial-frame residue and the stream position are kept in the plan, so
+ * any split of a stream into pushes gives the same frames (bit-identical) as
+ * one push of the whole stream.
+ * iq must stay valid until the work on `stream` completes.  On error nothing
+ * is enqueued and the stream state is unchanged.
+ * Errors: RFR_E_INVALID, RFR_E_SHORT (output capacity), RFR_E_CUDA.
+ */
+rfr_status rfr_push_into(rfr_plan* plan, const int16_t* iq, int64_t n_samples,
+                         rfr_output* out, void* stream);
+
+/*
+ * rfr_push / rfr_pull -- the queued form (Sec. III: the processing thread
+ * hands finished buffers to a streaming thread).  rfr_push processes like
+ * rfr_push_into but keeps the frames in a plan-owned device ring (grown on
+ * demand); rfr_pull copies all pending frames, in order, into `out` (device
+ * or host memory) on the stream of the last push and consumes them.  `out`
+ * must have room for every pending frame (RFR_E_SHORT otherwise, nothing
+ * consumed); out->frames is set to the number copied.
+ */
+rfr_status rfr_push(rfr_plan* plan, const int16_t* iq, int64_t n_samples, void* stream);
+rfr_status rfr_pull(rfr_plan* plan, rfr_output* out);
+
+/*
+ * rfr_process_host -- end-to-end form for host-resident data: copies the
+ * host samples to the device in chunks, processes them and copies the frames
+ * back into host `out` buffers, overlapping the copies with the compute on
+ * the plan's internal streams.  Host buffers should be pinned
+ * (cudaHostAlloc / cudaHostRegister) for full speed.  Synchronous: returns
+ * when `out` holds the results.  The stream state advances as for a push.
+ */
+rfr_status rfr_process_host(rfr_plan* plan, const int16_t* iq_host, int64_t n_samples,
+                            rfr_output* out_host);
+
+/* Zero history, residue and stream position (and drop pending frames). */
+rfr_status rfr_reset(rfr_plan* plan);
+
+/*
+ * Checkpoint / resume of the stream state (history, residue, position).
+ * Export with host == NULL stores the needed size in *bytes.  Import needs a
+ * plan created with the same parameters; it restores the state exactly, so
+ * the next push continues the stream bit-identically.  Both synchronise with
+ * the plan's outstanding work.
+ */
+rfr_status rfr_state_export(rfr_plan* plan, void* host, size_t* bytes);
+rfr_status rfr_state_import(rfr_plan* plan, const void* host, size_t bytes);
+
+/*
+ * Prototype taps (host memory): h64 in FP64 (may be NULL), h32 the FP32
+ * values the PFB kernels use (may be NULL).  *n receives the length (N*T or
+ * L); with both pointers NULL only *n is set.
+ */
+rfr_status rfr_plan_get_taps(const rfr_plan* plan, double* h64, float* h32, int64_t* n);
+
+/* PFB: bin of each tone (host int32[count]). */
+rfr_status rfr_plan_get_bins(const rfr_plan* plan, int32_t* bins, int32_t* count);
+
+/*
+ * rfr_plain_oneshot -- the plain FP32 GPU form of the same computation, for
+ * comparison: PFB as an FP32 FIR kernel, a batched cuFFT C2C transform and a
+ * gather kernel; demodulation as an FP32 CUDA-core kernel.  Processes one
+ * whole buffer with zero history (does not touch the plan's stream state).
+ * Scratch is allocated by the call on first use and cached in the plan.
+ */
+rfr_status rfr_plain_oneshot(rfr_plan* plan, const int16_t* iq, int64_t n_samples,
+                             rfr_output* out, void* stream);
+
+/* Frequency f_hz at sample rate fs_hz -> NCO word: f/fs wrapped into
+ * [-1/2, 1/2), times 2^64, rounded to nearest (two's complement). */
+uint64_t rfr_freq_to_word(double f_hz, double fs_hz);
+
+/* Bin of an NCO word in an n-channel PFB: round(word*n/2^64) mod n, ties
+ * up, in integer arithmetic; -1 if n is not a power of two >= 2. */
+int32_t rfr_word_to_bin(uint64_t word, int32_t n);
+
+const char* rfr_status_string(rfr_status status);
+const char* rfr_last_error(const rfr_plan* plan);
+
+/* Library version string. */
+const char* rfr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RFR_H */

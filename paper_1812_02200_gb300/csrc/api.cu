@@ -1,0 +1,691 @@
+// api.cu -- the C ABI (include/rfr.h): plan creation, streaming pushes,
+// queued pull, host-staged processing, checkpoint/resume and the plain FP32
+// comparison entry point.  All device work is enqueued on the caller's stream;
+// the stream state (carry of history + residue, position) stays on the device.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "dev_common.cuh"
+#include "fft_dev.cuh"
+#include "rfr_internal.h"
+
+using rfr::DEV_OK;
+using rfr::DEV_TIMEOUT;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+rfr_status fail(rfr_plan* p, rfr_status st, const char* msg) {
+    if (p) p->last_error = msg;
+    return st;
+}
+
+rfr_status cuda_fail(rfr_plan* p, cudaError_t e, const char* where) {
+    if (p) {
+        p->last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    }
+    return e == cudaErrorMemoryAllocation ? RFR_E_NOMEM : RFR_E_CUDA;
+}
+
+#define RFR_CUDA(p, call)                                      \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return cuda_fail((p), e_, #call); \
+    } while (0)
+
+template <typename T>
+cudaError_t dev_alloc(T** ptr, size_t bytes) {
+    void* v = nullptr;
+    cudaError_t e = cudaMalloc(&v, bytes ? bytes : 16);
+    *ptr = static_cast<T*>(v);
+    return e;
+}
+
+void dev_free(void* p) {
+    if (p) cudaFree(p);
+}
+
+// FFT twiddle tables for an N-point frame (layout of fft_dev.cuh), FP64 -> FP32.
+std::vector<float> make_twiddles(int log2n) {
+    std::vector<float> t;
+    const int n = 1 << log2n;
+    const int p16 = log2n / 4, rf = 1 << (log2n % 4);
+    auto push = [&](int64_t num, int64_t den) {
+        const double a = -2.0 * kPi * static_cast<double>(num) / static_cast<double>(den);
+        t.push_back(static_cast<float>(std::cos(a)));
+        t.push_back(static_cast<float>(std::sin(a)));
+    };
+    int ns = 16;
+    for (int s = 1; s < p16; ++s, ns *= 16)
+        for (int r = 1; r < 16; ++r)
+            for (int k = 0; k < ns; ++k) push(static_cast<int64_t>(r) * k, 16LL * ns);
+    if (rf > 1) {
+        const int span = n / rf;
+        for (int r = 1; r < rf; ++r)
+            for (int j = 0; j < span; ++j) push(static_cast<int64_t>(r) * j, n);
+    }
+    return t;
+}
+
+// -------------------------------------------------------------- carry copy
+__global__ void carry_update_kernel(const uint32_t* __restrict__ old_carry, int64_t cl,
+                                    const uint32_t* __restrict__ buf, int64_t from, int64_t count,
+                                    uint32_t* __restrict__ out) {
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < count;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t idx = from + i;
+        out[i] = idx < cl ? old_carry[idx] : buf[idx - cl];
+    }
+}
+
+int64_t frames_for_len(const rfr_plan* p, int64_t lv) {
+    return lv >= p->W ? (lv - p->W) / p->H + 1 : 0;
+}
+
+bool out_ok(const rfr_plan* p, const rfr_output* o, int64_t F) {
+    if (F == 0) return true;
+    if (o->frame_offset < 0) return false;
+    if (p->mode == RFR_MODE_PFB && (p->out_flags & RFR_OUT_FULL)) {
+        if (!o->full || o->full_ld < p->N || o->full_cap < o->frame_offset + F) return false;
+    }
+    const bool want_tones = p->mode == RFR_MODE_DEMOD || (p->out_flags & RFR_OUT_TONES);
+    if (want_tones && !p->words.empty()) {
+        if (!o->tones || o->tones_cap < o->frame_offset + F || o->tones_ld < o->frame_offset + F)
+            return false;
+    }
+    return true;
+}
+
+rfr_status check_status(rfr_plan* p) {
+    int st = 0;
+    RFR_CUDA(p, cudaMemcpy(&st, p->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st == DEV_TIMEOUT) return fail(p, RFR_E_TIMEOUT, "a device-side wait timed out");
+    if (st != DEV_OK) return fail(p, RFR_E_CUDA, "device status error");
+    return RFR_OK;
+}
+
+rfr_status ensure_demod_scratch(rfr_plan* p, int64_t F) {
+    const int64_t rows = static_cast<int64_t>(rfr::demod_xs_rows(F, p->Lpad, p->D));
+    if (rows > p->xs_rows_cap) {
+        cudaDeviceSynchronize();
+        dev_free(p->d_xs_hi);
+        dev_free(p->d_xs_lo);
+        p->d_xs_hi = p->d_xs_lo = nullptr;
+        p->xs_rows_cap = 0;
+        const size_t bytes = static_cast<size_t>(rows) * 2 * p->D * sizeof(uint16_t);
+        RFR_CUDA(p, dev_alloc(&p->d_xs_hi, bytes));
+        RFR_CUDA(p, dev_alloc(&p->d_xs_lo, bytes));
+        p->xs_rows_cap = rows;
+    }
+    const int64_t tiles = (F + rfr::kDemodBM - 1) / rfr::kDemodBM;
+    const int64_t rot = tiles * p->ntp + static_cast<int64_t>(p->ntp) * rfr::kDemodBM;
+    if (rot > p->rot_cap) {
+        cudaDeviceSynchronize();
+        dev_free(p->d_rot);
+        p->d_rot = nullptr;
+        p->rot_cap = 0;
+        RFR_CUDA(p, dev_alloc(&p->d_rot, static_cast<size_t>(rot) * 8));
+        p->rot_cap = rot;
+    }
+    return RFR_OK;
+}
+
+// Core of every push: enqueue the frames of [carry | buf] into `out`.
+rfr_status push_core(rfr_plan* p, const int16_t* iq, int64_t n, const rfr_output* o,
+                     int64_t* frames_out, cudaStream_t st) {
+    if (n < 0 || (n > 0 && iq == nullptr)) return fail(p, RFR_E_INVALID, "bad input buffer");
+    const int64_t lv = p->cl + n;
+    const int64_t F = frames_for_len(p, lv);
+    if (!out_ok(p, o, F)) return fail(p, RFR_E_SHORT, "output buffers missing or too small");
+    const int16_t* carry = p->d_carry[p->cur];
+    if (F > 0) {
+        if (p->mode == RFR_MODE_PFB) {
+            rfr::PfbLaunch L{};
+            L.carry = carry;
+            L.cl = p->cl;
+            L.buf = iq;
+            L.n = n;
+            L.F = F;
+            L.log2n = p->log2n;
+            L.taps_kernel = p->Tk;
+            L.h = p->d_h;
+            L.tw = p->d_tw;
+            L.tw_count = p->tw_count;
+            L.bins = p->d_bins;
+            L.n_tones = (p->out_flags & RFR_OUT_TONES) ? static_cast<int>(p->words.size()) : 0;
+            L.full = (p->out_flags & RFR_OUT_FULL) ? o->full : nullptr;
+            L.full_ld = o->full_ld;
+            L.tones = o->tones;
+            L.tones_ld = o->tones_ld;
+            L.frame_offset = o->frame_offset;
+            L.status = p->d_status;
+            L.n_sms = p->n_sms;
+            L.max_smem = p->max_smem;
+            RFR_CUDA(p, rfr::pfb_launch(L, st));
+        } else {
+            if (!p->words.empty()) {
+                rfr_status rs = ensure_demod_scratch(p, F);
+                if (rs != RFR_OK) return rs;
+                rfr::DemodLaunch L{};
+                L.carry = carry;
+                L.cl = p->cl;
+                L.buf = iq;
+                L.n = n;
+                L.F = F;
+                L.a0 = p->samples - p->cl;
+                L.L = p->L;
+                L.D = p->D;
+                L.Lpad = p->Lpad;
+                L.n_tones = static_cast<int>(p->words.size());
+                L.ntp = p->ntp;
+                L.words = p->d_words;
+                L.b_hi = p->d_bhi;
+                L.b_lo = p->d_blo;
+                L.inv_scale = std::ldexp(1.0, -p->tap_exp);
+                L.xs_hi = p->d_xs_hi;
+                L.xs_lo = p->d_xs_lo;
+                L.xs_rows = p->xs_rows_cap;
+                L.rot = p->d_rot;
+                L.tones = o->tones;
+                L.tones_ld = o->tones_ld;
+                L.frame_offset = o->frame_offset;
+                L.status = p->d_status;
+                L.n_sms = p->n_sms;
+                L.kchunk = 0;
+                RFR_CUDA(p, rfr::demod_launch(L, st));
+            }
+        }
+    }
+    // new carry = v[F*H, lv)
+    const int64_t ncl = lv - F * p->H;
+    if (ncl > 0) {
+        if (ncl > p->carry_cap) return fail(p, RFR_E_INVALID, "internal: carry overflow");
+        RFR_CUDA(p, rfr::carry_update(carry, p->cl, iq, n, F * p->H, ncl, p->d_carry[p->cur ^ 1], st));
+        p->cur ^= 1;
+    }
+    p->cl = ncl;
+    p->samples += n;
+    p->frames += F;
+    p->last_stream = st;
+    if (frames_out) *frames_out = F;
+    return RFR_OK;
+}
+
+rfr_status reset_state(rfr_plan* p) {
+    p->samples = 0;
+    p->frames = 0;
+    p->q_frames = 0;
+    p->cur = 0;
+    p->cl = p->W - p->H;     // zero history (negative: samples skipped before frame 0)
+    if (p->carry_cap > 0) {
+        RFR_CUDA(p, cudaMemset(p->d_carry[0], 0, static_cast<size_t>(p->carry_cap) * 4));
+        RFR_CUDA(p, cudaMemset(p->d_carry[1], 0, static_cast<size_t>(p->carry_cap) * 4));
+    }
+    RFR_CUDA(p, cudaMemset(p->d_status, 0, sizeof(int)));
+    return RFR_OK;
+}
+
+void destroy(rfr_plan* p) {
+    if (!p) return;
+    cudaDeviceSynchronize();
+    for (void* q : {static_cast<void*>(p->d_h), p->d_tw, static_cast<void*>(p->d_bins),
+                    static_cast<void*>(p->d_words), static_cast<void*>(p->d_h32), p->d_bhi, p->d_blo,
+                    static_cast<void*>(p->d_status), static_cast<void*>(p->d_carry[0]),
+                    static_cast<void*>(p->d_carry[1]), p->d_xs_hi, p->d_xs_lo, p->d_rot, p->d_qfull,
+                    p->d_qtones})
+        dev_free(q);
+    for (int i = 0; i < 2; ++i) {
+        dev_free(p->d_stage_in[i]);
+        dev_free(p->d_stage_full[i]);
+        dev_free(p->d_stage_tones[i]);
+        if (p->stage_st[i]) cudaStreamDestroy(p->stage_st[i]);
+    }
+    for (auto& e : p->stage_ev)
+        if (e) cudaEventDestroy(e);
+    rfr::plain_release(p->plain_scratch, p->plain_fft);
+    delete p;
+}
+
+}  // namespace
+
+namespace rfr {
+cudaError_t carry_update(const int16_t* old_carry, int64_t cl, const int16_t* buf, int64_t n,
+                         int64_t from, int64_t count, int16_t* new_carry, cudaStream_t st) {
+    (void)n;
+    if (count <= 0) return cudaSuccess;
+    const int threads = 256;
+    const int64_t blocks = std::min<int64_t>((count + threads - 1) / threads, 4096);
+    carry_update_kernel<<<static_cast<unsigned>(blocks), threads, 0, st>>>(
+        reinterpret_cast<const uint32_t*>(old_carry), cl, reinterpret_cast<const uint32_t*>(buf),
+        from, count, reinterpret_cast<uint32_t*>(new_carry));
+    return cudaGetLastError();
+}
+}  // namespace rfr
+
+// ===================================================================== ABI
+extern "C" {
+
+const char* rfr_version(void) { return "rfr 0.1 (sm_103a)"; }
+
+const char* rfr_status_string(rfr_status s) {
+    switch (s) {
+    case RFR_OK: return "ok";
+    case RFR_E_INVALID: return "invalid argument";
+    case RFR_E_NOMEM: return "out of memory";
+    case RFR_E_CUDA: return "CUDA error";
+    case RFR_E_TIMEOUT: return "device wait timed out";
+    case RFR_E_SHORT: return "output capacity too small";
+    case RFR_E_BUSY: return "busy";
+    case RFR_E_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char* rfr_last_error(const rfr_plan* p) { return p ? p->last_error.c_str() : ""; }
+
+uint64_t rfr_freq_to_word(double f_hz, double fs_hz) { return rfr::freq_to_word(f_hz, fs_hz); }
+
+int32_t rfr_word_to_bin(uint64_t word, int32_t n) { return rfr::word_to_bin(word, n); }
+
+rfr_status rfr_plan_create(rfr_plan** out, int32_t channels, int32_t taps, const rfr_window* window,
+                           const rfr_tones* tones, int32_t decimation, uint32_t out_flags) {
+    if (!out || !window) return RFR_E_INVALID;
+    *out = nullptr;
+    if (window->kind < RFR_WIN_RECT || window->kind > RFR_WIN_KAISER) return RFR_E_INVALID;
+    if (!(window->cutoff >= 0.0) || !(window->cutoff < 0.5) || !std::isfinite(window->beta))
+        return RFR_E_INVALID;
+    const int32_t nt = tones ? tones->count : 0;
+    if (nt < 0 || nt > 65536 || (nt > 0 && !tones->words)) return RFR_E_INVALID;
+
+    rfr_plan* p = new (std::nothrow) rfr_plan();
+    if (!p) return RFR_E_NOMEM;
+    p->window = *window;
+    p->out_flags = out_flags;
+    if (nt > 0) p->words.assign(tones->words, tones->words + nt);
+    cudaGetDevice(&p->device);
+    cudaDeviceGetAttribute(&p->n_sms, cudaDevAttrMultiProcessorCount, p->device);
+    cudaDeviceGetAttribute(&p->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+
+    auto bad = [&](rfr_status s) {
+        destroy(p);
+        return s;
+    };
+
+    if (channels > 0) {
+        // ------------------------------------------------------------- PFB
+        if ((channels & (channels - 1)) != 0 || channels < 16 || channels > 16384) return bad(RFR_E_INVALID);
+        if (taps < 1 || taps > 16 || decimation != channels) return bad(RFR_E_INVALID);
+        if (out_flags == 0 || (out_flags & ~uint32_t(RFR_OUT_FULL | RFR_OUT_TONES)) != 0) return bad(RFR_E_INVALID);
+        if ((out_flags & RFR_OUT_TONES) && nt == 0) return bad(RFR_E_INVALID);
+        p->mode = RFR_MODE_PFB;
+        p->N = channels;
+        p->T = taps;
+        while ((1 << p->log2n) < channels) ++p->log2n;
+        p->Tk = rfr::pfb_kernel_taps(p->log2n, taps);
+        const int64_t M = static_cast<int64_t>(channels) * taps;
+        p->h64.resize(M);
+        const double fc = window->cutoff > 0.0 ? window->cutoff : 0.5 / channels;
+        if (rfr::build_lowpass(window->kind, window->beta, fc, M, p->h64.data()) != 0) return bad(RFR_E_INVALID);
+        p->h32.resize(M);
+        for (int64_t j = 0; j < M; ++j) p->h32[j] = static_cast<float>(p->h64[j]);
+        // kernel taps: zero-padded at the oldest end to Tk*N
+        std::vector<float> hk(static_cast<size_t>(p->Tk) * channels, 0.0f);
+        std::copy(p->h32.begin(), p->h32.end(), hk.begin() + static_cast<size_t>(p->Tk - taps) * channels);
+        p->bins.resize(nt);
+        for (int s = 0; s < nt; ++s) p->bins[s] = rfr::word_to_bin(p->words[s], channels);
+        std::vector<float> tw = make_twiddles(p->log2n);
+        p->tw_count = static_cast<int>(tw.size() / 2);
+        p->W = static_cast<int64_t>(p->Tk) * channels;
+        p->H = channels;
+        p->carry_cap = p->W;
+        cudaError_t e = cudaSuccess;
+        if ((e = dev_alloc(&p->d_h, hk.size() * 4)) != cudaSuccess ||
+            (e = dev_alloc(&p->d_h32, p->h32.size() * 4)) != cudaSuccess ||
+            (e = dev_alloc(&p->d_tw, std::max<size_t>(tw.size(), 2) * 4)) != cudaSuccess ||
+            (e = dev_alloc(&p->d_bins, std::max<size_t>(nt, 1) * 4)) != cudaSuccess)
+            return bad(cuda_fail(p, e, "plan alloc"));
+        cudaMemcpy(p->d_h, hk.data(), hk.size() * 4, cudaMemcpyHostToDevice);
+        cudaMemcpy(p->d_h32, p->h32.data(), p->h32.size() * 4, cudaMemcpyHostToDevice);
+        if (!tw.empty()) cudaMemcpy(p->d_tw, tw.data(), tw.size() * 4, cudaMemcpyHostToDevice);
+        if (nt) cudaMemcpy(p->d_bins, p->bins.data(), nt * 4, cudaMemcpyHostToDevice);
+    } else if (channels == 0) {
+        // ----------------------------------------------------------- demod
+        if (taps < 1 || taps > 16384 || decimation < 32 || decimation % 32 != 0 ||
+            decimation > (1 << 20))
+            return bad(RFR_E_INVALID);
+        if (out_flags != RFR_OUT_TONES) return bad(RFR_E_INVALID);
+        p->mode = RFR_MODE_DEMOD;
+        p->L = taps;
+        p->D = decimation;
+        p->Lpad = (taps + 31) / 32 * 32;
+        p->h64.resize(taps);
+        if (rfr::build_lowpass(window->kind, window->beta, window->cutoff, taps, p->h64.data()) != 0)
+            return bad(RFR_E_INVALID);
+        p->h32.resize(taps);
+        for (int j = 0; j < taps; ++j) p->h32[j] = static_cast<float>(p->h64[j]);
+        p->W = taps;
+        p->H = decimation;
+        p->carry_cap = std::max<int64_t>(taps, 1);
+        p->ntp = (nt + rfr::kDemodBN / 2 - 1) / (rfr::kDemodBN / 2) * (rfr::kDemodBN / 2);
+        double hmax = 0.0;
+        for (double v : p->h64) hmax = std::max(hmax, std::fabs(v));
+        int e2 = 0;
+        std::frexp(hmax, &e2);               // hmax in [2^(e2-1), 2^e2)
+        p->tap_exp = 15 - e2;                // hmax * 2^e in [2^14, 2^15)
+        cudaError_t e = cudaSuccess;
+        double* d_h64 = nullptr;
+        if ((e = dev_alloc(&p->d_words, std::max<size_t>(nt, 1) * 8)) != cudaSuccess ||
+            (e = dev_alloc(&p->d_h32, static_cast<size_t>(taps) * 4)) != cudaSuccess)
+            return bad(cuda_fail(p, e, "plan alloc"));
+        cudaMemcpy(p->d_h32, p->h32.data(), static_cast<size_t>(taps) * 4, cudaMemcpyHostToDevice);
+        if (nt) {
+            cudaMemcpy(p->d_words, p->words.data(), static_cast<size_t>(nt) * 8, cudaMemcpyHostToDevice);
+            const size_t bbytes = static_cast<size_t>(2) * p->ntp * 2 * p->Lpad * sizeof(uint16_t);
+            if ((e = dev_alloc(&p->d_bhi, bbytes)) != cudaSuccess ||
+                (e = dev_alloc(&p->d_blo, bbytes)) != cudaSuccess ||
+                (e = dev_alloc(&d_h64, static_cast<size_t>(taps) * 8)) != cudaSuccess) {
+                dev_free(d_h64);
+                return bad(cuda_fail(p, e, "plan alloc"));
+            }
+            cudaMemcpy(d_h64, p->h64.data(), static_cast<size_t>(taps) * 8, cudaMemcpyHostToDevice);
+            e = rfr::demod_build_taps(d_h64, p->d_words, nt, p->ntp, taps, p->Lpad, p->tap_exp,
+                                      p->d_bhi, p->d_blo, nullptr);
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+            dev_free(d_h64);
+            if (e != cudaSuccess) return bad(cuda_fail(p, e, "modulated-tap build"));
+        }
+    } else {
+        return bad(RFR_E_INVALID);
+    }
+    cudaError_t e = cudaSuccess;
+    if ((e = dev_alloc(&p->d_status, sizeof(int))) != cudaSuccess ||
+        (e = dev_alloc(&p->d_carry[0], static_cast<size_t>(p->carry_cap) * 4)) != cudaSuccess ||
+        (e = dev_alloc(&p->d_carry[1], static_cast<size_t>(p->carry_cap) * 4)) != cudaSuccess)
+        return bad(cuda_fail(p, e, "plan alloc"));
+    if (reset_state(p) != RFR_OK) return bad(RFR_E_CUDA);
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return bad(cuda_fail(p, e, "plan create"));
+    *out = p;
+    return RFR_OK;
+}
+
+void rfr_plan_destroy(rfr_plan* p) { destroy(p); }
+
+rfr_status rfr_plan_get_info(const rfr_plan* p, rfr_plan_info* info) {
+    if (!p || !info) return RFR_E_INVALID;
+    info->mode = p->mode;
+    info->channels = p->N;
+    info->taps = p->mode == RFR_MODE_PFB ? p->T : p->L;
+    info->decimation = static_cast<int32_t>(p->H);
+    info->n_tones = static_cast<int32_t>(p->words.size());
+    info->out_flags = p->out_flags;
+    info->samples_consumed = p->samples;
+    info->frames_produced = p->frames;
+    info->frames_pending = p->q_frames;
+    info->tap_scale = p->mode == RFR_MODE_DEMOD ? std::ldexp(1.0, p->tap_exp) : 1.0;
+    return RFR_OK;
+}
+
+rfr_status rfr_frames_for(const rfr_plan* p, int64_t n, int64_t* frames) {
+    if (!p || !frames || n < 0) return RFR_E_INVALID;
+    *frames = frames_for_len(p, p->cl + n);
+    return RFR_OK;
+}
+
+rfr_status rfr_push_into(rfr_plan* p, const int16_t* iq, int64_t n, rfr_output* out, void* stream) {
+    if (!p || !out) return RFR_E_INVALID;
+    int64_t F = 0;
+    rfr_status s = push_core(p, iq, n, out, &F, static_cast<cudaStream_t>(stream));
+    out->frames = (s == RFR_OK) ? F : 0;
+    return s;
+}
+
+rfr_status rfr_push(rfr_plan* p, const int16_t* iq, int64_t n, void* stream) {
+    if (!p) return RFR_E_INVALID;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t F = frames_for_len(p, p->cl + n);
+    const int nt = static_cast<int>(p->words.size());
+    const bool want_full = p->mode == RFR_MODE_PFB && (p->out_flags & RFR_OUT_FULL);
+    const bool want_tones = nt > 0 && (p->mode == RFR_MODE_DEMOD || (p->out_flags & RFR_OUT_TONES));
+    if (p->q_frames + F > p->q_cap) {
+        int64_t cap = std::max<int64_t>(p->q_frames + F, 2 * p->q_cap);
+        void *nf = nullptr, *nt_ = nullptr;
+        if (want_full) RFR_CUDA(p, dev_alloc(&nf, static_cast<size_t>(cap) * p->N * 8));
+        if (want_tones) RFR_CUDA(p, dev_alloc(&nt_, static_cast<size_t>(cap) * nt * 8));
+        RFR_CUDA(p, cudaStreamSynchronize(st));
+        if (p->q_frames > 0) {
+            if (want_full)
+                RFR_CUDA(p, cudaMemcpy(nf, p->d_qfull, static_cast<size_t>(p->q_frames) * p->N * 8,
+                                       cudaMemcpyDeviceToDevice));
+            if (want_tones)
+                RFR_CUDA(p, cudaMemcpy2D(nt_, cap * 8, p->d_qtones, p->q_cap * 8, p->q_frames * 8, nt,
+                                         cudaMemcpyDeviceToDevice));
+        }
+        dev_free(p->d_qfull);
+        dev_free(p->d_qtones);
+        p->d_qfull = nf;
+        p->d_qtones = nt_;
+        p->q_cap = cap;
+    }
+    rfr_output o{};
+    o.full = p->d_qfull;
+    o.full_ld = p->N;
+    o.full_cap = p->q_cap;
+    o.tones = p->d_qtones;
+    o.tones_ld = p->q_cap;
+    o.tones_cap = p->q_cap;
+    o.frame_offset = p->q_frames;
+    int64_t got = 0;
+    rfr_status s = push_core(p, iq, n, &o, &got, st);
+    if (s == RFR_OK) p->q_frames += got;
+    return s;
+}
+
+rfr_status rfr_pull(rfr_plan* p, rfr_output* out) {
+    if (!p || !out) return RFR_E_INVALID;
+    const int64_t F = p->q_frames;
+    out->frames = 0;
+    if (!out_ok(p, out, F)) return fail(p, RFR_E_SHORT, "pull: output too small");
+    cudaStream_t st = p->last_stream;
+    const int nt = static_cast<int>(p->words.size());
+    if (F > 0) {
+        if (p->mode == RFR_MODE_PFB && (p->out_flags & RFR_OUT_FULL))
+            RFR_CUDA(p, cudaMemcpy2DAsync(static_cast<char*>(out->full) + out->frame_offset * out->full_ld * 8,
+                                          out->full_ld * 8, p->d_qfull, p->N * 8, p->N * 8, F,
+                                          cudaMemcpyDefault, st));
+        if (nt > 0 && (p->mode == RFR_MODE_DEMOD || (p->out_flags & RFR_OUT_TONES)))
+            RFR_CUDA(p, cudaMemcpy2DAsync(static_cast<char*>(out->tones) + out->frame_offset * 8,
+                                          out->tones_ld * 8, p->d_qtones, p->q_cap * 8, F * 8, nt,
+                                          cudaMemcpyDefault, st));
+    }
+    RFR_CUDA(p, cudaStreamSynchronize(st));
+    rfr_status s = check_status(p);
+    if (s != RFR_OK) return s;
+    p->q_frames = 0;
+    out->frames = F;
+    return RFR_OK;
+}
+
+rfr_status rfr_process_host(rfr_plan* p, const int16_t* iq_host, int64_t n, rfr_output* out) {
+    if (!p || !out || n < 0 || (n > 0 && !iq_host)) return RFR_E_INVALID;
+    const int64_t Ftot = frames_for_len(p, p->cl + n);
+    if (!out_ok(p, out, Ftot)) return fail(p, RFR_E_SHORT, "process_host: output too small");
+    const int nt = static_cast<int>(p->words.size());
+    const bool want_full = p->mode == RFR_MODE_PFB && (p->out_flags & RFR_OUT_FULL);
+    const bool want_tones = nt > 0 && (p->mode == RFR_MODE_DEMOD || (p->out_flags & RFR_OUT_TONES));
+    // chunk: a multiple of the hop, about 2^24 samples
+    const int64_t chunk = std::max<int64_t>(p->H, (int64_t(1) << 24) / p->H * p->H);
+    const int64_t fmax = chunk / p->H + 2;
+    if (p->stage_samples < chunk) {
+        cudaDeviceSynchronize();
+        for (int i = 0; i < 2; ++i) {
+            dev_free(p->d_stage_in[i]);
+            dev_free(p->d_stage_full[i]);
+            dev_free(p->d_stage_tones[i]);
+            p->d_stage_in[i] = p->d_stage_full[i] = p->d_stage_tones[i] = nullptr;
+        }
+        p->stage_samples = 0;
+        for (int i = 0; i < 2; ++i) {
+            RFR_CUDA(p, dev_alloc(&p->d_stage_in[i], static_cast<size_t>(chunk) * 4));
+            if (want_full) RFR_CUDA(p, dev_alloc(&p->d_stage_full[i], static_cast<size_t>(fmax) * p->N * 8));
+            if (want_tones) RFR_CUDA(p, dev_alloc(&p->d_stage_tones[i], static_cast<size_t>(fmax) * nt * 8));
+            if (!p->stage_st[i]) RFR_CUDA(p, cudaStreamCreateWithFlags(&p->stage_st[i], cudaStreamNonBlocking));
+        }
+        for (auto& e : p->stage_ev)
+            if (!e) RFR_CUDA(p, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        p->stage_samples = chunk;
+    }
+    int64_t done = 0, fo = out->frame_offset;
+    int i = 0;
+    cudaEvent_t prev = nullptr;
+    while (done < n) {
+        const int64_t cnt = std::min(chunk, n - done);
+        const int s = i & 1;
+        cudaStream_t st = p->stage_st[s];
+        RFR_CUDA(p, cudaMemcpyAsync(p->d_stage_in[s], iq_host + 2 * done, static_cast<size_t>(cnt) * 4,
+                                    cudaMemcpyHostToDevice, st));
+        if (prev) RFR_CUDA(p, cudaStreamWaitEvent(st, prev, 0));   // pushes stay in stream order
+        rfr_output o{};
+        o.full = p->d_stage_full[s];
+        o.full_ld = p->N;
+        o.full_cap = fmax;
+        o.tones = p->d_stage_tones[s];
+        o.tones_ld = fmax;
+        o.tones_cap = fmax;
+        int64_t F = 0;
+        rfr_status rs = push_core(p, static_cast<const int16_t*>(p->d_stage_in[s]), cnt, &o, &F, st);
+        if (rs != RFR_OK) return rs;
+        RFR_CUDA(p, cudaEventRecord(p->stage_ev[s], st));
+        prev = p->stage_ev[s];
+        if (F > 0) {
+            if (want_full)
+                RFR_CUDA(p, cudaMemcpy2DAsync(static_cast<char*>(out->full) + fo * out->full_ld * 8,
+                                              out->full_ld * 8, p->d_stage_full[s], p->N * 8, p->N * 8, F,
+                                              cudaMemcpyDeviceToHost, st));
+            if (want_tones)
+                RFR_CUDA(p, cudaMemcpy2DAsync(static_cast<char*>(out->tones) + fo * 8, out->tones_ld * 8,
+                                              p->d_stage_tones[s], fmax * 8, F * 8, nt,
+                                              cudaMemcpyDeviceToHost, st));
+        }
+        fo += F;
+        done += cnt;
+        ++i;
+    }
+    for (int s = 0; s < 2; ++s) RFR_CUDA(p, cudaStreamSynchronize(p->stage_st[s]));
+    p->last_stream = p->stage_st[(i + 1) & 1];
+    out->frames = fo - out->frame_offset;
+    return check_status(p);
+}
+
+rfr_status rfr_reset(rfr_plan* p) {
+    if (!p) return RFR_E_INVALID;
+    RFR_CUDA(p, cudaDeviceSynchronize());
+    return reset_state(p);
+}
+
+// State blob: magic, version, mode, N/L, T/D, W, H, samples, frames, cl,
+// then max(cl, 0) carry samples.
+namespace {
+struct StateHeader {
+    uint32_t magic, version;
+    int32_t mode, a, b, pad;
+    int64_t W, H, samples, frames, cl;
+};
+constexpr uint32_t kStateMagic = 0x52465253;  // "RFRS"
+}  // namespace
+
+rfr_status rfr_state_export(rfr_plan* p, void* host, size_t* bytes) {
+    if (!p || !bytes) return RFR_E_INVALID;
+    const int64_t keep = std::max<int64_t>(p->cl, 0);
+    const size_t need = sizeof(StateHeader) + static_cast<size_t>(keep) * 4;
+    if (!host) {
+        *bytes = need;
+        return RFR_OK;
+    }
+    if (*bytes < need) {
+        *bytes = need;
+        return fail(p, RFR_E_SHORT, "state buffer too small");
+    }
+    RFR_CUDA(p, cudaDeviceSynchronize());
+    StateHeader h{kStateMagic, 1, p->mode, p->mode == RFR_MODE_PFB ? p->N : p->L,
+                  p->mode == RFR_MODE_PFB ? p->T : p->D, 0, p->W, p->H, p->samples, p->frames, p->cl};
+    std::memcpy(host, &h, sizeof(h));
+    if (keep > 0)
+        RFR_CUDA(p, cudaMemcpy(static_cast<char*>(host) + sizeof(h), p->d_carry[p->cur],
+                               static_cast<size_t>(keep) * 4, cudaMemcpyDeviceToHost));
+    *bytes = need;
+    return RFR_OK;
+}
+
+rfr_status rfr_state_import(rfr_plan* p, const void* host, size_t bytes) {
+    if (!p || !host || bytes < sizeof(StateHeader)) return RFR_E_INVALID;
+    StateHeader h;
+    std::memcpy(&h, host, sizeof(h));
+    if (h.magic != kStateMagic || h.version != 1 || h.mode != p->mode ||
+        h.a != (p->mode == RFR_MODE_PFB ? p->N : p->L) || h.b != (p->mode == RFR_MODE_PFB ? p->T : p->D) ||
+        h.W != p->W || h.H != p->H)
+        return fail(p, RFR_E_INVALID, "state does not match this plan");
+    const int64_t keep = std::max<int64_t>(h.cl, 0);
+    if (keep > p->carry_cap || bytes < sizeof(h) + static_cast<size_t>(keep) * 4)
+        return fail(p, RFR_E_INVALID, "state blob truncated");
+    RFR_CUDA(p, cudaDeviceSynchronize());
+    p->cur = 0;
+    if (keep > 0)
+        RFR_CUDA(p, cudaMemcpy(p->d_carry[0], static_cast<const char*>(host) + sizeof(h),
+                               static_cast<size_t>(keep) * 4, cudaMemcpyHostToDevice));
+    p->samples = h.samples;
+    p->frames = h.frames;
+    p->cl = h.cl;
+    p->q_frames = 0;
+    return RFR_OK;
+}
+
+rfr_status rfr_plan_get_taps(const rfr_plan* p, double* h64, float* h32, int64_t* n) {
+    if (!p || !n) return RFR_E_INVALID;
+    *n = static_cast<int64_t>(p->h64.size());
+    if (h64) std::memcpy(h64, p->h64.data(), p->h64.size() * 8);
+    if (h32) std::memcpy(h32, p->h32.data(), p->h32.size() * 4);
+    return RFR_OK;
+}
+
+rfr_status rfr_plan_get_bins(const rfr_plan* p, int32_t* bins, int32_t* count) {
+    if (!p || !count) return RFR_E_INVALID;
+    *count = static_cast<int32_t>(p->bins.size());
+    if (bins && !p->bins.empty()) std::memcpy(bins, p->bins.data(), p->bins.size() * 4);
+    return RFR_OK;
+}
+
+rfr_status rfr_plain_oneshot(rfr_plan* p, const int16_t* iq, int64_t n, rfr_output* out, void* stream) {
+    if (!p || !out || n < 0 || (n > 0 && !iq)) return RFR_E_INVALID;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // zero history: frame k uses samples ((k+1)*hop - W, (k+1)*hop]
+    const int64_t W = p->mode == RFR_MODE_PFB ? static_cast<int64_t>(p->N) * p->T : p->L;
+    const int64_t F = n / p->H;
+    (void)W;
+    if (!out_ok(p, out, F)) return fail(p, RFR_E_SHORT, "plain: output too small");
+    const int nt = static_cast<int>(p->words.size());
+    if (F > 0) {
+        if (p->mode == RFR_MODE_PFB) {
+            const bool tones = (p->out_flags & RFR_OUT_TONES) != 0;
+            RFR_CUDA(p, rfr::plain_pfb(iq, n, p->N, p->T, p->d_h32, p->d_bins, tones ? nt : 0,
+                                       (p->out_flags & RFR_OUT_FULL) ? static_cast<char*>(out->full) + out->frame_offset * out->full_ld * 8 : nullptr,
+                                       out->full_ld,
+                                       tones ? static_cast<char*>(out->tones) + out->frame_offset * 8 : nullptr,
+                                       out->tones_ld, &p->plain_scratch, &p->plain_scratch_bytes,
+                                       &p->plain_fft, &p->plain_fft_batch, st));
+        } else if (nt > 0) {
+            RFR_CUDA(p, rfr::plain_demod(iq, n, p->L, p->D, p->d_h32, p->d_words, nt,
+                                         static_cast<char*>(out->tones) + out->frame_offset * 8, out->tones_ld, st));
+        }
+    }
+    out->frames = F;
+    return RFR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,392 @@
+// pfb_kernels.cu -- the fused polyphase filter bank (Sec. III.A of
+// arXiv:1812.02200): int16 IQ -> FP32 polyphase FIR -> N-point FFT -> full
+// spectrum and/or tone-bin gather, in one kernel per push.
+//
+// Stream view.  A push sees the virtual stream v = [carry | buffer]: `carry`
+// (plan-owned, device) holds the last W - N + r samples of the stream (zero
+// history at the start, r = partial-frame residue) and `buffer` the caller's
+// new samples.  Frame j of the push (0 <= j < F) uses v-blocks j .. j+T-1,
+// where v-block b is v[b*N, (b+1)*N):
+//     v_j[p] = sum_{t<T} h[t*N + p] * v[(j+t)*N + p]
+//     y_j[c] = sum_p v_j[p] exp(-2*pi*i*c*p/N)
+// which is frame (F0 + j) of the stream, F0 the frames before this push.
+//
+// Two variants:
+//  RING   (N <= 4096, T <= 8 after padding): each CTA owns a contiguous run
+//         of "super-blocks" (4096 samples = G = 4096/N frames' worth of new
+//         samples).  A ring of super-blocks in shared memory is filled by
+//         1-D TMA bulk copies (cp.async.bulk + mbarrier complete_tx), P
+//         super-blocks ahead; each sample is read from HBM once.  The FIR
+//         taps of the thread's 16 branches live in registers.
+//  DIRECT (any other N <= 16384, T <= 16): no ring; the T samples of every
+//         branch are read from global memory (L2 serves the T-fold reuse)
+//         and the taps with __ldg.
+// Both run the same in-CTA FFT (fft_dev.cuh) and write
+//   full[(frame_offset + j) * full_ld + c]      (natural bin order)
+//   tones[s * tones_ld + frame_offset + j] = y_j[bin[s]].
+#include <algorithm>
+#include <cstdio>
+
+#include "dev_common.cuh"
+#include "fft_dev.cuh"
+#include "rfr_internal.h"
+
+namespace rfr {
+
+constexpr int kSB = 4096;          // samples per super-block (16 KiB of IQ)
+constexpr int kRingThreads = 256;
+
+struct PfbArgs {
+    const uint32_t* carry;   // packed IQ words
+    int64_t cl;              // carry length (samples)
+    const uint32_t* buf;
+    int64_t n;               // buffer length (samples)
+    int64_t F;               // frames to produce
+    const float* h;          // taps [T*N] (kernel T)
+    const float2* tw;        // FFT twiddles
+    int tw_count;
+    int T;                   // kernel taps (DIRECT variant)
+    const int32_t* bins;
+    int n_tones;
+    float2* full;
+    int64_t full_ld;
+    float2* tones;
+    int64_t tones_ld;
+    int64_t frame_offset;
+    int use_tma;
+    int* status;
+    int64_t q_lo, q_hi;      // iteration range
+    int64_t iters_per_cta;
+    int ring_sb;             // RING: super-blocks in the ring
+};
+
+__host__ __device__ __forceinline__ int64_t min_i64(int64_t a, int64_t b) { return a < b ? a : b; }
+__host__ __device__ __forceinline__ int64_t max_i64(int64_t a, int64_t b) { return a > b ? a : b; }
+
+__device__ __forceinline__ uint32_t vload(const PfbArgs& a, int64_t idx) {
+    return idx < a.cl ? __ldg(a.carry + idx) : __ldg(a.buf + (idx - a.cl));
+}
+
+// Copies super-block q (its needed part) of v into ring slot `dst`.
+// TMA path: one elected thread, completion on `bar`.
+__device__ __forceinline__ void issue_sb_tma(const PfbArgs& a, int64_t q, int64_t need,
+                                             uint32_t* dst, uint64_t* bar) {
+    const int64_t lo = q * kSB;
+    const int64_t hi = min(lo + kSB, need);
+    const uint32_t bytes = static_cast<uint32_t>(hi - lo) * 4u;
+    mbar_arrive_expect_tx(bar, bytes);
+    const int64_t c_hi = min(hi, a.cl);
+    if (c_hi > lo) tma_bulk_g2s(dst, a.carry + lo, static_cast<uint32_t>(c_hi - lo) * 4u, bar);
+    const int64_t b_lo = max(lo, a.cl);
+    if (hi > b_lo)
+        tma_bulk_g2s(dst + (b_lo - lo), a.buf + (b_lo - a.cl), static_cast<uint32_t>(hi - b_lo) * 4u, bar);
+}
+
+__device__ __forceinline__ void copy_sb_threads(const PfbArgs& a, int64_t q, int64_t need,
+                                                uint32_t* dst) {
+    const int64_t lo = q * kSB;
+    const int64_t hi = min(lo + kSB, need);
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) dst[i - lo] = vload(a, i);
+}
+
+// Writes the frame's outputs: full spectrum from registers, then (if tones)
+// the spectrum to smem and the tone gather.  All threads call it.
+template <int LOG2N>
+__device__ __forceinline__ void pfb_outputs(const PfbArgs& a, float2 (&v)[16], float2* xbuf,
+                                            int g, int tf, int64_t j, bool valid, int G,
+                                            int64_t j0) {
+    constexpr int N = 1 << LOG2N;
+    constexpr int FSTRIDE = N + N / 16;
+    if (a.full && valid) {
+        float2* row = a.full + (a.frame_offset + j) * a.full_ld;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) row[fft_out_index<LOG2N>(tf, i)] = v[i];
+    }
+    if (a.n_tones > 0) {
+        __syncthreads();   // the passes are done reading xbuf
+        float2* fb = xbuf + g * FSTRIDE;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) fb[fpad(fft_out_index<LOG2N>(tf, i))] = v[i];
+        __syncthreads();
+        const int items = G * a.n_tones;
+        for (int it = threadIdx.x; it < items; it += blockDim.x) {
+            const int s = it / G, gg = it - s * G;
+            const int64_t jj = j0 + gg;
+            if (jj >= 0 && jj < a.F) {
+                const int b = __ldg(a.bins + s);
+                a.tones[s * a.tones_ld + a.frame_offset + jj] = xbuf[gg * FSTRIDE + fpad(b)];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- RING
+template <int LOG2N, int T>
+__global__ void __launch_bounds__(kRingThreads, 1) pfb_ring_kernel(const PfbArgs a) {
+    constexpr int N = 1 << LOG2N;
+    constexpr int NT = N / 16;                 // threads per frame
+    constexpr int G = kRingThreads / NT;       // frames per iteration
+    constexpr int HB = (T - 1 + G - 1) / G;    // history super-blocks
+    constexpr int FSTRIDE = N + N / 16;
+    static_assert(G * N == kSB, "super-block = G frames");
+
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int RS = a.ring_sb;
+    uint32_t* ring = reinterpret_cast<uint32_t*>(smem);
+    float2* xbuf = reinterpret_cast<float2*>(smem + static_cast<size_t>(RS) * kSB * 4);
+    float2* tw = xbuf + G * FSTRIDE;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(tw + ((a.tw_count + 1) & ~1));
+
+    const int tid = threadIdx.x;
+    const int g = tid / NT, tf = tid % NT;
+    const int64_t need = (a.F + T - 1) * static_cast<int64_t>(N);   // v samples used
+    const int64_t n_sb = (need + kSB - 1) / kSB;
+    const int64_t qa = a.q_lo + static_cast<int64_t>(blockIdx.x) * a.iters_per_cta;
+    const int64_t qb = min(a.q_hi, qa + a.iters_per_cta);
+    if (qa >= qb) return;
+    const int P = RS - HB - 1;                 // super-blocks of look-ahead
+
+    for (int i = tid; i < a.tw_count; i += blockDim.x) tw[i] = __ldg(a.tw + i);
+    // taps of the thread's branches p = tf + r*NT
+    float hr[T][16];
+#pragma unroll
+    for (int t = 0; t < T; ++t)
+#pragma unroll
+        for (int r = 0; r < 16; ++r) hr[t][r] = __ldg(a.h + t * N + tf + r * NT);
+
+    // Super-blocks are issued in order from qs; the fill index of super-block
+    // q in its slot (q mod RS) is (q - qs) / RS, which gives the phase parity.
+    const int64_t qs = max_i64(qa - HB, 0);
+    if (a.use_tma) {
+        if (tid == 0) {
+            for (int s = 0; s < RS; ++s) mbar_init(&bars[s], 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+        if (tid == 0) {
+            for (int64_t q = qs; q < min_i64(qa + P + 1, n_sb); ++q)
+                issue_sb_tma(a, q, need, ring + static_cast<int64_t>(q % RS) * kSB, &bars[q % RS]);
+        }
+        for (int64_t q = qs; q < qa; ++q)   // history of the first iteration
+            if (!mbar_wait(&bars[q % RS], static_cast<uint32_t>(((q - qs) / RS) & 1), a.status)) return;
+    } else {
+        for (int64_t q = qs; q < qa; ++q)
+            copy_sb_threads(a, q, need, ring + static_cast<int64_t>(q % RS) * kSB);
+    }
+    const int rlen = RS * kSB;
+
+    for (int64_t q = qa; q < qb; ++q) {
+        const int slot = static_cast<int>(q % RS);
+        if (a.use_tma) {
+            if (!mbar_wait(&bars[slot], static_cast<uint32_t>(((q - qs) / RS) & 1), a.status)) return;
+        } else {
+            __syncthreads();
+            copy_sb_threads(a, q, need, ring + static_cast<int64_t>(slot) * kSB);
+            __syncthreads();
+        }
+        const int64_t j0 = q * G - (T - 1);    // first frame of this iteration
+        const int64_t j = j0 + g;
+        const bool valid = (j >= 0) && (j < a.F);
+
+        // polyphase FIR
+        float2 v[16];
+        if (valid) {
+            int base = static_cast<int>((j * N) % rlen);
+#pragma unroll
+            for (int r = 0; r < 16; ++r) v[r] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                const uint32_t* blk = ring + base + tf;
+#pragma unroll
+                for (int r = 0; r < 16; ++r) {
+                    const float2 x = iq_to_f2(blk[r * NT]);
+                    v[r].x = fmaf(hr[t][r], x.x, v[r].x);
+                    v[r].y = fmaf(hr[t][r], x.y, v[r].y);
+                }
+                base += N;
+                if (base >= rlen) base -= rlen;
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < 16; ++r) v[r] = make_float2(0.f, 0.f);
+        }
+        __syncthreads();   // ring reads of this iteration are done
+        if (a.use_tma && tid == 0) {
+            const int64_t qn = q + P + 1;
+            if (qn < n_sb) issue_sb_tma(a, qn, need, ring + static_cast<int64_t>(qn % RS) * kSB, &bars[qn % RS]);
+        }
+        float2* fb = xbuf + g * FSTRIDE;
+        fft_frame<LOG2N, true>(v, fb, tf, tw);
+        pfb_outputs<LOG2N>(a, v, xbuf, g, tf, j, valid, G, j0);
+    }
+    // Drain: the look-ahead copies issued past this CTA's range were never
+    // waited for; wait for them so no bulk copy lands in freed shared memory.
+    if (a.use_tma) {
+        for (int64_t q = qb; q < min_i64(qb + P + 1, n_sb); ++q)
+            if (!mbar_wait(&bars[q % RS], static_cast<uint32_t>(((q - qs) / RS) & 1), a.status)) return;
+    }
+}
+
+// -------------------------------------------------------------- DIRECT
+template <int LOG2N>
+__global__ void __launch_bounds__(1024, 1) pfb_direct_kernel(const PfbArgs a) {
+    constexpr int N = 1 << LOG2N;
+    constexpr int NT = N / 16;
+    constexpr int FSTRIDE = N + N / 16;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    float2* xbuf = reinterpret_cast<float2*>(smem);
+    const int G = blockDim.x / NT;
+    const int tid = threadIdx.x;
+    const int g = tid / NT, tf = tid % NT;
+    const int T = a.T;
+    const int64_t n_iter = (a.F + G - 1) / G;
+    for (int64_t q = blockIdx.x; q < n_iter; q += gridDim.x) {
+        const int64_t j0 = q * G;
+        const int64_t j = j0 + g;
+        const bool valid = j < a.F;
+        float2 v[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = make_float2(0.f, 0.f);
+        if (valid) {
+            for (int t = 0; t < T; ++t) {
+                const int64_t base = (j + t) * N + tf;
+#pragma unroll
+                for (int r = 0; r < 16; ++r) {
+                    const float hv = __ldg(a.h + t * N + tf + r * NT);
+                    const float2 x = iq_to_f2(vload(a, base + r * NT));
+                    v[r].x = fmaf(hv, x.x, v[r].x);
+                    v[r].y = fmaf(hv, x.y, v[r].y);
+                }
+            }
+        }
+        __syncthreads();   // previous iteration's gather is done with xbuf
+        fft_frame<LOG2N, false>(v, xbuf + g * FSTRIDE, tf, a.tw);
+        pfb_outputs<LOG2N>(a, v, xbuf, g, tf, j, valid, G, j0);
+    }
+}
+
+// ------------------------------------------------------------ launcher
+namespace {
+
+template <int LOG2N, int T>
+size_t ring_smem_bytes(int rs, int tw_count) {
+    constexpr int N = 1 << LOG2N;
+    constexpr int G = kRingThreads / (N / 16);
+    return static_cast<size_t>(rs) * kSB * 4 + static_cast<size_t>(G) * (N + N / 16) * 8 +
+           static_cast<size_t>((tw_count + 1) & ~1) * 8 + static_cast<size_t>(rs) * 8;
+}
+
+template <int LOG2N, int T>
+cudaError_t launch_ring(PfbArgs a, int n_sms, int max_smem, cudaStream_t st) {
+    constexpr int N = 1 << LOG2N;
+    constexpr int G = kRingThreads / (N / 16);
+    constexpr int HB = (T - 1 + G - 1) / G;
+    int rs = HB + 1 + 3;
+    while (rs > HB + 2 && ring_smem_bytes<LOG2N, T>(rs, a.tw_count) > static_cast<size_t>(max_smem)) --rs;
+    const size_t smem = ring_smem_bytes<LOG2N, T>(rs, a.tw_count);
+    if (smem > static_cast<size_t>(max_smem)) return cudaErrorInvalidConfiguration;
+    a.ring_sb = rs;
+    a.q_lo = (T - 1) / G;
+    a.q_hi = (a.F + T - 1 + G - 1) / G;
+    const int64_t iters = a.q_hi - a.q_lo;
+    const int64_t grid = std::min<int64_t>(iters, n_sms);
+    a.iters_per_cta = (iters + grid - 1) / grid;
+    const int64_t grid2 = (iters + a.iters_per_cta - 1) / a.iters_per_cta;
+    auto k = pfb_ring_kernel<LOG2N, T>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<static_cast<unsigned>(grid2), kRingThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int LOG2N>
+cudaError_t launch_direct(PfbArgs a, int n_sms, int max_smem, cudaStream_t st) {
+    constexpr int N = 1 << LOG2N;
+    constexpr int NT = N / 16;
+    const int threads = NT >= 256 ? NT : 256;
+    const int G = threads / NT;
+    const size_t smem = static_cast<size_t>(G) * (N + N / 16) * 8;
+    if (smem > static_cast<size_t>(max_smem)) return cudaErrorInvalidConfiguration;
+    const int64_t n_iter = (a.F + G - 1) / G;
+    int per_sm = 1;
+    auto k = pfb_direct_kernel<LOG2N>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(n_iter, static_cast<int64_t>(n_sms) * std::max(per_sm, 1)));
+    k<<<static_cast<unsigned>(grid), threads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int LOG2N>
+cudaError_t dispatch_ring_T(PfbArgs a, int tk, int n_sms, int max_smem, cudaStream_t st) {
+    switch (tk) {
+    case 4: return launch_ring<LOG2N, 4>(a, n_sms, max_smem, st);
+    case 8: return launch_ring<LOG2N, 8>(a, n_sms, max_smem, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+bool pfb_uses_ring(int log2n, int taps) { return log2n >= 4 && log2n <= 12 && taps <= 8; }
+int pfb_kernel_taps(int log2n, int taps) {
+    if (pfb_uses_ring(log2n, taps)) return taps <= 4 ? 4 : 8;
+    return taps;
+}
+
+cudaError_t pfb_launch(const PfbLaunch& L, cudaStream_t st) {
+    PfbArgs a{};
+    a.carry = reinterpret_cast<const uint32_t*>(L.carry);
+    a.cl = L.cl;
+    a.buf = reinterpret_cast<const uint32_t*>(L.buf);
+    a.n = L.n;
+    a.F = L.F;
+    a.h = L.h;
+    a.tw = reinterpret_cast<const float2*>(L.tw);
+    a.tw_count = L.tw_count;
+    a.T = L.taps_kernel;
+    a.bins = L.bins;
+    a.n_tones = L.n_tones;
+    a.full = reinterpret_cast<float2*>(L.full);
+    a.full_ld = L.full_ld;
+    a.tones = reinterpret_cast<float2*>(L.tones);
+    a.tones_ld = L.tones_ld;
+    a.frame_offset = L.frame_offset;
+    a.status = L.status;
+    if (a.F <= 0) return cudaSuccess;
+    const bool aligned = (reinterpret_cast<uintptr_t>(L.buf) % 16 == 0) && (L.cl % 4 == 0) &&
+                         (reinterpret_cast<uintptr_t>(L.carry) % 16 == 0);
+    a.use_tma = aligned ? 1 : 0;
+    const int lg = L.log2n;
+    if (pfb_uses_ring(lg, L.taps_kernel)) {
+        switch (lg) {
+        case 4: return dispatch_ring_T<4>(a, L.taps_kernel, L.n_sms, L.max_smem, st);
+        case 5: return dispatch_ring_T<5>(a, L.taps_kernel, L.n_sms, L.max_smem, st);
+        case 6: return dispatch_ring_T<6>(a, L.taps_kernel, L.n_sms, L.max_smem, st);
+        case 7: return dispatch_ring_T<7>(a, L.taps_kernel, L.n_sms, L.max_smem, st);
+        case 8: return dispatch_ring_T<8>(a, L.taps_kernel, L.n_sms, L.max_smem, st);
+        case 9: return dispatch_ring_T<9>(a, L.taps_kernel, L.n_sms, L.max_smem, st);
+        case 10: return dispatch_ring_T<10>(a, L.taps_kernel, L.n_sms, L.max_smem, st);
+        case 11: return dispatch_ring_T<11>(a, L.taps_kernel, L.n_sms, L.max_smem, st);
+        case 12: return dispatch_ring_T<12>(a, L.taps_kernel, L.n_sms, L.max_smem, st);
+        default: return cudaErrorInvalidValue;
+        }
+    }
+    switch (lg) {
+    case 4: return launch_direct<4>(a, L.n_sms, L.max_smem, st);
+    case 5: return launch_direct<5>(a, L.n_sms, L.max_smem, st);
+    case 6: return launch_direct<6>(a, L.n_sms, L.max_smem, st);
+    case 7: return launch_direct<7>(a, L.n_sms, L.max_smem, st);
+    case 8: return launch_direct<8>(a, L.n_sms, L.max_smem, st);
+    case 9: return launch_direct<9>(a, L.n_sms, L.max_smem, st);
+    case 10: return launch_direct<10>(a, L.n_sms, L.max_smem, st);
+    case 11: return launch_direct<11>(a, L.n_sms, L.max_smem, st);
+    case 12: return launch_direct<12>(a, L.n_sms, L.max_smem, st);
+    case 13: return launch_direct<13>(a, L.n_sms, L.max_smem, st);
+    case 14: return launch_direct<14>(a, L.n_sms, L.max_smem, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace rfr

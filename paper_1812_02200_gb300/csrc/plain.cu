@@ -1,0 +1,119 @@
+// plain.cu -- the plain FP32 GPU forms used as the comparison baseline:
+//   PFB:   an FP32 polyphase-FIR kernel writing the filtered frames, a batched
+//          cuFFT C2C transform (the library route of Sec. III.A), and a gather
+//          kernel for the tone bins;
+//   demod: an FP32 CUDA-core kernel over the Toeplitz view of the stream with
+//          FP32 modulated taps (mix + filter + decimate of Sec. III.B).
+// One-shot with zero history (frame k uses samples (k+1)*hop - W .. (k+1)*hop - 1).
+#include <cufft.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "dev_common.cuh"
+#include "rfr_internal.h"
+
+namespace rfr {
+
+namespace {
+
+__global__ void plain_fir_kernel(const uint32_t* __restrict__ x, int64_t n, int N, int T,
+                                 const float* __restrict__ h, int64_t F, float2* __restrict__ v) {
+    const int64_t total = F * N;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t k = i / N;
+        const int p = static_cast<int>(i - k * N);
+        const int64_t start = (k + 1) * N - static_cast<int64_t>(N) * T;
+        float re = 0.f, im = 0.f;
+        for (int t = 0; t < T; ++t) {
+            const int64_t m = start + static_cast<int64_t>(t) * N + p;
+            if (m < 0) continue;
+            const float2 s = iq_to_f2(x[m]);
+            const float c = h[t * N + p];
+            re = fmaf(c, s.x, re);
+            im = fmaf(c, s.y, im);
+        }
+        v[i] = make_float2(re, im);
+    }
+}
+
+__global__ void plain_gather_kernel(const float2* __restrict__ y, int N, int64_t F,
+                                    const int32_t* __restrict__ bins, int n_tones,
+                                    float2* __restrict__ tones, int64_t ld) {
+    const int64_t total = F * n_tones;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int s = static_cast<int>(i / F);
+        const int64_t k = i - static_cast<int64_t>(s) * F;
+        tones[s * ld + k] = y[k * N + bins[s]];
+    }
+}
+
+__global__ void plain_copy_rows(const float2* __restrict__ y, int N, int64_t F, float2* __restrict__ out,
+                                int64_t ld) {
+    const int64_t total = F * N;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t k = i / N;
+        out[k * ld + (i - k * N)] = y[i];
+    }
+}
+
+unsigned grid_for(int64_t work) {
+    return static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, 152 * 32)));
+}
+
+}  // namespace
+
+cudaError_t plain_pfb(const int16_t* iq, int64_t n, int N, int T, const float* h, const int32_t* bins,
+                      int n_tones, void* full, int64_t full_ld, void* tones, int64_t tones_ld,
+                      void** scratch, size_t* scratch_bytes, void** fft_plan, int64_t* fft_batch,
+                      cudaStream_t st) {
+    const int64_t F = n / N;
+    if (F <= 0) return cudaSuccess;
+    const bool direct = full && full_ld == N;   // cuFFT can write straight into `full`
+    const size_t need = static_cast<size_t>(F) * N * 8 * (direct ? 1 : 2);
+    if (*scratch_bytes < need) {
+        if (*scratch) cudaFree(*scratch);
+        *scratch = nullptr;
+        *scratch_bytes = 0;
+        cudaError_t e = cudaMalloc(scratch, need);
+        if (e != cudaSuccess) return e;
+        *scratch_bytes = need;
+    }
+    float2* v = static_cast<float2*>(*scratch);
+    float2* y = direct ? static_cast<float2*>(full) : v + F * N;
+    if (*fft_batch != F * 1000000LL + N) {
+        if (*fft_plan) {
+            cufftDestroy(static_cast<cufftHandle>(reinterpret_cast<uintptr_t>(*fft_plan)));
+            *fft_plan = nullptr;
+        }
+        cufftHandle ph;
+        int dims[1] = {N};
+        if (cufftPlanMany(&ph, 1, dims, nullptr, 1, N, nullptr, 1, N, CUFFT_C2C, static_cast<int>(F)) !=
+            CUFFT_SUCCESS)
+            return cudaErrorUnknown;
+        *fft_plan = reinterpret_cast<void*>(static_cast<uintptr_t>(ph));
+        *fft_batch = F * 1000000LL + N;
+    }
+    const cufftHandle ph = static_cast<cufftHandle>(reinterpret_cast<uintptr_t>(*fft_plan));
+    cufftSetStream(ph, st);
+    plain_fir_kernel<<<grid_for(F * N), 256, 0, st>>>(reinterpret_cast<const uint32_t*>(iq), n, N, T, h, F, v);
+    if (cufftExecC2C(ph, reinterpret_cast<cufftComplex*>(v), reinterpret_cast<cufftComplex*>(y),
+                     CUFFT_FORWARD) != CUFFT_SUCCESS)
+        return cudaErrorUnknown;
+    if (full && !direct)
+        plain_copy_rows<<<grid_for(F * N), 256, 0, st>>>(y, N, F, static_cast<float2*>(full), full_ld);
+    if (tones && n_tones > 0)
+        plain_gather_kernel<<<grid_for(F * n_tones), 256, 0, st>>>(y, N, F, bins, n_tones,
+                                                                     static_cast<float2*>(tones), tones_ld);
+    return cudaGetLastError();
+}
+
+void plain_release(void* scratch, void* fft_plan) {
+    if (scratch) cudaFree(scratch);
+    if (fft_plan) cufftDestroy(static_cast<cufftHandle>(reinterpret_cast<uintptr_t>(fft_plan)));
+}
+
+}  // namespace rfr

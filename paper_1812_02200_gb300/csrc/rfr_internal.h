@@ -1,0 +1,166 @@
+// rfr_internal.h -- internal structures of the readout library (not part of
+// the ABI).  The plan holds the host-built coefficient tables (FP64), their
+// device copies, the stream state kept on the device across pushes, and
+// cached scratch buffers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/rfr.h"
+
+namespace rfr {
+
+// ------------------------------------------------------------ host tables
+// Window and prototype builders (FP64), written from the definitions in
+// Sec. III.A/B; see plan_host.cpp.
+int build_window(int kind, double beta, int64_t m, double* w);
+int build_lowpass(int kind, double beta, double fc, int64_t m, double* h);
+uint64_t freq_to_word(double f, double fs);
+int32_t word_to_bin(uint64_t word, int32_t n);
+
+// --------------------------------------------------------------- PFB
+struct PfbLaunch {
+    const int16_t* carry;
+    int64_t cl;
+    const int16_t* buf;
+    int64_t n;
+    int64_t F;
+    int log2n;
+    int taps_kernel;
+    const float* h;
+    const void* tw;
+    int tw_count;
+    const int32_t* bins;
+    int n_tones;
+    void* full;
+    int64_t full_ld;
+    void* tones;
+    int64_t tones_ld;
+    int64_t frame_offset;
+    int* status;
+    int n_sms;
+    int max_smem;
+};
+bool pfb_uses_ring(int log2n, int taps);
+int pfb_kernel_taps(int log2n, int taps);
+cudaError_t pfb_launch(const PfbLaunch& L, cudaStream_t st);
+
+// ------------------------------------------------------------- demod
+// Split-FP16 tensor-core demodulation; see demod_*.cu.
+constexpr int kDemodBM = 128;         // frames per tile
+constexpr int kDemodBN = 256;         // real output columns (= 128 tones) per tile
+constexpr int kDemodBK = 64;          // halfs of K per k-block (32 complex taps)
+
+struct DemodLaunch {
+    const int16_t* carry;
+    int64_t cl;
+    const int16_t* buf;
+    int64_t n;
+    int64_t F;
+    int64_t a0;                 // absolute sample index of v[0]
+    int32_t L, D, Lpad, n_tones, ntp;   // ntp = tones padded to kDemodBN/2
+    const uint64_t* words;      // device [n_tones]
+    const void* b_hi;           // device fp16 [2*ntp][2*Lpad]
+    const void* b_lo;
+    double inv_scale;           // 2^-e
+    void* xs_hi;                // scratch fp16 [rows][2*D]
+    void* xs_lo;
+    int64_t xs_rows;
+    void* rot;                  // scratch float2 rotation anchors
+    void* tones;
+    int64_t tones_ld;
+    int64_t frame_offset;
+    int* status;
+    int n_sms;
+    int kchunk;                 // k-blocks per TMEM accumulation chunk
+};
+cudaError_t demod_build_taps(const double* d_h, const uint64_t* d_words, int n_tones, int ntp,
+                             int L, int Lpad, int e, void* b_hi, void* b_lo, cudaStream_t st);
+cudaError_t demod_launch(const DemodLaunch& L, cudaStream_t st);
+size_t demod_xs_rows(int64_t F, int L, int D);
+
+// -------------------------------------------------------------- plain
+cudaError_t plain_pfb(const int16_t* iq, int64_t n, int N, int T, const float* h, const int32_t* bins,
+                      int n_tones, void* full, int64_t full_ld, void* tones, int64_t tones_ld,
+                      void** scratch, size_t* scratch_bytes, void** fft_plan, int64_t* fft_batch,
+                      cudaStream_t st);
+cudaError_t plain_demod(const int16_t* iq, int64_t n, int L, int D, const float* h32,
+                        const uint64_t* words, int n_tones, void* tones, int64_t tones_ld,
+                        cudaStream_t st);
+void plain_release(void* scratch, void* fft_plan);
+
+// ------------------------------------------------------------- state
+cudaError_t carry_update(const int16_t* old_carry, int64_t cl, const int16_t* buf, int64_t n,
+                         int64_t from, int64_t count, int16_t* new_carry, cudaStream_t st);
+
+}  // namespace rfr
+
+// The plan.  Mode-specific members are unused in the other mode.
+struct rfr_plan {
+    int mode = 0;
+    int32_t N = 0, T = 0, Tk = 0, log2n = 0;   // PFB (Tk: kernel taps, zero-padded)
+    int32_t L = 0, D = 0, Lpad = 0;            // demod
+    int64_t W = 0, H = 0;                      // window and hop (samples)
+    uint32_t out_flags = 0;
+    rfr_window window{};
+    std::vector<uint64_t> words;
+    std::vector<int32_t> bins;
+    std::vector<double> h64;                   // prototype, FP64 (length N*T or L)
+    std::vector<float> h32;
+    int device = 0, n_sms = 0, max_smem = 0;
+
+    // device tables
+    float* d_h = nullptr;          // PFB kernel taps [Tk*N] (zero-padded oldest taps)
+    void* d_tw = nullptr;          // FFT twiddles
+    int tw_count = 0;
+    int32_t* d_bins = nullptr;
+    uint64_t* d_words = nullptr;
+    float* d_h32 = nullptr;        // taps as FP32 (plain forms)
+    void* d_bhi = nullptr;         // demod modulated taps, fp16 hi/lo
+    void* d_blo = nullptr;
+    int32_t ntp = 0;               // demod tones padded
+    int tap_exp = 0;               // demod power-of-two tap scale exponent
+    int* d_status = nullptr;
+
+    // stream state
+    int64_t samples = 0;           // samples consumed
+    int64_t frames = 0;            // frames produced
+    int64_t cl = 0;                // carry length (may be <= 0: samples to skip)
+    int16_t* d_carry[2] = {nullptr, nullptr};
+    int cur = 0;
+    int64_t carry_cap = 0;
+
+    // demod scratch
+    void* d_xs_hi = nullptr;
+    void* d_xs_lo = nullptr;
+    int64_t xs_rows_cap = 0;
+    void* d_rot = nullptr;
+    int64_t rot_cap = 0;
+
+    // queued output ring (rfr_push / rfr_pull)
+    void* d_qfull = nullptr;
+    void* d_qtones = nullptr;
+    int64_t q_cap = 0;             // frames
+    int64_t q_frames = 0;          // pending frames
+    cudaStream_t last_stream = nullptr;
+
+    // host-staging (rfr_process_host)
+    void* d_stage_in[2] = {nullptr, nullptr};
+    void* d_stage_full[2] = {nullptr, nullptr};
+    void* d_stage_tones[2] = {nullptr, nullptr};
+    int64_t stage_samples = 0;
+    cudaStream_t stage_st[2] = {nullptr, nullptr};
+    cudaEvent_t stage_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+
+    // plain-form scratch
+    void* plain_scratch = nullptr;
+    size_t plain_scratch_bytes = 0;
+    void* plain_fft = nullptr;
+    int64_t plain_fft_batch = 0;
+
+    std::string last_error;
+};

@@ -1,0 +1,233 @@
+"""Thin Python binding of the C ABI in include/rfr.h (argument marshalling
+only; every step of the computation runs in the library's CUDA kernels).
+
+Device memory and streams come from PyTorch tensors (``data_ptr()``,
+``torch.cuda.current_stream().cuda_stream``).  The library must have been
+built (``paper_1812_02200_gb300.build.build()``); importing this module
+fails loudly otherwise -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"librfr.so not found at {LIB_PATH}: build it first with "
+        "`python -c 'import __graft_entry__ as g; g.build()'` (nvcc, sm_103a)")
+
+_lib = C.CDLL(LIB_PATH)
+
+OK, E_INVALID, E_NOMEM, E_CUDA, E_TIMEOUT, E_SHORT, E_BUSY, E_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
+WIN = {"rect": 0, "hann": 1, "hamming": 2, "blackman": 3, "kaiser": 4}
+OUT_FULL, OUT_TONES = 1, 2
+MODE_PFB, MODE_DEMOD = 1, 2
+
+
+class Window(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("beta", C.c_double), ("cutoff", C.c_double)]
+
+
+class Tones(C.Structure):
+    _fields_ = [("words", C.POINTER(C.c_uint64)), ("count", C.c_int32)]
+
+
+class Output(C.Structure):
+    _fields_ = [("full", C.c_void_p), ("full_ld", C.c_int64), ("full_cap", C.c_int64),
+                ("tones", C.c_void_p), ("tones_ld", C.c_int64), ("tones_cap", C.c_int64),
+                ("frame_offset", C.c_int64), ("frames", C.c_int64)]
+
+
+class PlanInfo(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("channels", C.c_int32), ("taps", C.c_int32),
+                ("decimation", C.c_int32), ("n_tones", C.c_int32), ("out_flags", C.c_uint32),
+                ("samples_consumed", C.c_int64), ("frames_produced", C.c_int64),
+                ("frames_pending", C.c_int64), ("tap_scale", C.c_double)]
+
+
+_P = C.c_void_p
+_SIGS = {
+    "rfr_plan_create": (C.c_int, [C.POINTER(_P), C.c_int32, C.c_int32, C.POINTER(Window),
+                                  C.POINTER(Tones), C.c_int32, C.c_uint32]),
+    "rfr_plan_destroy": (None, [_P]),
+    "rfr_plan_get_info": (C.c_int, [_P, C.POINTER(PlanInfo)]),
+    "rfr_frames_for": (C.c_int, [_P, C.c_int64, C.POINTER(C.c_int64)]),
+    "rfr_push_into": (C.c_int, [_P, _P, C.c_int64, C.POINTER(Output), _P]),
+    "rfr_push": (C.c_int, [_P, _P, C.c_int64, _P]),
+    "rfr_pull": (C.c_int, [_P, C.POINTER(Output)]),
+    "rfr_process_host": (C.c_int, [_P, _P, C.c_int64, C.POINTER(Output)]),
+    "rfr_reset": (C.c_int, [_P]),
+    "rfr_state_export": (C.c_int, [_P, _P, C.POINTER(C.c_size_t)]),
+    "rfr_state_import": (C.c_int, [_P, _P, C.c_size_t]),
+    "rfr_plan_get_taps": (C.c_int, [_P, _P, _P, C.POINTER(C.c_int64)]),
+    "rfr_plan_get_bins": (C.c_int, [_P, _P, C.POINTER(C.c_int32)]),
+    "rfr_plain_oneshot": (C.c_int, [_P, _P, C.c_int64, C.POINTER(Output), _P]),
+    "rfr_freq_to_word": (C.c_uint64, [C.c_double, C.c_double]),
+    "rfr_word_to_bin": (C.c_int32, [C.c_uint64, C.c_int32]),
+    "rfr_status_string": (C.c_char_p, [C.c_int]),
+    "rfr_last_error": (C.c_char_p, [_P]),
+    "rfr_version": (C.c_char_p, []),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype, _f.argtypes = _res, _args
+
+
+class RfrError(RuntimeError):
+    def __init__(self, status: int, msg: str = ""):
+        self.status = status
+        super().__init__(f"{_lib.rfr_status_string(status).decode()} ({status}): {msg}")
+
+
+def version() -> str:
+    return _lib.rfr_version().decode()
+
+
+def freq_to_word(f_hz: float, fs_hz: float) -> int:
+    return int(_lib.rfr_freq_to_word(float(f_hz), float(fs_hz)))
+
+
+def word_to_bin(word: int, n: int) -> int:
+    return int(_lib.rfr_word_to_bin(int(word) & (2 ** 64 - 1), int(n)))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+class Plan:
+    """A PFB (channels > 0) or direct-demodulation (channels == 0) plan."""
+
+    def __init__(self, channels: int, taps: int, *, window: str = "hann", beta: float = 0.0,
+                 cutoff: float = 0.0, words=None, decimation: int | None = None,
+                 full: bool = True, tones: bool = True):
+        words = np.ascontiguousarray(np.asarray([] if words is None else words, dtype=np.uint64))
+        self.words = words
+        self.channels = channels
+        if channels > 0:
+            flags = (OUT_FULL if full else 0) | (OUT_TONES if (tones and len(words)) else 0)
+            dec = channels if decimation is None else decimation
+        else:
+            flags = OUT_TONES
+            dec = decimation
+        w = Window(WIN[window], float(beta), float(cutoff))
+        tn = Tones(words.ctypes.data_as(C.POINTER(C.c_uint64)) if len(words) else None, len(words))
+        h = _P()
+        st = _lib.rfr_plan_create(C.byref(h), int(channels), int(taps), C.byref(w), C.byref(tn),
+                                  int(dec), flags)
+        if st != OK:
+            raise RfrError(st, "rfr_plan_create")
+        self._h = h
+        self.taps = taps
+        self.decimation = dec
+        self.out_flags = flags
+        self.n_tones = len(words)
+
+    # --------------------------------------------------------------- utils
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.rfr_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st != OK:
+            raise RfrError(st, f"{what}: {_lib.rfr_last_error(self._h).decode()}")
+
+    def info(self) -> dict:
+        i = PlanInfo()
+        self._check(_lib.rfr_plan_get_info(self._h, C.byref(i)), "info")
+        return {f: getattr(i, f) for f, _ in PlanInfo._fields_}
+
+    def frames_for(self, n: int) -> int:
+        f = C.c_int64()
+        self._check(_lib.rfr_frames_for(self._h, int(n), C.byref(f)), "frames_for")
+        return f.value
+
+    def taps_table(self):
+        n = C.c_int64()
+        self._check(_lib.rfr_plan_get_taps(self._h, None, None, C.byref(n)), "taps")
+        h64 = np.empty(n.value, np.float64)
+        h32 = np.empty(n.value, np.float32)
+        self._check(_lib.rfr_plan_get_taps(self._h, h64.ctypes.data, h32.ctypes.data, C.byref(n)), "taps")
+        return h64, h32
+
+    def bins(self):
+        c = C.c_int32()
+        self._check(_lib.rfr_plan_get_bins(self._h, None, C.byref(c)), "bins")
+        b = np.empty(c.value, np.int32)
+        if c.value:
+            self._check(_lib.rfr_plan_get_bins(self._h, b.ctypes.data, C.byref(c)), "bins")
+        return b
+
+    @staticmethod
+    def _out(full, tones, frame_offset):
+        o = Output()
+        if full is not None:
+            o.full, o.full_ld, o.full_cap = full.data_ptr(), full.shape[1], full.shape[0]
+        if tones is not None:
+            o.tones, o.tones_ld, o.tones_cap = tones.data_ptr(), tones.shape[1], tones.shape[1]
+        o.frame_offset = frame_offset
+        return o
+
+    # ---------------------------------------------------------------- work
+    def push_into(self, x, full=None, tones=None, frame_offset: int = 0, stream=None) -> int:
+        """x: int16 [n, 2] device tensor; full: complex64 [cap, >=N]; tones:
+        complex64 [n_tones, cap] (device).  Returns frames written."""
+        o = self._out(full, tones, frame_offset)
+        n = 0 if x is None else x.shape[0]
+        self._check(_lib.rfr_push_into(self._h, _ptr(x), n, C.byref(o), _stream_ptr(stream)),
+                    "push_into")
+        return o.frames
+
+    def push(self, x, stream=None):
+        self._check(_lib.rfr_push(self._h, _ptr(x), x.shape[0], _stream_ptr(stream)), "push")
+
+    def pull(self, full=None, tones=None, frame_offset: int = 0) -> int:
+        o = self._out(full, tones, frame_offset)
+        self._check(_lib.rfr_pull(self._h, C.byref(o)), "pull")
+        return o.frames
+
+    def process_host(self, x, full=None, tones=None, frame_offset: int = 0) -> int:
+        """Host (ideally pinned) int16 [n, 2] in, host outputs."""
+        o = self._out(full, tones, frame_offset)
+        self._check(_lib.rfr_process_host(self._h, _ptr(x), x.shape[0], C.byref(o)), "process_host")
+        return o.frames
+
+    def plain_oneshot(self, x, full=None, tones=None, stream=None) -> int:
+        o = self._out(full, tones, 0)
+        self._check(_lib.rfr_plain_oneshot(self._h, _ptr(x), x.shape[0], C.byref(o),
+                                           _stream_ptr(stream)), "plain_oneshot")
+        return o.frames
+
+    def reset(self):
+        self._check(_lib.rfr_reset(self._h), "reset")
+
+    def state_export(self) -> bytes:
+        n = C.c_size_t()
+        self._check(_lib.rfr_state_export(self._h, None, C.byref(n)), "state_export")
+        buf = C.create_string_buffer(n.value)
+        self._check(_lib.rfr_state_export(self._h, buf, C.byref(n)), "state_export")
+        return buf.raw[: n.value]
+
+    def state_import(self, blob: bytes):
+        buf = C.create_string_buffer(blob, len(blob))
+        self._check(_lib.rfr_state_import(self._h, buf, len(blob)), "state_import")

@@ -47,6 +47,24 @@ def _period(words: np.ndarray) -> int:
     return 0
 
 
+class PeriodicComb:
+    """A comb whose period P divides 2^16: x[m] = one[m mod P], materialised
+    chunk by chunk (slicing returns an ndarray)."""
+
+    def __init__(self, one: np.ndarray, n: int):
+        self.one, self.shape, self.dtype = one, (n,), one.dtype
+
+    def __len__(self):
+        return self.shape[0]
+
+    def __getitem__(self, sl):
+        a, b, _ = sl.indices(self.shape[0])
+        return self.one[np.arange(a, b) % len(self.one)]
+
+    def __array__(self, dtype=None, copy=None):
+        return self[0:self.shape[0]].astype(dtype or self.dtype)
+
+
 def tone_comb(n: int, words, amps, phases, block: int = 4096,
               dtype=np.complex128) -> np.ndarray:
     """Noise-free complex comb sum_i A_i exp(i(phi_i(m) + theta_i)), m < n."""
@@ -59,9 +77,8 @@ def tone_comb(n: int, words, amps, phases, block: int = 4096,
         if P and P <= 65536:
             m = np.arange(P, dtype=np.uint64)
             E = np.exp(1j * _angle(np.multiply.outer(m, words)))      # [P, tones]
-            one = E @ coef
-            reps = -(-n // P)
-            return np.tile(one.astype(dtype), reps)[:n]
+            one = (E @ coef).astype(dtype)
+            return PeriodicComb(one, n)
         # general comb: x[B*q + j] = sum_i E[j, i] * c_q[i] with
         # E[j, i] = exp(i*phi_i(j)) and c_q[i] = coef_i * exp(i*phi_i(B*q))
         B = block
