@@ -193,12 +193,13 @@ def run_reference(args, ws, rank):
     if rank != 0:
         return
     frames = max(16, int(args.ref_frames))
+    c = siggen.c2(n=(frames + TAPS - 1) * N_CHAN)
     for _ in range(args.warmup):
-        oracle_pfb_rate(frames)
+        oracle_pfb_rate(frames, c)
     times = []
     samples = 0
     for _ in range(args.steps):
-        _, dt, samples = oracle_pfb_rate(frames)
+        _, dt, samples = oracle_pfb_rate(frames, c)
         times.append(dt)
     tot = float(np.sum(times))
     val = args.steps * samples / tot / 1e6
@@ -225,7 +226,7 @@ def run_ours(args, ws, rank, local):
     dev = torch.device("cuda", local if ws > 1 else 0)
     hbm_peak, bf16_peak, bf16_sus, peak_kind = measured_peaks()
     t_gen = time.time()
-    c = siggen.c2()
+    c = siggen.c2(n=1 << args.log2_samples)
     log(f"[bench] generated c2 input in {time.time() - t_gen:.1f}s")
     x = torch.from_numpy(c["x"]).to(dev)
     plan = rfr.Plan(N_CHAN, TAPS, window="kaiser", beta=BETA, words=c["words"])
@@ -316,9 +317,10 @@ def run_ours(args, ws, rank, local):
     # -- oracle on the host cores, bounded sample (rank 0 only)
     cpu = None
     if rank == 0 and not args.no_cpu:
-        v, dt, s = oracle_pfb_rate(args.cpu_frames, c)
+        nf = min(args.cpu_frames, F - TAPS)
+        v, dt, s = oracle_pfb_rate(nf, c)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{args.cpu_frames} frames ({s} samples) of the workload, {dt:.1f} s"}
+               "sample": f"{nf} frames ({s} samples) of the workload, {dt:.1f} s"}
 
     if rank != 0:
         return
@@ -327,7 +329,8 @@ def run_ours(args, ws, rank, local):
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "PFB N=4096 T=8 Kaiser(9) windowed sinc, 1000 tones at random "
-                               "bin centres, 2^28 complex int16 samples, full spectrum + tones",
+                               f"bin centres, 2^{args.log2_samples} complex int16 samples, "
+                               "full spectrum + tones",
                    "samples_per_step": samples_step, "frames_per_step": F,
                    "l2": "inputs and outputs larger than L2 (no flush)",
                    "parallelism": f"replicas x{ws}"},
@@ -356,6 +359,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--log2-samples", type=int, default=28,
+                    help="stream length (28 = the workload; smaller only for profiling)")
     ap.add_argument("--cpu-frames", type=int, default=32768)
     ap.add_argument("--ref-frames", type=int, default=2048)
     args = ap.parse_args()

@@ -110,7 +110,7 @@ rfr_status check_status(rfr_plan* p) {
     return RFR_OK;
 }
 
-rfr_status ensure_demod_scratch(rfr_plan* p, int64_t F) {
+rfr_status ensure_demod_scratch(rfr_plan* p, int64_t F, int64_t F0) {
     const int64_t rows = static_cast<int64_t>(rfr::demod_xs_rows(F, p->Lpad, p->D));
     if (rows > p->xs_rows_cap) {
         cudaDeviceSynchronize();
@@ -123,8 +123,8 @@ rfr_status ensure_demod_scratch(rfr_plan* p, int64_t F) {
         RFR_CUDA(p, dev_alloc(&p->d_xs_lo, bytes));
         p->xs_rows_cap = rows;
     }
-    const int64_t tiles = (F + rfr::kDemodBM - 1) / rfr::kDemodBM;
-    const int64_t rot = tiles * p->ntp + static_cast<int64_t>(p->ntp) * rfr::kDemodBM;
+    const int64_t rot = static_cast<int64_t>(rfr::demod_anchor_rows(F0, F)) * p->ntp +
+                        static_cast<int64_t>(p->ntp) * rfr::kDemodBM;
     if (rot > p->rot_cap) {
         cudaDeviceSynchronize();
         dev_free(p->d_rot);
@@ -170,7 +170,7 @@ rfr_status push_core(rfr_plan* p, const int16_t* iq, int64_t n, const rfr_output
             RFR_CUDA(p, rfr::pfb_launch(L, st));
         } else {
             if (!p->words.empty()) {
-                rfr_status rs = ensure_demod_scratch(p, F);
+                rfr_status rs = ensure_demod_scratch(p, F, p->frames);
                 if (rs != RFR_OK) return rs;
                 rfr::DemodLaunch L{};
                 L.carry = carry;
@@ -179,6 +179,7 @@ rfr_status push_core(rfr_plan* p, const int16_t* iq, int64_t n, const rfr_output
                 L.n = n;
                 L.F = F;
                 L.a0 = p->samples - p->cl;
+                L.F0 = p->frames;
                 L.L = p->L;
                 L.D = p->D;
                 L.Lpad = p->Lpad;
@@ -235,7 +236,7 @@ void destroy(rfr_plan* p) {
     if (!p) return;
     cudaDeviceSynchronize();
     for (void* q : {static_cast<void*>(p->d_h), p->d_tw, static_cast<void*>(p->d_bins),
-                    static_cast<void*>(p->d_words), static_cast<void*>(p->d_h32), p->d_bhi, p->d_blo,
+                    static_cast<void*>(p->d_words), static_cast<void*>(p->d_h32), p->d_c32, p->d_bhi, p->d_blo,
                     static_cast<void*>(p->d_status), static_cast<void*>(p->d_carry[0]),
                     static_cast<void*>(p->d_carry[1]), p->d_xs_hi, p->d_xs_lo, p->d_rot, p->d_qfull,
                     p->d_qtones})
@@ -680,7 +681,11 @@ rfr_status rfr_plain_oneshot(rfr_plan* p, const int16_t* iq, int64_t n, rfr_outp
                                        out->tones_ld, &p->plain_scratch, &p->plain_scratch_bytes,
                                        &p->plain_fft, &p->plain_fft_batch, st));
         } else if (nt > 0) {
-            RFR_CUDA(p, rfr::plain_demod(iq, n, p->L, p->D, p->d_h32, p->d_words, nt,
+            if (!p->d_c32) {
+                RFR_CUDA(p, dev_alloc(&p->d_c32, static_cast<size_t>(nt) * p->L * 8));
+                RFR_CUDA(p, rfr::plain_demod_taps(p->d_h32, p->d_words, nt, p->L, p->d_c32, st));
+            }
+            RFR_CUDA(p, rfr::plain_demod(iq, n, p->L, p->D, p->d_c32, p->d_words, nt,
                                          static_cast<char*>(out->tones) + out->frame_offset * 8, out->tones_ld, st));
         }
     }

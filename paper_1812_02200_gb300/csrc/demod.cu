@@ -1,0 +1,426 @@
+// demod.cu -- direct multi-tone demodulation (Sec. III.B of arXiv:1812.02200)
+// as the dense contraction it is, on the tcgen05 tensor cores.
+//
+// Definition (per tone t with NCO word w_t, frame k, b_k = first sample of
+// the frame, taps h[0..L)):
+//   out[t][k] = sum_n h[n] x[b_k+n] exp(-i*phi_t(b_k+n)),  phi_t(m) = 2*pi*(w_t*m mod 2^64)/2^64.
+// Because w_t*(b+n) = w_t*b + w_t*n (mod 2^64) exactly,
+//   out[t][k] = exp(-i*phi_t(b_k)) * sum_n x[b_k+n] * C_t[n],   C_t[n] = h[n] exp(-i*phi_t(n)),
+// i.e. a GEMM of the Toeplitz matrix A[k][n] = x[b_k+n] (row stride D) with
+// the modulated taps C (plan constant), followed by a per-(t,k) rotation.
+//
+// Precision.  x is a 14-bit integer: x = xh + xl with xh = fp16(x) and
+// xl = x - xh, both exact in FP16.  C (scaled by 2^e so max|C| is in
+// [2^14, 2^15)) is split into ch = fp16(C) and cl = fp16(C - ch).  The MMAs
+// accumulate xh*ch + xh*cl + xl*ch (the dropped xl*cl is ~2^-22 relative) in
+// FP32.  To keep the tensor cores' internal accumulation error small, each
+// TMEM accumulator collects only a short chunk of K and the epilogue warps add
+// the chunks into FP32 register sums (the accumulator is double-buffered, so
+// the MMAs of the next chunk overlap the drain of the previous one).
+//
+// Real embedding: K' = 2L (re, im of x interleaved), N' = 2*tones with
+//   B'[2t][2n] = Re C, B'[2t][2n+1] = -Im C, B'[2t+1][2n] = Im C, B'[2t+1][2n+1] = Re C
+// so column 2t of the product is Re(x.C_t) and column 2t+1 is Im(x.C_t).
+//
+// Kernels:
+//   build_taps  (plan time) FP64 modulated taps -> FP16 hi/lo, K-major B'.
+//   rot         (per push)  FP64 rotation anchors exp(-i*phi_t(b)) at every
+//                           128-frame tile start and steps exp(-i*w_t*D*j).
+//   presplit    (per push)  int16 IQ of [carry | buffer] -> FP16 hi/lo rows of D
+//                           samples (the Toeplitz view's 2-D tensor).
+//   gemm        (per push)  TMA -> smem (128B swizzle) -> tcgen05.mma -> TMEM
+//                           -> register sums -> rotation -> [tone][frame] out.
+#include <cuda.h>
+#include <cuda_fp16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <mutex>
+
+#include "dev_common.cuh"
+#include "rfr_internal.h"
+#include "umma.cuh"
+
+namespace rfr {
+
+namespace {
+
+constexpr int BM = kDemodBM, BN = kDemodBN, BK = kDemodBK;
+constexpr int STAGES = 2;
+constexpr uint32_t A_BYTES = BM * BK * 2;
+constexpr uint32_t B_BYTES = BN * BK * 2;
+constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+constexpr int EPI_WARPS = 8;
+constexpr int GEMM_THREADS = (EPI_WARPS + 2) * 32;
+constexpr uint32_t TMEM_COLS = 512;       // two 256-column FP32 accumulators
+constexpr size_t GEMM_SMEM = 1024 + STAGES * STAGE_BYTES + 256;
+
+__device__ __forceinline__ float2 expmi_u64(uint64_t phase) {
+    // exp(-i * 2*pi*phase/2^64) in FP64, rounded to FP32
+    const double xs = static_cast<double>(static_cast<int64_t>(phase)) * 0x1p-63;   // in [-1, 1)
+    double s, c;
+    sincospi(xs, &s, &c);
+    return make_float2(static_cast<float>(c), static_cast<float>(-s));
+}
+
+__device__ __forceinline__ void split_store(__half* hi, __half* lo, size_t i, double v) {
+    const __half h = __double2half(v);
+    hi[i] = h;
+    lo[i] = __double2half(v - static_cast<double>(__half2float(h)));
+}
+
+__global__ void build_taps_kernel(const double* __restrict__ h, const uint64_t* __restrict__ words,
+                                  int n_tones, int ntp, int L, int Lpad, double scale,
+                                  __half* __restrict__ bh, __half* __restrict__ bl) {
+    const int64_t total = static_cast<int64_t>(ntp) * Lpad;
+    const size_t ldk = static_cast<size_t>(2) * Lpad;
+    for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
+         idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int t = static_cast<int>(idx / Lpad);
+        const int n = static_cast<int>(idx - static_cast<int64_t>(t) * Lpad);
+        double cr = 0.0, ci = 0.0;
+        if (t < n_tones && n < L) {
+            const uint64_t ph = words[t] * static_cast<uint64_t>(n);
+            const double xs = static_cast<double>(static_cast<int64_t>(ph)) * 0x1p-63;
+            double s, c;
+            sincospi(xs, &s, &c);
+            const double a = h[n] * scale;
+            cr = a * c;      // C = h * exp(-i*theta) = h*(cos - i sin)
+            ci = -a * s;
+        }
+        const size_t r0 = static_cast<size_t>(2 * t) * ldk, r1 = r0 + ldk;
+        split_store(bh, bl, r0 + 2 * n, cr);
+        split_store(bh, bl, r0 + 2 * n + 1, -ci);
+        split_store(bh, bl, r1 + 2 * n, ci);
+        split_store(bh, bl, r1 + 2 * n + 1, cr);
+    }
+}
+
+// Rotation factors on ABSOLUTE frame indices K = 128*A + i (so a stream split
+// into pushes rotates every frame by the same FP32 factors):
+//   anchors[a] = exp(-i*phi_t(b(128*(A0 + a)))),  steps[t][i] = exp(-i*w_t*D*i),
+// with b(K) = (K+1)*D - L the first sample of frame K and A0 = F0/128.
+__global__ void rot_kernel(const uint64_t* __restrict__ words, int n_tones, int ntp, int64_t A0, int L,
+                           int D, int n_anch, float2* __restrict__ anchors, float2* __restrict__ steps) {
+    const int64_t na = static_cast<int64_t>(n_anch) * ntp;
+    const int64_t total = na + static_cast<int64_t>(ntp) * BM;
+    for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
+         idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        if (idx < na) {
+            const int a = static_cast<int>(idx / ntp);
+            const int t = static_cast<int>(idx - static_cast<int64_t>(a) * ntp);
+            float2 r = make_float2(0.f, 0.f);
+            if (t < n_tones) {
+                const int64_t K = (A0 + a) * BM;
+                const int64_t b = (K + 1) * D - L;
+                r = expmi_u64(words[t] * static_cast<uint64_t>(b));
+            }
+            anchors[idx] = r;
+        } else {
+            const int64_t j = idx - na;
+            const int t = static_cast<int>(j / BM);
+            const int i = static_cast<int>(j - static_cast<int64_t>(t) * BM);
+            float2 r = make_float2(0.f, 0.f);
+            if (t < n_tones) r = expmi_u64(words[t] * static_cast<uint64_t>(static_cast<int64_t>(i) * D));
+            steps[j] = r;
+        }
+    }
+}
+
+// Sample s of the virtual stream [carry | buffer] -> FP16 hi/lo pairs.
+__global__ void presplit_kernel(const uint32_t* __restrict__ carry, int64_t cl,
+                                const uint32_t* __restrict__ buf, int64_t lv, int64_t total,
+                                __half2* __restrict__ hi, __half2* __restrict__ lo) {
+    for (int64_t s = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; s < total;
+         s += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        uint32_t w = 0;
+        if (s < lv) w = s < cl ? carry[s] : buf[s - cl];
+        const float2 f = iq_to_f2(w);
+        const __half hr = __float2half_rn(f.x), hq = __float2half_rn(f.y);
+        hi[s] = __halves2half2(hr, hq);
+        lo[s] = __halves2half2(__float2half_rn(f.x - __half2float(hr)),
+                               __float2half_rn(f.y - __half2float(hq)));
+    }
+}
+
+struct GemmArgs {
+    int64_t F;
+    int64_t F0;           // frames of the stream before this push
+    int n_tones, ntp, KB, kchunk, two_d, n_mt, n_nt;
+    const float2* anchors;
+    const float2* steps;
+    float inv_scale;
+    float2* out;
+    int64_t ld, fo;
+    int* status;
+};
+
+__global__ void __launch_bounds__(GEMM_THREADS, 1)
+demod_gemm_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+                  const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
+                  const GemmArgs g) {
+    extern __shared__ unsigned char smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    unsigned char* smem = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* tfull = empty + STAGES;
+    uint64_t* tempty = tfull + 2;
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(tempty + 2);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], EPI_WARPS * 32);
+        }
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == EPI_WARPS + 1) {
+        umma::alloc(tmem_holder, TMEM_COLS);
+        umma::relinquish();
+    }
+    if (warp == EPI_WARPS && lane == 0) {
+        tma_prefetch_desc(&tmAh);
+        tma_prefetch_desc(&tmAl);
+        tma_prefetch_desc(&tmBh);
+        tma_prefetch_desc(&tmBl);
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = *tmem_holder;
+    const int n_tiles = g.n_mt * g.n_nt;
+    constexpr uint32_t IDESC = umma::idesc_f16_f32(BM, BN);
+
+    if (warp == EPI_WARPS) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            uint32_t it = 0;
+            for (int tile = blockIdx.x; tile < n_tiles && !*abort_flag; tile += gridDim.x) {
+                const int m0 = (tile / g.n_nt) * BM, n0 = (tile % g.n_nt) * BN;
+                for (int kb = 0; kb < g.KB; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (it / STAGES) & 1;
+                    if (!mbar_wait(&empty[s], ph ^ 1, g.status)) { *abort_flag = 1; break; }
+                    unsigned char* st = smem + s * STAGE_BYTES;
+                    mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+                    const int kh = kb * BK;
+                    const int c0 = kh % g.two_d, c1 = m0 + kh / g.two_d;
+                    tma_load_2d(st, &tmAh, c0, c1, &full[s]);
+                    tma_load_2d(st + A_BYTES, &tmAl, c0, c1, &full[s]);
+                    tma_load_2d(st + 2 * A_BYTES, &tmBh, kh, n0, &full[s]);
+                    tma_load_2d(st + 2 * A_BYTES + B_BYTES, &tmBl, kh, n0, &full[s]);
+                }
+            }
+            // wait for the copies still in flight before leaving
+            for (uint32_t k = 0; k < STAGES && it > 0; ++k) {
+                const uint32_t j = it - 1 - k;
+                if (static_cast<int32_t>(j) < 0) break;
+                // the last STAGES fills: their full barriers complete on arrival
+                mbar_wait(&full[j % STAGES], (j / STAGES) & 1, g.status);
+            }
+        }
+    } else if (warp == EPI_WARPS + 1) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            uint32_t it = 0, cc = 0;
+            for (int tile = blockIdx.x; tile < n_tiles && !*abort_flag; tile += gridDim.x) {
+                for (int kb0 = 0; kb0 < g.KB && !*abort_flag; kb0 += g.kchunk, ++cc) {
+                    const uint32_t ab = cc & 1, aph = (cc >> 1) & 1;
+                    if (!mbar_wait(&tempty[ab], aph ^ 1, g.status)) { *abort_flag = 1; break; }
+                    umma::fence_after_sync();
+                    const uint32_t d_tmem = tmem + ab * BN;
+                    const int kb1 = min(kb0 + g.kchunk, g.KB);
+                    for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                        const int s = it % STAGES;
+                        const uint32_t ph = (it / STAGES) & 1;
+                        if (!mbar_wait(&full[s], ph, g.status)) { *abort_flag = 1; break; }
+                        umma::fence_after_sync();
+                        const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+                        const uint32_t ah = sa, al = sa + A_BYTES;
+                        const uint32_t bh = sa + 2 * A_BYTES, bl = bh + B_BYTES;
+#pragma unroll
+                        for (int k = 0; k < BK / 16; ++k) {
+                            const uint32_t off = k * 32;   // 16 fp16 of K = 32 bytes
+                            const uint32_t acc = (kb > kb0 || k > 0) ? 1u : 0u;
+                            umma::mma_f16(d_tmem, umma::desc_k_sw128(ah + off), umma::desc_k_sw128(bh + off), IDESC, acc);
+                            umma::mma_f16(d_tmem, umma::desc_k_sw128(ah + off), umma::desc_k_sw128(bl + off), IDESC, 1u);
+                            umma::mma_f16(d_tmem, umma::desc_k_sw128(al + off), umma::desc_k_sw128(bh + off), IDESC, 1u);
+                        }
+                        umma::commit(&empty[s]);
+                    }
+                    umma::commit(&tfull[ab]);
+                }
+            }
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------ epilogue (8 warps)
+        const int q = warp & 3, half_sel = warp >> 2;
+        const int row = q * 32 + lane;
+        uint32_t cc = 0;
+        for (int tile = blockIdx.x; tile < n_tiles && !*abort_flag; tile += gridDim.x) {
+            const int mt = tile / g.n_nt;
+            const int m0 = mt * BM, n0 = (tile % g.n_nt) * BN;
+            float sums[128];
+#pragma unroll
+            for (int i = 0; i < 128; ++i) sums[i] = 0.f;
+            bool ok = true;
+            for (int kb0 = 0; kb0 < g.KB; kb0 += g.kchunk, ++cc) {
+                const uint32_t ab = cc & 1, aph = (cc >> 1) & 1;
+                if (!mbar_wait(&tfull[ab], aph, g.status)) { *abort_flag = 1; ok = false; break; }
+                umma::fence_after_sync();
+                const uint32_t base = tmem + (static_cast<uint32_t>(q * 32) << 16) + ab * BN + half_sel * 128;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    uint32_t r[32];
+                    umma::ld_32x32b_x32(base + j * 32, r);
+                    umma::wait_ld();
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) sums[j * 32 + i] += __uint_as_float(r[i]);
+                }
+                umma::fence_before_sync();
+                mbar_arrive(&tempty[ab]);
+            }
+            if (!ok) break;
+            const int64_t k = static_cast<int64_t>(m0) + row;
+            if (k < g.F) {
+                const int tb = n0 / 2 + half_sel * 64;
+                const int64_t K = g.F0 + k;                       // absolute frame
+                const int64_t arow = K / BM - g.F0 / BM;          // anchor row of this push
+                const int si = static_cast<int>(K % BM);
+#pragma unroll
+                for (int tl = 0; tl < 64; ++tl) {
+                    const int t = tb + tl;
+                    if (t < g.n_tones) {
+                        const float2 an = __ldg(g.anchors + arow * g.ntp + t);
+                        const float2 sp = __ldg(g.steps + static_cast<int64_t>(t) * BM + si);
+                        const float2 rot = cmul(an, sp);
+                        const float2 acc = make_float2(sums[2 * tl] * g.inv_scale, sums[2 * tl + 1] * g.inv_scale);
+                        g.out[static_cast<int64_t>(t) * g.ld + g.fo + k] = cmul(acc, rot);
+                    }
+                }
+            }
+        }
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == EPI_WARPS + 1) {
+        umma::fence_after_sync();
+        umma::dealloc(tmem, TMEM_COLS);
+    }
+}
+
+// ------------------------------------------------------------ host side
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// 2-D fp16 tensor [rows][cols] (cols contiguous), box [box_rows][64], 128B swizzle.
+bool make_map(CUtensorMap* m, const void* base, uint64_t cols, uint64_t rows, uint32_t box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {cols, rows};
+    cuuint64_t strides[1] = {cols * 2};
+    cuuint32_t box[2] = {static_cast<cuuint32_t>(BK), box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+unsigned grid_for(int64_t work, int n_sms) {
+    return static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, int64_t(n_sms) * 16)));
+}
+
+}  // namespace
+
+int demod_anchor_rows(int64_t F0, int64_t F) {
+    return static_cast<int>((F0 + F - 1) / BM - F0 / BM + 1);
+}
+
+size_t demod_xs_rows(int64_t F, int Lpad, int D) {
+    // frame F-1 reads rows F-1 .. F-1 + (Lpad-1)/D
+    return static_cast<size_t>(F + (Lpad - 1) / D);
+}
+
+cudaError_t demod_build_taps(const double* d_h, const uint64_t* d_words, int n_tones, int ntp, int L,
+                             int Lpad, int e, void* b_hi, void* b_lo, cudaStream_t st) {
+    const int64_t total = static_cast<int64_t>(ntp) * Lpad;
+    build_taps_kernel<<<grid_for(total, 152), 256, 0, st>>>(d_h, d_words, n_tones, ntp, L, Lpad,
+                                                             std::ldexp(1.0, e), static_cast<__half*>(b_hi),
+                                                             static_cast<__half*>(b_lo));
+    return cudaGetLastError();
+}
+
+cudaError_t demod_launch(const DemodLaunch& L, cudaStream_t st) {
+    if (L.F <= 0) return cudaSuccess;
+    if (L.D % 32 != 0 || L.Lpad % 32 != 0) return cudaErrorInvalidValue;
+    const int64_t rows = static_cast<int64_t>(demod_xs_rows(L.F, L.Lpad, L.D));
+    if (rows > L.xs_rows) return cudaErrorInvalidValue;
+    const int n_mt = static_cast<int>((L.F + BM - 1) / BM);
+    const int n_nt = (2 * L.ntp) / BN;
+    const int n_anch = demod_anchor_rows(L.F0, L.F);
+    float2* anchors = static_cast<float2*>(L.rot);
+    float2* steps = anchors + static_cast<int64_t>(n_anch) * L.ntp;
+    // rotation tables
+    const int64_t nrot = static_cast<int64_t>(n_anch) * L.ntp + static_cast<int64_t>(L.ntp) * BM;
+    rot_kernel<<<grid_for(nrot, L.n_sms), 256, 0, st>>>(L.words, L.n_tones, L.ntp, L.F0 / BM, L.L, L.D,
+                                                         n_anch, anchors, steps);
+    // pre-split of the Toeplitz source rows
+    const int64_t total = rows * L.D;
+    presplit_kernel<<<grid_for(total, L.n_sms), 256, 0, st>>>(
+        reinterpret_cast<const uint32_t*>(L.carry), L.cl, reinterpret_cast<const uint32_t*>(L.buf),
+        L.cl + L.n, total, static_cast<__half2*>(L.xs_hi), static_cast<__half2*>(L.xs_lo));
+    // tensor maps
+    CUtensorMap mAh, mAl, mBh, mBl;
+    const uint64_t two_d = static_cast<uint64_t>(2) * L.D;
+    if (!make_map(&mAh, L.xs_hi, two_d, rows, BM) || !make_map(&mAl, L.xs_lo, two_d, rows, BM) ||
+        !make_map(&mBh, L.b_hi, static_cast<uint64_t>(2) * L.Lpad, static_cast<uint64_t>(2) * L.ntp, BN) ||
+        !make_map(&mBl, L.b_lo, static_cast<uint64_t>(2) * L.Lpad, static_cast<uint64_t>(2) * L.ntp, BN))
+        return cudaErrorInvalidValue;
+    GemmArgs g{};
+    g.F = L.F;
+    g.F0 = L.F0;
+    g.n_tones = L.n_tones;
+    g.ntp = L.ntp;
+    g.KB = 2 * L.Lpad / BK;
+    g.kchunk = L.kchunk > 0 ? L.kchunk : 2;
+    g.two_d = static_cast<int>(two_d);
+    g.n_mt = n_mt;
+    g.n_nt = n_nt;
+    g.anchors = anchors;
+    g.steps = steps;
+    g.inv_scale = static_cast<float>(L.inv_scale);
+    g.out = static_cast<float2*>(L.tones);
+    g.ld = L.tones_ld;
+    g.fo = L.frame_offset;
+    g.status = L.status;
+    cudaError_t e = cudaFuncSetAttribute(demod_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(GEMM_SMEM));
+    if (e != cudaSuccess) return e;
+    const int tiles = n_mt * n_nt;
+    const int grid = std::min(tiles, L.n_sms);
+    demod_gemm_kernel<<<grid, GEMM_THREADS, GEMM_SMEM, st>>>(mAh, mAl, mBh, mBl, g);
+    return cudaGetLastError();
+}
+
+}  // namespace rfr

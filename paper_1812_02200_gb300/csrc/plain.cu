@@ -117,3 +117,111 @@ void plain_release(void* scratch, void* fft_plan) {
 }
 
 }  // namespace rfr
+
+// ------------------------------------------------------------- demod (FP32)
+namespace rfr {
+namespace {
+
+__global__ void plain_taps_kernel(const float* __restrict__ h, const uint64_t* __restrict__ words,
+                                  int n_tones, int L, float2* __restrict__ c) {
+    const int64_t total = static_cast<int64_t>(n_tones) * L;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int t = static_cast<int>(i / L);
+        const int n = static_cast<int>(i - static_cast<int64_t>(t) * L);
+        const uint64_t ph = words[t] * static_cast<uint64_t>(n);
+        double s, co;
+        sincospi(static_cast<double>(static_cast<int64_t>(ph)) * 0x1p-63, &s, &co);
+        c[i] = make_float2(static_cast<float>(h[n] * co), static_cast<float>(-h[n] * s));
+    }
+}
+
+constexpr int PT = 64;     // frames and tones per block tile
+constexpr int PK = 16;     // taps per k step
+
+// out[t][k] = exp(-i*phi_t(b_k)) * sum_n x[b_k + n] * C_t[n], plain FP32 FMAs;
+// each thread accumulates 4 frames x 4 tones.
+__global__ void __launch_bounds__(256) plain_demod_kernel(const uint32_t* __restrict__ x, int64_t n_samples,
+                                                          int L, int D, const float2* __restrict__ C,
+                                                          const uint64_t* __restrict__ words, int n_tones,
+                                                          int64_t F, float2* __restrict__ out, int64_t ld) {
+    __shared__ float2 xs[PT][PK + 1];
+    __shared__ float2 cs[PK][PT];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int64_t k0 = static_cast<int64_t>(blockIdx.x) * PT;
+    const int t0 = blockIdx.y * PT;
+    float2 acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = make_float2(0.f, 0.f);
+    for (int n0 = 0; n0 < L; n0 += PK) {
+        for (int e = threadIdx.x; e < PT * PK; e += 256) {
+            const int f = e / PK, j = e % PK;
+            const int64_t k = k0 + f;
+            const int64_t m = (k + 1) * D - L + n0 + j;
+            float2 v = make_float2(0.f, 0.f);
+            if (k < F && n0 + j < L && m >= 0 && m < n_samples) v = iq_to_f2(x[m]);
+            xs[f][j] = v;
+        }
+        for (int e = threadIdx.x; e < PT * PK; e += 256) {
+            const int j = e / PT, tt = e % PT;
+            const int t = t0 + tt;
+            cs[j][tt] = (t < n_tones && n0 + j < L) ? C[static_cast<int64_t>(t) * L + n0 + j] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < PK; ++j) {
+            float2 xv[4], cv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) xv[a] = xs[ty + 16 * a][j];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) cv[b] = cs[j][tx + 16 * b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    acc[a][b].x = fmaf(xv[a].x, cv[b].x, fmaf(-xv[a].y, cv[b].y, acc[a][b].x));
+                    acc[a][b].y = fmaf(xv[a].x, cv[b].y, fmaf(xv[a].y, cv[b].x, acc[a][b].y));
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int64_t k = k0 + ty + 16 * a;
+        if (k >= F) continue;
+        const int64_t b_k = (k + 1) * D - L;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int t = t0 + tx + 16 * b;
+            if (t >= n_tones) continue;
+            const uint64_t ph = words[t] * static_cast<uint64_t>(b_k);
+            float s, c;
+            sincospif(static_cast<float>(static_cast<int32_t>(ph >> 32)) * 0x1p-31f, &s, &c);
+            out[static_cast<int64_t>(t) * ld + k] = cmul(acc[a][b], make_float2(c, -s));
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t plain_demod_taps(const float* h32, const uint64_t* words, int n_tones, int L, void* c32,
+                             cudaStream_t st) {
+    const int64_t total = static_cast<int64_t>(n_tones) * L;
+    plain_taps_kernel<<<grid_for(total), 256, 0, st>>>(h32, words, n_tones, L, static_cast<float2*>(c32));
+    return cudaGetLastError();
+}
+
+cudaError_t plain_demod(const int16_t* iq, int64_t n, int L, int D, const void* c32, const uint64_t* words,
+                        int n_tones, void* tones, int64_t tones_ld, cudaStream_t st) {
+    const int64_t F = n / D;
+    if (F <= 0 || n_tones <= 0) return cudaSuccess;
+    dim3 grid(static_cast<unsigned>((F + PT - 1) / PT), static_cast<unsigned>((n_tones + PT - 1) / PT));
+    plain_demod_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<const uint32_t*>(iq), n, L, D,
+                                             static_cast<const float2*>(c32), words, n_tones, F,
+                                             static_cast<float2*>(tones), tones_ld);
+    return cudaGetLastError();
+}
+
+}  // namespace rfr

@@ -62,6 +62,7 @@ struct DemodLaunch {
     int64_t n;
     int64_t F;
     int64_t a0;                 // absolute sample index of v[0]
+    int64_t F0;                 // frames of the stream before this push
     int32_t L, D, Lpad, n_tones, ntp;   // ntp = tones padded to kDemodBN/2
     const uint64_t* words;      // device [n_tones]
     const void* b_hi;           // device fp16 [2*ntp][2*Lpad]
@@ -81,14 +82,17 @@ struct DemodLaunch {
 cudaError_t demod_build_taps(const double* d_h, const uint64_t* d_words, int n_tones, int ntp,
                              int L, int Lpad, int e, void* b_hi, void* b_lo, cudaStream_t st);
 cudaError_t demod_launch(const DemodLaunch& L, cudaStream_t st);
-size_t demod_xs_rows(int64_t F, int L, int D);
+size_t demod_xs_rows(int64_t F, int Lpad, int D);
+int demod_anchor_rows(int64_t F0, int64_t F);
 
 // -------------------------------------------------------------- plain
 cudaError_t plain_pfb(const int16_t* iq, int64_t n, int N, int T, const float* h, const int32_t* bins,
                       int n_tones, void* full, int64_t full_ld, void* tones, int64_t tones_ld,
                       void** scratch, size_t* scratch_bytes, void** fft_plan, int64_t* fft_batch,
                       cudaStream_t st);
-cudaError_t plain_demod(const int16_t* iq, int64_t n, int L, int D, const float* h32,
+cudaError_t plain_demod_taps(const float* h32, const uint64_t* words, int n_tones, int L, void* c32,
+                             cudaStream_t st);
+cudaError_t plain_demod(const int16_t* iq, int64_t n, int L, int D, const void* c32,
                         const uint64_t* words, int n_tones, void* tones, int64_t tones_ld,
                         cudaStream_t st);
 void plain_release(void* scratch, void* fft_plan);
@@ -120,6 +124,7 @@ struct rfr_plan {
     int32_t* d_bins = nullptr;
     uint64_t* d_words = nullptr;
     float* d_h32 = nullptr;        // taps as FP32 (plain forms)
+    void* d_c32 = nullptr;         // plain demod: FP32 modulated taps [tones][L]
     void* d_bhi = nullptr;         // demod modulated taps, fp16 hi/lo
     void* d_blo = nullptr;
     int32_t ntp = 0;               // demod tones padded

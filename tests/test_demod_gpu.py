@@ -1,0 +1,192 @@
+"""GPU parity of the split-FP16 tensor-core demodulation (Sec. III.B) against
+the FP64 oracle, through the C ABI.  Tolerance: relative RMS error <= 1e-5 per
+tone over the checked frames (the split operands carry ~2^-22 relative
+error; the FP32 accumulation of short K chunks and the FP32 rotation add
+~1e-7 relative to the composite signal, which for the weakest tones of the
+workload (about 1/270 of the composite RMS) stays below 1e-5)."""
+import numpy as np
+import pytest
+
+import oracle
+import siggen
+from helpers import TOL, rel_rows
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+def _plan(lib, L, D, words, win="blackman", fc=40e3 / 200e6, beta=0.0):
+    return lib.Plan(0, L, window=win, beta=beta, cutoff=fc, words=words, decimation=D)
+
+
+def _run(plan, x_np, n_tones):
+    x = torch.from_numpy(x_np).to(DEV)
+    F = plan.frames_for(x.shape[0])
+    out = torch.zeros((n_tones, F), dtype=torch.complex64, device=DEV)
+    assert plan.push_into(x, tones=out) == F
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+SHAPES = [
+    # L, D, tones, frames, window, cutoff
+    (256, 64, 8, 200, "blackman", 0.01),
+    (1000, 512, 130, 140, "hann", 0.002),       # L not a multiple of 32; 2 tone tiles
+    (1024, 512, 64, 300, "blackman", 2e-4),
+    (4096, 2048, 160, 130, "blackman", 2e-4),   # the workload's filter
+    (4096, 512, 40, 150, "kaiser", 1e-3),       # L = 8 D
+    (1024, 2048, 50, 160, "hamming", 1e-3),     # L < D: samples between frames skipped
+    (512, 512, 30, 260, "rect", 0.0),           # the paper's moving average, D = L
+]
+
+
+@pytest.mark.parametrize("L,D,nt,frames,win,fc", SHAPES)
+def test_demod_parity_shapes(lib, L, D, nt, frames, win, fc):
+    beta = 9.0 if win == "kaiser" else 0.0
+    case = siggen.demod_case(frames * D + D // 3, nt, seed=3000 + L + D + nt)
+    plan = _plan(lib, L, D, case["words"], win, fc, beta)
+    got = _run(plan, case["x"], nt)
+    assert got.shape[1] == frames
+    h64p, _ = plan.taps_table()
+    h = oracle.lowpass(win, L, fc, beta)
+    assert np.allclose(h64p, h, rtol=1e-12, atol=1e-18)
+    ref = oracle.demod(case["x"], L, D, h, case["words"])
+    e = rel_rows(got, ref)
+    print(f"L={L} D={D} tones={nt}: max rel err {e.max():.3e}")
+    assert e.max() < TOL
+
+
+def test_demod_weak_tones_workload_statistics(lib):
+    """All 2048 tones of the demodulation workload (amplitudes U(100, 1000)
+    scaled to 1/6 of full scale RMS, off-bin words, L=4096 Blackman-sinc
+    40 kHz, D=2048), 2^21 samples; the 8 weakest and 8 random tones checked
+    over 64 frames spread through the stream."""
+    c = siggen.c3(n=1 << 21)
+    L, D = 4096, 2048
+    plan = _plan(lib, L, D, c["words"])
+    got = _run(plan, c["x"], 2048)
+    h = oracle.lowpass("blackman", L, 40e3 / 200e6)
+    weak = np.argsort(c["amps"])[:8]
+    rnd = np.random.default_rng(1).choice(2048, 8, replace=False)
+    sel = np.concatenate([weak, rnd])
+    F = got.shape[1]
+    frames = np.unique(np.linspace(0, F - 1, 64).astype(int))
+    errs = []
+    for s in sel:
+        ref = np.concatenate([oracle.demod(c["x"], L, D, h, [c["words"][s]], k, k + 1)[0] for k in frames])
+        errs.append(np.linalg.norm(got[s, frames] - ref) / np.linalg.norm(ref))
+    errs = np.array(errs)
+    print(f"weakest-tone rel err {errs[:8].max():.3e}, random {errs[8:].max():.3e}")
+    assert errs.max() < TOL
+
+
+def test_demod_c3_full_size_sampled(lib):
+    """Workload 3 at full size (2^27 samples, 2048 tones, L=4096, D=2048 ->
+    65536 frames), the launch the benchmark times; weakest and random tones
+    over frames at the start, middle and end checked one by one."""
+    c = siggen.c3()
+    L, D = 4096, 2048
+    plan = _plan(lib, L, D, c["words"])
+    got = _run(plan, c["x"], 2048)
+    assert got.shape == (2048, 65536)
+    h = oracle.lowpass("blackman", L, 40e3 / 200e6)
+    sel = np.concatenate([np.argsort(c["amps"])[:4], [0, 1000, 2047]])
+    for a, b in [(0, 8), (32760, 32768), (65528, 65536)]:
+        ref = oracle.demod(c["x"], L, D, h, c["words"][sel], a, b)
+        e = np.linalg.norm(got[sel, a:b] - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        assert e.max() < TOL, (a, e.max())
+
+
+def test_demod_streamed_equals_one_shot_bit_exact(lib):
+    L, D, nt = 1024, 512, 150
+    case = siggen.demod_case(D * 400 + 77, nt, seed=31)
+    one = _plan(lib, L, D, case["words"])
+    ref = _run(one, case["x"], nt)
+    st = _plan(lib, L, D, case["words"])
+    x = torch.from_numpy(case["x"]).to(DEV)
+    F = ref.shape[1]
+    out = torch.zeros((nt, F), dtype=torch.complex64, device=DEV)
+    rng = np.random.default_rng(8)
+    pos = off = 0
+    while pos < x.shape[0]:
+        cnt = int(min(x.shape[0] - pos, rng.integers(1, 40 * D)))
+        off += st.push_into(x[pos:pos + cnt], tones=out, frame_offset=off)
+        pos += cnt
+    torch.cuda.synchronize()
+    assert off == F
+    assert np.array_equal(out.cpu().numpy(), ref)
+
+
+def test_demod_state_queue_host(lib):
+    L, D, nt = 2048, 512, 70
+    case = siggen.demod_case(D * 300 + 5, nt, seed=41)
+    ref = _run(_plan(lib, L, D, case["words"]), case["x"], nt)
+    F = ref.shape[1]
+    x = torch.from_numpy(case["x"]).to(DEV)
+    # checkpoint / resume
+    a = _plan(lib, L, D, case["words"])
+    out = torch.zeros((nt, F), dtype=torch.complex64, device=DEV)
+    cut = 123457
+    k = a.push_into(x[:cut], tones=out)
+    blob = a.state_export()
+    b = _plan(lib, L, D, case["words"])
+    b.state_import(blob)
+    k += b.push_into(x[cut:], tones=out, frame_offset=k)
+    torch.cuda.synchronize()
+    assert k == F and np.array_equal(out.cpu().numpy(), ref)
+    # queued push / pull
+    q = _plan(lib, L, D, case["words"])
+    for lo, hi in [(0, 1000), (1000, 90000), (90000, x.shape[0])]:
+        q.push(x[lo:hi])
+    out2 = torch.zeros((nt, F), dtype=torch.complex64, device=DEV)
+    assert q.pull(tones=out2) == F
+    assert np.array_equal(out2.cpu().numpy(), ref)
+    # host-staged end to end
+    hp = _plan(lib, L, D, case["words"])
+    th = torch.zeros((nt, F), dtype=torch.complex64).pin_memory()
+    assert hp.process_host(torch.from_numpy(case["x"]).pin_memory(), tones=th) == F
+    assert np.array_equal(th.numpy(), ref)
+
+
+def test_demod_plain_fp32_form(lib):
+    L, D, nt = 1024, 512, 40
+    case = siggen.demod_case(D * 200, nt, seed=51)
+    plan = _plan(lib, L, D, case["words"])
+    x = torch.from_numpy(case["x"]).to(DEV)
+    F = x.shape[0] // D
+    out = torch.zeros((nt, F), dtype=torch.complex64, device=DEV)
+    assert plan.plain_oneshot(x, tones=out) == F
+    torch.cuda.synchronize()
+    h = oracle.lowpass("blackman", L, 40e3 / 200e6)
+    ref = oracle.demod(case["x"], L, D, h, case["words"])
+    e = rel_rows(out.cpu().numpy(), ref)
+    print(f"plain FP32 demod max rel err {e.max():.3e}")
+    assert e.max() < 1e-3          # reported; the FP32 form is not held to 1e-5
+
+
+def test_demod_invalid_plans(lib):
+    w = np.array([12345], np.uint64)
+    for L, D in [(0, 512), (16385, 512), (1024, 100), (1024, 16), (1024, 0)]:
+        with pytest.raises(lib.RfrError) as ei:
+            lib.Plan(0, L, window="hann", words=w, decimation=D)
+        assert ei.value.status == lib.E_INVALID
+
+
+def test_demod_no_tones_and_tiny_pushes(lib):
+    L, D = 256, 64
+    p = lib.Plan(0, L, window="hann", words=None, decimation=D)
+    x = torch.zeros((1000, 2), dtype=torch.int16, device=DEV)
+    assert p.push_into(x) == p.info()["frames_produced"]
+    case = siggen.demod_case(D * 50, 4, seed=61)
+    q = _plan(lib, L, D, case["words"])
+    xx = torch.from_numpy(case["x"]).to(DEV)
+    out = torch.zeros((4, 50), dtype=torch.complex64, device=DEV)
+    off = 0
+    for i in range(0, xx.shape[0], 7):             # pushes far shorter than a frame
+        off += q.push_into(xx[i:i + 7], tones=out, frame_offset=off)
+    torch.cuda.synchronize()
+    ref = oracle.demod(case["x"], L, D, oracle.lowpass("blackman", L, 40e3 / 200e6), case["words"])
+    assert off == ref.shape[1]
+    assert rel_rows(out.cpu().numpy(), ref).max() < TOL
