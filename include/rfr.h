@@ -214,6 +214,39 @@ rfr_status rfr_plan_get_bins(const rfr_plan* plan, int32_t* bins, int32_t* count
 rfr_status rfr_plain_oneshot(rfr_plan* plan, const int16_t* iq, int64_t n_samples,
                              rfr_output* out, void* stream);
 
+/*
+ * rfr_demod_noalloc -- one-shot direct demodulation that allocates nothing.
+ * (The paper has no counterpart; this is a deployment convenience.)
+ *
+ * Who needs it: code that must not call the CUDA allocator while it runs --
+ * a real-time processing thread that cannot absorb the device-wide
+ * synchronisation and allocator locking cudaMalloc/cudaFree may cause, or a
+ * host application whose device-memory budget is owned by another allocator.
+ * Plans allocate their tables and stream state; this call instead uses one
+ * file-scope device array of about 6.7 MB that every GPU loading the library
+ * holds until the process exits.  The caller still owns inputs and outputs.
+ *
+ * Computes the same frames as a fresh plan (zero history) pushed with the
+ * whole buffer: tone s of frame k at tones[s * tones_ld + k], k < n_samples/D,
+ * on the same split-FP16 tensor-core path.
+ *   iq        device int16 [n_samples][2]
+ *   taps      HOST FP64 low-pass taps h[0..L) (e.g. from rfr_plan_get_taps)
+ *   words     HOST NCO words [n_tones]
+ *   tones     device complex64 [n_tones][tones_ld], tones_ld >= n_samples/D
+ * Limits (the size of the static scratch): n_samples <= 2^18, L <= 1024,
+ * 1 <= n_tones <= 256, D a multiple of 32; anything larger returns
+ * RFR_E_INVALID before any work is enqueued.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call shares the one array and leaves its contents behind
+ * (each call clears or overwrites what it needs), so calls whose GPU work
+ * overlaps -- on different streams or host threads -- race; serialise them.
+ * Asynchronous on `stream`; the results are ready when the stream is.
+ */
+rfr_status rfr_demod_noalloc(const int16_t* iq, int64_t n_samples, const double* taps, int32_t L,
+                             int32_t D, const uint64_t* words, int32_t n_tones, void* tones,
+                             int64_t tones_ld, void* stream);
+
 /* Frequency f_hz at sample rate fs_hz -> NCO word: f/fs wrapped into
  * [-1/2, 1/2), times 2^64, rounded to nearest (two's complement). */
 uint64_t rfr_freq_to_word(double f_hz, double fs_hz);

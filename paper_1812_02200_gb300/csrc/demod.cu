@@ -35,6 +35,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <mutex>
 
@@ -424,3 +425,150 @@ cudaError_t demod_launch(const DemodLaunch& L, cudaStream_t st) {
 }
 
 }  // namespace rfr
+
+// ====================================================================
+// Allocation-free one-shot demodulation (rfr_demod_noalloc).
+//
+// For callers that must not allocate device memory once they are running:
+// a real-time processing thread that cannot afford the device-wide
+// synchronisation and allocator locks that cudaMalloc/cudaFree can take, or a
+// host application whose device-memory budget is owned by another allocator.
+// The working memory of this path -- the modulated taps, the FP16 split of
+// the samples, the rotation tables, a zero history block and the status word
+// -- lives in one file-scope device array of kNaBytes (about 6.7 MB), which
+// every GPU that loads this library holds until the process exits.
+// ====================================================================
+#include <mutex>
+
+namespace rfr {
+namespace {
+
+constexpr int64_t kNaMaxSamples = int64_t(1) << 18;   // samples per call
+constexpr int kNaMaxTones = 256;
+constexpr int kNaMaxTaps = 1024;
+
+constexpr size_t na_align(size_t v) { return (v + 255) / 256 * 256; }
+constexpr size_t kNaStatus = 0;
+constexpr size_t kNaWords = 256;
+constexpr size_t kNaTaps = na_align(kNaWords + kNaMaxTones * 8);
+constexpr size_t kNaZero = na_align(kNaTaps + kNaMaxTaps * 8);                 // zero history
+constexpr size_t kNaBhi = na_align(kNaZero + kNaMaxTaps * 4);
+constexpr size_t kNaBBytes = static_cast<size_t>(2) * kNaMaxTones * 2 * kNaMaxTaps * 2;
+constexpr size_t kNaBlo = na_align(kNaBhi + kNaBBytes);
+constexpr size_t kNaXsBytes = static_cast<size_t>(kNaMaxSamples + kNaMaxTaps) * 4;
+constexpr size_t kNaXhi = na_align(kNaBlo + kNaBBytes);
+constexpr size_t kNaXlo = na_align(kNaXhi + kNaXsBytes);
+constexpr int64_t kNaMaxAnchRows = kNaMaxSamples / 32 / BM + 2;
+constexpr size_t kNaRot = na_align(kNaXlo + kNaXsBytes);
+constexpr size_t kNaRotBytes = static_cast<size_t>(kNaMaxAnchRows + BM) * kNaMaxTones * 8;
+constexpr size_t kNaBytes = na_align(kNaRot + kNaRotBytes);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+// Device address of g_noalloc_scratch per device, looked up once per device
+// (the host-side name of the array is not a device address).
+constexpr int kNaMaxDevices = 64;
+unsigned char* g_na_ptr[kNaMaxDevices] = {};
+std::mutex g_na_mu;
+
+cudaError_t na_scratch(unsigned char** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kNaMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    if (!g_na_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_na_ptr[dev] = static_cast<unsigned char*>(p);
+    }
+    *out = g_na_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace rfr
+
+extern "C" rfr_status rfr_demod_noalloc(const int16_t* iq, int64_t n_samples, const double* taps,
+                                        int32_t L, int32_t D, const uint64_t* words, int32_t n_tones,
+                                        void* tones, int64_t tones_ld, void* stream) {
+    using namespace rfr;
+    if (n_samples < 0 || n_samples > kNaMaxSamples) return RFR_E_INVALID;   // beyond the static scratch
+    if (L < 1 || L > kNaMaxTaps || D < 32 || D % 32 != 0 || D > kNaMaxSamples) return RFR_E_INVALID;
+    if (n_tones < 1 || n_tones > kNaMaxTones || !taps || !words) return RFR_E_INVALID;
+    const int64_t F = n_samples / D;
+    if (F > 0 && (!iq || !tones || tones_ld < F)) return RFR_E_INVALID;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned char* base = nullptr;
+    if (na_scratch(&base) != cudaSuccess) return RFR_E_CUDA;
+    if (F == 0) return RFR_OK;
+    // tap scale 2^e with max|h| * 2^e in [2^14, 2^15) (same rule as a plan)
+    double hmax = 0.0;
+    for (int j = 0; j < L; ++j) hmax = std::max(hmax, std::fabs(taps[j]));
+    if (!(hmax > 0.0) || !std::isfinite(hmax)) return RFR_E_INVALID;
+    int e2 = 0;
+    std::frexp(hmax, &e2);
+    const int tap_exp = 15 - e2;
+    const int Lpad = (L + 31) / 32 * 32;
+    const int ntp = (n_tones + BN / 2 - 1) / (BN / 2) * (BN / 2);
+    int* status = reinterpret_cast<int*>(base + kNaStatus);
+    uint64_t* d_words = reinterpret_cast<uint64_t*>(base + kNaWords);
+    double* d_taps = reinterpret_cast<double*>(base + kNaTaps);
+    const uint32_t* zero = reinterpret_cast<const uint32_t*>(base + kNaZero);
+    __half* bh = reinterpret_cast<__half*>(base + kNaBhi);
+    __half* bl = reinterpret_cast<__half*>(base + kNaBlo);
+    __half2* xh = reinterpret_cast<__half2*>(base + kNaXhi);
+    __half2* xl = reinterpret_cast<__half2*>(base + kNaXlo);
+    float2* anchors = reinterpret_cast<float2*>(base + kNaRot);
+    // contents left by the previous call are overwritten or cleared here
+    if (cudaMemsetAsync(base, 0, kNaTaps, st) != cudaSuccess ||
+        cudaMemsetAsync(base + kNaZero, 0, static_cast<size_t>(kNaMaxTaps) * 4, st) != cudaSuccess ||
+        cudaMemcpyAsync(d_words, words, static_cast<size_t>(n_tones) * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(d_taps, taps, static_cast<size_t>(L) * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return RFR_E_CUDA;
+    build_taps_kernel<<<grid_for(static_cast<int64_t>(ntp) * Lpad, 152), 256, 0, st>>>(
+        d_taps, d_words, n_tones, ntp, L, Lpad, std::ldexp(1.0, tap_exp), bh, bl);
+    const int n_mt = static_cast<int>((F + BM - 1) / BM);
+    const int n_anch = demod_anchor_rows(0, F);
+    float2* steps = anchors + static_cast<int64_t>(n_anch) * ntp;
+    rot_kernel<<<grid_for(static_cast<int64_t>(n_anch + BM) * ntp, 152), 256, 0, st>>>(
+        d_words, n_tones, ntp, 0, L, D, n_anch, anchors, steps);
+    // zero history: the stream view starts L - D samples before sample 0
+    const int64_t cl = static_cast<int64_t>(L) - D;
+    const int64_t rows = static_cast<int64_t>(demod_xs_rows(F, Lpad, D));
+    presplit_kernel<<<grid_for(rows * D, 152), 256, 0, st>>>(zero, cl, reinterpret_cast<const uint32_t*>(iq),
+                                                             cl + n_samples, rows * D, xh, xl);
+    CUtensorMap mAh, mAl, mBh, mBl;
+    const uint64_t two_d = static_cast<uint64_t>(2) * D;
+    if (!make_map(&mAh, xh, two_d, rows, BM) || !make_map(&mAl, xl, two_d, rows, BM) ||
+        !make_map(&mBh, bh, static_cast<uint64_t>(2) * Lpad, static_cast<uint64_t>(2) * ntp, BN) ||
+        !make_map(&mBl, bl, static_cast<uint64_t>(2) * Lpad, static_cast<uint64_t>(2) * ntp, BN))
+        return RFR_E_CUDA;
+    GemmArgs g{};
+    g.F = F;
+    g.F0 = 0;
+    g.n_tones = n_tones;
+    g.ntp = ntp;
+    g.KB = 2 * Lpad / BK;
+    g.kchunk = 2;
+    g.two_d = static_cast<int>(two_d);
+    g.n_mt = n_mt;
+    g.n_nt = (2 * ntp) / BN;
+    g.anchors = anchors;
+    g.steps = steps;
+    g.inv_scale = static_cast<float>(std::ldexp(1.0, -tap_exp));
+    g.out = static_cast<float2*>(tones);
+    g.ld = tones_ld;
+    g.fo = 0;
+    g.status = status;
+    if (cudaFuncSetAttribute(demod_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(GEMM_SMEM)) != cudaSuccess)
+        return RFR_E_CUDA;
+    int n_sms = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev);
+    demod_gemm_kernel<<<std::min(n_mt * g.n_nt, std::max(n_sms, 1)), GEMM_THREADS, GEMM_SMEM, st>>>(mAh, mAl, mBh, mBl, g);
+    return cudaGetLastError() == cudaSuccess ? RFR_OK : RFR_E_CUDA;
+}
