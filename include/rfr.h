@@ -214,6 +214,52 @@ rfr_status rfr_plan_get_bins(const rfr_plan* plan, int32_t* bins, int32_t* count
 rfr_status rfr_plain_oneshot(rfr_plan* plan, const int16_t* iq, int64_t n_samples,
                              rfr_output* out, void* stream);
 
+/* ------------------------------------------------------------------ batch */
+typedef struct rfr_batch rfr_batch;
+
+/*
+ * rfr_batch_create -- group n distinct plans (PFB and/or demodulation, any
+ * shapes) that advance together, one buffer per plan per step (the paper's
+ * Rx processing of many detector readouts, Sec. III; the batched workload).
+ * The batch borrows the plans (they must outlive it and must not be pushed
+ * elsewhere while it runs).  Errors: RFR_E_INVALID (n < 1, NULL or repeated
+ * plan), RFR_E_NOMEM, RFR_E_CUDA.
+ */
+rfr_status rfr_batch_create(rfr_batch** batch, rfr_plan* const* plans, int32_t n);
+void rfr_batch_destroy(rfr_batch* batch);
+
+/*
+ * rfr_batch_push -- one step: plan i pushes bufs[i] (device, n_samples[i]
+ * samples) into outs[i] exactly as rfr_push_into would (bit-identical
+ * results, stream state kept per plan), but all plans' kernels run
+ * concurrently from ONE CUDA-graph launch into `stream`.  The executable
+ * graph is kept and updated in place on the next step.  outs[i].frames is set.
+ * Every push is checked before anything is enqueued (RFR_E_INVALID /
+ * RFR_E_SHORT leave all plans unchanged).  Scratch growth happens before the
+ * graph is built.
+ */
+rfr_status rfr_batch_push(rfr_batch* batch, const int16_t* const* bufs, const int64_t* n_samples,
+                          rfr_output* outs, void* stream);
+
+/* Steps run, graph updates in place and graph instantiations so far. */
+rfr_status rfr_batch_stats(const rfr_batch* batch, int64_t* steps, int64_t* graph_updates,
+                           int64_t* graph_instantiations);
+const char* rfr_batch_last_error(const rfr_batch* batch);
+
+/*
+ * rfr_plan_autotune -- time the plan's result-neutral launch choices (PFB:
+ * ring look-ahead of 1..3 super-blocks; demodulation: GEMM tile raster
+ * groups) on a push of n_samples and keep the fastest.  Outputs stay
+ * bit-identical whatever is chosen.  With use_cache != 0 the choice is read
+ * from / written to the JSON file named by RFR_TUNE_CACHE (default
+ * ./rfr_tune_cache.json), keyed by plan shape, push size and GPU.  The
+ * stream state is left unchanged.  *best_ms (may be NULL) receives the time
+ * of the chosen configuration (-1 when it came from the cache).
+ */
+rfr_status rfr_plan_autotune(rfr_plan* plan, int64_t n_samples, int32_t use_cache, double* best_ms);
+rfr_status rfr_plan_get_tune(const rfr_plan* plan, int32_t* pfb_lookahead, int32_t* demod_raster,
+                             int32_t* tuned);
+
 /*
  * rfr_demod_noalloc -- one-shot direct demodulation that allocates nothing.
  * (The paper has no counterpart; this is a deployment convenience.)

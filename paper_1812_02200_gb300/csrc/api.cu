@@ -136,6 +136,23 @@ rfr_status ensure_demod_scratch(rfr_plan* p, int64_t F, int64_t F0) {
     return RFR_OK;
 }
 
+}  // namespace
+
+namespace rfr {
+int64_t frames_for_samples(const rfr_plan* p, int64_t n) { return frames_for_len(p, p->cl + n); }
+
+rfr_status push_check(rfr_plan* p, const int16_t* iq, int64_t n, const rfr_output* o) {
+    if (n < 0 || (n > 0 && iq == nullptr)) return fail(p, RFR_E_INVALID, "bad input buffer");
+    if (!out_ok(p, o, frames_for_len(p, p->cl + n))) return fail(p, RFR_E_SHORT, "output buffers missing or too small");
+    return RFR_OK;
+}
+
+rfr_status ensure_scratch(rfr_plan* p, int64_t n) {
+    const int64_t F = frames_for_len(p, p->cl + n);
+    if (p->mode == RFR_MODE_DEMOD && F > 0 && !p->words.empty()) return ensure_demod_scratch(p, F, p->frames);
+    return RFR_OK;
+}
+
 // Core of every push: enqueue the frames of [carry | buf] into `out`.
 rfr_status push_core(rfr_plan* p, const int16_t* iq, int64_t n, const rfr_output* o,
                      int64_t* frames_out, cudaStream_t st) {
@@ -167,6 +184,7 @@ rfr_status push_core(rfr_plan* p, const int16_t* iq, int64_t n, const rfr_output
             L.status = p->d_status;
             L.n_sms = p->n_sms;
             L.max_smem = p->max_smem;
+            L.lookahead = p->tune.pfb_lookahead;
             RFR_CUDA(p, rfr::pfb_launch(L, st));
         } else {
             if (!p->words.empty()) {
@@ -199,6 +217,7 @@ rfr_status push_core(rfr_plan* p, const int16_t* iq, int64_t n, const rfr_output
                 L.status = p->d_status;
                 L.n_sms = p->n_sms;
                 L.kchunk = 0;
+                L.raster_group = p->tune.demod_raster;
                 RFR_CUDA(p, rfr::demod_launch(L, st));
             }
         }
@@ -217,6 +236,10 @@ rfr_status push_core(rfr_plan* p, const int16_t* iq, int64_t n, const rfr_output
     if (frames_out) *frames_out = F;
     return RFR_OK;
 }
+}  // namespace rfr
+
+namespace {
+using rfr::push_core;
 
 rfr_status reset_state(rfr_plan* p) {
     p->samples = 0;

@@ -1,0 +1,341 @@
+// batch.cu -- many readout streams per step (the batched workload), and the
+// launch autotuner.
+//
+// rfr_batch_push enqueues one push per plan.  Each plan's kernels go on its
+// own branch (fork/join with events), the whole step is captured into a CUDA
+// graph, and the graph is launched into the caller's stream as ONE launch.
+// The executable graph is kept and updated in place (cudaGraphExecUpdate) on
+// the next step, so steady-state steps re-instantiate nothing.  Allocation
+// (scratch growth) happens before capture, never inside it.
+//
+// rfr_plan_autotune times the launch choices that never change results
+// (bit-identical outputs) -- the PFB ring look-ahead and the GEMM tile raster
+// -- on a buffer of the caller's size, keeps the fastest in the plan and in a
+// JSON cache file (RFR_TUNE_CACHE, default ./rfr_tune_cache.json) keyed by
+// the plan shape and the GPU, so later plans of the same shape load it.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <new>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "rfr_internal.h"
+
+struct rfr_batch {
+    std::vector<rfr_plan*> plans;
+    std::vector<cudaStream_t> branches;
+    std::vector<cudaEvent_t> ev_join;
+    cudaStream_t origin = nullptr;
+    cudaEvent_t ev_fork = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t steps = 0, updates = 0, instantiations = 0;
+    std::string last_error;
+};
+
+namespace {
+
+rfr_status batch_fail(rfr_batch* b, rfr_status s, const std::string& msg) {
+    if (b) b->last_error = msg;
+    return s;
+}
+
+void batch_destroy(rfr_batch* b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (auto s : b->branches) cudaStreamDestroy(s);
+    for (auto e : b->ev_join) cudaEventDestroy(e);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->origin) cudaStreamDestroy(b->origin);
+    delete b;
+}
+
+// ------------------------------------------------------------ tune cache
+std::mutex g_tune_mu;
+
+std::string tune_path() {
+    const char* p = std::getenv("RFR_TUNE_CACHE");
+    return p && *p ? std::string(p) : std::string("rfr_tune_cache.json");
+}
+
+std::string tune_key(const rfr_plan* p, int64_t n) {
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, p->device);
+    int lg = 0;
+    while ((int64_t(1) << (lg + 1)) <= n) ++lg;
+    std::ostringstream k;
+    k << (p->mode == RFR_MODE_PFB ? "pfb" : "demod") << ":N" << p->N << ":T" << p->T << ":L" << p->L
+      << ":D" << p->D << ":tones" << p->words.size() << ":flags" << p->out_flags << ":n2^" << lg
+      << ":sm" << prop.major << prop.minor << "x" << prop.multiProcessorCount;
+    return k.str();
+}
+
+// Minimal line-oriented JSON map: {"key": [pfb_lookahead, demod_raster], ...}
+std::map<std::string, std::pair<int, int>> tune_load() {
+    std::map<std::string, std::pair<int, int>> m;
+    std::ifstream f(tune_path());
+    std::string line;
+    while (std::getline(f, line)) {
+        const size_t q0 = line.find('"'), q1 = line.find('"', q0 + 1);
+        const size_t b0 = line.find('[', q1 == std::string::npos ? 0 : q1);
+        if (q0 == std::string::npos || q1 == std::string::npos || b0 == std::string::npos) continue;
+        int a = 0, c = 1;
+        if (std::sscanf(line.c_str() + b0, "[%d, %d]", &a, &c) == 2) m[line.substr(q0 + 1, q1 - q0 - 1)] = {a, c};
+    }
+    return m;
+}
+
+void tune_store(const std::map<std::string, std::pair<int, int>>& m) {
+    const std::string path = tune_path(), tmp = path + ".tmp";
+    {
+        std::ofstream f(tmp);
+        f << "{\n";
+        size_t i = 0;
+        for (const auto& kv : m) {
+            f << "  \"" << kv.first << "\": [" << kv.second.first << ", " << kv.second.second << "]"
+              << (++i < m.size() ? "," : "") << "\n";
+        }
+        f << "}\n";
+    }
+    std::rename(tmp.c_str(), path.c_str());
+}
+
+}  // namespace
+
+extern "C" {
+
+rfr_status rfr_batch_create(rfr_batch** out, rfr_plan* const* plans, int32_t n) {
+    if (!out || !plans || n < 1 || n > 4096) return RFR_E_INVALID;
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        if (!plans[i]) return RFR_E_INVALID;
+        for (int j = 0; j < i; ++j)
+            if (plans[j] == plans[i]) return RFR_E_INVALID;   // a plan's pushes must stay ordered
+    }
+    rfr_batch* b = new (std::nothrow) rfr_batch();
+    if (!b) return RFR_E_NOMEM;
+    b->plans.assign(plans, plans + n);
+    const int nb = std::min(n, 32);
+    b->branches.resize(nb, nullptr);
+    b->ev_join.resize(n, nullptr);
+    bool ok = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    for (auto& s : b->branches) ok = ok && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess;
+    for (auto& e : b->ev_join) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        batch_destroy(b);
+        return RFR_E_CUDA;
+    }
+    *out = b;
+    return RFR_OK;
+}
+
+void rfr_batch_destroy(rfr_batch* b) {
+    if (b) cudaDeviceSynchronize();
+    batch_destroy(b);
+}
+
+rfr_status rfr_batch_push(rfr_batch* b, const int16_t* const* bufs, const int64_t* n_samples,
+                          rfr_output* outs, void* stream) {
+    if (!b || !bufs || !n_samples || !outs) return RFR_E_INVALID;
+    const int n = static_cast<int>(b->plans.size());
+    // 1. validate and grow scratch outside of any capture
+    for (int i = 0; i < n; ++i) {
+        rfr_plan* p = b->plans[i];
+        rfr_status s = rfr::push_check(p, bufs[i], n_samples[i], &outs[i]);
+        if (s != RFR_OK) return batch_fail(b, s, "push " + std::to_string(i) + ": " + p->last_error);
+        s = rfr::ensure_scratch(p, n_samples[i]);
+        if (s != RFR_OK) return batch_fail(b, s, "scratch: " + p->last_error);
+    }
+    // 2. capture the step: fork one branch per plan, join back
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return batch_fail(b, RFR_E_CUDA, "begin capture");
+    rfr_status err = RFR_OK;
+    cudaEventRecord(b->ev_fork, b->origin);
+    for (int i = 0; i < n && err == RFR_OK; ++i) {
+        cudaStream_t br = b->branches[i % b->branches.size()];
+        cudaStreamWaitEvent(br, b->ev_fork, 0);
+        int64_t F = 0;
+        err = rfr::push_core(b->plans[i], bufs[i], n_samples[i], &outs[i], &F, br);
+        outs[i].frames = F;
+        if (err != RFR_OK) b->last_error = "push " + std::to_string(i) + ": " + b->plans[i]->last_error;
+        cudaEventRecord(b->ev_join[i], br);
+        cudaStreamWaitEvent(b->origin, b->ev_join[i], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(b->origin, &graph);
+    if (err != RFR_OK) {
+        // only a CUDA error can get here (arguments were checked above); the
+        // plans' stream state is no longer meaningful: reset them before reuse
+        if (graph) cudaGraphDestroy(graph);
+        return err;
+    }
+    if (ce != cudaSuccess || !graph) return batch_fail(b, RFR_E_CUDA, "end capture");
+    // 3. update the executable graph in place, or instantiate it
+    bool updated = false;
+    if (b->exec) {
+        cudaGraphExecUpdateResultInfo info{};
+        if (cudaGraphExecUpdate(b->exec, graph, &info) == cudaSuccess) {
+            updated = true;
+            ++b->updates;
+        } else {
+            cudaGetLastError();
+            cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+        }
+    }
+    if (!updated) {
+        if (cudaGraphInstantiate(&b->exec, graph, 0) != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            return batch_fail(b, RFR_E_CUDA, "graph instantiate");
+        }
+        ++b->instantiations;
+    }
+    cudaGraphDestroy(graph);
+    if (cudaGraphLaunch(b->exec, st) != cudaSuccess) return batch_fail(b, RFR_E_CUDA, "graph launch");
+    for (auto* p : b->plans) p->last_stream = st;
+    ++b->steps;
+    return RFR_OK;
+}
+
+rfr_status rfr_batch_stats(const rfr_batch* b, int64_t* steps, int64_t* graph_updates,
+                           int64_t* graph_instantiations) {
+    if (!b) return RFR_E_INVALID;
+    if (steps) *steps = b->steps;
+    if (graph_updates) *graph_updates = b->updates;
+    if (graph_instantiations) *graph_instantiations = b->instantiations;
+    return RFR_OK;
+}
+
+const char* rfr_batch_last_error(const rfr_batch* b) { return b ? b->last_error.c_str() : ""; }
+
+rfr_status rfr_plan_autotune(rfr_plan* p, int64_t n_samples, int32_t use_cache, double* best_ms) {
+    if (!p || n_samples < 1 || n_samples > (int64_t(1) << 31)) return RFR_E_INVALID;
+    const std::string key = tune_key(p, n_samples);
+    if (use_cache) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto m = tune_load();
+        auto it = m.find(key);
+        if (it != m.end()) {
+            p->tune.pfb_lookahead = it->second.first;
+            p->tune.demod_raster = it->second.second;
+            p->tune.tuned = true;
+            if (best_ms) *best_ms = -1.0;
+            return RFR_OK;
+        }
+    }
+    // candidates (all give bit-identical results)
+    std::vector<std::pair<int, int>> cand;
+    if (p->mode == RFR_MODE_PFB) {
+        for (int la : {1, 2, 3}) cand.push_back({la, 1});
+    } else {
+        for (int r : {1, 8, 19, 38}) cand.push_back({0, r});
+    }
+    // scratch buffers: zero input, outputs sized for the push
+    const int64_t F = rfr::frames_for_samples(p, n_samples) + 1;
+    const int nt = static_cast<int>(p->words.size());
+    void *x = nullptr, *full = nullptr, *tones = nullptr;
+    const bool want_full = p->mode == RFR_MODE_PFB && (p->out_flags & RFR_OUT_FULL);
+    const bool want_tones = nt > 0 && (p->mode == RFR_MODE_DEMOD || (p->out_flags & RFR_OUT_TONES));
+    auto cleanup = [&]() {
+        if (x) cudaFree(x);
+        if (full) cudaFree(full);
+        if (tones) cudaFree(tones);
+    };
+    if (cudaMalloc(&x, static_cast<size_t>(n_samples) * 4) != cudaSuccess ||
+        (want_full && cudaMalloc(&full, static_cast<size_t>(F) * p->N * 8) != cudaSuccess) ||
+        (want_tones && cudaMalloc(&tones, static_cast<size_t>(F) * nt * 8) != cudaSuccess)) {
+        cleanup();
+        return RFR_E_NOMEM;
+    }
+    cudaMemset(x, 0, static_cast<size_t>(n_samples) * 4);
+    // time on a scratch copy of the stream state, then restore it
+    const int64_t s_samples = p->samples, s_frames = p->frames, s_cl = p->cl;
+    const int s_cur = p->cur;
+    std::vector<unsigned char> carry_save(static_cast<size_t>(std::max<int64_t>(p->cl, 0)) * 4);
+    if (!carry_save.empty())
+        cudaMemcpy(carry_save.data(), p->d_carry[p->cur], carry_save.size(), cudaMemcpyDeviceToHost);
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    rfr_output o{};
+    o.full = full;
+    o.full_ld = p->N;
+    o.full_cap = F;
+    o.tones = tones;
+    o.tones_ld = F;
+    o.tones_cap = F;
+    const rfr::TuneConfig keep = p->tune;
+    double best = 1e30;
+    std::pair<int, int> best_c = cand.front();
+    rfr_status rs = rfr::ensure_scratch(p, n_samples);
+    for (size_t c = 0; c < cand.size() && rs == RFR_OK; ++c) {
+        p->tune.pfb_lookahead = cand[c].first;
+        p->tune.demod_raster = cand[c].second;
+        float ms_best = 1e30f;
+        for (int rep = 0; rep < 4 && rs == RFR_OK; ++rep) {
+            p->samples = s_samples;
+            p->frames = s_frames;
+            p->cl = s_cl;
+            p->cur = s_cur;
+            cudaEventRecord(e0, st);
+            int64_t got = 0;
+            rs = rfr::push_core(p, static_cast<const int16_t*>(x), n_samples, &o, &got, st);
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) ms_best = std::min(ms_best, ms);   // first run warms up
+        }
+        if (ms_best < best) {
+            best = ms_best;
+            best_c = cand[c];
+        }
+    }
+    // restore the stream state (the carry may have been rewritten)
+    p->samples = s_samples;
+    p->frames = s_frames;
+    p->cl = s_cl;
+    p->cur = s_cur;
+    if (!carry_save.empty())
+        cudaMemcpy(p->d_carry[p->cur], carry_save.data(), carry_save.size(), cudaMemcpyHostToDevice);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(st);
+    cleanup();
+    if (rs != RFR_OK) {
+        p->tune = keep;
+        return rs;
+    }
+    p->tune.pfb_lookahead = best_c.first;
+    p->tune.demod_raster = best_c.second;
+    p->tune.tuned = true;
+    if (best_ms) *best_ms = best;
+    if (use_cache) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto m = tune_load();
+        m[key] = best_c;
+        tune_store(m);
+    }
+    return RFR_OK;
+}
+
+rfr_status rfr_plan_get_tune(const rfr_plan* p, int32_t* pfb_lookahead, int32_t* demod_raster, int32_t* tuned) {
+    if (!p) return RFR_E_INVALID;
+    if (pfb_lookahead) *pfb_lookahead = p->tune.pfb_lookahead;
+    if (demod_raster) *demod_raster = p->tune.demod_raster;
+    if (tuned) *tuned = p->tune.tuned ? 1 : 0;
+    return RFR_OK;
+}
+
+}  // extern "C"

@@ -146,6 +146,7 @@ __global__ void presplit_kernel(const uint32_t* __restrict__ carry, int64_t cl,
 }
 
 struct GemmArgs {
+    int raster;           // tile order: groups of `raster` M tiles sweep all N tiles
     int64_t F;
     int64_t F0;           // frames of the stream before this push
     int n_tones, ntp, KB, kchunk, two_d, n_mt, n_nt;
@@ -156,6 +157,23 @@ struct GemmArgs {
     int64_t ld, fo;
     int* status;
 };
+
+// Tile index -> (M tile, N tile): groups of g.raster M tiles are swept
+// N-tile-major, so concurrently running CTAs share the same tap slices in L2.
+__device__ __forceinline__ void tile_coords(const GemmArgs& g, int tile, int& mt, int& nt) {
+    const int r = g.raster > 1 ? g.raster : 1;
+    if (r == 1) {
+        mt = tile / g.n_nt;
+        nt = tile % g.n_nt;
+        return;
+    }
+    const int per_group = r * g.n_nt;
+    const int grp = tile / per_group, in = tile % per_group;
+    const int m_base = grp * r;
+    const int rows = min(r, g.n_mt - m_base);
+    nt = in / rows;
+    mt = m_base + in % rows;
+}
 
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
 demod_gemm_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
@@ -206,7 +224,9 @@ demod_gemm_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constan
         if (lane == 0) {
             uint32_t it = 0;
             for (int tile = blockIdx.x; tile < n_tiles && !*abort_flag; tile += gridDim.x) {
-                const int m0 = (tile / g.n_nt) * BM, n0 = (tile % g.n_nt) * BN;
+                int tm, tn;
+                tile_coords(g, tile, tm, tn);
+                const int m0 = tm * BM, n0 = tn * BN;
                 for (int kb = 0; kb < g.KB; ++kb, ++it) {
                     const int s = it % STAGES;
                     const uint32_t ph = (it / STAGES) & 1;
@@ -269,8 +289,9 @@ demod_gemm_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constan
         const int row = q * 32 + lane;
         uint32_t cc = 0;
         for (int tile = blockIdx.x; tile < n_tiles && !*abort_flag; tile += gridDim.x) {
-            const int mt = tile / g.n_nt;
-            const int m0 = mt * BM, n0 = (tile % g.n_nt) * BN;
+            int mt, tn;
+            tile_coords(g, tile, mt, tn);
+            const int m0 = mt * BM, n0 = tn * BN;
             float sums[128];
 #pragma unroll
             for (int i = 0; i < 128; ++i) sums[i] = 0.f;
@@ -399,6 +420,7 @@ cudaError_t demod_launch(const DemodLaunch& L, cudaStream_t st) {
         !make_map(&mBl, L.b_lo, static_cast<uint64_t>(2) * L.Lpad, static_cast<uint64_t>(2) * L.ntp, BN))
         return cudaErrorInvalidValue;
     GemmArgs g{};
+    g.raster = L.raster_group;
     g.F = L.F;
     g.F0 = L.F0;
     g.n_tones = L.n_tones;
@@ -546,6 +568,7 @@ extern "C" rfr_status rfr_demod_noalloc(const int16_t* iq, int64_t n_samples, co
         !make_map(&mBl, bl, static_cast<uint64_t>(2) * Lpad, static_cast<uint64_t>(2) * ntp, BN))
         return RFR_E_CUDA;
     GemmArgs g{};
+    g.raster = 1;
     g.F = F;
     g.F0 = 0;
     g.n_tones = n_tones;

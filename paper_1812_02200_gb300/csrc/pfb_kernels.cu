@@ -277,11 +277,11 @@ size_t ring_smem_bytes(int rs, int tw_count) {
 }
 
 template <int LOG2N, int T>
-cudaError_t launch_ring(PfbArgs a, int n_sms, int max_smem, cudaStream_t st) {
+cudaError_t launch_ring(PfbArgs a, int n_sms, int max_smem, int lookahead, cudaStream_t st) {
     constexpr int N = 1 << LOG2N;
     constexpr int G = kRingThreads / (N / 16);
     constexpr int HB = (T - 1 + G - 1) / G;
-    int rs = HB + 1 + 3;
+    int rs = HB + 1 + ((lookahead >= 1 && lookahead <= 3) ? lookahead : 3);
     while (rs > HB + 2 && ring_smem_bytes<LOG2N, T>(rs, a.tw_count) > static_cast<size_t>(max_smem)) --rs;
     const size_t smem = ring_smem_bytes<LOG2N, T>(rs, a.tw_count);
     if (smem > static_cast<size_t>(max_smem)) return cudaErrorInvalidConfiguration;
@@ -319,10 +319,10 @@ cudaError_t launch_direct(PfbArgs a, int n_sms, int max_smem, cudaStream_t st) {
 }
 
 template <int LOG2N>
-cudaError_t dispatch_ring_T(PfbArgs a, int tk, int n_sms, int max_smem, cudaStream_t st) {
+cudaError_t dispatch_ring_T(PfbArgs a, int tk, int n_sms, int max_smem, int la, cudaStream_t st) {
     switch (tk) {
-    case 4: return launch_ring<LOG2N, 4>(a, n_sms, max_smem, st);
-    case 8: return launch_ring<LOG2N, 8>(a, n_sms, max_smem, st);
+    case 4: return launch_ring<LOG2N, 4>(a, n_sms, max_smem, la, st);
+    case 8: return launch_ring<LOG2N, 8>(a, n_sms, max_smem, la, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -361,15 +361,15 @@ cudaError_t pfb_launch(const PfbLaunch& L, cudaStream_t st) {
     const int lg = L.log2n;
     if (pfb_uses_ring(lg, L.taps_kernel)) {
         switch (lg) {
-        case 4: return dispatch_ring_T<4>(a, L.taps_kernel, L.n_sms, L.max_smem, st);
-        case 5: return dispatch_ring_T<5>(a, L.taps_kernel, L.n_sms, L.max_smem, st);
-        case 6: return dispatch_ring_T<6>(a, L.taps_kernel, L.n_sms, L.max_smem, st);
-        case 7: return dispatch_ring_T<7>(a, L.taps_kernel, L.n_sms, L.max_smem, st);
-        case 8: return dispatch_ring_T<8>(a, L.taps_kernel, L.n_sms, L.max_smem, st);
-        case 9: return dispatch_ring_T<9>(a, L.taps_kernel, L.n_sms, L.max_smem, st);
-        case 10: return dispatch_ring_T<10>(a, L.taps_kernel, L.n_sms, L.max_smem, st);
-        case 11: return dispatch_ring_T<11>(a, L.taps_kernel, L.n_sms, L.max_smem, st);
-        case 12: return dispatch_ring_T<12>(a, L.taps_kernel, L.n_sms, L.max_smem, st);
+        case 4: return dispatch_ring_T<4>(a, L.taps_kernel, L.n_sms, L.max_smem, L.lookahead, st);
+        case 5: return dispatch_ring_T<5>(a, L.taps_kernel, L.n_sms, L.max_smem, L.lookahead, st);
+        case 6: return dispatch_ring_T<6>(a, L.taps_kernel, L.n_sms, L.max_smem, L.lookahead, st);
+        case 7: return dispatch_ring_T<7>(a, L.taps_kernel, L.n_sms, L.max_smem, L.lookahead, st);
+        case 8: return dispatch_ring_T<8>(a, L.taps_kernel, L.n_sms, L.max_smem, L.lookahead, st);
+        case 9: return dispatch_ring_T<9>(a, L.taps_kernel, L.n_sms, L.max_smem, L.lookahead, st);
+        case 10: return dispatch_ring_T<10>(a, L.taps_kernel, L.n_sms, L.max_smem, L.lookahead, st);
+        case 11: return dispatch_ring_T<11>(a, L.taps_kernel, L.n_sms, L.max_smem, L.lookahead, st);
+        case 12: return dispatch_ring_T<12>(a, L.taps_kernel, L.n_sms, L.max_smem, L.lookahead, st);
         default: return cudaErrorInvalidValue;
         }
     }

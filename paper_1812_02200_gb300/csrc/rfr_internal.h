@@ -44,6 +44,7 @@ struct PfbLaunch {
     int* status;
     int n_sms;
     int max_smem;
+    int lookahead;      // ring super-blocks fetched ahead (0 = as many as fit, <= 3)
 };
 bool pfb_uses_ring(int log2n, int taps);
 int pfb_kernel_taps(int log2n, int taps);
@@ -78,6 +79,7 @@ struct DemodLaunch {
     int* status;
     int n_sms;
     int kchunk;                 // k-blocks per TMEM accumulation chunk
+    int raster_group;           // tile order: groups of this many 128-frame tiles sweep all tones
 };
 cudaError_t demod_build_taps(const double* d_h, const uint64_t* d_words, int n_tones, int ntp,
                              int L, int Lpad, int e, void* b_hi, void* b_lo, cudaStream_t st);
@@ -96,6 +98,14 @@ cudaError_t plain_demod(const int16_t* iq, int64_t n, int L, int D, const void* 
                         const uint64_t* words, int n_tones, void* tones, int64_t tones_ld,
                         cudaStream_t st);
 void plain_release(void* scratch, void* fft_plan);
+
+// ------------------------------------------------------------- tuning
+// Launch choices that never change results (bit-identical outputs).
+struct TuneConfig {
+    int pfb_lookahead = 0;      // 0 = as many ring super-blocks as shared memory allows
+    int demod_raster = 1;       // 1 = tones fastest across the whole grid
+    bool tuned = false;
+};
 
 // ------------------------------------------------------------- state
 cudaError_t carry_update(const int16_t* old_carry, int64_t cl, const int16_t* buf, int64_t n,
@@ -167,5 +177,19 @@ struct rfr_plan {
     void* plain_fft = nullptr;
     int64_t plain_fft_batch = 0;
 
+    rfr::TuneConfig tune;
     std::string last_error;
 };
+
+namespace rfr {
+// Enqueue one push of [carry | iq] into `o` on `st` (no allocation when the
+// scratch is already large enough; see ensure_scratch).
+rfr_status push_core(rfr_plan* p, const int16_t* iq, int64_t n, const rfr_output* o,
+                     int64_t* frames_out, cudaStream_t st);
+// Grow the plan's per-push scratch for a push of n samples (may allocate and
+// synchronise the device; never call it during stream capture).
+rfr_status ensure_scratch(rfr_plan* p, int64_t n);
+int64_t frames_for_samples(const rfr_plan* p, int64_t n);
+// Argument and capacity checks of push_core without side effects.
+rfr_status push_check(rfr_plan* p, const int16_t* iq, int64_t n, const rfr_output* o);
+}  // namespace rfr

@@ -73,6 +73,14 @@ _SIGS = {
     "rfr_status_string": (C.c_char_p, [C.c_int]),
     "rfr_last_error": (C.c_char_p, [_P]),
     "rfr_version": (C.c_char_p, []),
+    "rfr_batch_create": (C.c_int, [C.POINTER(_P), C.POINTER(_P), C.c_int32]),
+    "rfr_batch_destroy": (None, [_P]),
+    "rfr_batch_push": (C.c_int, [_P, C.POINTER(_P), C.POINTER(C.c_int64), C.POINTER(Output), _P]),
+    "rfr_batch_stats": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "rfr_batch_last_error": (C.c_char_p, [_P]),
+    "rfr_plan_autotune": (C.c_int, [_P, C.c_int64, C.c_int32, C.POINTER(C.c_double)]),
+    "rfr_plan_get_tune": (C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "rfr_demod_noalloc": (C.c_int, [_P, C.c_int64, _P, C.c_int32, C.c_int32, _P, C.c_int32, _P, C.c_int64, _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -221,6 +229,17 @@ class Plan:
     def reset(self):
         self._check(_lib.rfr_reset(self._h), "reset")
 
+    def autotune(self, n_samples: int, use_cache: bool = True) -> float:
+        ms = C.c_double()
+        self._check(_lib.rfr_plan_autotune(self._h, int(n_samples), 1 if use_cache else 0,
+                                           C.byref(ms)), "autotune")
+        return ms.value
+
+    def tune(self) -> dict:
+        a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
+        self._check(_lib.rfr_plan_get_tune(self._h, C.byref(a), C.byref(b), C.byref(c)), "tune")
+        return {"pfb_lookahead": a.value, "demod_raster": b.value, "tuned": bool(c.value)}
+
     def state_export(self) -> bytes:
         n = C.c_size_t()
         self._check(_lib.rfr_state_export(self._h, None, C.byref(n)), "state_export")
@@ -231,3 +250,47 @@ class Plan:
     def state_import(self, blob: bytes):
         buf = C.create_string_buffer(blob, len(blob))
         self._check(_lib.rfr_state_import(self._h, buf, len(blob)), "state_import")
+
+
+class Batch:
+    """Plans that advance together; one step = one CUDA-graph launch."""
+
+    def __init__(self, plans):
+        self.plans = list(plans)
+        arr = (_P * len(self.plans))(*[p._h for p in self.plans])
+        h = _P()
+        st = _lib.rfr_batch_create(C.byref(h), arr, len(self.plans))
+        if st != OK:
+            raise RfrError(st, "rfr_batch_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.rfr_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def push(self, xs, fulls=None, tones=None, frame_offsets=None, stream=None):
+        """xs: list of int16 [n_i, 2] device tensors; fulls/tones: lists of
+        output tensors (or None) per plan.  Returns frames per plan."""
+        n = len(self.plans)
+        fulls = fulls or [None] * n
+        tones = tones or [None] * n
+        frame_offsets = frame_offsets or [0] * n
+        bufs = (_P * n)(*[x.data_ptr() if x is not None and x.shape[0] else None for x in xs])
+        ns = (C.c_int64 * n)(*[0 if x is None else x.shape[0] for x in xs])
+        outs = (Output * n)(*[Plan._out(f, t, o) for f, t, o in zip(fulls, tones, frame_offsets)])
+        st = _lib.rfr_batch_push(self._h, bufs, ns, outs, _stream_ptr(stream))
+        if st != OK:
+            raise RfrError(st, _lib.rfr_batch_last_error(self._h).decode())
+        return [outs[i].frames for i in range(n)]
+
+    def stats(self) -> dict:
+        a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+        _lib.rfr_batch_stats(self._h, C.byref(a), C.byref(b), C.byref(c))
+        return {"steps": a.value, "graph_updates": b.value, "graph_instantiations": c.value}
