@@ -260,6 +260,66 @@ rfr_status rfr_plan_autotune(rfr_plan* plan, int64_t n_samples, int32_t use_cach
 rfr_status rfr_plan_get_tune(const rfr_plan* plan, int32_t* pfb_lookahead, int32_t* demod_raster,
                              int32_t* tuned);
 
+/* ---------------------------------------------------------------- serving */
+typedef struct rfr_server rfr_server;
+
+typedef struct {
+    uint64_t tag;           /* as given to rfr_server_submit */
+    int32_t readout;
+    int32_t status;         /* rfr_status of the request */
+    int64_t frames;         /* frames written to the request's output */
+    int64_t samples;
+    double t_submit_us;     /* rfr_now_us() clock: submit, admission, completion seen */
+    double t_admit_us;
+    double t_done_us;
+} rfr_completion;
+
+typedef struct {
+    int64_t submitted, admitted, completed, queued, in_flight;
+    int64_t budget_bytes, peak_bytes;   /* staging arena: size and high-water mark */
+} rfr_server_stats;
+
+/*
+ * rfr_server_create -- a serving loop over n readouts (plans[i] serves
+ * readout i; plans must outlive the server and not be pushed elsewhere).
+ * The paper's host runtime passes acquired buffers between threads through
+ * queues of pointers into pre-allocated memory (Sec. III); here one worker
+ * thread admits submitted buffers in arrival order as device memory frees up
+ * and enqueues each at once on its readout's stream (copy in, push, copy the
+ * frames out, completion event), so requests that arrive while others are on
+ * the GPU run concurrently with them (continuous batching).  Each readout's
+ * buffers are processed in submission order and its filter history and NCO
+ * phase stay on the device between buffers.
+ *   mem_budget_bytes   device staging arena allocated once here (inputs of
+ *                      host buffers + produced frames of every admitted
+ *                      request must fit); nothing is allocated while serving.
+ *   max_buffer_samples largest buffer a request may carry (plan scratch is
+ *                      pre-sized for it).
+ */
+rfr_status rfr_server_create(rfr_server** server, rfr_plan* const* plans, int32_t n,
+                             size_t mem_budget_bytes, int64_t max_buffer_samples);
+
+/*
+ * rfr_server_submit -- queue a buffer (host -- ideally pinned -- or device
+ * memory, [n_samples][2] int16) of `readout`; its frames go to `out` (host or
+ * device buffers, layout of rfr_output).  Returns immediately; iq and out must
+ * stay valid until the request's completion is polled.  RFR_E_NOMEM if the
+ * request could never fit in the budget, RFR_E_INVALID for bad arguments.
+ */
+rfr_status rfr_server_submit(rfr_server* server, int32_t readout, const int16_t* iq, int64_t n_samples,
+                             const rfr_output* out, uint64_t tag);
+
+/* Up to cap completions (oldest first); waits up to wait_ms for the first. */
+rfr_status rfr_server_poll(rfr_server* server, rfr_completion* done, int32_t cap, int32_t* n_done,
+                           int32_t wait_ms);
+rfr_status rfr_server_get_stats(const rfr_server* server, rfr_server_stats* stats);
+
+/* Finishes every submitted request, then frees the server. */
+void rfr_server_destroy(rfr_server* server);
+
+/* The host clock (microseconds, steady) the server stamps requests with. */
+double rfr_now_us(void);
+
 /*
  * rfr_demod_noalloc -- one-shot direct demodulation that allocates nothing.
  * (The paper has no counterpart; this is a deployment convenience.)

@@ -51,6 +51,18 @@ class PlanInfo(C.Structure):
                 ("frames_pending", C.c_int64), ("tap_scale", C.c_double)]
 
 
+class Completion(C.Structure):
+    _fields_ = [("tag", C.c_uint64), ("readout", C.c_int32), ("status", C.c_int32),
+                ("frames", C.c_int64), ("samples", C.c_int64), ("t_submit_us", C.c_double),
+                ("t_admit_us", C.c_double), ("t_done_us", C.c_double)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64),
+                ("queued", C.c_int64), ("in_flight", C.c_int64), ("budget_bytes", C.c_int64),
+                ("peak_bytes", C.c_int64)]
+
+
 _P = C.c_void_p
 _SIGS = {
     "rfr_plan_create": (C.c_int, [C.POINTER(_P), C.c_int32, C.c_int32, C.POINTER(Window),
@@ -80,6 +92,12 @@ _SIGS = {
     "rfr_batch_last_error": (C.c_char_p, [_P]),
     "rfr_plan_autotune": (C.c_int, [_P, C.c_int64, C.c_int32, C.POINTER(C.c_double)]),
     "rfr_plan_get_tune": (C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "rfr_server_create": (C.c_int, [C.POINTER(_P), C.POINTER(_P), C.c_int32, C.c_size_t, C.c_int64]),
+    "rfr_server_submit": (C.c_int, [_P, C.c_int32, _P, C.c_int64, C.POINTER(Output), C.c_uint64]),
+    "rfr_server_poll": (C.c_int, [_P, C.POINTER(Completion), C.c_int32, C.POINTER(C.c_int32), C.c_int32]),
+    "rfr_server_get_stats": (C.c_int, [_P, C.POINTER(ServerStats)]),
+    "rfr_server_destroy": (None, [_P]),
+    "rfr_now_us": (C.c_double, []),
     "rfr_demod_noalloc": (C.c_int, [_P, C.c_int64, _P, C.c_int32, C.c_int32, _P, C.c_int32, _P, C.c_int64, _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -294,3 +312,53 @@ class Batch:
         a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
         _lib.rfr_batch_stats(self._h, C.byref(a), C.byref(b), C.byref(c))
         return {"steps": a.value, "graph_updates": b.value, "graph_instantiations": c.value}
+
+
+def now_us() -> float:
+    return float(_lib.rfr_now_us())
+
+
+class Server:
+    """Serving loop over readouts (plans[i] serves readout i)."""
+
+    def __init__(self, plans, mem_budget_bytes: int, max_buffer_samples: int):
+        self.plans = list(plans)
+        arr = (_P * len(self.plans))(*[p._h for p in self.plans])
+        h = _P()
+        st = _lib.rfr_server_create(C.byref(h), arr, len(self.plans), int(mem_budget_bytes),
+                                    int(max_buffer_samples))
+        if st != OK:
+            raise RfrError(st, "rfr_server_create")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, readout: int, x, full=None, tones=None, frame_offset: int = 0, tag: int = 0):
+        o = Plan._out(full, tones, frame_offset)
+        st = _lib.rfr_server_submit(self._h, int(readout), _ptr(x), 0 if x is None else x.shape[0],
+                                    C.byref(o), int(tag))
+        if st != OK:
+            raise RfrError(st, "rfr_server_submit")
+
+    def poll(self, cap: int = 256, wait_ms: int = 0):
+        buf = (Completion * cap)()
+        n = C.c_int32()
+        st = _lib.rfr_server_poll(self._h, buf, cap, C.byref(n), int(wait_ms))
+        if st != OK:
+            raise RfrError(st, "rfr_server_poll")
+        return [{f: getattr(buf[i], f) for f, _ in Completion._fields_} for i in range(n.value)]
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _lib.rfr_server_get_stats(self._h, C.byref(s))
+        return {f: getattr(s, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.rfr_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
