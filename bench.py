@@ -296,6 +296,165 @@ def run_demod(args, dev, stream, rank):
     return res
 
 
+# ------------------------------------------------------------------- batch
+def make_spec_plan(rfr, spec, words, full=False):
+    if spec["kind"] == "pfb":
+        return rfr.Plan(spec["N"], spec["T"], window="kaiser", beta=BETA, words=words, full=full)
+    return rfr.Plan(0, spec["L"], window="blackman", cutoff=DEMOD_FC, words=words, decimation=spec["D"])
+
+
+def run_batch(args, dev, stream):
+    """Workload 4: 24 mixed PFB / demodulation streams of 2^22..2^26 samples
+    per step, one CUDA-graph launch per step, launch choices autotuned."""
+    import torch
+
+    from paper_1812_02200_gb300 import rfr
+    t0 = time.time()
+    specs = siggen.c4_specs()
+    cases = [siggen.spec_input(sp) for sp in specs]
+    log(f"[bench] generated batch inputs in {time.time() - t0:.1f}s")
+    xs = [torch.from_numpy(c["x"]).to(dev) for c in cases]
+    plans = [make_spec_plan(rfr, sp, c["words"]) for sp, c in zip(specs, cases)]
+    seq_plans = [make_spec_plan(rfr, sp, c["words"]) for sp, c in zip(specs, cases)]
+    # tune each stream shape once; the sequential comparison loads the same
+    # choices from the cache file
+    os.environ.setdefault("RFR_TUNE_CACHE", os.path.join(ROOT, "gpurun_out", "rfr_tune_cache.json")
+                          if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/rfr_tune_cache.json")
+    for p, q, x in zip(plans, seq_plans, xs):
+        p.autotune(x.shape[0], use_cache=True)
+        q.autotune(x.shape[0], use_cache=True)
+    outs = [torch.empty((p.n_tones, p.frames_for(x.shape[0]) + 1), dtype=torch.complex64, device=dev)
+            for p, x in zip(plans, xs)]
+    batch = rfr.Batch(plans)
+    samples = sum(x.shape[0] for x in xs)
+    for _ in range(2):
+        batch.push(xs, None, outs)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k = max(3, args.steps // 4)
+    e0.record(stream)
+    for _ in range(k):
+        batch.push(xs, None, outs, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_batch = e0.elapsed_time(e1) / k
+    # the same streams as sequential per-stream pushes (no graph, one stream)
+    for p, x, o in zip(seq_plans, xs, outs):
+        p.push_into(x, tones=o, stream=stream)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(k):
+        for p, x, o in zip(seq_plans, xs, outs):
+            p.push_into(x, tones=o, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_seq = e0.elapsed_time(e1) / k
+    # per-stream plain FP32 launches
+    ms_plain = None
+    if not args.no_plain:
+        for p, x, o in zip(seq_plans, xs, outs):
+            p.plain_oneshot(x, tones=o, stream=stream)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for p, x, o in zip(seq_plans, xs, outs):
+            p.plain_oneshot(x, tones=o, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_plain = e0.elapsed_time(e1)
+    st = batch.stats()
+    res = {"workload": "24 streams of 2^22..2^26 samples (log-uniform), 16 PFB "
+                       "(N in {256..16384}, T in {4,8,16}, tones out) + 8 demodulation "
+                       "(64..4096 tones, L in {1024,4096}, D in {512,2048})",
+           "samples_per_step": samples,
+           "value": samples / (ms_batch * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms_batch,
+           "graph": st,
+           "sequential_fused": {"value": samples / (ms_seq * 1e-3) / 1e6, "ms_per_step": ms_seq},
+           "plain_fp32_per_stream": None if ms_plain is None else
+           {"value": samples / (ms_plain * 1e-3) / 1e6, "ms_per_step": ms_plain},
+           "tune": [p.tune() for p in plans][:4] + ["..."]}
+    batch.close()
+    del outs, xs
+    return res
+
+
+# ------------------------------------------------------------------- serve
+def run_serve(args, dev):
+    """Workload 5: 32 readouts (plans drawn as in the batched workload),
+    buffers of 1..32 MB arriving as Poisson processes, host-resident input and
+    output (pinned), admission under a 40 GB device budget; p50/p99 latency
+    from submit to completion and the sustained rate per offered load."""
+    import threading as th
+
+    import torch
+
+    from paper_1812_02200_gb300 import rfr
+    specs = siggen.c5_specs()
+    max_n = 8 << 20                      # 32 MB of complex int16
+    t0 = time.time()
+    host_x, plans, outs = [], [], []
+    for sp in specs:
+        c = siggen.spec_input(sp, n=max_n)
+        host_x.append(torch.from_numpy(c["x"]).pin_memory())
+        plans.append(make_spec_plan(rfr, sp, c["words"]))
+    for p in plans:
+        f = p.frames_for(max_n) + 2
+        outs.append(torch.empty((max(p.n_tones, 1), 4 * f), dtype=torch.complex64).pin_memory())
+    log(f"[bench] serve setup {time.time() - t0:.1f}s")
+    srv = rfr.Server(plans, 40 << 30, max_n)
+    loads = [float(v) for v in args.serve_loads.split(",") if v]
+    rng = np.random.default_rng(55)
+    points = []
+    for load in loads:
+        mean_n = float(np.mean(siggen.c5_buffer_samples(rng, 4096)))
+        rate = load * 1e9 / mean_n / len(specs)          # buffers/s per readout
+        dur = args.serve_seconds
+        arr = []
+        for r in range(len(specs)):
+            t = rng.exponential(1.0 / rate)
+            while t < dur:
+                arr.append((t, r))
+                t += rng.exponential(1.0 / rate)
+        arr.sort()
+        sizes = siggen.c5_buffer_samples(rng, len(arr))
+        done = []
+        stop = [False]
+
+        def poller():
+            while not stop[0] or len(done) < len(arr):
+                done.extend(srv.poll(1024, wait_ms=20))
+                if stop[0] and len(done) >= len(arr):
+                    break
+
+        pt = th.Thread(target=poller, daemon=True)
+        pt.start()
+        slot = [0] * len(specs)
+        base = rfr.now_us()
+        for tag, ((t, r), n) in enumerate(zip(arr, sizes)):
+            while rfr.now_us() - base < t * 1e6:
+                pass
+            # four rotating output regions per readout, each large enough for
+            # the frames of the largest buffer
+            off = (slot[r] % 4) * (outs[r].shape[1] // 4)
+            slot[r] += 1
+            srv.submit(r, host_x[r][: int(n)], tones=outs[r], frame_offset=off, tag=tag)
+        stop[0] = True
+        pt.join(timeout=120)
+        lat = np.array([d["t_done_us"] - d["t_submit_us"] for d in done]) / 1e3
+        t_first = min(d["t_submit_us"] for d in done)
+        t_last = max(d["t_done_us"] for d in done)
+        tot = float(sum(d["samples"] for d in done))
+        points.append({"offered_gsps": load, "buffers": len(done),
+                       "sustained_gsps": tot / ((t_last - t_first) * 1e-6) / 1e9,
+                       "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                       "max_ms": float(lat.max())})
+        log(f"[bench] serve load {load}: {points[-1]}")
+    st = srv.stats()
+    srv.close()
+    return {"workload": "32 readouts (plans as the batched workload), Poisson arrivals, "
+                        "buffers log-uniform 1..32 MB, pinned host in/out, 40 GB budget",
+            "points": points, "peak_device_bytes": st["peak_bytes"], "seconds_per_point": args.serve_seconds}
+
+
 # --------------------------------------------------------------------- ours
 def run_ours(args, ws, rank, local):
     import torch
@@ -402,10 +561,13 @@ def run_ours(args, ws, rank, local):
                "sample": f"{nf} frames ({s} samples) of the workload, {dt:.1f} s"}
 
     demod = None
+    del full, tones
+    torch.cuda.empty_cache()
     if not args.no_demod:
-        del full, tones
-        torch.cuda.empty_cache()
         demod = run_demod(args, dev, stream, rank)
+    batch = None if args.no_batch else run_batch(args, dev, stream)
+    torch.cuda.empty_cache()
+    serve = None if (args.no_serve or ws > 1) else run_serve(args, dev)
 
     if rank != 0:
         return
@@ -429,6 +591,8 @@ def run_ours(args, ws, rank, local):
                      "peak_kind": f"{peak_kind} (STREAM copy)"},
         "plain_fp32": plain,
         "demod": demod,
+        "batch": batch,
+        "serve": serve,
         "e2e": e2e,
         "cpu_baseline": cpu,
         "clocks": clk,
@@ -448,6 +612,10 @@ def main():
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-demod", action="store_true")
     ap.add_argument("--demod-log2-samples", type=int, default=27)
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-loads", default="1,5,10,20", help="offered loads, Gsamples/s")
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--log2-samples", type=int, default=28,
                     help="stream length (28 = the workload; smaller only for profiling)")
     ap.add_argument("--cpu-frames", type=int, default=32768)

@@ -215,3 +215,53 @@ def c3(seed: int = SEED_BASE + 3, n: int | None = None, n_tones: int | None = No
        dtype=np.complex64):
     return demod_case(n or C3["n"], n_tones or C3["n_tones"], seed=seed, sigma=C3["sigma"],
                       dtype=dtype)
+
+
+def mixed_specs(count: int, seed: int, log2_n=(22.0, 26.0), round_to: int = 1024):
+    """Stream specs of the batched workload: each stream is a PFB (p = 0.5;
+    N in {256, 1024, 4096, 16384}, T in {4, 8, 16}, min(1000, N/4) tones at bin
+    centres, Kaiser(9)) or a demodulation (2^U(6, 12) tones, L in {1024, 4096},
+    D in {512, 2048}, Blackman 40 kHz), with 2^U(log2_n) samples rounded to a
+    multiple of `round_to`."""
+    r = rng_for(seed)
+    specs = []
+    for i in range(count):
+        n = int(round(2.0 ** r.uniform(*log2_n)))
+        n = max(round_to, n - n % round_to)
+        if r.uniform() < 0.5:
+            N = int(r.choice([256, 1024, 4096, 16384]))
+            T = int(r.choice([4, 8, 16]))
+            specs.append(dict(kind="pfb", N=N, T=T, tones=min(1000, N // 4), n=n, seed=seed * 100 + i))
+        else:
+            nt = int(round(2.0 ** r.uniform(6.0, 12.0)))
+            L = int(r.choice([1024, 4096]))
+            D = int(r.choice([512, 2048]))
+            specs.append(dict(kind="demod", tones=nt, L=L, D=D, n=n, seed=seed * 100 + i))
+    return specs
+
+
+def spec_input(spec: dict, n: int | None = None):
+    """Synthetic input of one mixed-workload stream (signal model as in the
+    PFB and demodulation workloads)."""
+    n = n or spec["n"]
+    if spec["kind"] == "pfb":
+        sep = 2 if 2 * spec["tones"] <= spec["N"] else 1
+        return pfb_case(n, spec["N"], spec["tones"], seed=spec["seed"], sigma=4.0, rule="sum", min_sep=sep)
+    return demod_case(n, spec["tones"], seed=spec["seed"], dtype=np.complex64)
+
+
+def c4_specs(seed: int = SEED_BASE + 4):
+    """24 streams of 2^22 .. 2^26 samples (log-uniform), PFB or demodulation."""
+    return mixed_specs(24, seed)
+
+
+def c5_specs(seed: int = SEED_BASE + 5):
+    """32 readouts with plans drawn as in the batched workload."""
+    return mixed_specs(32, seed)
+
+
+def c5_buffer_samples(rng: np.random.Generator, count: int) -> np.ndarray:
+    """Buffer sizes of the serving workload: log-uniform 1 .. 32 MB of complex
+    int16 (4 bytes per sample), rounded to a multiple of 1024 samples."""
+    b = np.exp(rng.uniform(np.log(1 << 20), np.log(32 << 20), count)) / 4.0
+    return np.maximum(1024, (b // 1024).astype(np.int64) * 1024)
