@@ -30,6 +30,7 @@
 #include "dev_common.cuh"
 #include "fft_dev.cuh"
 #include "rfr_internal.h"
+#include "umma.cuh"
 
 namespace rfr {
 
@@ -227,6 +228,130 @@ __global__ void __launch_bounds__(kRingThreads, 1) pfb_ring_kernel(const PfbArgs
     }
 }
 
+// ---------------------------------------------------------------- TMEM
+// N = 4096, T <= 8 (after padding): the FP32 delay line lives in tensor
+// memory.  Each sample is converted from int16 once, stored with tcgen05.st
+// into the thread's TMEM columns (slot = block mod 8: 8 blocks x 16 complex
+// FP32 per thread = the whole 256 KiB of TMEM for 256 threads), and read back
+// for every tap with tcgen05.ld.  int16 blocks arrive by 1-D TMA into a small
+// staging ring.  The taps are summed in the same order as the other variants
+// (t = 0..T-1 from zero), so results are bit-identical to them.
+constexpr int kTmemStage = 4;        // staging slots (blocks of 4096 samples)
+constexpr int kTmemSlots = 8;        // delay-line blocks held in TMEM
+
+__host__ __device__ constexpr size_t tmem_smem_bytes(int tw_count, int n_bins_smem) {
+    return static_cast<size_t>(kTmemStage) * 4096 * 4 + static_cast<size_t>(4096 + 256) * 8 +
+           static_cast<size_t>((tw_count + 1) & ~1) * 8 + static_cast<size_t>((n_bins_smem + 1) & ~1) * 4 +
+           kTmemStage * 8 + 16;
+}
+
+template <int T>
+__global__ void __launch_bounds__(kRingThreads, 1) pfb_tmem_kernel(const PfbArgs a) {
+    constexpr int LOG2N = 12, N = 4096, NT = 256;
+    static_assert(T <= kTmemSlots, "delay line fits in TMEM");
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint32_t* stage = reinterpret_cast<uint32_t*>(smem);
+    float2* xbuf = reinterpret_cast<float2*>(smem + static_cast<size_t>(kTmemStage) * N * 4);
+    float2* tw = xbuf + (N + N / 16);
+    const int nb_smem = a.n_tones <= 4096 ? a.n_tones : 0;
+    int32_t* sbins = reinterpret_cast<int32_t*>(tw + ((a.tw_count + 1) & ~1));
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sbins + ((nb_smem + 1) & ~1));
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + kTmemStage);
+
+    const int tid = threadIdx.x, warp = tid >> 5, tf = tid;
+    const int64_t ja = static_cast<int64_t>(blockIdx.x) * a.iters_per_cta;
+    const int64_t jb = min_i64(a.F, ja + a.iters_per_cta);
+    if (ja >= jb) return;
+    const int64_t b0 = ja, b1 = jb + T - 1;                     // blocks [b0, b1)
+    const int64_t need = (a.F + T - 1) * static_cast<int64_t>(N);
+
+    if (warp == 0) {
+        umma::alloc(tmem_holder, 512);
+        umma::relinquish();
+    }
+    if (tid == 0) {
+        for (int s = 0; s < kTmemStage; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    for (int i = tid; i < a.tw_count; i += blockDim.x) tw[i] = __ldg(a.tw + i);
+    for (int i = tid; i < nb_smem; i += blockDim.x) sbins[i] = __ldg(a.bins + i);
+    float hr[T][16];
+#pragma unroll
+    for (int t = 0; t < T; ++t)
+#pragma unroll
+        for (int r = 0; r < 16; ++r) hr[t][r] = __ldg(a.h + t * N + tf + r * NT);
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tbase = *tmem_holder + (static_cast<uint32_t>(32 * (warp & 3)) << 16) +
+                           static_cast<uint32_t>(256 * (warp >> 2));
+    if (tid == 0)
+        for (int64_t b = b0; b < min_i64(b0 + kTmemStage, b1); ++b)
+            issue_sb_tma(a, b, need, stage + (b % kTmemStage) * N, &bars[b % kTmemStage]);
+
+    bool ok = true;
+    for (int64_t b = b0; b < b1; ++b) {
+        const int s = static_cast<int>(b % kTmemStage);
+        if (!mbar_wait(&bars[s], static_cast<uint32_t>(((b - b0) / kTmemStage) & 1), a.status)) {
+            ok = false;
+            break;
+        }
+        uint32_t xr[32];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const float2 f = iq_to_f2(stage[s * N + tf + r * NT]);
+            xr[2 * r] = __float_as_uint(f.x);
+            xr[2 * r + 1] = __float_as_uint(f.y);
+        }
+        umma::st_32x32b_x32(tbase + 32u * static_cast<uint32_t>(b % kTmemSlots), xr);
+        __syncthreads();   // staging slot s fully read
+        if (tid == 0 && b + kTmemStage < b1)
+            issue_sb_tma(a, b + kTmemStage, need, stage + s * N, &bars[s]);
+        umma::wait_st();
+        const int64_t j = b - (T - 1);                           // frame completed by block b
+        if (j < ja) continue;                                    // uniform across the CTA
+        float2 v[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            uint32_t x[32];
+            umma::ld_32x32b_x32(tbase + 32u * static_cast<uint32_t>((j + t) % kTmemSlots), x);
+            umma::wait_ld();
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                v[r].x = fmaf(hr[t][r], __uint_as_float(x[2 * r]), v[r].x);
+                v[r].y = fmaf(hr[t][r], __uint_as_float(x[2 * r + 1]), v[r].y);
+            }
+        }
+        fft_frame<LOG2N, true>(v, xbuf, tf, tw);
+        if (a.full) {
+            float2* row = a.full + (a.frame_offset + j) * a.full_ld;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) row[fft_out_index<LOG2N>(tf, i)] = v[i];
+        }
+        if (a.n_tones > 0) {
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) xbuf[fpad(fft_out_index<LOG2N>(tf, i))] = v[i];
+            __syncthreads();
+            float2* col = a.tones + a.frame_offset + j;
+            for (int t = tid; t < a.n_tones; t += NT) {
+                const int bin = t < nb_smem ? sbins[t] : __ldg(a.bins + t);
+                col[t * a.tones_ld] = xbuf[fpad(bin)];
+            }
+        }
+        __syncthreads();   // xbuf reused by the next frame's first pass
+    }
+    (void)ok;
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        umma::fence_after_sync();
+        umma::dealloc(*tmem_holder, 512);
+    }
+}
+
 // -------------------------------------------------------------- DIRECT
 template <int LOG2N>
 __global__ void __launch_bounds__(1024, 1) pfb_direct_kernel(const PfbArgs a) {
@@ -318,6 +443,21 @@ cudaError_t launch_direct(PfbArgs a, int n_sms, int max_smem, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+template <int T>
+cudaError_t launch_tmem(PfbArgs a, int n_sms, int max_smem, cudaStream_t st) {
+    const int nb_smem = a.n_tones <= 4096 ? a.n_tones : 0;
+    const size_t smem = tmem_smem_bytes(a.tw_count, nb_smem);
+    if (smem > static_cast<size_t>(max_smem)) return cudaErrorInvalidConfiguration;
+    const int64_t grid = std::min<int64_t>(a.F, n_sms);
+    a.iters_per_cta = (a.F + grid - 1) / grid;
+    const int64_t grid2 = (a.F + a.iters_per_cta - 1) / a.iters_per_cta;
+    auto k = pfb_tmem_kernel<T>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<static_cast<unsigned>(grid2), kRingThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
 template <int LOG2N>
 cudaError_t dispatch_ring_T(PfbArgs a, int tk, int n_sms, int max_smem, int la, cudaStream_t st) {
     switch (tk) {
@@ -359,6 +499,10 @@ cudaError_t pfb_launch(const PfbLaunch& L, cudaStream_t st) {
                          (reinterpret_cast<uintptr_t>(L.carry) % 16 == 0);
     a.use_tma = aligned ? 1 : 0;
     const int lg = L.log2n;
+    if (lg == 12 && a.use_tma && L.variant != 1) {
+        if (L.taps_kernel == 4) return launch_tmem<4>(a, L.n_sms, L.max_smem, st);
+        if (L.taps_kernel == 8) return launch_tmem<8>(a, L.n_sms, L.max_smem, st);
+    }
     if (pfb_uses_ring(lg, L.taps_kernel)) {
         switch (lg) {
         case 4: return dispatch_ring_T<4>(a, L.taps_kernel, L.n_sms, L.max_smem, L.lookahead, st);

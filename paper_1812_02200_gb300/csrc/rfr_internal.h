@@ -45,6 +45,7 @@ struct PfbLaunch {
     int n_sms;
     int max_smem;
     int lookahead;      // ring super-blocks fetched ahead (0 = as many as fit, <= 3)
+    int variant;        // 0 = best available, 1 = shared-memory int16 ring only
 };
 bool pfb_uses_ring(int log2n, int taps);
 int pfb_kernel_taps(int log2n, int taps);
