@@ -195,6 +195,30 @@ rfr_status rfr_state_export(rfr_plan* plan, void* host, size_t* bytes);
 rfr_status rfr_state_import(rfr_plan* plan, const void* host, size_t bytes);
 
 /*
+ * rfr_plan_seek -- position a fresh or used plan at absolute sample
+ * start_sample of a stream (a multiple of the hop), as if every sample before
+ * it had been pushed: the next push's first frame is frame start_sample/hop,
+ * with NCO phases taken from the absolute sample index.  `history` (device or
+ * host) holds the n_history = min(H, start_sample) samples just before
+ * start_sample, H = (T-1)*N for the PFB and max(L - D, 0) for demodulation;
+ * earlier samples count as zero.  This is how a
+ * long stream is split along time across plans or GPUs: each shard gets its
+ * slice plus this halo, and the shards' frames concatenate to the one-shot
+ * result bit-identically.  Synchronises the device.
+ */
+rfr_status rfr_plan_seek(rfr_plan* plan, int64_t start_sample, const int16_t* history,
+                         int64_t n_history);
+
+/*
+ * rfr_wait_selftest -- launch a kernel whose bounded device-side wait can
+ * never be satisfied and check that it gives up after limit_ns (1 us .. 2 s)
+ * with the library's timeout status: returns RFR_E_TIMEOUT (and the device
+ * status word in *device_status) when the failure detection works.  Nothing
+ * faults or traps; the context stays usable.
+ */
+rfr_status rfr_wait_selftest(int64_t limit_ns, int32_t* device_status);
+
+/*
  * Prototype taps (host memory): h64 in FP64 (may be NULL), h32 the FP32
  * values the PFB kernels use (may be NULL).  *n receives the length (N*T or
  * L); with both pointers NULL only *n is set.

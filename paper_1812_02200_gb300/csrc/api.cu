@@ -84,6 +84,18 @@ __global__ void carry_update_kernel(const uint32_t* __restrict__ old_carry, int6
     }
 }
 
+// Self-test of the bounded waits: one thread waits on an mbarrier phase that
+// nothing completes; the wait must give up after limit_ns and record
+// DEV_TIMEOUT (no trap, no fault).
+__global__ void wait_selftest_kernel(int* status, uint64_t limit_ns) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        rfr::mbar_init(&bar, 1);
+        rfr::fence_mbar_init();
+        rfr::mbar_wait(&bar, 0, status, limit_ns);   // phase 0 never completes
+    }
+}
+
 int64_t frames_for_len(const rfr_plan* p, int64_t lv) {
     return lv >= p->W ? (lv - p->W) / p->H + 1 : 0;
 }
@@ -605,6 +617,47 @@ rfr_status rfr_process_host(rfr_plan* p, const int16_t* iq_host, int64_t n, rfr_
     p->last_stream = p->stage_st[(i + 1) & 1];
     out->frames = fo - out->frame_offset;
     return check_status(p);
+}
+
+rfr_status rfr_wait_selftest(int64_t limit_ns, int32_t* device_status) {
+    if (limit_ns < 1000 || limit_ns > 2000000000LL) return RFR_E_INVALID;
+    int* d = nullptr;
+    if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return RFR_E_NOMEM;
+    cudaMemset(d, 0, sizeof(int));
+    wait_selftest_kernel<<<1, 32>>>(d, static_cast<uint64_t>(limit_ns));
+    int st = 0;
+    const cudaError_t e1 = cudaGetLastError();
+    const cudaError_t e2 = cudaMemcpy(&st, d, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) return RFR_E_CUDA;
+    if (device_status) *device_status = st;
+    return st == DEV_TIMEOUT ? RFR_E_TIMEOUT : RFR_OK;
+}
+
+rfr_status rfr_plan_seek(rfr_plan* p, int64_t start_sample, const int16_t* history, int64_t n_history) {
+    if (!p || start_sample < 0 || start_sample % p->H != 0 || n_history < 0) return RFR_E_INVALID;
+    const int64_t halo = p->W - p->H;                 // internal window minus hop
+    // history the caller provides: (T-1)*N (PFB) or L - D (demodulation); the
+    // kernel's zero-padded extra taps (if any) see zeros, which they ignore
+    const int64_t user_halo = p->mode == RFR_MODE_PFB ? static_cast<int64_t>(p->T - 1) * p->N
+                                                      : static_cast<int64_t>(p->L) - p->D;
+    const int64_t want = std::min<int64_t>(std::max<int64_t>(user_halo, 0), start_sample);
+    if (n_history != want || (want > 0 && !history))
+        return fail(p, RFR_E_INVALID, "seek: history must hold the min(W - hop, start) samples before start");
+    RFR_CUDA(p, cudaDeviceSynchronize());
+    p->cur = 0;
+    p->q_frames = 0;
+    p->samples = start_sample;
+    p->frames = start_sample / p->H;
+    p->cl = halo;                                     // = W - H (may be <= 0 for L <= D)
+    if (halo > 0) {
+        char* dst = reinterpret_cast<char*>(p->d_carry[0]);
+        const int64_t zeros = halo - want;            // before the stream start
+        if (zeros > 0) RFR_CUDA(p, cudaMemset(dst, 0, static_cast<size_t>(zeros) * 4));
+        if (want > 0)
+            RFR_CUDA(p, cudaMemcpy(dst + zeros * 4, history, static_cast<size_t>(want) * 4, cudaMemcpyDefault));
+    }
+    return RFR_OK;
 }
 
 rfr_status rfr_reset(rfr_plan* p) {

@@ -296,12 +296,16 @@ __global__ void __launch_bounds__(kRingThreads, 1) pfb_tmem_kernel(const PfbArgs
             ok = false;
             break;
         }
+        // planar pairs in TMEM: (re_r, re_r+1, im_r, im_r+1) for even r
         uint32_t xr[32];
 #pragma unroll
-        for (int r = 0; r < 16; ++r) {
-            const float2 f = iq_to_f2(stage[s * N + tf + r * NT]);
-            xr[2 * r] = __float_as_uint(f.x);
-            xr[2 * r + 1] = __float_as_uint(f.y);
+        for (int r = 0; r < 16; r += 2) {
+            const float2 f0 = iq_to_f2(stage[s * N + tf + r * NT]);
+            const float2 f1 = iq_to_f2(stage[s * N + tf + (r + 1) * NT]);
+            xr[2 * r] = __float_as_uint(f0.x);
+            xr[2 * r + 1] = __float_as_uint(f1.x);
+            xr[2 * r + 2] = __float_as_uint(f0.y);
+            xr[2 * r + 3] = __float_as_uint(f1.y);
         }
         umma::st_32x32b_x32(tbase + 32u * static_cast<uint32_t>(b % kTmemSlots), xr);
         __syncthreads();   // staging slot s fully read
@@ -310,20 +314,25 @@ __global__ void __launch_bounds__(kRingThreads, 1) pfb_tmem_kernel(const PfbArgs
         umma::wait_st();
         const int64_t j = b - (T - 1);                           // frame completed by block b
         if (j < ja) continue;                                    // uniform across the CTA
-        float2 v[16];
+        float are[16], aim[16];
 #pragma unroll
-        for (int r = 0; r < 16; ++r) v[r] = make_float2(0.f, 0.f);
+        for (int r = 0; r < 16; ++r) are[r] = aim[r] = 0.f;
 #pragma unroll
         for (int t = 0; t < T; ++t) {
             uint32_t x[32];
             umma::ld_32x32b_x32(tbase + 32u * static_cast<uint32_t>((j + t) % kTmemSlots), x);
             umma::wait_ld();
 #pragma unroll
-            for (int r = 0; r < 16; ++r) {
-                v[r].x = fmaf(hr[t][r], __uint_as_float(x[2 * r]), v[r].x);
-                v[r].y = fmaf(hr[t][r], __uint_as_float(x[2 * r + 1]), v[r].y);
+            for (int r = 0; r < 16; r += 2) {
+                ffma2(are[r], are[r + 1], hr[t][r], hr[t][r + 1], __uint_as_float(x[2 * r]),
+                      __uint_as_float(x[2 * r + 1]));
+                ffma2(aim[r], aim[r + 1], hr[t][r], hr[t][r + 1], __uint_as_float(x[2 * r + 2]),
+                      __uint_as_float(x[2 * r + 3]));
             }
         }
+        float2 v[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = make_float2(are[r], aim[r]);
         fft_frame<LOG2N, true>(v, xbuf, tf, tw);
         if (a.full) {
             float2* row = a.full + (a.frame_offset + j) * a.full_ld;

@@ -98,6 +98,8 @@ _SIGS = {
     "rfr_server_get_stats": (C.c_int, [_P, C.POINTER(ServerStats)]),
     "rfr_server_destroy": (None, [_P]),
     "rfr_now_us": (C.c_double, []),
+    "rfr_plan_seek": (C.c_int, [_P, C.c_int64, _P, C.c_int64]),
+    "rfr_wait_selftest": (C.c_int, [C.c_int64, C.POINTER(C.c_int32)]),
     "rfr_demod_noalloc": (C.c_int, [_P, C.c_int64, _P, C.c_int32, C.c_int32, _P, C.c_int32, _P, C.c_int64, _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -247,6 +249,12 @@ class Plan:
     def reset(self):
         self._check(_lib.rfr_reset(self._h), "reset")
 
+    def seek(self, start_sample: int, history=None):
+        """Start at absolute sample `start_sample` (a multiple of the hop) with
+        `history` = the samples just before it (int16 [n, 2] tensor)."""
+        n = 0 if history is None else history.shape[0]
+        self._check(_lib.rfr_plan_seek(self._h, int(start_sample), _ptr(history), n), "seek")
+
     def autotune(self, n_samples: int, use_cache: bool = True) -> float:
         ms = C.c_double()
         self._check(_lib.rfr_plan_autotune(self._h, int(n_samples), 1 if use_cache else 0,
@@ -312,6 +320,13 @@ class Batch:
         a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
         _lib.rfr_batch_stats(self._h, C.byref(a), C.byref(b), C.byref(c))
         return {"steps": a.value, "graph_updates": b.value, "graph_instantiations": c.value}
+
+
+def wait_selftest(limit_ns: int = 20_000_000):
+    """Returns (status, device_status) of the bounded-wait self-test."""
+    d = C.c_int32()
+    st = _lib.rfr_wait_selftest(int(limit_ns), C.byref(d))
+    return st, d.value
 
 
 def now_us() -> float:
