@@ -46,7 +46,8 @@ DEMOD_SOURCES = ["paper_1812_02200_gb300/csrc/demod.cu", "paper_1812_02200_gb300
                  "paper_1812_02200_gb300/csrc/dev_common.cuh"]
 PFB_SOURCES = ["paper_1812_02200_gb300/csrc/pfb_kernels.cu",
                "paper_1812_02200_gb300/csrc/fft_dev.cuh",
-               "paper_1812_02200_gb300/csrc/dev_common.cuh"]
+               "paper_1812_02200_gb300/csrc/dev_common.cuh",
+               "paper_1812_02200_gb300/csrc/umma.cuh"]
 
 
 def log(*a):
@@ -524,7 +525,7 @@ def run_ours(args, ws, rank, local):
     value = aggregate_rate(ws, args.steps, samples_step, ms_max)
     kernel_ms = ms / args.steps          # fused kernel + the tiny carry-update kernel
     achieved = samples_step * BYTES_PER_SAMPLE / (kernel_ms * 1e-3) / 1e9
-    traffic = profile_traffic("pfb_ring_kernel_c2.md", PFB_SOURCES)
+    traffic = profile_traffic("pfb_tmem_kernel_c2.md", PFB_SOURCES)
 
     # -- plain FP32 GPU form on the same input (FP32 FIR + cuFFT + gather)
     plain = None
@@ -596,7 +597,7 @@ def run_ours(args, ws, rank, local):
         "gpu_launches_note": "fused PFB kernel + carry-update kernel per step",
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": traffic,
-                     "kernel": "pfb_ring_kernel<12,8>",
+                     "kernel": "pfb_tmem_kernel<8> (N=4096 TMA-fed, FP32 delay line in TMEM)",
                      "bytes_per_sample": BYTES_PER_SAMPLE,
                      "peak_kind": f"{peak_kind} (STREAM copy)"},
         "plain_fp32": plain,

@@ -240,7 +240,7 @@ constexpr int kTmemStage = 4;        // staging slots (blocks of 4096 samples)
 constexpr int kTmemSlots = 8;        // delay-line blocks held in TMEM
 
 __host__ __device__ constexpr size_t tmem_smem_bytes(int tw_count, int n_bins_smem) {
-    return static_cast<size_t>(kTmemStage) * 4096 * 4 + static_cast<size_t>(4096 + 256) * 8 +
+    return static_cast<size_t>(kTmemStage) * 4096 * 4 + static_cast<size_t>(2) * (4096 + 256) * 8 +
            static_cast<size_t>((tw_count + 1) & ~1) * 8 + static_cast<size_t>((n_bins_smem + 1) & ~1) * 4 +
            kTmemStage * 8 + 16;
 }
@@ -251,8 +251,11 @@ __global__ void __launch_bounds__(kRingThreads, 1) pfb_tmem_kernel(const PfbArgs
     static_assert(T <= kTmemSlots, "delay line fits in TMEM");
     extern __shared__ __align__(1024) unsigned char smem[];
     uint32_t* stage = reinterpret_cast<uint32_t*>(smem);
-    float2* xbuf = reinterpret_cast<float2*>(smem + static_cast<size_t>(kTmemStage) * N * 4);
-    float2* tw = xbuf + (N + N / 16);
+    // two exchange buffers used alternately (frame parity), so consecutive
+    // passes and frames need only three barriers per frame
+    float2* const xb0 = reinterpret_cast<float2*>(smem + static_cast<size_t>(kTmemStage) * N * 4);
+    float2* const xb1 = xb0 + (N + N / 16);
+    float2* tw = xb1 + (N + N / 16);
     const int nb_smem = a.n_tones <= 4096 ? a.n_tones : 0;
     int32_t* sbins = reinterpret_cast<int32_t*>(tw + ((a.tw_count + 1) & ~1));
     uint64_t* bars = reinterpret_cast<uint64_t*>(sbins + ((nb_smem + 1) & ~1));
@@ -308,12 +311,14 @@ __global__ void __launch_bounds__(kRingThreads, 1) pfb_tmem_kernel(const PfbArgs
             xr[2 * r + 3] = __float_as_uint(f1.y);
         }
         umma::st_32x32b_x32(tbase + 32u * static_cast<uint32_t>(b % kTmemSlots), xr);
-        __syncthreads();   // staging slot s fully read
-        if (tid == 0 && b + kTmemStage < b1)
-            issue_sb_tma(a, b + kTmemStage, need, stage + s * N, &bars[s]);
         umma::wait_st();
         const int64_t j = b - (T - 1);                           // frame completed by block b
-        if (j < ja) continue;                                    // uniform across the CTA
+        if (j < ja) {                                            // uniform across the CTA
+            __syncthreads();                                     // staging slot s fully read
+            if (tid == 0 && b + kTmemStage < b1)
+                issue_sb_tma(a, b + kTmemStage, need, stage + s * N, &bars[s]);
+            continue;
+        }
         float are[16], aim[16];
 #pragma unroll
         for (int r = 0; r < 16; ++r) are[r] = aim[r] = 0.f;
@@ -333,24 +338,52 @@ __global__ void __launch_bounds__(kRingThreads, 1) pfb_tmem_kernel(const PfbArgs
         float2 v[16];
 #pragma unroll
         for (int r = 0; r < 16; ++r) v[r] = make_float2(are[r], aim[r]);
-        fft_frame<LOG2N, true>(v, xbuf, tf, tw);
+        // 4096-point Stockham FFT, 3 radix-16 passes (as fft_frame<12>):
+        // pass 0 -> P, pass 1 P -> Q, pass 2 Q -> registers; spectrum -> P.
+        float2* const P = (j & 1) ? xb1 : xb0;
+        float2* const Q = (j & 1) ? xb0 : xb1;
+        dft16(v);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) P[fpad(16 * tf + r)] = v[r];
+        __syncthreads();                                         // (A) pass 0 written, staging read
+        if (tid == 0 && b + kTmemStage < b1)
+            issue_sb_tma(a, b + kTmemStage, need, stage + s * N, &bars[s]);
+        {
+            const int k = tf & 15;
+#pragma unroll
+            for (int r = 0; r < 16; ++r) v[r] = P[fpad(tf + r * NT)];
+#pragma unroll
+            for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], tw[(r - 1) * 16 + k]);
+            dft16(v);
+            const int base = (tf >> 4) * 256 + k;
+#pragma unroll
+            for (int r = 0; r < 16; ++r) Q[fpad(base + r * 16)] = v[r];
+        }
+        __syncthreads();                                         // (B) pass 1 written
+        {
+#pragma unroll
+            for (int r = 0; r < 16; ++r) v[r] = Q[fpad(tf + r * NT)];
+#pragma unroll
+            for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], tw[240 + (r - 1) * 256 + tf]);
+            dft16(v);                                            // v[r] = bin tf + 256 r
+        }
         if (a.full) {
             float2* row = a.full + (a.frame_offset + j) * a.full_ld;
 #pragma unroll
-            for (int i = 0; i < 16; ++i) row[fft_out_index<LOG2N>(tf, i)] = v[i];
+            for (int i = 0; i < 16; ++i) row[tf + i * NT] = v[i];
         }
         if (a.n_tones > 0) {
-            __syncthreads();
 #pragma unroll
-            for (int i = 0; i < 16; ++i) xbuf[fpad(fft_out_index<LOG2N>(tf, i))] = v[i];
-            __syncthreads();
+            for (int i = 0; i < 16; ++i) P[fpad(tf + i * NT)] = v[i];
+            __syncthreads();                                     // (C) spectrum in P
             float2* col = a.tones + a.frame_offset + j;
             for (int t = tid; t < a.n_tones; t += NT) {
                 const int bin = t < nb_smem ? sbins[t] : __ldg(a.bins + t);
-                col[t * a.tones_ld] = xbuf[fpad(bin)];
+                col[t * a.tones_ld] = P[fpad(bin)];
             }
+        } else {
+            __syncthreads();   // pass-2 reads of Q done before the next frame writes it
         }
-        __syncthreads();   // xbuf reused by the next frame's first pass
     }
     (void)ok;
     umma::fence_before_sync();
