@@ -55,6 +55,8 @@ struct PfbArgs {
     int64_t tones_ld;
     int64_t frame_offset;
     int use_tma;
+    int tones_vec;           // tones rows/offsets 16-byte aligned for grouped stores
+    int nb_smem;             // TMEM variant: tones whose bins and values are staged in smem (0 or n_tones)
     int* status;
     int64_t q_lo, q_hi;      // iteration range
     int64_t iters_per_cta;
@@ -238,11 +240,12 @@ __global__ void __launch_bounds__(kRingThreads, 1) pfb_ring_kernel(const PfbArgs
 // (t = 0..T-1 from zero), so results are bit-identical to them.
 constexpr int kTmemStage = 4;        // staging slots (blocks of 4096 samples)
 constexpr int kTmemSlots = 8;        // delay-line blocks held in TMEM
+constexpr int kToneGroup = 4;        // frames of tone values staged before one store
 
 __host__ __device__ constexpr size_t tmem_smem_bytes(int tw_count, int n_bins_smem) {
     return static_cast<size_t>(kTmemStage) * 4096 * 4 + static_cast<size_t>(2) * (4096 + 256) * 8 +
            static_cast<size_t>((tw_count + 1) & ~1) * 8 + static_cast<size_t>((n_bins_smem + 1) & ~1) * 4 +
-           kTmemStage * 8 + 16;
+           static_cast<size_t>(kToneGroup) * n_bins_smem * 8 + kTmemStage * 8 + 16;
 }
 
 template <int T>
@@ -256,9 +259,11 @@ __global__ void __launch_bounds__(kRingThreads, 1) pfb_tmem_kernel(const PfbArgs
     float2* const xb0 = reinterpret_cast<float2*>(smem + static_cast<size_t>(kTmemStage) * N * 4);
     float2* const xb1 = xb0 + (N + N / 16);
     float2* tw = xb1 + (N + N / 16);
-    const int nb_smem = a.n_tones <= 4096 ? a.n_tones : 0;
+    const int nb_smem = a.nb_smem;
     int32_t* sbins = reinterpret_cast<int32_t*>(tw + ((a.tw_count + 1) & ~1));
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sbins + ((nb_smem + 1) & ~1));
+    // tone values of kToneGroup frames: tstage[q * nb_smem + t]
+    float2* tstage = reinterpret_cast<float2*>(sbins + ((nb_smem + 1) & ~1));
+    uint64_t* bars = reinterpret_cast<uint64_t*>(tstage + static_cast<size_t>(kToneGroup) * nb_smem);
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + kTmemStage);
 
     const int tid = threadIdx.x, warp = tid >> 5, tf = tid;
@@ -376,10 +381,35 @@ __global__ void __launch_bounds__(kRingThreads, 1) pfb_tmem_kernel(const PfbArgs
 #pragma unroll
             for (int i = 0; i < 16; ++i) P[fpad(tf + i * NT)] = v[i];
             __syncthreads();                                     // (C) spectrum in P
-            float2* col = a.tones + a.frame_offset + j;
-            for (int t = tid; t < a.n_tones; t += NT) {
-                const int bin = t < nb_smem ? sbins[t] : __ldg(a.bins + t);
-                col[t * a.tones_ld] = P[fpad(bin)];
+            if (nb_smem == a.n_tones) {
+                // stage this frame's tone values; store kToneGroup frames per
+                // tone at once (full 32-byte sectors instead of 8-byte pieces)
+                const int q = static_cast<int>((j - ja) % kToneGroup);
+                for (int t = tid; t < nb_smem; t += NT) tstage[q * nb_smem + t] = P[fpad(sbins[t])];
+                if (q == kToneGroup - 1 || j == jb - 1) {
+                    __syncthreads();
+                    const int64_t j0 = j - q;                    // first frame of the group
+                    const int nq = q + 1;
+                    float2* base = a.tones + a.frame_offset + j0;
+                    if (a.tones_vec && nq == kToneGroup) {
+                        // 2 threads per tone, 16 bytes (2 frames) each
+                        for (int it = tid; it < 2 * nb_smem; it += NT) {
+                            const int t = it >> 1, h = it & 1;
+                            const float2 v0 = tstage[(2 * h) * nb_smem + t];
+                            const float2 v1 = tstage[(2 * h + 1) * nb_smem + t];
+                            *reinterpret_cast<float4*>(base + static_cast<int64_t>(t) * a.tones_ld + 2 * h) =
+                                make_float4(v0.x, v0.y, v1.x, v1.y);
+                        }
+                    } else {
+                        for (int it = tid; it < nq * nb_smem; it += NT) {
+                            const int t = it / nq, qq = it - t * nq;
+                            base[static_cast<int64_t>(t) * a.tones_ld + qq] = tstage[qq * nb_smem + t];
+                        }
+                    }
+                }
+            } else {
+                float2* col = a.tones + a.frame_offset + j;
+                for (int t = tid; t < a.n_tones; t += NT) col[t * a.tones_ld] = P[fpad(__ldg(a.bins + t))];
             }
         } else {
             __syncthreads();   // pass-2 reads of Q done before the next frame writes it
@@ -487,12 +517,16 @@ cudaError_t launch_direct(PfbArgs a, int n_sms, int max_smem, cudaStream_t st) {
 
 template <int T>
 cudaError_t launch_tmem(PfbArgs a, int n_sms, int max_smem, cudaStream_t st) {
-    const int nb_smem = a.n_tones <= 4096 ? a.n_tones : 0;
-    const size_t smem = tmem_smem_bytes(a.tw_count, nb_smem);
+    a.nb_smem = (a.n_tones > 0 && tmem_smem_bytes(a.tw_count, a.n_tones) <= static_cast<size_t>(max_smem))
+                    ? a.n_tones : 0;
+    const size_t smem = tmem_smem_bytes(a.tw_count, a.nb_smem);
     if (smem > static_cast<size_t>(max_smem)) return cudaErrorInvalidConfiguration;
     const int64_t grid = std::min<int64_t>(a.F, n_sms);
-    a.iters_per_cta = (a.F + grid - 1) / grid;
+    // whole tone groups per CTA, so every CTA's groups start on an even frame
+    a.iters_per_cta = ((a.F + grid - 1) / grid + kToneGroup - 1) / kToneGroup * kToneGroup;
     const int64_t grid2 = (a.F + a.iters_per_cta - 1) / a.iters_per_cta;
+    a.tones_vec = (a.tones != nullptr && (reinterpret_cast<uintptr_t>(a.tones) % 16) == 0 &&
+                   (a.tones_ld % 2) == 0 && (a.frame_offset % 2) == 0) ? 1 : 0;
     auto k = pfb_tmem_kernel<T>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

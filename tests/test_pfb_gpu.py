@@ -272,3 +272,23 @@ def test_c2_full_size_sampled(lib):
         assert np.linalg.norm(got_f - ref["full"]) / np.linalg.norm(ref["full"]) < TOL
         e_t = np.linalg.norm(got_t - ref["tones"], axis=1) / np.linalg.norm(ref["tones"], axis=1)
         assert e_t.max() < TOL, e_t.max()
+
+
+@pytest.mark.parametrize("n_tones,frame_offset", [(1500, 0), (1500, 3), (2048, 0)])
+def test_many_tones_and_offsets(lib, n_tones, frame_offset):
+    """Tone counts that fit the shared-memory tone staging (1500) and one that
+    does not (2048 -> direct stores), at even and odd output frame offsets."""
+    N, T = 4096, 8
+    case = siggen.pfb_case(N * 70, N, n_tones, seed=n_tones + frame_offset, amp=(100.0, 900.0))
+    plan = _plan(lib, N, T, "kaiser", 9.0, case["words"])
+    x = torch.from_numpy(case["x"]).to(DEV)
+    F = plan.frames_for(x.shape[0])
+    fo = torch.zeros((F + frame_offset, N), dtype=torch.complex64, device=DEV)
+    to = torch.zeros((n_tones, F + frame_offset + 1), dtype=torch.complex64, device=DEV)
+    assert plan.push_into(x, fo, to, frame_offset=frame_offset) == F
+    torch.cuda.synchronize()
+    ref = oracle.pfb(case["x"], N, T, _oracle_taps(N, T, "kaiser", 9.0), bins=plan.bins())
+    got_t = to[:, frame_offset:frame_offset + F].cpu().numpy()
+    assert rel_rows(got_t, ref["tones"]).max() < TOL
+    assert np.array_equal(got_t, fo[frame_offset:].cpu().numpy()[:, plan.bins()].T)
+    assert not to[:, :frame_offset].abs().any() and not to[:, frame_offset + F:].abs().any()
