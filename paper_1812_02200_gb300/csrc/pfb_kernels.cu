@@ -57,6 +57,7 @@ struct PfbArgs {
     int use_tma;
     int tones_vec;           // tones rows/offsets 16-byte aligned for grouped stores
     int nb_smem;             // TMEM variant: tones whose bins and values are staged in smem (0 or n_tones)
+    int full_bulk;           // TMEM variant: full rows written by one TMA bulk store each
     int* status;
     int64_t q_lo, q_hi;      // iteration range
     int64_t iters_per_cta;
@@ -350,6 +351,7 @@ __global__ void __launch_bounds__(kRingThreads, 1) pfb_tmem_kernel(const PfbArgs
         dft16(v);
 #pragma unroll
         for (int r = 0; r < 16; ++r) P[fpad(16 * tf + r)] = v[r];
+        if (a.full_bulk && tid == 0) bulk_wait_read_all();     // previous row left Q (= this P's twin)
         __syncthreads();                                         // (A) pass 0 written, staging read
         if (tid == 0 && b + kTmemStage < b1)
             issue_sb_tma(a, b + kTmemStage, need, stage + s * N, &bars[s]);
@@ -372,20 +374,37 @@ __global__ void __launch_bounds__(kRingThreads, 1) pfb_tmem_kernel(const PfbArgs
             for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], tw[240 + (r - 1) * 256 + tf]);
             dft16(v);                                            // v[r] = bin tf + 256 r
         }
-        if (a.full) {
+        // spectrum -> P: unpadded natural order when the full row goes out by
+        // one bulk store, padded otherwise (only the tone gather reads it)
+        const bool bulk = a.full_bulk != 0;
+        if (a.full && !bulk) {
             float2* row = a.full + (a.frame_offset + j) * a.full_ld;
 #pragma unroll
             for (int i = 0; i < 16; ++i) row[tf + i * NT] = v[i];
         }
-        if (a.n_tones > 0) {
+        if (bulk) {
 #pragma unroll
-            for (int i = 0; i < 16; ++i) P[fpad(tf + i * NT)] = v[i];
+            for (int i = 0; i < 16; ++i) P[tf + i * NT] = v[i];
+            fence_proxy_async_smem();
+        }
+        if (bulk || a.n_tones > 0) {
+            if (!bulk) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) P[fpad(tf + i * NT)] = v[i];
+            }
             __syncthreads();                                     // (C) spectrum in P
+            if (bulk && tid == 0) {
+                tma_bulk_s2g(a.full + (a.frame_offset + j) * a.full_ld, P, N * 8);
+                bulk_commit();
+            }
+        }
+        if (a.n_tones > 0) {
             if (nb_smem == a.n_tones) {
                 // stage this frame's tone values; store kToneGroup frames per
                 // tone at once (full 32-byte sectors instead of 8-byte pieces)
                 const int q = static_cast<int>((j - ja) % kToneGroup);
-                for (int t = tid; t < nb_smem; t += NT) tstage[q * nb_smem + t] = P[fpad(sbins[t])];
+                for (int t = tid; t < nb_smem; t += NT)
+                    tstage[q * nb_smem + t] = P[bulk ? sbins[t] : fpad(sbins[t])];
                 if (q == kToneGroup - 1 || j == jb - 1) {
                     __syncthreads();
                     const int64_t j0 = j - q;                    // first frame of the group
@@ -409,12 +428,16 @@ __global__ void __launch_bounds__(kRingThreads, 1) pfb_tmem_kernel(const PfbArgs
                 }
             } else {
                 float2* col = a.tones + a.frame_offset + j;
-                for (int t = tid; t < a.n_tones; t += NT) col[t * a.tones_ld] = P[fpad(__ldg(a.bins + t))];
+                for (int t = tid; t < a.n_tones; t += NT) {
+                    const int bin = __ldg(a.bins + t);
+                    col[t * a.tones_ld] = P[bulk ? bin : fpad(bin)];
+                }
             }
-        } else {
+        } else if (!bulk) {
             __syncthreads();   // pass-2 reads of Q done before the next frame writes it
         }
     }
+    if (a.full_bulk && tid == 0) bulk_wait_all();
     (void)ok;
     umma::fence_before_sync();
     __syncthreads();
@@ -527,6 +550,8 @@ cudaError_t launch_tmem(PfbArgs a, int n_sms, int max_smem, cudaStream_t st) {
     const int64_t grid2 = (a.F + a.iters_per_cta - 1) / a.iters_per_cta;
     a.tones_vec = (a.tones != nullptr && (reinterpret_cast<uintptr_t>(a.tones) % 16) == 0 &&
                    (a.tones_ld % 2) == 0 && (a.frame_offset % 2) == 0) ? 1 : 0;
+    a.full_bulk = (a.full != nullptr && (reinterpret_cast<uintptr_t>(a.full) % 16) == 0 &&
+                   (a.full_ld % 2) == 0) ? 1 : 0;
     auto k = pfb_tmem_kernel<T>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
