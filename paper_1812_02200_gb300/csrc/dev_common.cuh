@@ -112,10 +112,21 @@ __device__ __forceinline__ void tma_prefetch_desc(const void* tmap) {
 // Exact conversion of the two int16 halves of a packed IQ word with integer
 // logic and one FP32 add each: for a 16-bit two's complement value s,
 // (bits(s) ^ 0x8000) | 0x4B400000 read as float is 12582912 + 32768 + s.
+// Flip both sign bits with one XOR, place each half under the exponent
+// 0x4B40 with a byte permute, then subtract 12615680 from both with one packed
+// FP32x2 subtract (exact: every intermediate is an integer below 2^24).
 __device__ __forceinline__ float2 iq_to_f2(uint32_t w) {
-    const float re = __uint_as_float((w & 0xFFFFu) ^ 0x4B408000u) - 12615680.0f;
-    const float im = __uint_as_float((w >> 16) ^ 0x4B408000u) - 12615680.0f;
-    return make_float2(re, im);
+    const uint32_t u = w ^ 0x80008000u;
+    const uint32_t re_bits = __byte_perm(u, 0x4B400000u, 0x7610);
+    const uint32_t im_bits = __byte_perm(u, 0x4B400000u, 0x7632);
+    float2 r;
+    asm("{\n\t.reg .b64 pa, pb, pd;\n\t"
+        "mov.b64 pa, {%2, %3};\n\t"
+        "mov.b64 pb, {%4, %4};\n\t"
+        "sub.rn.f32x2 pd, pa, pb;\n\t"
+        "mov.b64 {%0, %1}, pd;\n\t}"
+        : "=f"(r.x), "=f"(r.y) : "f"(__uint_as_float(re_bits)), "f"(__uint_as_float(im_bits)), "f"(12615680.0f));
+    return r;
 }
 
 // ---------------------------------------------------------------- complex
