@@ -245,6 +245,7 @@ def run_demod(args, dev, stream, rank):
     x = torch.from_numpy(c["x"]).to(dev)
     plan = rfr.Plan(0, DEMOD_L, window="blackman", cutoff=DEMOD_FC, words=c["words"],
                     decimation=DEMOD_D)
+    tune_ms = plan.autotune(x.shape[0], use_cache=False)      # result-neutral choices
     F = plan.frames_for(x.shape[0])
     out = torch.empty((DEMOD_TONES, F), dtype=torch.complex64, device=dev)
     plan.push_into(x, tones=out, stream=stream)
@@ -277,6 +278,7 @@ def run_demod(args, dev, stream, rank):
     achieved = flops / (ms * 1e-3) / 1e12
     res = {"workload": "demod: 2^%d complex int16 samples, 2048 off-bin tones, L=4096 "
                        "Blackman-sinc 40 kHz, D=2048" % args.demod_log2_samples,
+           "tune": plan.tune(),
            "value": samples / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms,
            "rel_err_max_checked_tones": rel,
            "roofline": {"bound": "tensor", "achieved": achieved, "peak": bf16_peak,

@@ -195,6 +195,17 @@ rfr_status rfr_state_export(rfr_plan* plan, void* host, size_t* bytes);
 rfr_status rfr_state_import(rfr_plan* plan, const void* host, size_t bytes);
 
 /*
+ * rfr_plan_set_accum_chunk -- demodulation only: how many 32-tap K blocks
+ * (1..64, default 2) the tensor cores accumulate in TMEM before the epilogue
+ * adds the partial sums into FP32 registers.  Longer chunks are slightly
+ * faster and less accurate (the tensor cores' internal accumulation error
+ * grows with the partial sums); the default keeps the weakest tones of the
+ * 2048-tone workload near 2e-6 relative error.  Changes the results' rounding,
+ * so set it before the first push.
+ */
+rfr_status rfr_plan_set_accum_chunk(rfr_plan* plan, int32_t k_blocks);
+
+/*
  * rfr_plan_seek -- position a fresh or used plan at absolute sample
  * start_sample of a stream (a multiple of the hop), as if every sample before
  * it had been pushed: the next push's first frame is frame start_sample/hop,

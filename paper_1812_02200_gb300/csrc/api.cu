@@ -228,7 +228,7 @@ rfr_status push_core(rfr_plan* p, const int16_t* iq, int64_t n, const rfr_output
                 L.frame_offset = o->frame_offset;
                 L.status = p->d_status;
                 L.n_sms = p->n_sms;
-                L.kchunk = 0;
+                L.kchunk = p->accum_chunk;
                 L.raster_group = p->tune.demod_raster;
                 RFR_CUDA(p, rfr::demod_launch(L, st));
             }
@@ -657,6 +657,12 @@ rfr_status rfr_plan_seek(rfr_plan* p, int64_t start_sample, const int16_t* histo
         if (want > 0)
             RFR_CUDA(p, cudaMemcpy(dst + zeros * 4, history, static_cast<size_t>(want) * 4, cudaMemcpyDefault));
     }
+    return RFR_OK;
+}
+
+rfr_status rfr_plan_set_accum_chunk(rfr_plan* p, int32_t k_blocks) {
+    if (!p || p->mode != RFR_MODE_DEMOD || k_blocks < 1 || k_blocks > 64) return RFR_E_INVALID;
+    p->accum_chunk = k_blocks;
     return RFR_OK;
 }
 

@@ -140,6 +140,7 @@ struct rfr_plan {
     void* d_blo = nullptr;
     int32_t ntp = 0;               // demod tones padded
     int tap_exp = 0;               // demod power-of-two tap scale exponent
+    int accum_chunk = 2;           // demod: K blocks per TMEM accumulation chunk
     int* d_status = nullptr;
 
     // stream state

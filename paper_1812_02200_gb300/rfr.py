@@ -99,6 +99,7 @@ _SIGS = {
     "rfr_server_destroy": (None, [_P]),
     "rfr_now_us": (C.c_double, []),
     "rfr_plan_seek": (C.c_int, [_P, C.c_int64, _P, C.c_int64]),
+    "rfr_plan_set_accum_chunk": (C.c_int, [_P, C.c_int32]),
     "rfr_wait_selftest": (C.c_int, [C.c_int64, C.POINTER(C.c_int32)]),
     "rfr_demod_noalloc": (C.c_int, [_P, C.c_int64, _P, C.c_int32, C.c_int32, _P, C.c_int32, _P, C.c_int64, _P]),
 }
@@ -248,6 +249,9 @@ class Plan:
 
     def reset(self):
         self._check(_lib.rfr_reset(self._h), "reset")
+
+    def set_accum_chunk(self, k_blocks: int):
+        self._check(_lib.rfr_plan_set_accum_chunk(self._h, int(k_blocks)), "set_accum_chunk")
 
     def seek(self, start_sample: int, history=None):
         """Start at absolute sample `start_sample` (a multiple of the hop) with
