@@ -10,7 +10,10 @@ Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 (brute-force DFT, library windows and Bessel function, closed forms for pure
 tones and the Dirichlet kernel, Parseval, linearity, shift, the PFB/demod
 identity for bin-centred tones, integer phase and bin rules, the paper's -6 dB
-cross-over of adjacent channels).  No function is "parity unpinned".
+cross-over of adjacent channels, Eq. 1's chirp phase checked with Python
+integers and against its FP64 formula, the zero-rate chirp equal to the NCO
+demodulator, a chirp demodulated against itself).  No function is "parity
+unpinned".
 """
 from __future__ import annotations
 
@@ -66,6 +69,10 @@ def _load():
             "orc_pfb_i16": (C.c_int, [P, i64, i32, i32, P, i64, i64, P, P, i32, P]),
             "orc_demod_f64": (C.c_int, [P, i64, i32, i32, P, P, i32, i64, i64, P]),
             "orc_demod_i16": (C.c_int, [P, i64, i32, i32, P, P, i32, i64, i64, P]),
+            "orc_chirp_phase": (u64, [u64, u64, i64]),
+            "orc_chirp_rate_word": (u64, [dbl, dbl]),
+            "orc_chirp_synth": (C.c_int, [u64, u64, dbl, i64, i64, P]),
+            "orc_chirp_demod_i16": (C.c_int, [P, i64, i32, i32, P, P, P, i32, i64, i64, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -191,4 +198,37 @@ def demod(x: np.ndarray, L: int, D: int, h: np.ndarray, words, k_begin: int = 0,
         xc = np.ascontiguousarray(x, np.complex128)
         rc = lib.orc_demod_f64(_ptr(xc), n, L, D, _ptr(h), _ptr(w), len(w), k_begin, k_end, _ptr(out))
     _check(rc, "demod")
+    return out
+
+
+def chirp_phase(start_word: int, rate_word: int, m: int) -> int:
+    """Eq. 1 in sample units: start*m + rate*m^2 mod 2^64."""
+    return int(_load().orc_chirp_phase(int(start_word) & (2 ** 64 - 1), int(rate_word) & (2 ** 64 - 1), int(m)))
+
+
+def chirp_rate_word(k_hz_per_s: float, fs: float) -> int:
+    return int(_load().orc_chirp_rate_word(float(k_hz_per_s), float(fs)))
+
+
+def chirp_synth(start_word: int, rate_word: int, amp: float, m0: int, n: int) -> np.ndarray:
+    out = np.empty((n, 2), np.int16)
+    _check(_load().orc_chirp_synth(int(start_word) & (2 ** 64 - 1), int(rate_word) & (2 ** 64 - 1),
+                                   float(amp), int(m0), int(n), _ptr(out)), "chirp_synth")
+    return out
+
+
+def chirp_demod(x: np.ndarray, L: int, D: int, h: np.ndarray, start_words, rate_words,
+                k_begin: int = 0, k_end: int | None = None) -> np.ndarray:
+    """Demodulation against chirps; x int16 [n, 2]; returns complex128 [n_chirps, nk]."""
+    lib = _load()
+    h = np.ascontiguousarray(h, np.float64)
+    sw = np.ascontiguousarray(np.asarray(start_words, dtype=np.uint64))
+    rw = np.ascontiguousarray(np.asarray(rate_words, dtype=np.uint64))
+    n = x.shape[0]
+    if k_end is None:
+        k_end = n // D
+    out = np.empty((len(sw), k_end - k_begin), np.complex128)
+    xi = np.ascontiguousarray(x, np.int16)
+    _check(lib.orc_chirp_demod_i16(_ptr(xi), n, L, D, _ptr(h), _ptr(sw), _ptr(rw), len(sw), k_begin,
+                                   k_end, _ptr(out)), "chirp_demod")
     return out

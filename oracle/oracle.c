@@ -368,3 +368,77 @@ int orc_demod_i16(const int16_t* iq, int64_t n_samples, int32_t L, int32_t D,
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Chirped readout (Sec. III.C, Eq. 1)                                       */
+/* ------------------------------------------------------------------------ */
+
+/* Eq. 1 in sample units: phi(m) = 2*pi*(f0*t + k*t^2) with t = m/fs becomes
+ * the uint64 phase  p(m) = s*m + r*m^2  (mod 2^64)  in units of 2*pi/2^64,
+ * with s = f0/fs * 2^64 (a start word) and r = k/fs^2 * 2^64 (a rate word).
+ * m may be negative (two's complement, reduced mod 2^64). */
+uint64_t orc_chirp_phase(uint64_t start_word, uint64_t rate_word, int64_t m)
+{
+    const uint64_t um = (uint64_t)m;
+    return start_word * um + rate_word * (um * um);
+}
+
+/* The rate word of a chirp rate k (Hz/s) at sample rate fs: k/fs^2 * 2^64,
+ * rounded to nearest (two's complement for negative rates). */
+uint64_t orc_chirp_rate_word(double k_hz_per_s, double fs)
+{
+    return (uint64_t)(int64_t)llround(ldexp(k_hz_per_s / (fs * fs), 64));
+}
+
+/* Transmit buffer of a chirp of amplitude A (Sec. III.C: generated in real
+ * time instead of stored): samples m0 .. m0+n-1 as complex int16
+ * (round half to even of A*cos(theta), A*sin(theta), theta = 2*pi*p(m)/2^64,
+ * clamped to the int16 range). */
+int orc_chirp_synth(uint64_t start_word, uint64_t rate_word, double amp, int64_t m0, int64_t n,
+                    int16_t* iq)
+{
+    if (n < 0 || !iq) return -1;
+    for (int64_t i = 0; i < n; ++i) {
+        const uint64_t p = orc_chirp_phase(start_word, rate_word, m0 + i);
+        const double a = (double)(int64_t)p * ldexp(M_PI, -63);
+        double re = nearbyint(amp * cos(a)), im = nearbyint(amp * sin(a));
+        if (re > 32767.0) re = 32767.0;
+        if (re < -32768.0) re = -32768.0;
+        if (im > 32767.0) im = 32767.0;
+        if (im < -32768.0) im = -32768.0;
+        iq[2 * i] = (int16_t)re;
+        iq[2 * i + 1] = (int16_t)im;
+    }
+    return 0;
+}
+
+/* Demodulation against chirps (Sec. III.C, "using the algorithm outlined in
+ * section III.B"): as orc_demod_i16 with the linear NCO phase replaced by the
+ * chirp phase p(m): for each chirp s and frame k, b_k = (k+1)*D - L,
+ *   out[s][k] = sum_{n<L} h[n] * x[b_k+n] * exp(-i*2*pi*p_s(b_k+n)/2^64). */
+int orc_chirp_demod_i16(const int16_t* iq, int64_t n_samples, int32_t L, int32_t D, const double* h,
+                        const uint64_t* start_words, const uint64_t* rate_words, int32_t n_sel,
+                        int64_t k_begin, int64_t k_end, double* out)
+{
+    if (!iq || L <= 0 || D <= 0 || k_end < k_begin || k_end * (int64_t)D > n_samples) return -1;
+    if (n_sel > 0 && (!start_words || !rate_words || !out)) return -1;
+    const int64_t nk = k_end - k_begin;
+    for (int32_t s = 0; s < n_sel; ++s) {
+        for (int64_t k = k_begin; k < k_end; ++k) {
+            const int64_t b = (k + 1) * (int64_t)D - L;
+            double ar = 0.0, ai = 0.0;
+            for (int64_t n = 0; n < L; ++n) {
+                const int64_t m = b + n;
+                if (m < 0) continue;
+                double cr, ci;
+                orc_mixer(orc_chirp_phase(start_words[s], rate_words[s], m), &cr, &ci);
+                const double xr = (double)iq[2 * m], xi = (double)iq[2 * m + 1];
+                ar += h[n] * (xr * cr - xi * ci);
+                ai += h[n] * (xr * ci + xi * cr);
+            }
+            out[2 * ((int64_t)s * nk + (k - k_begin))] = ar;
+            out[2 * ((int64_t)s * nk + (k - k_begin)) + 1] = ai;
+        }
+    }
+    return 0;
+}

@@ -302,3 +302,55 @@ def test_demod_int16_matches_f64():
     assert np.array_equal(a, b)
     s = oracle.demod(xi, L, D, h, ws, k_begin=4, k_end=20)
     assert np.array_equal(s, a[:, 4:20])
+
+
+# ----------------------------------------------------------- chirp pins
+def test_chirp_phase_is_eq1_in_sample_units():
+    """Eq. 1, phi_t = 2 pi (f0 t + k t^2), sampled at t = m/fs: the uint64
+    phase start*m + rate*m^2 (mod 2^64) with start = f0/fs*2^64, rate =
+    k/fs^2*2^64; checked with Python integers and against the FP64 formula."""
+    fs, f0, k = 100e6, 3.1e6, 2.5e12            # 2.5 MHz/us sweep
+    s = oracle.freq_to_word(f0, fs)
+    r = oracle.chirp_rate_word(k, fs)
+    for m in (0, 1, 7, 1000, 123457, -5):
+        assert oracle.chirp_phase(s, r, m) == (s * m + r * m * m) % 2 ** 64
+    for m in (0, 10, 1000, 20000):
+        t = m / fs
+        turns = (f0 * t + k * t * t) % 1.0
+        got = oracle.chirp_phase(s, r, m) / 2 ** 64
+        d = abs(got - turns)
+        assert min(d, 1 - d) < 1e-9
+    # instantaneous frequency: first difference = start + rate*(2m+1) exactly
+    for m in (0, 99, 4096):
+        d = (oracle.chirp_phase(s, r, m + 1) - oracle.chirp_phase(s, r, m)) % 2 ** 64
+        assert d == (s + r * (2 * m + 1)) % 2 ** 64
+
+
+def test_chirp_with_zero_rate_is_the_nco_demodulator():
+    L, D = 64, 16
+    rng = np.random.default_rng(9)
+    x = rng.integers(-8192, 8192, size=(D * 40, 2)).astype(np.int16)
+    h = oracle.lowpass("hann", L, 0.03)
+    ws = [int(v) for v in rng.integers(0, 2 ** 64, 3, dtype=np.uint64)]
+    a = oracle.chirp_demod(x, L, D, h, ws, [0, 0, 0])
+    b = oracle.demod(x, L, D, h, ws)
+    assert np.array_equal(a, b)
+
+
+def test_chirp_loopback_own_chirp_is_constant():
+    """A chirp demodulated against itself (square window) gives A*e^{i0}
+    apart from the rounding of the synthesised int16 samples."""
+    L = D = 128
+    s = oracle.freq_to_word(0.01, 1.0)
+    r = oracle.chirp_rate_word(1e-6, 1.0)
+    amp = 6000.0
+    x = oracle.chirp_synth(s, r, amp, 0, D * 30)
+    h = oracle.lowpass("rect", L, 0.0)
+    out = oracle.chirp_demod(x, L, D, h, [s], [r])[0]
+    assert np.allclose(out, amp, atol=0.5)        # int16 rounding: |err| <= 0.5*sqrt(2)/sqrt(L)-ish
+    # synthesis matches the FP64 formula up to rounding
+    m = np.arange(D * 30)
+    ph = np.array([oracle.chirp_phase(s, r, int(i)) for i in m], dtype=np.uint64)
+    th = ph.view(np.int64).astype(np.float64) * (np.pi / 2 ** 63)
+    assert np.all(np.abs(x[:, 0] - amp * np.cos(th)) <= 0.5 + 1e-9)
+    assert np.all(np.abs(x[:, 1] - amp * np.sin(th)) <= 0.5 + 1e-9)
