@@ -79,7 +79,7 @@ typedef struct {
 } rfr_tones;
 
 enum { RFR_OUT_FULL = 1, RFR_OUT_TONES = 2 };
-enum { RFR_MODE_PFB = 1, RFR_MODE_DEMOD = 2 };
+enum { RFR_MODE_PFB = 1, RFR_MODE_DEMOD = 2, RFR_MODE_CHIRP = 3 };
 
 /* Caller-owned output buffers of one push (device memory).
  *   full : complex64 [frames][full_ld], channel c of frame f at
@@ -102,7 +102,7 @@ typedef struct {
 } rfr_output;
 
 typedef struct {
-    int32_t mode;           /* RFR_MODE_PFB or RFR_MODE_DEMOD */
+    int32_t mode;           /* RFR_MODE_PFB, RFR_MODE_DEMOD or RFR_MODE_CHIRP */
     int32_t channels;       /* N (PFB) or 0 */
     int32_t taps;           /* T per channel (PFB) or L (demodulation) */
     int32_t decimation;     /* hop: N (PFB) or D */
@@ -135,6 +135,40 @@ typedef struct {
 rfr_status rfr_plan_create(rfr_plan** plan, int32_t channels, int32_t taps,
                            const rfr_window* window, const rfr_tones* tones,
                            int32_t decimation, uint32_t out_flags);
+
+/*
+ * Chirped readout (Sec. III.C, Eq. 1).  Eq. 1, phi_t = 2*pi*(f0*t + k*t^2), in
+ * sample units t = m/fs is the exact uint64 phase
+ *     p(m) = start*m + rate*m^2  (mod 2^64, units of 2*pi/2^64),
+ * start = rfr_freq_to_word(f0, fs), rate = rfr_chirp_rate_word(k, fs).
+ *
+ * rfr_plan_create_chirp -- a plan that demodulates the stream against
+ * n_chirps chirps (the algorithm of Sec. III.B with the chirp as the mixer):
+ * for chirp c and frame k (b_k = (k+1)*D - L, zero history)
+ *     out[c][k] = sum_{n<L} h[n] x[b_k+n] exp(-i*2*pi*p_c(b_k+n)/2^64),
+ * h the low-pass of `window` (as for demodulation; cut-off 0 = pure window).
+ * Output layout and streaming as for demodulation plans (RFR_OUT_TONES, one
+ * row per chirp).  1 <= L <= 16384, 1 <= D, 1 <= n_chirps <= 4096; start and
+ * rate words are host arrays, copied.
+ */
+rfr_status rfr_plan_create_chirp(rfr_plan** plan, int32_t taps, const rfr_window* window,
+                                 const uint64_t* start_words, const uint64_t* rate_words,
+                                 int32_t n_chirps, int32_t decimation);
+
+/* Rate word of a chirp rate k (Hz/s) at sample rate fs: round(k/fs^2 * 2^64). */
+uint64_t rfr_chirp_rate_word(double k_hz_per_s, double fs_hz);
+
+/*
+ * rfr_chirp_synthesize -- the transmit buffer of a chirp generated on the
+ * GPU in real time (Sec. III.C): samples m0 .. m0+n-1 of
+ *     x[m] = (round(A*cos(2*pi*p(m)/2^64)), round(A*sin(2*pi*p(m)/2^64)))
+ * as complex int16 (round half to even, clamped to the int16 range) into the
+ * device buffer iq_out [n][2].  Computed in FP32; samples within 0.02 of a
+ * rounding tie are recomputed in FP64, so every sample is the FP64-rounded
+ * value.  0 <= amplitude <= 32767.  Asynchronous on `stream`.
+ */
+rfr_status rfr_chirp_synthesize(uint64_t start_word, uint64_t rate_word, double amplitude, int64_t m0,
+                                int64_t n_samples, int16_t* iq_out, void* stream);
 
 /* Frees everything the plan owns (waits for its outstanding work). */
 void rfr_plan_destroy(rfr_plan* plan);
@@ -245,6 +279,8 @@ rfr_status rfr_plan_get_bins(const rfr_plan* plan, int32_t* bins, int32_t* count
  * gather kernel; demodulation as an FP32 CUDA-core kernel.  Processes one
  * whole buffer with zero history (does not touch the plan's stream state).
  * Scratch is allocated by the call on first use and cached in the plan.
+ * Chirp plans have no separate plain form (RFR_E_UNSUPPORTED): their kernel
+ * already is plain FP32 CUDA-core code.
  */
 rfr_status rfr_plain_oneshot(rfr_plan* plan, const int16_t* iq, int64_t n_samples,
                              rfr_output* out, void* stream);

@@ -106,7 +106,7 @@ bool out_ok(const rfr_plan* p, const rfr_output* o, int64_t F) {
     if (p->mode == RFR_MODE_PFB && (p->out_flags & RFR_OUT_FULL)) {
         if (!o->full || o->full_ld < p->N || o->full_cap < o->frame_offset + F) return false;
     }
-    const bool want_tones = p->mode == RFR_MODE_DEMOD || (p->out_flags & RFR_OUT_TONES);
+    const bool want_tones = p->mode != RFR_MODE_PFB || (p->out_flags & RFR_OUT_TONES);
     if (want_tones && !p->words.empty()) {
         if (!o->tones || o->tones_cap < o->frame_offset + F || o->tones_ld < o->frame_offset + F)
             return false;
@@ -198,6 +198,24 @@ rfr_status push_core(rfr_plan* p, const int16_t* iq, int64_t n, const rfr_output
             L.max_smem = p->max_smem;
             L.lookahead = p->tune.pfb_lookahead;
             RFR_CUDA(p, rfr::pfb_launch(L, st));
+        } else if (p->mode == RFR_MODE_CHIRP) {
+            rfr::ChirpLaunch L{};
+            L.carry = carry;
+            L.cl = p->cl;
+            L.buf = iq;
+            L.F = F;
+            L.a0 = p->samples - p->cl;
+            L.L = p->L;
+            L.D = p->D;
+            L.h32 = p->d_h32;
+            L.start_words = p->d_words;
+            L.rate_words = p->d_rates;
+            L.n_chirps = static_cast<int>(p->words.size());
+            L.tones = o->tones;
+            L.tones_ld = o->tones_ld;
+            L.frame_offset = o->frame_offset;
+            L.n_sms = p->n_sms;
+            RFR_CUDA(p, rfr::chirp_demod_launch(L, st));
         } else {
             if (!p->words.empty()) {
                 rfr_status rs = ensure_demod_scratch(p, F, p->frames);
@@ -271,7 +289,7 @@ void destroy(rfr_plan* p) {
     if (!p) return;
     cudaDeviceSynchronize();
     for (void* q : {static_cast<void*>(p->d_h), p->d_tw, static_cast<void*>(p->d_bins),
-                    static_cast<void*>(p->d_words), static_cast<void*>(p->d_h32), p->d_c32, p->d_bhi, p->d_blo,
+                    static_cast<void*>(p->d_words), static_cast<void*>(p->d_rates), static_cast<void*>(p->d_h32), p->d_c32, p->d_bhi, p->d_blo,
                     static_cast<void*>(p->d_status), static_cast<void*>(p->d_carry[0]),
                     static_cast<void*>(p->d_carry[1]), p->d_xs_hi, p->d_xs_lo, p->d_rot, p->d_qfull,
                     p->d_qtones})
@@ -451,13 +469,80 @@ rfr_status rfr_plan_create(rfr_plan** out, int32_t channels, int32_t taps, const
     return RFR_OK;
 }
 
+rfr_status rfr_plan_create_chirp(rfr_plan** out, int32_t taps, const rfr_window* window,
+                                 const uint64_t* start_words, const uint64_t* rate_words, int32_t n_chirps,
+                                 int32_t decimation) {
+    if (!out || !window || !start_words || !rate_words) return RFR_E_INVALID;
+    *out = nullptr;
+    if (window->kind < RFR_WIN_RECT || window->kind > RFR_WIN_KAISER || !(window->cutoff >= 0.0) ||
+        !(window->cutoff < 0.5) || !std::isfinite(window->beta))
+        return RFR_E_INVALID;
+    if (taps < 1 || taps > 16384 || decimation < 1 || decimation > (1 << 24) || n_chirps < 1 || n_chirps > 4096)
+        return RFR_E_INVALID;
+    rfr_plan* p = new (std::nothrow) rfr_plan();
+    if (!p) return RFR_E_NOMEM;
+    p->mode = RFR_MODE_CHIRP;
+    p->window = *window;
+    p->out_flags = RFR_OUT_TONES;
+    p->words.assign(start_words, start_words + n_chirps);
+    p->rates.assign(rate_words, rate_words + n_chirps);
+    cudaGetDevice(&p->device);
+    cudaDeviceGetAttribute(&p->n_sms, cudaDevAttrMultiProcessorCount, p->device);
+    cudaDeviceGetAttribute(&p->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+    p->L = taps;
+    p->D = decimation;
+    p->h64.resize(taps);
+    if (rfr::build_lowpass(window->kind, window->beta, window->cutoff, taps, p->h64.data()) != 0) {
+        destroy(p);
+        return RFR_E_INVALID;
+    }
+    p->h32.resize(taps);
+    for (int j = 0; j < taps; ++j) p->h32[j] = static_cast<float>(p->h64[j]);
+    p->W = taps;
+    p->H = decimation;
+    p->carry_cap = std::max<int64_t>(taps, 1);
+    cudaError_t e = cudaSuccess;
+    if ((e = dev_alloc(&p->d_words, static_cast<size_t>(n_chirps) * 8)) != cudaSuccess ||
+        (e = dev_alloc(&p->d_rates, static_cast<size_t>(n_chirps) * 8)) != cudaSuccess ||
+        (e = dev_alloc(&p->d_h32, static_cast<size_t>(taps) * 4)) != cudaSuccess ||
+        (e = dev_alloc(&p->d_status, sizeof(int))) != cudaSuccess ||
+        (e = dev_alloc(&p->d_carry[0], static_cast<size_t>(p->carry_cap) * 4)) != cudaSuccess ||
+        (e = dev_alloc(&p->d_carry[1], static_cast<size_t>(p->carry_cap) * 4)) != cudaSuccess) {
+        const rfr_status st = cuda_fail(p, e, "plan alloc");
+        destroy(p);
+        return st;
+    }
+    cudaMemcpy(p->d_words, start_words, static_cast<size_t>(n_chirps) * 8, cudaMemcpyHostToDevice);
+    cudaMemcpy(p->d_rates, rate_words, static_cast<size_t>(n_chirps) * 8, cudaMemcpyHostToDevice);
+    cudaMemcpy(p->d_h32, p->h32.data(), static_cast<size_t>(taps) * 4, cudaMemcpyHostToDevice);
+    if (reset_state(p) != RFR_OK || cudaDeviceSynchronize() != cudaSuccess) {
+        destroy(p);
+        return RFR_E_CUDA;
+    }
+    *out = p;
+    return RFR_OK;
+}
+
+uint64_t rfr_chirp_rate_word(double k_hz_per_s, double fs_hz) {
+    return static_cast<uint64_t>(static_cast<int64_t>(std::llround(std::ldexp(k_hz_per_s / (fs_hz * fs_hz), 64))));
+}
+
+rfr_status rfr_chirp_synthesize(uint64_t start_word, uint64_t rate_word, double amplitude, int64_t m0,
+                                int64_t n, int16_t* iq_out, void* stream) {
+    if (n < 0 || (n > 0 && !iq_out) || !(amplitude >= 0.0) || amplitude > 32767.0) return RFR_E_INVALID;
+    return rfr::chirp_synth(start_word, rate_word, amplitude, m0, n, iq_out, static_cast<cudaStream_t>(stream)) ==
+                   cudaSuccess
+               ? RFR_OK
+               : RFR_E_CUDA;
+}
+
 void rfr_plan_destroy(rfr_plan* p) { destroy(p); }
 
 rfr_status rfr_plan_get_info(const rfr_plan* p, rfr_plan_info* info) {
     if (!p || !info) return RFR_E_INVALID;
     info->mode = p->mode;
     info->channels = p->N;
-    info->taps = p->mode == RFR_MODE_PFB ? p->T : p->L;
+    info->taps = p->mode == RFR_MODE_PFB ? p->T : p->L;   // L for demodulation and chirps
     info->decimation = static_cast<int32_t>(p->H);
     info->n_tones = static_cast<int32_t>(p->words.size());
     info->out_flags = p->out_flags;
@@ -746,6 +831,7 @@ rfr_status rfr_plan_get_bins(const rfr_plan* p, int32_t* bins, int32_t* count) {
 
 rfr_status rfr_plain_oneshot(rfr_plan* p, const int16_t* iq, int64_t n, rfr_output* out, void* stream) {
     if (!p || !out || n < 0 || (n > 0 && !iq)) return RFR_E_INVALID;
+    if (p->mode == RFR_MODE_CHIRP) return fail(p, RFR_E_UNSUPPORTED, "no plain form for chirp plans");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // zero history: frame k uses samples ((k+1)*hop - W, (k+1)*hop]
     const int64_t W = p->mode == RFR_MODE_PFB ? static_cast<int64_t>(p->N) * p->T : p->L;

@@ -88,6 +88,26 @@ cudaError_t demod_launch(const DemodLaunch& L, cudaStream_t st);
 size_t demod_xs_rows(int64_t F, int Lpad, int D);
 int demod_anchor_rows(int64_t F0, int64_t F);
 
+// -------------------------------------------------------------- chirp
+struct ChirpLaunch {
+    const int16_t* carry;
+    int64_t cl;
+    const int16_t* buf;
+    int64_t F;
+    int64_t a0;
+    int L, D;
+    const float* h32;
+    const uint64_t* start_words;
+    const uint64_t* rate_words;
+    int n_chirps;
+    void* tones;
+    int64_t tones_ld, frame_offset;
+    int n_sms;
+};
+cudaError_t chirp_synth(uint64_t start_word, uint64_t rate_word, double amp, int64_t m0, int64_t n,
+                        void* out, cudaStream_t st);
+cudaError_t chirp_demod_launch(const ChirpLaunch& L, cudaStream_t st);
+
 // -------------------------------------------------------------- plain
 cudaError_t plain_pfb(const int16_t* iq, int64_t n, int N, int T, const float* h, const int32_t* bins,
                       int n_tones, void* full, int64_t full_ld, void* tones, int64_t tones_ld,
@@ -134,6 +154,8 @@ struct rfr_plan {
     int tw_count = 0;
     int32_t* d_bins = nullptr;
     uint64_t* d_words = nullptr;
+    uint64_t* d_rates = nullptr;   // chirp mode: rate words (d_words holds the start words)
+    std::vector<uint64_t> rates;
     float* d_h32 = nullptr;        // taps as FP32 (plain forms)
     void* d_c32 = nullptr;         // plain demod: FP32 modulated taps [tones][L]
     void* d_bhi = nullptr;         // demod modulated taps, fp16 hi/lo

@@ -101,6 +101,10 @@ _SIGS = {
     "rfr_plan_seek": (C.c_int, [_P, C.c_int64, _P, C.c_int64]),
     "rfr_plan_set_accum_chunk": (C.c_int, [_P, C.c_int32]),
     "rfr_wait_selftest": (C.c_int, [C.c_int64, C.POINTER(C.c_int32)]),
+    "rfr_plan_create_chirp": (C.c_int, [C.POINTER(_P), C.c_int32, C.POINTER(Window), _P, _P, C.c_int32,
+                                        C.c_int32]),
+    "rfr_chirp_rate_word": (C.c_uint64, [C.c_double, C.c_double]),
+    "rfr_chirp_synthesize": (C.c_int, [C.c_uint64, C.c_uint64, C.c_double, C.c_int64, C.c_int64, _P, _P]),
     "rfr_demod_noalloc": (C.c_int, [_P, C.c_int64, _P, C.c_int32, C.c_int32, _P, C.c_int32, _P, C.c_int64, _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -137,8 +141,39 @@ def _ptr(t):
     return None if t is None else t.data_ptr()
 
 
+def chirp_rate_word(k_hz_per_s: float, fs_hz: float) -> int:
+    return int(_lib.rfr_chirp_rate_word(float(k_hz_per_s), float(fs_hz)))
+
+
+def chirp_synthesize(start_word: int, rate_word: int, amplitude: float, m0: int, out, stream=None):
+    """Chirp transmit buffer (Sec. III.C) into the int16 [n, 2] device tensor `out`."""
+    st = _lib.rfr_chirp_synthesize(int(start_word) & (2 ** 64 - 1), int(rate_word) & (2 ** 64 - 1),
+                                   float(amplitude), int(m0), out.shape[0], out.data_ptr(), _stream_ptr(stream))
+    if st != OK:
+        raise RfrError(st, "rfr_chirp_synthesize")
+
+
 class Plan:
-    """A PFB (channels > 0) or direct-demodulation (channels == 0) plan."""
+    """A PFB (channels > 0) or direct-demodulation (channels == 0) plan; a
+    chirp-demodulation plan with Plan.chirp(...)."""
+
+    @classmethod
+    def chirp(cls, taps: int, start_words, rate_words, *, window: str = "rect", beta: float = 0.0,
+              cutoff: float = 0.0, decimation: int):
+        self = cls.__new__(cls)
+        sw = np.ascontiguousarray(np.asarray(start_words, dtype=np.uint64))
+        rw = np.ascontiguousarray(np.asarray(rate_words, dtype=np.uint64))
+        w = Window(WIN[window], float(beta), float(cutoff))
+        h = _P()
+        st = _lib.rfr_plan_create_chirp(C.byref(h), int(taps), C.byref(w), sw.ctypes.data, rw.ctypes.data,
+                                        len(sw), int(decimation))
+        if st != OK:
+            raise RfrError(st, "rfr_plan_create_chirp")
+        self._h = h
+        self.words, self.rates = sw, rw
+        self.channels, self.taps, self.decimation = 0, taps, decimation
+        self.out_flags, self.n_tones = OUT_TONES, len(sw)
+        return self
 
     def __init__(self, channels: int, taps: int, *, window: str = "hann", beta: float = 0.0,
                  cutoff: float = 0.0, words=None, decimation: int | None = None,
