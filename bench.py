@@ -318,6 +318,57 @@ def run_demod(args, dev, stream, rank):
     return res
 
 
+# ------------------------------------------------------------------- chirp
+def run_chirp(args, dev, stream):
+    """Chirped readout (Sec. III.C): synthesis of a 2^28-sample transmit chirp
+    on the GPU (HBM-bound: 4 B written per sample), and demodulation of a
+    2^26-sample stream against 8 chirps (L = 4096 Blackman, D = 2048)."""
+    import torch
+
+    from paper_1812_02200_gb300 import rfr
+    hbm_peak = measured_peaks()[0]
+    fs = 200e6
+    s0, r0 = rfr.freq_to_word(-90e6, fs), rfr.chirp_rate_word(1.8e8 / 1.34, fs)   # -90..+90 MHz in 1.34 s
+    n = 1 << 28
+    tx = torch.empty((n, 2), dtype=torch.int16, device=dev)
+    rfr.chirp_synthesize(s0, r0, 8000.0, 0, tx, stream=stream)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(5):
+        rfr.chirp_synthesize(s0, r0, 8000.0, i * n, tx, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_syn = e0.elapsed_time(e1) / 5
+    del tx
+    r = np.random.default_rng(3)
+    sw = [rfr.freq_to_word(f, fs) for f in r.uniform(-80e6, 80e6, 8)]
+    rw = [rfr.chirp_rate_word(k, fs) for k in r.uniform(-5e13, 5e13, 8)]
+    c = siggen.c3(n=1 << 26, n_tones=256)
+    x = torch.from_numpy(c["x"]).to(dev)
+    plan = rfr.Plan.chirp(DEMOD_L, sw, rw, window="blackman", cutoff=DEMOD_FC, decimation=DEMOD_D)
+    F = plan.frames_for(x.shape[0])
+    out = torch.empty((8, F), dtype=torch.complex64, device=dev)
+    plan.push_into(x, tones=out, stream=stream)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(3):
+        plan.push_into(x, tones=out, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_dem = e0.elapsed_time(e1) / 3
+    res = {"synthesis": {"workload": "2^28-sample complex int16 chirp, -90..+90 MHz sweep at 200 Ms/s",
+                         "value": n / (ms_syn * 1e-3) / 1e6, "unit": UNIT, "ms": ms_syn,
+                         "roofline": {"bound": "hbm", "achieved": 4.0 * n / (ms_syn * 1e-3) / 1e9,
+                                      "peak": hbm_peak, "unit": "GB/s",
+                                      "frac": 4.0 * n / (ms_syn * 1e-3) / 1e9 / hbm_peak}},
+           "demod": {"workload": "2^26 samples against 8 chirps, L=4096 Blackman-sinc, D=2048",
+                     "value": x.shape[0] / (ms_dem * 1e-3) / 1e6, "unit": UNIT, "ms": ms_dem}}
+    plan.close()
+    del x, out
+    return res
+
+
 # ------------------------------------------------------------------- batch
 def make_spec_plan(rfr, spec, words, full=False):
     if spec["kind"] == "pfb":
@@ -587,6 +638,7 @@ def run_ours(args, ws, rank, local):
     torch.cuda.empty_cache()
     if not args.no_demod:
         demod = run_demod(args, dev, stream, rank)
+    chirp = None if args.no_chirp else run_chirp(args, dev, stream)
     batch = None if args.no_batch else run_batch(args, dev, stream)
     torch.cuda.empty_cache()
     serve = None if (args.no_serve or ws > 1) else run_serve(args, dev)
@@ -615,6 +667,7 @@ def run_ours(args, ws, rank, local):
         "demod": demod,
         "batch": batch,
         "serve": serve,
+        "chirp": chirp,
         "e2e": e2e,
         "cpu_baseline": cpu,
         "clocks": clk,
@@ -635,6 +688,7 @@ def main():
     ap.add_argument("--no-demod", action="store_true")
     ap.add_argument("--demod-log2-samples", type=int, default=27)
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-chirp", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-loads", default="1,5,10,20", help="offered loads, Gsamples/s")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
