@@ -7,19 +7,21 @@
 // chirp_synth_kernel: the transmit buffer generated on the GPU in real time
 // (instead of a stored table): round-half-even of A*cos, A*sin of the phase,
 // as complex int16.  The sine and cosine are computed in FP32 (the paper's
-// "32 bit precision"); a sample whose FP32 value lies within 0.02 of a
-// rounding tie is recomputed in FP64, so every int16 is the FP64 decision.
+// "32 bit precision"); a component whose FP32 value lies within twice its
+// error bound of a rounding tie is recomputed in FP64, so every int16 is the
+// FP64 decision.
 //
 // chirp_demod_kernel: demodulation of the Rx stream against chirps ("using
 // the algorithm outlined in section III.B"): for chirp c and frame k,
 //   out[c][k] = sum_{n<L} h[n] x[b_k+n] exp(-i*2*pi*p_c(b_k+n)/2^64),
 // the mix fused into the filter (the mixer depends on the frame through the
 // quadratic term, so there is no fixed modulated-tap matrix to multiply).
-// One CTA per (chirp, frame): each thread mixes and filters L/256 taps in
-// FP32; the partial sums are reduced in FP64.
+// One CTA per frame, all chirps: each thread mixes and filters L/256 taps per
+// chirp in FP32; the partial sums are reduced in FP64.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 
 #include "dev_common.cuh"
@@ -34,37 +36,99 @@ __device__ __forceinline__ uint64_t chirp_phase(uint64_t s, uint64_t r, int64_t 
     return s * um + r * (um * um);
 }
 
-// One component: round-half-even of v32 unless it is near a tie, in which
-// case the FP64 value decides; clamped to int16.
-__device__ __forceinline__ int16_t round_component(float v32, double amp, double unit, bool is_sin) {
-    const float r32 = rintf(v32);
-    float v = r32;
-    if (fabsf(v32 - r32) > 0.48f) {
-        double s, c;
-        sincospi(unit, &s, &c);
-        v = static_cast<float>(rint(amp * (is_sin ? s : c)));
-    }
-    v = fminf(fmaxf(v, -32768.f), 32767.f);
-    return static_cast<int16_t>(v);
+// ---------------------------------------------------------------- synthesis
+//
+// A sample is A*exp(i*2*pi*p/2^64).  The phase is reduced exactly in uint64 to
+// the nearest quarter turn q and an offset f in [-2^61, 2^61), x = f/2^63 in
+// [-1/4, 1/4] (angle / pi), so the FP32 argument carries 24 significant bits of
+// the offset.  Error of the FP32 value v = fl(fl(A) * sincospif(x)) against
+// A*sin (or cos) of the exact angle, |v - v_exact| <= e with
+//   e = A*(pi*2^-27 + 2^-23 + 2^-24) + |fl(A) - A|
+// (argument rounding, 1 ulp of sincospif, product rounding).  When
+// |v - rint(v)| <= 1/2 - 2e, rint(v) is the rounding of the exact value; every
+// other component goes to a per-tile queue in shared memory and is recomputed
+// in FP64, so the FP64 work is proportional to the few near-tie components
+// instead of stalling whole warps.
+constexpr int kSynThreads = 256;
+constexpr int kSynTile = 2048;          // samples per tile (8 per thread)
+
+__device__ __forceinline__ int16_t clamp16(float v) {
+    return static_cast<int16_t>(fminf(fmaxf(v, -32768.f), 32767.f));
 }
 
-__global__ void chirp_synth_kernel(uint64_t s, uint64_t r, double amp, int64_t m0, int64_t n,
-                                   short2* __restrict__ out) {
-    const float ampf = static_cast<float>(amp);
-    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const uint64_t p = chirp_phase(s, r, m0 + i);
-        // angle / pi in [-1, 1): FP32 from the top 32 bits, FP64 from all 64
-        const float x32 = static_cast<float>(static_cast<int32_t>(p >> 32)) * 0x1p-31f;
-        float sn, cs;
-        sincospif(x32, &sn, &cs);
-        const double x64 = static_cast<double>(static_cast<int64_t>(p)) * 0x1p-63;
-        out[i] = make_short2(round_component(ampf * cs, amp, x64, false),
-                             round_component(ampf * sn, amp, x64, true));
+__global__ void __launch_bounds__(kSynThreads) chirp_synth_kernel(uint64_t s, uint64_t r, float ampf,
+                                                                  double amp, float tie_lo, int64_t m0,
+                                                                  int64_t n, short2* __restrict__ out) {
+    __shared__ __align__(16) short2 tile[kSynTile];
+    __shared__ uint16_t fix[2 * kSynTile];
+    __shared__ int nfix;
+    const int tid = threadIdx.x;
+    for (int64_t base = static_cast<int64_t>(blockIdx.x) * kSynTile; base < n;
+         base += static_cast<int64_t>(gridDim.x) * kSynTile) {
+        if (tid == 0) nfix = 0;
+        __syncthreads();
+        const int cnt = static_cast<int>(n - base < kSynTile ? n - base : kSynTile);
+        // p(m + 256) = p(m) + d(m), d(m + 256) = d(m) + 2*256^2*r  (all mod 2^64)
+        const uint64_t m = static_cast<uint64_t>(m0 + base + tid);
+        uint64_t p = chirp_phase(s, r, static_cast<int64_t>(m));
+        uint64_t d = s * 256ull + r * (512ull * m + 65536ull);
+        const uint64_t dd = r * 131072ull;
+        for (int i = tid; i < cnt; i += kSynThreads) {
+            const uint32_t q = static_cast<uint32_t>((p + (1ull << 61)) >> 62);
+            const int64_t f = static_cast<int64_t>(p - (static_cast<uint64_t>(q) << 62));
+            float sx, cx;
+            sincospif(static_cast<float>(f) * 0x1p-63f, &sx, &cx);
+            float c = cx, sn = sx;                 // rotate by q quarter turns
+            if (q & 1) {
+                c = -sx;
+                sn = cx;
+            }
+            if (q & 2) {
+                c = -c;
+                sn = -sn;
+            }
+            const float vc = ampf * c, vs = ampf * sn;
+            const float rc = rintf(vc), rs = rintf(vs);
+            if (fabsf(vc - rc) > tie_lo) fix[atomicAdd(&nfix, 1)] = static_cast<uint16_t>(i << 1);
+            if (fabsf(vs - rs) > tie_lo) fix[atomicAdd(&nfix, 1)] = static_cast<uint16_t>((i << 1) | 1);
+            tile[i] = make_short2(clamp16(rc), clamp16(rs));
+            p += d;
+            d += dd;
+        }
+        __syncthreads();
+        const int nf = nfix;
+        int16_t* comp = reinterpret_cast<int16_t*>(tile);
+        for (int j = tid; j < nf; j += kSynThreads) {
+            const int e = fix[j];
+            const uint64_t pe = chirp_phase(s, r, m0 + base + (e >> 1));
+            double sd, cd;
+            sincospi(static_cast<double>(static_cast<int64_t>(pe)) * 0x1p-63, &sd, &cd);
+            comp[e] = clamp16(static_cast<float>(rint(amp * ((e & 1) ? sd : cd))));
+        }
+        __syncthreads();
+        short2* dst = out + base;
+        if (cnt == kSynTile && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+            const uint4* src4 = reinterpret_cast<const uint4*>(tile);
+            uint4* dst4 = reinterpret_cast<uint4*>(dst);
+            for (int i = tid; i < kSynTile / 4; i += kSynThreads) dst4[i] = src4[i];
+        } else {
+            for (int i = tid; i < cnt; i += kSynThreads) dst[i] = tile[i];
+        }
+        __syncthreads();
     }
 }
 
+// ---------------------------------------------------------- demodulation
+//
+// One CTA per frame (grid-stride): the frame's L samples are converted to FP32
+// once into shared memory and reused by every chirp.  For chirp c a thread
+// walks its taps n = tid, tid + 256, ... with the exact phase recurrence
+// p(m + 256) = p(m) + d, d += 2*256^2*r; the mixer is sincospif of the top 32
+// bits in FP32 and the products are summed in FP32 per thread; the 256 partial
+// sums are reduced in FP64 (warp shuffles, then 8 warps through shared memory,
+// a group of 32 chirps at a time).
 constexpr int kChirpThreads = 256;
+constexpr int kChirpGroup = 32;
 
 struct ChirpArgs {
     const uint32_t* carry;
@@ -82,47 +146,57 @@ struct ChirpArgs {
 };
 
 __global__ void __launch_bounds__(kChirpThreads) chirp_demod_kernel(const ChirpArgs a) {
-    __shared__ double red[2][kChirpThreads / 32];
-    const int64_t items = a.F * a.n_chirps;
-    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
-        const int c = static_cast<int>(it / a.F);
-        const int64_t k = it - static_cast<int64_t>(c) * a.F;
-        const uint64_t s = __ldg(a.s + c), r = __ldg(a.r + c);
-        float ar = 0.f, ai = 0.f;
-        for (int n = threadIdx.x; n < a.L; n += kChirpThreads) {
-            const int64_t vi = k * a.D + n;                          // index in [carry | buffer]
-            const uint32_t w = vi < a.cl ? __ldg(a.carry + vi) : __ldg(a.buf + (vi - a.cl));
-            const float2 x = iq_to_f2(w);
-            const uint64_t p = chirp_phase(s, r, a.a0 + vi);
-            float sn, cs;
-            sincospif(static_cast<float>(static_cast<int32_t>(p >> 32)) * 0x1p-31f, &sn, &cs);
-            // x * exp(-i*theta) = (x.re*cos + x.im*sin, x.im*cos - x.re*sin)
-            const float mr = fmaf(x.x, cs, x.y * sn), mi = fmaf(x.y, cs, -x.x * sn);
-            const float hn = __ldg(a.h + n);
-            ar = fmaf(hn, mr, ar);
-            ai = fmaf(hn, mi, ai);
+    extern __shared__ float2 xs[];                      // [L]
+    __shared__ double2 red[kChirpGroup][kChirpThreads / 32];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int64_t k = blockIdx.x; k < a.F; k += gridDim.x) {
+        __syncthreads();                                // previous frame's readers are done
+        for (int n = tid; n < a.L; n += kChirpThreads) {
+            const int64_t vi = k * a.D + n;             // index in [carry | buffer]
+            xs[n] = iq_to_f2(vi < a.cl ? __ldg(a.carry + vi) : __ldg(a.buf + (vi - a.cl)));
         }
-        double dr = ar, di = ai;
+        __syncthreads();
+        const uint64_t m = static_cast<uint64_t>(a.a0 + k * a.D + tid);
+        for (int c0 = 0; c0 < a.n_chirps; c0 += kChirpGroup) {
+            const int cn = a.n_chirps - c0 < kChirpGroup ? a.n_chirps - c0 : kChirpGroup;
+            for (int cc = 0; cc < cn; ++cc) {
+                const uint64_t s = __ldg(a.s + c0 + cc), r = __ldg(a.r + c0 + cc);
+                uint64_t p = chirp_phase(s, r, static_cast<int64_t>(m));
+                uint64_t d = s * 256ull + r * (512ull * m + 65536ull);
+                const uint64_t dd = r * 131072ull;
+                float ar = 0.f, ai = 0.f;
+                for (int n = tid; n < a.L; n += kChirpThreads) {
+                    const float2 x = xs[n];
+                    float sn, cs;
+                    sincospif(static_cast<float>(static_cast<int32_t>(p >> 32)) * 0x1p-31f, &sn, &cs);
+                    // x * exp(-i*theta) = (x.re*cos + x.im*sin, x.im*cos - x.re*sin)
+                    const float mr = fmaf(x.x, cs, x.y * sn), mi = fmaf(x.y, cs, -x.x * sn);
+                    const float hn = __ldg(a.h + n);
+                    ar = fmaf(hn, mr, ar);
+                    ai = fmaf(hn, mi, ai);
+                    p += d;
+                    d += dd;
+                }
+                double dr = ar, di = ai;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            dr += __shfl_xor_sync(0xffffffffu, dr, o);
-            di += __shfl_xor_sync(0xffffffffu, di, o);
-        }
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        if (lane == 0) {
-            red[0][warp] = dr;
-            red[1][warp] = di;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double tr = 0.0, ti = 0.0;
-            for (int w8 = 0; w8 < kChirpThreads / 32; ++w8) {
-                tr += red[0][w8];
-                ti += red[1][w8];
+                for (int o = 16; o > 0; o >>= 1) {
+                    dr += __shfl_xor_sync(0xffffffffu, dr, o);
+                    di += __shfl_xor_sync(0xffffffffu, di, o);
+                }
+                if (lane == 0) red[cc][warp] = make_double2(dr, di);
             }
-            a.out[static_cast<int64_t>(c) * a.ld + a.fo + k] = make_float2(static_cast<float>(tr), static_cast<float>(ti));
+            __syncthreads();
+            if (tid < cn) {
+                double tr = 0.0, ti = 0.0;
+                for (int w = 0; w < kChirpThreads / 32; ++w) {
+                    tr += red[tid][w].x;
+                    ti += red[tid][w].y;
+                }
+                a.out[static_cast<int64_t>(c0 + tid) * a.ld + a.fo + k] =
+                    make_float2(static_cast<float>(tr), static_cast<float>(ti));
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
 }
 
@@ -131,9 +205,14 @@ __global__ void __launch_bounds__(kChirpThreads) chirp_demod_kernel(const ChirpA
 cudaError_t chirp_synth(uint64_t s, uint64_t r, double amp, int64_t m0, int64_t n, void* out,
                         cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 16);
-    chirp_synth_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(s, r, amp, m0, n,
-                                                                       static_cast<short2*>(out));
+    const float ampf = static_cast<float>(amp);
+    const double e = amp * (3.14159265358979 * 0x1p-27 + 0x1p-23 + 0x1p-24) +
+                     std::fabs(static_cast<double>(ampf) - amp);
+    const float tie_lo = static_cast<float>(0.5 - 2.0 * e);
+    const int64_t tiles = (n + kSynTile - 1) / kSynTile;
+    const int64_t blocks = std::min<int64_t>(tiles, 152 * 8);
+    chirp_synth_kernel<<<static_cast<unsigned>(blocks), kSynThreads, 0, st>>>(
+        s, r, ampf, amp, tie_lo, m0, n, static_cast<short2*>(out));
     return cudaGetLastError();
 }
 
@@ -154,9 +233,15 @@ cudaError_t chirp_demod_launch(const ChirpLaunch& L, cudaStream_t st) {
     a.out = static_cast<float2*>(L.tones);
     a.ld = L.tones_ld;
     a.fo = L.frame_offset;
-    const int64_t items = L.F * L.n_chirps;
-    const int64_t blocks = std::min<int64_t>(items, static_cast<int64_t>(L.n_sms) * 8);
-    chirp_demod_kernel<<<static_cast<unsigned>(blocks), kChirpThreads, 0, st>>>(a);
+    const size_t smem = static_cast<size_t>(L.L) * sizeof(float2);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(chirp_demod_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+    }
+    const int per_sm = std::max(1, std::min(8, static_cast<int>((220u * 1024u) / (smem + 5u * 1024u))));
+    const int64_t blocks = std::min<int64_t>(L.F, static_cast<int64_t>(L.n_sms) * per_sm);
+    chirp_demod_kernel<<<static_cast<unsigned>(blocks), kChirpThreads, smem, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -25,7 +25,8 @@ def _chirps(n, seed):
     return np.array(s, np.uint64), np.array(rw, np.uint64)
 
 
-@pytest.mark.parametrize("amp,m0,n", [(8000.0, 0, 1 << 20), (32767.0, -12345, 300001), (123.456, 10 ** 9, 4097)])
+@pytest.mark.parametrize("amp,m0,n", [(8000.0, 0, 1 << 20), (32767.0, -12345, 300001), (123.456, 10 ** 9, 4097),
+                                      (32767.0, 7, 1 << 22), (30000.3, -(1 << 40), 2049), (0.0, 0, 100), (1.5, 3, 1)])
 def test_chirp_synthesis_matches_oracle(lib, amp, m0, n):
     s, r = _chirps(1, 3 + n)
     assert lib.chirp_rate_word(2.5e13, FS) == oracle.chirp_rate_word(2.5e13, FS)
@@ -37,7 +38,8 @@ def test_chirp_synthesis_matches_oracle(lib, amp, m0, n):
 
 
 @pytest.mark.parametrize("L,D,nc,win,fc", [(1024, 512, 3, "rect", 0.0), (4096, 2048, 8, "blackman", 2e-4),
-                                           (700, 1000, 2, "hann", 1e-3)])
+                                           (700, 1000, 2, "hann", 1e-3), (16384, 4096, 3, "blackman", 1e-4),
+                                           (256, 64, 40, "hamming", 5e-3)])
 def test_chirp_demod_parity(lib, L, D, nc, win, fc):
     s, r = _chirps(nc, 11 + L)
     n = D * 120 + 77
