@@ -7,10 +7,12 @@ TEST INFRASTRUCTURE ONLY: the product package never imports this module.  Only
 FP64 and shares no code with the CUDA path.
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
-(brute-force DFT, library windows and Bessel function, closed forms for pure
-tones and the Dirichlet kernel, Parseval, linearity, shift, the PFB/demod
-identity for bin-centred tones, integer phase and bin rules, the paper's -6 dB
-cross-over of adjacent channels, Eq. 1's chirp phase checked with Python
+(brute-force DFT and library FFT for power-of-two and mixed-radix lengths,
+library windows and Bessel function, closed forms for pure tones and the
+Dirichlet kernel, Parseval, linearity, shift, the PFB/demod identity for
+bin-centred tones, integer phase and bin rules for any N, the paper's -6 dB
+cross-over of adjacent channels from the prototype and from a whole PFB run at
+Fig. 3's N = 10^5, Eq. 1's chirp phase checked with Python
 integers and against its FP64 formula, the zero-rate chirp equal to the NCO
 demodulator, a chirp demodulated against itself).  No function is "parity
 unpinned".

@@ -136,14 +136,14 @@ uint64_t orc_freq_to_word(double f, double fs)
 }
 
 /* The PFB bin that holds an NCO word: round(word * N / 2^64) mod N with ties
- * rounded up, in integer arithmetic (N a power of two, 2 <= N <= 2^30). */
+ * rounded up, in exact integer arithmetic for any N >= 2:
+ *   bin = floor((word * N + 2^63) / 2^64) mod N,
+ * the 128-bit product formed with unsigned __int128. */
 int32_t orc_word_to_bin(uint64_t word, int32_t n_chan)
 {
-    if (n_chan < 2 || (n_chan & (n_chan - 1))) return -1;
-    int b = 0;
-    while ((1 << b) < n_chan) ++b;
-    const uint64_t half = (uint64_t)1 << (63 - b);
-    return (int32_t)((word + half) >> (64 - b));
+    if (n_chan < 2) return -1;
+    const unsigned __int128 q = (unsigned __int128)word * (uint64_t)n_chan + ((unsigned __int128)1 << 63);
+    return (int32_t)((uint64_t)(q >> 64) % (uint64_t)n_chan);
 }
 
 /* Phase of NCO word w at absolute sample m: w*m mod 2^64. */
@@ -158,7 +158,7 @@ static void orc_mixer(uint64_t phase, double* re, double* im)
 }
 
 /* ------------------------------------------------------------------------ */
-/* DFT: brute force and radix-2 FFT                                          */
+/* DFT: brute force and FFT                                                   */
 /* ------------------------------------------------------------------------ */
 
 /* y[c] = sum_p x[p] exp(-2*pi*i*c*p/N), O(N^2).  The index c*p is reduced
@@ -182,11 +182,10 @@ int orc_dft(int32_t n, const double* x, double* y)
 }
 
 /* In-place iterative radix-2 decimation-in-time FFT, same sign and order as
- * orc_dft; N must be a power of two.  Twiddles are evaluated directly from
+ * orc_dft, for N a power of two.  Twiddles are evaluated directly from
  * cos/sin of the exact angle for every butterfly. */
-int orc_fft(int32_t n, double* x)
+static void orc_fft_radix2(int32_t n, double* x)
 {
-    if (n <= 0 || (n & (n - 1)) || !x) return -1;
     for (int32_t i = 1, j = 0; i < n; ++i) {          /* bit reversal */
         int32_t bit = n >> 1;
         for (; j & bit; bit >>= 1) j ^= bit;
@@ -211,7 +210,75 @@ int orc_fft(int32_t n, double* x)
             }
         }
     }
-    return 0;
+}
+
+/* Mixed-radix decimation in time for any N (Cooley-Tukey on the smallest
+ * prime factor p of N, N = p*m):
+ *   X_q[k]   = sum_{j<m} x[j*p + q] W_m^{jk}            (p transforms of size m)
+ *   y[k+m*s] = sum_{q<p} W_N^{q*(k+m*s)} X_q[k]         (k < m, s < p)
+ * with W_N = exp(-2*pi*i/N); a prime N is the direct sum.  The twiddles are
+ * read from a table of cos/sin of -2*pi*e/N, e < N, with e reduced mod N in
+ * integer arithmetic.  x is read with the given stride (complex elements). */
+static int orc_fft_rec(int64_t n, const double* x, int64_t stride, double* y)
+{
+    if (n == 1) {
+        y[0] = x[0];
+        y[1] = x[1];
+        return 0;
+    }
+    int64_t p = 2;
+    while (p * p <= n && n % p != 0) ++p;
+    if (n % p != 0) p = n;                           /* n is prime */
+    const int64_t m = n / p;
+    double* w = (double*)malloc(sizeof(double) * 2 * (size_t)n);
+    double* sub = (double*)malloc(sizeof(double) * 2 * (size_t)n);
+    if (!w || !sub) {
+        free(w);
+        free(sub);
+        return -2;
+    }
+    for (int64_t e = 0; e < n; ++e) {
+        const double a = -2.0 * M_PI * (double)e / (double)n;
+        w[2 * e] = cos(a);
+        w[2 * e + 1] = sin(a);
+    }
+    int rc = 0;
+    for (int64_t q = 0; q < p && rc == 0; ++q)
+        rc = orc_fft_rec(m, x + 2 * q * stride, stride * p, sub + 2 * q * m);
+    for (int64_t s = 0; s < p && rc == 0; ++s) {
+        for (int64_t k = 0; k < m; ++k) {
+            const int64_t c = k + m * s;
+            double ar = 0.0, ai = 0.0;
+            for (int64_t q = 0; q < p; ++q) {
+                const int64_t e = (q * c) % n;
+                const double* xq = sub + 2 * (q * m + k);
+                ar += xq[0] * w[2 * e] - xq[1] * w[2 * e + 1];
+                ai += xq[0] * w[2 * e + 1] + xq[1] * w[2 * e];
+            }
+            y[2 * c] = ar;
+            y[2 * c + 1] = ai;
+        }
+    }
+    free(w);
+    free(sub);
+    return rc;
+}
+
+/* In-place FFT of any length N >= 1, same sign and order as orc_dft: the
+ * radix-2 form for powers of two, the mixed-radix recursion otherwise. */
+int orc_fft(int32_t n, double* x)
+{
+    if (n <= 0 || !x) return -1;
+    if ((n & (n - 1)) == 0) {
+        orc_fft_radix2(n, x);
+        return 0;
+    }
+    double* y = (double*)malloc(sizeof(double) * 2 * (size_t)n);
+    if (!y) return -2;
+    const int rc = orc_fft_rec(n, x, 1, y);
+    if (rc == 0) memcpy(x, y, sizeof(double) * 2 * (size_t)n);
+    free(y);
+    return rc;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -236,7 +303,7 @@ int orc_pfb_f64(const double* x, int64_t n_samples, int32_t n_chan, int32_t taps
                 double* v_out, double* full,
                 const int32_t* bins, int32_t n_bins, double* tones)
 {
-    if (n_chan <= 0 || (n_chan & (n_chan - 1)) || taps <= 0 || !h) return -1;
+    if (n_chan <= 0 || taps <= 0 || !h) return -1;
     if (k_begin < 0 || k_end < k_begin) return -1;
     if ((k_end) * (int64_t)n_chan > n_samples) return -1;
     if (n_bins > 0 && (!bins || !tones)) return -1;
@@ -260,7 +327,10 @@ int orc_pfb_f64(const double* x, int64_t n_samples, int32_t n_chan, int32_t taps
             y[2 * p + 1] = ai;
         }
         if (v_out) memcpy(v_out + 2 * (k - k_begin) * n, y, sizeof(double) * 2 * (size_t)n);
-        orc_fft((int32_t)n, y);
+        if (orc_fft((int32_t)n, y) != 0) {
+            free(y);
+            return -2;
+        }
         if (full) memcpy(full + 2 * (k - k_begin) * n, y, sizeof(double) * 2 * (size_t)n);
         for (int32_t s = 0; s < n_bins; ++s) {
             tones[2 * ((int64_t)s * nk + (k - k_begin))] = y[2 * bins[s]];

@@ -20,7 +20,7 @@ def crandn(*shape):
 
 
 # ---------------------------------------------------------------- DFT / FFT
-@pytest.mark.parametrize("n", [1, 2, 4, 8, 16, 32, 64])
+@pytest.mark.parametrize("n", [1, 2, 4, 8, 16, 32, 64, 3, 5, 6, 7, 9, 12, 15, 30, 49, 60, 97, 100, 210])
 def test_fft_matches_bruteforce_dft(n):
     x = crandn(n)
     # brute force written independently here: explicit double loop
@@ -31,19 +31,19 @@ def test_fft_matches_bruteforce_dft(n):
     assert np.linalg.norm(oracle.fft(x) - ref) / scale < 1e-13
 
 
-@pytest.mark.parametrize("n", [128, 1024, 4096, 16384])
+@pytest.mark.parametrize("n", [128, 1024, 4096, 16384, 1000, 6720, 26880, 100000])
 def test_fft_matches_library_fft(n):
     x = crandn(n)
     ref = np.fft.fft(x)
     assert np.linalg.norm(oracle.fft(x) - ref) / np.linalg.norm(ref) < 1e-13
 
 
-def test_fft_unit_impulse_and_dc():
-    n = 64
+@pytest.mark.parametrize("n", [64, 60, 1000])
+def test_fft_unit_impulse_and_dc(n):
     e = np.zeros(n, complex); e[3] = 1.0
     c = np.arange(n)
-    assert np.allclose(oracle.fft(e), np.exp(-2j * np.pi * 3 * c / n), atol=1e-14)
-    assert np.allclose(oracle.fft(np.ones(n)), n * (c == 0), atol=1e-12)
+    assert np.allclose(oracle.fft(e), np.exp(-2j * np.pi * ((3 * c) % n) / n), atol=1e-13)
+    assert np.allclose(oracle.fft(np.ones(n)), n * (c == 0), atol=1e-10)
 
 
 # ---------------------------------------------------------------- windows
@@ -119,6 +119,31 @@ def test_paper_adjacent_channel_crossover_6db():
         assert abs(db - g["crossover_db"]) < g["tolerance_db"], (case, db)
 
 
+def test_paper_fig3_pfb_run_crossover():
+    """Sec. III.A, Fig. 3: with N = 10^5 channels, A_v = 4 taps and a Hamming
+    window, a tone half-way between two channels shows in both at about -6 dB
+    of a channel-centred tone.  Runs the whole oracle PFB (FIR + length-10^5
+    FFT) at the paper's size on an FP64 tone."""
+    with open(os.path.join(GOLDEN, "paper_pfb_crossover.json")) as f:
+        g = json.load(f)
+    case = g["cases"][0]
+    N, T = case["n_chan"], case["taps"]
+    h64, _ = oracle.pfb_prototype(N, T, case["window"])
+    m = np.arange(N * (T + 1), dtype=np.float64)
+    b = 31415
+    centred = np.exp(2j * np.pi * ((b * m) % N) / N)
+    half = np.exp(2j * np.pi * (((2 * b + 1) * m) % (2 * N)) / (2 * N))
+    yc = oracle.pfb(centred, N, T, h64, k_begin=T, k_end=T + 1)["full"][0]
+    yh = oracle.pfb(half, N, T, h64, k_begin=T, k_end=T + 1)["full"][0]
+    ref = abs(yc[b])
+    for c in (b, b + 1):
+        db = 20 * np.log10(abs(yh[c]) / ref)
+        assert abs(db - g["crossover_db"]) < g["tolerance_db"], (c, db)
+    # and nothing else above the two channels
+    others = np.delete(np.abs(yh), [b, b + 1])
+    assert others.max() < abs(yh[b])
+
+
 # ---------------------------------------------------------- integer rules
 def test_freq_to_word_exact_values():
     fs = 200e6
@@ -147,6 +172,15 @@ def test_word_to_bin_rule():
             q = Fraction(w * n, 2 ** 64)
             ref = int((q + Fraction(1, 2)).__floor__()) % n   # round half up
             assert oracle.word_to_bin(w, n) == ref
+    # any N: random words, words just below and above every half-bin boundary
+    for n in (3, 100, 1000, 10 ** 5, 10 ** 7):
+        words = [int(w) for w in r.integers(0, 2 ** 64, 200, dtype=np.uint64)]
+        for c in range(0, n, max(1, n // 7)):
+            edge = (Fraction(2 * c + 1, 2 * n) * 2 ** 64).__ceil__()   # first word of bin c+1
+            words += [(edge - 1) % 2 ** 64, edge % 2 ** 64]
+        for w in words:
+            ref = int((Fraction(w * n, 2 ** 64) + Fraction(1, 2)).__floor__()) % n
+            assert oracle.word_to_bin(w, n) == ref
 
 
 def test_nco_phase_is_product_mod_2_64():
@@ -161,7 +195,8 @@ def _tone(n, c0, N, A, th):
 
 
 @pytest.mark.parametrize("N,T,win,beta", [(8, 4, "hann", 0.0), (16, 3, "kaiser", 9.0),
-                                          (32, 8, "hamming", 0.0)])
+                                          (32, 8, "hamming", 0.0), (12, 3, "hann", 0.0),
+                                          (100, 4, "hamming", 0.0), (35, 2, "kaiser", 5.0)])
 def test_pfb_equals_filtered_mixed_stream(N, T, win, beta):
     """Library-routine pin: each PFB channel c is the stream mixed down by
     exp(-2*pi*i*c*m/N), convolved with the time-reversed prototype
@@ -179,11 +214,12 @@ def test_pfb_equals_filtered_mixed_stream(N, T, win, beta):
         assert np.allclose(y[:, c], ref, rtol=1e-12, atol=1e-10)
 
 
-def test_pfb_bin_centred_tone_closed_form():
+@pytest.mark.parametrize("N,c0", [(64, 13), (100, 37), (1000, 999)])
+def test_pfb_bin_centred_tone_closed_form(N, c0):
     """A pure tone at bin c0 (FP64, unquantised) gives, after T-1 warm-up frames,
     y_k[c] = A e^{i th} DFT(P)[c - c0] with P[p] = sum_t h[tN+p]; so y_k[c0] =
     A e^{i th} sum(h)."""
-    N, T, c0, A, th = 64, 4, 13, 1234.5, 0.7
+    T, A, th = 4, 1234.5, 0.7
     _, h32 = oracle.pfb_prototype(N, T, "hann")
     h = h32.astype(np.float64)
     x = _tone(N * 40, c0, N, A, th)
