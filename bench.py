@@ -369,6 +369,46 @@ def run_chirp(args, dev, stream):
     return res
 
 
+# ----------------------------------------------------------- any-N PFB
+def run_large_n(args, dev, stream, x, words):
+    """PFB at channel counts that are not powers of two (Sec. III.A): Fig. 3's
+    N = 10^5 and the section's largest, 10^7, with A_v = T = 4 and a Hamming
+    window, on the workload's 2^28-sample stream, full spectrum + its 1000
+    tones (mixed-radix kernels: four-step two-pass form at these N)."""
+    import torch
+
+    from paper_1812_02200_gb300 import rfr
+    hbm_peak = measured_peaks()[0]
+    out = []
+    n = x.shape[0]
+    for N, reps in ((100000, 5), (10 ** 7, 3)):
+        plan = rfr.Plan(N, 4, window="hamming", words=words, full=True, tones=True)
+        F = plan.frames_for(n)
+        # pushes after the first may complete one more frame (residue)
+        full = torch.empty((F + 1, N), dtype=torch.complex64, device=dev)
+        tones = torch.empty((len(words), F + 1), dtype=torch.complex64, device=dev)
+        plan.push_into(x, full, tones, stream=stream)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            plan.push_into(x, full, tones, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / reps
+        bps = 4.0 + 8.0 + 8.0 * len(words) / N
+        gbs = bps * n / (ms * 1e-3) / 1e9
+        out.append({"workload": f"PFB N={N} T=4 Hamming, 2^{int(np.log2(n))} complex int16 samples, "
+                                f"full spectrum + {len(words)} tones",
+                    "value": n / (ms * 1e-3) / 1e6, "unit": UNIT, "ms": ms, "frames": F,
+                    "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                                 "frac": gbs / hbm_peak, "bytes_per_sample": bps}})
+        plan.close()
+        del full, tones
+        torch.cuda.empty_cache()
+    return out
+
+
 # ------------------------------------------------------------------- batch
 def make_spec_plan(rfr, spec, words, full=False):
     if spec["kind"] == "pfb":
@@ -636,6 +676,7 @@ def run_ours(args, ws, rank, local):
     demod = None
     del full, tones
     torch.cuda.empty_cache()
+    large_n = None if args.no_large_n else run_large_n(args, dev, stream, x, c["words"])
     if not args.no_demod:
         demod = run_demod(args, dev, stream, rank)
     chirp = None if args.no_chirp else run_chirp(args, dev, stream)
@@ -668,6 +709,7 @@ def run_ours(args, ws, rank, local):
         "batch": batch,
         "serve": serve,
         "chirp": chirp,
+        "any_n_pfb": large_n,
         "e2e": e2e,
         "cpu_baseline": cpu,
         "clocks": clk,
@@ -689,6 +731,7 @@ def main():
     ap.add_argument("--demod-log2-samples", type=int, default=27)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-chirp", action="store_true")
+    ap.add_argument("--no-large-n", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-loads", default="1,5,10,20", help="offered loads, Gsamples/s")
     ap.add_argument("--serve-seconds", type=float, default=2.0)

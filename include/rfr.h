@@ -118,7 +118,12 @@ typedef struct {
 /*
  * rfr_plan_create -- build a plan (Sec. III.A for channels > 0, Sec. III.B
  * for channels == 0).
- *   channels   N > 0: PFB with N channels, N a power of two, 16 <= N <= 16384.
+ *   channels   N > 0: PFB with N channels, 2 <= N <= 2^24 (Sec. III.A: Fig. 3
+ *              uses N = 10^5, the section reports up to 10^7 bins).  N must have
+ *              no prime factor above 7 (N = 2^a 3^b 5^c 7^d); any other N
+ *              returns RFR_E_UNSUPPORTED.  Powers of two from 16 to 16384 run
+ *              the fused single-CTA kernels, every other N the mixed-radix
+ *              kernels (one pass up to 8192, a four-step two-pass form above).
  *              0: direct demodulation.
  *   taps       PFB: T taps per channel, 1 <= T <= 16 (prototype length N*T).
  *              Demodulation: filter length L, 1 <= L <= 16384.
@@ -429,7 +434,8 @@ rfr_status rfr_demod_noalloc(const int16_t* iq, int64_t n_samples, const double*
 uint64_t rfr_freq_to_word(double f_hz, double fs_hz);
 
 /* Bin of an NCO word in an n-channel PFB: round(word*n/2^64) mod n, ties
- * up, in integer arithmetic; -1 if n is not a power of two >= 2. */
+ * up, i.e. floor((word*n + 2^63) / 2^64) mod n in exact 128-bit integer
+ * arithmetic, for any n >= 2; -1 if n < 2. */
 int32_t rfr_word_to_bin(uint64_t word, int32_t n);
 
 const char* rfr_status_string(rfr_status status);

@@ -197,7 +197,7 @@ rfr_status push_core(rfr_plan* p, const int16_t* iq, int64_t n, const rfr_output
             L.n_sms = p->n_sms;
             L.max_smem = p->max_smem;
             L.lookahead = p->tune.pfb_lookahead;
-            RFR_CUDA(p, rfr::pfb_launch(L, st));
+            RFR_CUDA(p, p->gen ? rfr::gen_pfb_launch(L, p->gplan, st) : rfr::pfb_launch(L, st));
         } else if (p->mode == RFR_MODE_CHIRP) {
             rfr::ChirpLaunch L{};
             L.carry = carry;
@@ -303,6 +303,7 @@ void destroy(rfr_plan* p) {
     for (auto& e : p->stage_ev)
         if (e) cudaEventDestroy(e);
     rfr::plain_release(p->plain_scratch, p->plain_fft);
+    rfr::gen_plan_free(&p->gplan);
     delete p;
 }
 
@@ -373,15 +374,24 @@ rfr_status rfr_plan_create(rfr_plan** out, int32_t channels, int32_t taps, const
 
     if (channels > 0) {
         // ------------------------------------------------------------- PFB
-        if ((channels & (channels - 1)) != 0 || channels < 16 || channels > 16384) return bad(RFR_E_INVALID);
+        if (channels < 2 || channels > (1 << 24)) return bad(RFR_E_INVALID);
         if (taps < 1 || taps > 16 || decimation != channels) return bad(RFR_E_INVALID);
         if (out_flags == 0 || (out_flags & ~uint32_t(RFR_OUT_FULL | RFR_OUT_TONES)) != 0) return bad(RFR_E_INVALID);
         if ((out_flags & RFR_OUT_TONES) && nt == 0) return bad(RFR_E_INVALID);
+        const bool pow2 = (channels & (channels - 1)) == 0;
         p->mode = RFR_MODE_PFB;
         p->N = channels;
         p->T = taps;
-        while ((1 << p->log2n) < channels) ++p->log2n;
-        p->Tk = rfr::pfb_kernel_taps(p->log2n, taps);
+        // powers of two from 16 to 16384: the fused single-CTA kernels;
+        // every other N = 2^a 3^b 5^c 7^d up to 2^24: the mixed-radix kernels
+        p->gen = !pow2 || channels < 16 || channels > 16384;
+        if (p->gen && !rfr::gen_supported(channels)) return bad(RFR_E_UNSUPPORTED);
+        if (p->gen) {
+            p->Tk = taps;
+        } else {
+            while ((1 << p->log2n) < channels) ++p->log2n;
+            p->Tk = rfr::pfb_kernel_taps(p->log2n, taps);
+        }
         const int64_t M = static_cast<int64_t>(channels) * taps;
         p->h64.resize(M);
         const double fc = window->cutoff > 0.0 ? window->cutoff : 0.5 / channels;
@@ -393,7 +403,7 @@ rfr_status rfr_plan_create(rfr_plan** out, int32_t channels, int32_t taps, const
         std::copy(p->h32.begin(), p->h32.end(), hk.begin() + static_cast<size_t>(p->Tk - taps) * channels);
         p->bins.resize(nt);
         for (int s = 0; s < nt; ++s) p->bins[s] = rfr::word_to_bin(p->words[s], channels);
-        std::vector<float> tw = make_twiddles(p->log2n);
+        std::vector<float> tw = p->gen ? std::vector<float>() : make_twiddles(p->log2n);
         p->tw_count = static_cast<int>(tw.size() / 2);
         p->W = static_cast<int64_t>(p->Tk) * channels;
         p->H = channels;
@@ -403,6 +413,10 @@ rfr_status rfr_plan_create(rfr_plan** out, int32_t channels, int32_t taps, const
             (e = dev_alloc(&p->d_h32, p->h32.size() * 4)) != cudaSuccess ||
             (e = dev_alloc(&p->d_tw, std::max<size_t>(tw.size(), 2) * 4)) != cudaSuccess ||
             (e = dev_alloc(&p->d_bins, std::max<size_t>(nt, 1) * 4)) != cudaSuccess)
+            return bad(cuda_fail(p, e, "plan alloc"));
+        // the between-pass buffer of the two-pass form: a batch of frames
+        // that stays in L2 (48 MB), at least one frame
+        if (p->gen && (e = rfr::gen_plan_init(&p->gplan, channels, int64_t(48) << 20)) != cudaSuccess)
             return bad(cuda_fail(p, e, "plan alloc"));
         cudaMemcpy(p->d_h, hk.data(), hk.size() * 4, cudaMemcpyHostToDevice);
         cudaMemcpy(p->d_h32, p->h32.data(), p->h32.size() * 4, cudaMemcpyHostToDevice);

@@ -1,0 +1,474 @@
+// pfb_general.cu -- the PFB of Sec. III.A for channel counts that are not a
+// power of two, or too large for one CTA (Fig. 3 channelizes with N = 10^5;
+// the section reports up to 10^7 bins): any N = 2^a 3^b 5^c 7^d with
+// 2 <= N <= 2^24, T <= 16 taps per channel, critically sampled (hop N).
+//
+// Frame k of the virtual stream [carry | buffer] uses the T*N samples from
+// k*N on:  v_k[p] = sum_{t<T} h[t*N + p] * x[k*N + t*N + p],  y_k = DFT_N(v_k).
+//
+// Single pass (N <= 8192): one CTA per frame computes the FIR straight into
+// shared memory, runs an in-place mixed-radix Stockham FFT there and writes
+// the spectrum row and the tone channels.
+//
+// Two passes (N > 8192): the four-step split N = N1*N2 with input index
+// p = N2*p1 + p2 and output index c = c1 + N1*c2,
+//   Z[c1][p2]     = W_N^{p2*c1} * sum_{p1} v[N2*p1 + p2] W_{N1}^{p1*c1}   (pass A)
+//   y[c1 + N1*c2] = sum_{p2} Z[c1][p2] W_{N2}^{p2*c2}                     (pass B)
+// with W_L = exp(-2*pi*i/L).  Pass A: one CTA per (frame, GA consecutive p2):
+// the FIR of its N1 x GA points (input read in runs of GA samples), GA
+// interleaved FFTs of length N1, the twiddle W_N^{p2*c1} (the product of two
+// FP64-built table entries), Z stored in runs of GA points.  Pass B: one CTA
+// per (frame, GB consecutive c1): GB rows of Z, GB interleaved FFTs of length
+// N2, the spectrum stored in runs of GB points, and the tone channels.  Z
+// holds a batch of frames small enough to stay in L2 between the passes.
+//
+// FFT stages follow the conventions of fft_dev.cuh (Stockham autosort,
+// butterfly j reads x[j + r*n/R], twiddle W_{R*Ns}^{r*k} with k = j mod Ns,
+// writes y[(j/Ns)*R*Ns + k + r*Ns]; twiddle table [(r-1)*Ns + k] per stage).
+// Stages alternate between two shared-memory buffers of the G x n <= 8192
+// points (G transforms interleaved, element (i, g) at i*G + g, padded one
+// element in 16).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <vector>
+
+#include "dev_common.cuh"
+#include "fft_dev.cuh"
+#include "rfr_internal.h"
+
+namespace rfr {
+
+namespace {
+
+constexpr int kGThreads = 512;
+constexpr int kGElems = 8192;                      // points per CTA (G * n)
+constexpr int kTwSplit = 4096;                     // inter-pass twiddle: m = hi*4096 + lo
+
+__device__ __forceinline__ int gpad(int e) { return e + (e >> 4); }
+
+// cos(2*pi*j/R) and sin(2*pi*j/R) for R = 3, 5, 7 and 0 <= j < R.
+template <int R>
+__device__ __forceinline__ constexpr float cos_r(int j) {
+    if (j == 0) return 1.0f;
+    if (R == 3) return -0.5f;
+    if (R == 5) return (j == 1 || j == 4) ? 0.30901699437494742f : -0.80901699437494742f;
+    return (j == 1 || j == 6) ? 0.62348980185873353f
+                              : ((j == 2 || j == 5) ? -0.22252093395631440f : -0.90096886790241913f);
+}
+template <int R>
+__device__ __forceinline__ constexpr float sin_r(int j) {
+    if (j == 0) return 0.0f;
+    const float s = R == 3   ? 0.86602540378443865f
+                    : R == 5 ? ((j == 1 || j == 4) ? 0.95105651629515357f : 0.58778525229247313f)
+                             : ((j == 1 || j == 6) ? 0.78183148246802981f
+                                                   : ((j == 2 || j == 5) ? 0.97492791218182361f : 0.43388373911755812f));
+    return 2 * j < R ? s : -s;
+}
+
+// Length-R DFT for odd R (3, 5, 7) from the definition, pairing q with R-q:
+//   y_k     = a_0 + sum_{q=1}^{(R-1)/2} [c_kq (a_q + a_{R-q}) - i s_kq (a_q - a_{R-q})]
+//   y_{R-k} = the same with +i,
+// c_j = cos(2*pi*j/R), s_j = sin(2*pi*j/R), indices mod R.
+template <int R>
+__device__ __forceinline__ void dft_odd(float2* x) {
+    constexpr int H = (R - 1) / 2;
+    float2 b[H], d[H];
+    float2 y0 = x[0];
+#pragma unroll
+    for (int q = 1; q <= H; ++q) {
+        b[q - 1] = cadd(x[q], x[R - q]);
+        d[q - 1] = csub(x[q], x[R - q]);
+        y0 = cadd(y0, b[q - 1]);
+    }
+    float2 out[R];
+    out[0] = y0;
+#pragma unroll
+    for (int k = 1; k <= H; ++k) {
+        float tr = x[0].x, ti = x[0].y, ur = 0.f, ui = 0.f;
+#pragma unroll
+        for (int q = 1; q <= H; ++q) {
+            const float c = cos_r<R>((k * q) % R), s = sin_r<R>((k * q) % R);
+            tr = fmaf(c, b[q - 1].x, tr);
+            ti = fmaf(c, b[q - 1].y, ti);
+            ur = fmaf(s, d[q - 1].x, ur);
+            ui = fmaf(s, d[q - 1].y, ui);
+        }
+        out[k] = make_float2(tr + ui, ti - ur);          // t - i*u
+        out[R - k] = make_float2(tr - ui, ti + ur);      // t + i*u
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r] = out[r];
+}
+
+template <int R>
+__device__ __forceinline__ void dft_any(float2* x) {
+    if constexpr (R == 3 || R == 5 || R == 7) dft_odd<R>(x);
+    else dft_small<R>(x);
+}
+
+// One Stockham stage of radix R over G = 2^gl2 interleaved transforms of
+// length n, from src to dst (points at [gpad(i*G + g)]).
+template <int R>
+__device__ __forceinline__ void gen_stage(const float2* __restrict__ src, float2* __restrict__ dst, int n, int gl2,
+                                          int Ns, const float2* __restrict__ tw) {
+    const int nR = n / R;
+    const int nb = nR << gl2;
+    const int gm = (1 << gl2) - 1;
+    for (int u = threadIdx.x; u < nb; u += kGThreads) {
+        const int g = u & gm, j = u >> gl2;
+        const int k = j % Ns;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = src[gpad(((j + r * nR) << gl2) + g)];
+        if (Ns > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], __ldg(tw + (r - 1) * Ns + k));
+        }
+        dft_any<R>(v);
+        const int base = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[gpad(((base + r * Ns) << gl2) + g)] = v[r];
+    }
+    __syncthreads();
+}
+
+// The whole transform: the points start in buf0; returns the buffer that
+// holds the result (buf0 or buf1, by the parity of the stage count).
+__device__ float2* gen_fft(float2* buf0, float2* buf1, const GenFft& f, int gl2, const float2* __restrict__ tw) {
+    float2* src = buf0;
+    float2* dst = buf1;
+    for (int s = 0; s < f.nst; ++s) {
+        const float2* t = tw + f.tw_off[s];
+        switch (f.radix[s]) {
+        case 16: gen_stage<16>(src, dst, f.n, gl2, f.ns[s], t); break;
+        case 8: gen_stage<8>(src, dst, f.n, gl2, f.ns[s], t); break;
+        case 4: gen_stage<4>(src, dst, f.n, gl2, f.ns[s], t); break;
+        case 2: gen_stage<2>(src, dst, f.n, gl2, f.ns[s], t); break;
+        case 3: gen_stage<3>(src, dst, f.n, gl2, f.ns[s], t); break;
+        case 5: gen_stage<5>(src, dst, f.n, gl2, f.ns[s], t); break;
+        default: gen_stage<7>(src, dst, f.n, gl2, f.ns[s], t); break;
+        }
+        float2* tmp = src;
+        src = dst;
+        dst = tmp;
+    }
+    return src;
+}
+
+struct GenArgs {
+    const uint32_t* carry;
+    int64_t cl;
+    const uint32_t* buf;
+    int64_t F;              // frames in this launch
+    int64_t k0;             // index of the launch's first frame within the push
+    int N, T;
+    const float* h;         // [T*N]
+    GenFft fa, fb;          // pass A (length N1) and pass B / single (length N2 = N)
+    const float2* tw_a;
+    const float2* tw_b;
+    const float2* th;       // W_N^{4096*i}
+    const float2* tl;       // W_N^{i}, i < 4096
+    int N1, N2, gla, glb;
+    float2* z;              // [F][N1][N2]
+    const int32_t* bins;
+    int n_tones;
+    float2* full;
+    int64_t full_ld;
+    float2* tones;
+    int64_t tones_ld;
+    int64_t fo;             // frame offset in the caller's outputs
+};
+
+__device__ __forceinline__ float2 load_x(const GenArgs& a, int64_t vi) {
+    return iq_to_f2(vi < a.cl ? __ldg(a.carry + vi) : __ldg(a.buf + (vi - a.cl)));
+}
+
+__device__ __forceinline__ float2 fir_point(const GenArgs& a, int64_t base, int pos) {
+    float ar = 0.f, ai = 0.f;
+    for (int t = 0; t < a.T; ++t) {
+        const float hv = __ldg(a.h + static_cast<int64_t>(t) * a.N + pos);
+        const float2 x = load_x(a, base + static_cast<int64_t>(t) * a.N + pos);
+        ar = fmaf(hv, x.x, ar);
+        ai = fmaf(hv, x.y, ai);
+    }
+    return make_float2(ar, ai);
+}
+
+// Shared memory: two buffers of gpad(elems) points each.
+__device__ __forceinline__ float2* second_buffer(float2* sm, int elems) { return sm + gpad(elems) + 1; }
+
+__global__ void __launch_bounds__(kGThreads, 1) gen_single_kernel(const GenArgs a) {
+    extern __shared__ float2 sm[];
+    float2* sm1 = second_buffer(sm, a.N);
+    for (int64_t kk = blockIdx.x; kk < a.F; kk += gridDim.x) {
+        const int64_t k = a.k0 + kk;
+        const int64_t base = k * a.N;
+        for (int p = threadIdx.x; p < a.N; p += kGThreads) sm[gpad(p)] = fir_point(a, base, p);
+        __syncthreads();
+        const float2* y = gen_fft(sm, sm1, a.fb, 0, a.tw_b);
+        if (a.full) {
+            float2* row = a.full + (a.fo + k) * a.full_ld;
+            for (int c = threadIdx.x; c < a.N; c += kGThreads) row[c] = y[gpad(c)];
+        }
+        for (int t = threadIdx.x; t < a.n_tones; t += kGThreads)
+            a.tones[t * a.tones_ld + a.fo + k] = y[gpad(__ldg(a.bins + t))];
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kGThreads, 1) gen_pass_a_kernel(const GenArgs a) {
+    extern __shared__ float2 sm[];
+    const int GA = 1 << a.gla;
+    const int groups = (a.N2 + GA - 1) >> a.gla;
+    const int E = a.N1 << a.gla;
+    float2* sm1 = second_buffer(sm, E);
+    for (int64_t it = blockIdx.x; it < a.F * groups; it += gridDim.x) {
+        const int64_t kk = it / groups;
+        const int g0 = static_cast<int>(it - kk * groups) << a.gla;
+        const int64_t base = (a.k0 + kk) * a.N;
+        for (int e = threadIdx.x; e < E; e += kGThreads) {
+            const int g = e & (GA - 1), p1 = e >> a.gla;
+            sm[gpad(e)] = g0 + g < a.N2 ? fir_point(a, base, p1 * a.N2 + g0 + g) : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        const float2* y = gen_fft(sm, sm1, a.fa, a.gla, a.tw_a);
+        float2* zf = a.z + kk * a.N;
+        for (int e = threadIdx.x; e < E; e += kGThreads) {
+            const int g = e & (GA - 1), c1 = e >> a.gla, p2 = g0 + g;
+            if (p2 < a.N2) {
+                const int m = p2 * c1;                       // < N1*N2 = N
+                const float2 w = cmul(__ldg(a.th + (m / kTwSplit)), __ldg(a.tl + (m % kTwSplit)));
+                zf[static_cast<int64_t>(c1) * a.N2 + p2] = cmul(y[gpad(e)], w);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kGThreads, 1) gen_pass_b_kernel(const GenArgs a) {
+    extern __shared__ float2 sm[];
+    const int GB = 1 << a.glb;
+    const int groups = (a.N1 + GB - 1) >> a.glb;
+    const int E = a.N2 << a.glb;
+    float2* sm1 = second_buffer(sm, E);
+    for (int64_t it = blockIdx.x; it < a.F * groups; it += gridDim.x) {
+        const int64_t kk = it / groups;
+        const int c0 = static_cast<int>(it - kk * groups) << a.glb;
+        const float2* zf = a.z + kk * a.N;
+        for (int g = 0; g < GB; ++g) {
+            const int c1 = c0 + g;
+            for (int p2 = threadIdx.x; p2 < a.N2; p2 += kGThreads)
+                sm[gpad((p2 << a.glb) + g)] =
+                    c1 < a.N1 ? zf[static_cast<int64_t>(c1) * a.N2 + p2] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        const float2* y = gen_fft(sm, sm1, a.fb, a.glb, a.tw_b);
+        const int64_t k = a.k0 + kk;
+        if (a.full) {
+            float2* row = a.full + (a.fo + k) * a.full_ld;
+            for (int e = threadIdx.x; e < E; e += kGThreads) {
+                const int g = e & (GB - 1), c2 = e >> a.glb;
+                if (c0 + g < a.N1) row[c0 + g + static_cast<int64_t>(a.N1) * c2] = y[gpad(e)];
+            }
+        }
+        for (int t = threadIdx.x; t < a.n_tones; t += kGThreads) {
+            const int b = __ldg(a.bins + t);
+            const int c1 = b % a.N1;
+            if (c1 >= c0 && c1 < c0 + GB)
+                a.tones[t * a.tones_ld + a.fo + k] = y[gpad(((b / a.N1) << a.glb) + c1 - c0)];
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- host side
+bool smooth7(int64_t n) {
+    for (int p : {2, 3, 5, 7})
+        while (n % p == 0) n /= p;
+    return n == 1;
+}
+
+int floor_log2(int v) {
+    int l = 0;
+    while ((2 << l) <= v) ++l;
+    return l;
+}
+
+// Radices of a length-n transform (16s first, then one 8/4/2, then 3, 5, 7),
+// stage spans and twiddle-table offsets; appends the FP64-built twiddles to
+// `tw` (offsets are absolute positions in `tw`).
+bool build_fft(int n, GenFft* f, std::vector<float2>& tw) {
+    *f = GenFft{};
+    f->n = n;
+    int m = n, ns = 1;
+    auto add = [&](int r) {
+        if (f->nst >= kGenMaxStages) return false;
+        f->radix[f->nst] = r;
+        f->ns[f->nst] = ns;
+        f->tw_off[f->nst] = static_cast<int>(tw.size());
+        if (ns > 1) {
+            for (int rr = 1; rr < r; ++rr)
+                for (int k = 0; k < ns; ++k) {
+                    const int64_t e = static_cast<int64_t>(rr) * k, L = static_cast<int64_t>(r) * ns;
+                    const double a = -2.0 * 3.14159265358979323846 * static_cast<double>(e % L) / static_cast<double>(L);
+                    tw.push_back(make_float2(static_cast<float>(std::cos(a)), static_cast<float>(std::sin(a))));
+                }
+        }
+        ++f->nst;
+        ns *= r;
+        return true;
+    };
+    while (m % 16 == 0) {
+        if (!add(16)) return false;
+        m /= 16;
+    }
+    for (int r : {8, 4, 2})
+        if (m % r == 0) {
+            if (!add(r)) return false;
+            m /= r;
+        }
+    for (int r : {3, 5, 7})
+        while (m % r == 0) {
+            if (!add(r)) return false;
+            m /= r;
+        }
+    return m == 1;
+}
+
+}  // namespace
+
+bool gen_supported(int64_t n) { return n >= 2 && n <= (int64_t(1) << 24) && smooth7(n); }
+
+void gen_plan_free(GenPlan* g) {
+    for (void* q : {static_cast<void*>(g->d_tw), static_cast<void*>(g->d_th), static_cast<void*>(g->d_tl),
+                    static_cast<void*>(g->d_z)})
+        if (q) cudaFree(q);
+    *g = GenPlan{};
+}
+
+cudaError_t gen_plan_init(GenPlan* g, int N, int64_t z_budget_bytes) {
+    *g = GenPlan{};
+    if (!gen_supported(N)) return cudaErrorInvalidValue;
+    g->N = N;
+    std::vector<float2> tw;
+    if (N <= kGElems) {
+        g->N1 = 1;
+        g->N2 = N;
+        if (!build_fft(N, &g->fb, tw)) return cudaErrorInvalidValue;
+    } else {
+        // N = N1*N2 with N1, N2 <= 8192; pick the split with the largest
+        // min(GA, GB) (the longest contiguous runs), then the more balanced.
+        int best = -1, best_score = -1, best_bal = 0;
+        for (int n2 = 2; n2 <= kGElems; ++n2) {
+            if (N % n2 != 0) continue;
+            const int n1 = N / n2;
+            if (n1 < 2 || n1 > kGElems) continue;
+            const int ga = std::min(16, 1 << floor_log2(kGElems / n1));
+            const int gb = std::min(16, 1 << floor_log2(kGElems / n2));
+            const int score = std::min(ga, gb), bal = -std::abs(n1 - n2);
+            if (score > best_score || (score == best_score && bal > best_bal)) {
+                best = n2;
+                best_score = score;
+                best_bal = bal;
+            }
+        }
+        if (best < 0) return cudaErrorInvalidValue;
+        g->N2 = best;
+        g->N1 = N / best;
+        g->gla = floor_log2(std::min(16, 1 << floor_log2(kGElems / g->N1)));
+        g->glb = floor_log2(std::min(16, 1 << floor_log2(kGElems / g->N2)));
+        if (!build_fft(g->N1, &g->fa, tw)) return cudaErrorInvalidValue;
+        if (!build_fft(g->N2, &g->fb, tw)) return cudaErrorInvalidValue;
+    }
+    cudaError_t e;
+    const size_t twn = std::max<size_t>(tw.size(), 1);
+    if ((e = cudaMalloc(&g->d_tw, twn * sizeof(float2))) != cudaSuccess) return e;
+    if (!tw.empty() &&
+        (e = cudaMemcpy(g->d_tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return e;
+    if (g->N1 > 1) {
+        const int nh = (N + kTwSplit - 1) / kTwSplit;
+        std::vector<float2> th(nh), tl(kTwSplit);
+        auto w = [&](int64_t m) {
+            const double a = -2.0 * 3.14159265358979323846 * static_cast<double>(m % N) / static_cast<double>(N);
+            return make_float2(static_cast<float>(std::cos(a)), static_cast<float>(std::sin(a)));
+        };
+        for (int i = 0; i < nh; ++i) th[i] = w(static_cast<int64_t>(i) * kTwSplit);
+        for (int i = 0; i < kTwSplit; ++i) tl[i] = w(i);
+        if ((e = cudaMalloc(&g->d_th, nh * sizeof(float2))) != cudaSuccess ||
+            (e = cudaMalloc(&g->d_tl, kTwSplit * sizeof(float2))) != cudaSuccess ||
+            (e = cudaMemcpy(g->d_th, th.data(), nh * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (e = cudaMemcpy(g->d_tl, tl.data(), kTwSplit * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return e;
+        g->z_frames = std::max<int64_t>(1, z_budget_bytes / (static_cast<int64_t>(N) * 8));
+        if ((e = cudaMalloc(&g->d_z, static_cast<size_t>(g->z_frames) * N * 8)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+namespace {
+size_t smem_bytes(int elems) { return static_cast<size_t>(2 * (elems + elems / 16 + 1)) * sizeof(float2); }
+
+template <typename K>
+cudaError_t launch_gen(K kernel, const GenArgs& a, int64_t items, int elems, int n_sms, cudaStream_t st) {
+    const size_t smem = smem_bytes(elems);
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    int occ = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kGThreads, smem) != cudaSuccess || occ < 1)
+        occ = 1;
+    const int64_t grid = std::min<int64_t>(items, static_cast<int64_t>(n_sms) * occ);
+    kernel<<<static_cast<unsigned>(grid), kGThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t gen_pfb_launch(const PfbLaunch& L, const GenPlan& g, cudaStream_t st) {
+    if (L.F <= 0) return cudaSuccess;
+    GenArgs a{};
+    a.carry = reinterpret_cast<const uint32_t*>(L.carry);
+    a.cl = L.cl;
+    a.buf = reinterpret_cast<const uint32_t*>(L.buf);
+    a.N = g.N;
+    a.T = L.taps_kernel;
+    a.h = L.h;
+    a.fa = g.fa;
+    a.fb = g.fb;
+    a.tw_a = g.d_tw;               // stage offsets of fa and fb index the one table
+    a.tw_b = g.d_tw;
+    a.th = g.d_th;
+    a.tl = g.d_tl;
+    a.N1 = g.N1;
+    a.N2 = g.N2;
+    a.gla = g.gla;
+    a.glb = g.glb;
+    a.z = g.d_z;
+    a.bins = L.bins;
+    a.n_tones = L.n_tones;
+    a.full = static_cast<float2*>(L.full);
+    a.full_ld = L.full_ld;
+    a.tones = static_cast<float2*>(L.tones);
+    a.tones_ld = L.tones_ld;
+    a.fo = L.frame_offset;
+    if (g.N1 == 1) {
+        a.F = L.F;
+        a.k0 = 0;
+        return launch_gen(gen_single_kernel, a, L.F, g.N, L.n_sms, st);
+    }
+    const int ga = 1 << g.gla, gb = 1 << g.glb;
+    const int64_t groups_a = (g.N2 + ga - 1) / ga, groups_b = (g.N1 + gb - 1) / gb;
+    for (int64_t k0 = 0; k0 < L.F; k0 += g.z_frames) {
+        a.k0 = k0;
+        a.F = std::min<int64_t>(g.z_frames, L.F - k0);
+        cudaError_t e = launch_gen(gen_pass_a_kernel, a, a.F * groups_a, g.N1 * ga, L.n_sms, st);
+        if (e != cudaSuccess) return e;
+        e = launch_gen(gen_pass_b_kernel, a, a.F * groups_b, g.N2 * gb, L.n_sms, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace rfr

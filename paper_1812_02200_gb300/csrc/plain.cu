@@ -84,7 +84,7 @@ cudaError_t plain_pfb(const int16_t* iq, int64_t n, int N, int T, const float* h
     }
     float2* v = static_cast<float2*>(*scratch);
     float2* y = direct ? static_cast<float2*>(full) : v + F * N;
-    if (*fft_batch != F * 1000000LL + N) {
+    if (*fft_batch != F * 33554432LL + N) {
         if (*fft_plan) {
             cufftDestroy(static_cast<cufftHandle>(reinterpret_cast<uintptr_t>(*fft_plan)));
             *fft_plan = nullptr;
@@ -95,7 +95,7 @@ cudaError_t plain_pfb(const int16_t* iq, int64_t n, int N, int T, const float* h
             CUFFT_SUCCESS)
             return cudaErrorUnknown;
         *fft_plan = reinterpret_cast<void*>(static_cast<uintptr_t>(ph));
-        *fft_batch = F * 1000000LL + N;
+        *fft_batch = F * 33554432LL + N;
     }
     const cufftHandle ph = static_cast<cufftHandle>(reinterpret_cast<uintptr_t>(*fft_plan));
     cufftSetStream(ph, st);

@@ -83,11 +83,11 @@ uint64_t freq_to_word(double f, double fs) {
 }
 
 int32_t word_to_bin(uint64_t word, int32_t n) {
-    if (n < 2 || (n & (n - 1)) != 0) return -1;
-    int lg = 0;
-    while ((int32_t(1) << lg) != n) ++lg;
-    const uint64_t rounded = word + (uint64_t(1) << (63 - lg));   // + half a bin
-    return static_cast<int32_t>(rounded >> (64 - lg));
+    // round(word * n / 2^64) mod n, ties up: floor((word*n + 2^63) / 2^64) mod n
+    if (n < 2) return -1;
+    const unsigned __int128 q = static_cast<unsigned __int128>(word) * static_cast<uint64_t>(n) +
+                                (static_cast<unsigned __int128>(1) << 63);
+    return static_cast<int32_t>(static_cast<uint64_t>(q >> 64) % static_cast<uint64_t>(n));
 }
 
 }  // namespace rfr

@@ -48,8 +48,33 @@ struct PfbLaunch {
     int variant;        // 0 = best available, 1 = shared-memory int16 ring only
 };
 bool pfb_uses_ring(int log2n, int taps);
+
+// PFB for any N = 2^a 3^b 5^c 7^d <= 2^24 (pfb_general.cu): mixed-radix
+// in-CTA FFT, one pass for N <= 16384, the four-step split N = N1*N2 above.
+constexpr int kGenMaxStages = 24;
+struct GenFft {                 // one mixed-radix transform length
+    int n = 0;
+    int nst = 0;                // stages
+    int radix[kGenMaxStages];
+    int ns[kGenMaxStages];      // span: product of the earlier radices
+    int tw_off[kGenMaxStages];  // offset of the stage's twiddles in the table
+};
+struct GenPlan {
+    int N = 0, N1 = 1, N2 = 0;  // N1 == 1: single pass
+    int gla = 0, glb = 0;       // log2 of the transforms per CTA in pass A / B
+    GenFft fa{}, fb{};          // lengths N1 (pass A) and N2 (pass B / single pass)
+    float2* d_tw = nullptr;     // stage twiddles of fa and fb (absolute tw_off)
+    float2* d_th = nullptr;     // W_N^(4096 i)
+    float2* d_tl = nullptr;     // W_N^i, i < 4096
+    float2* d_z = nullptr;      // between-pass buffer, z_frames x N
+    int64_t z_frames = 0;
+};
+bool gen_supported(int64_t n);
+cudaError_t gen_plan_init(GenPlan* g, int N, int64_t z_budget_bytes);
+void gen_plan_free(GenPlan* g);
 int pfb_kernel_taps(int log2n, int taps);
 cudaError_t pfb_launch(const PfbLaunch& L, cudaStream_t st);
+cudaError_t gen_pfb_launch(const PfbLaunch& L, const GenPlan& g, cudaStream_t st);
 
 // ------------------------------------------------------------- demod
 // Split-FP16 tensor-core demodulation; see demod_*.cu.
@@ -138,6 +163,8 @@ cudaError_t carry_update(const int16_t* old_carry, int64_t cl, const int16_t* bu
 struct rfr_plan {
     int mode = 0;
     int32_t N = 0, T = 0, Tk = 0, log2n = 0;   // PFB (Tk: kernel taps, zero-padded)
+    bool gen = false;                          // PFB through the any-N kernels
+    rfr::GenPlan gplan;
     int32_t L = 0, D = 0, Lpad = 0;            // demod
     int64_t W = 0, H = 0;                      // window and hop (samples)
     uint32_t out_flags = 0;

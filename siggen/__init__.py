@@ -145,9 +145,10 @@ def distinct_bins(rng: np.random.Generator, n_chan: int, count: int, min_sep: in
 
 
 def bin_words(bins, n_chan: int) -> np.ndarray:
-    """Bin-centred uint64 words c * 2^64 / N (exact for N a power of two)."""
-    sh = 64 - int(np.log2(n_chan))
-    return np.array([(int(c) << sh) & (2 ** 64 - 1) for c in bins], np.uint64)
+    """Bin-centred uint64 words c * 2^64 / N, rounded to the nearest integer
+    (exact for N a power of two)."""
+    n = int(n_chan)
+    return np.array([((int(c) << 64) + n // 2) // n % 2 ** 64 for c in bins], np.uint64)
 
 
 def random_words(rng: np.random.Generator, count: int) -> np.ndarray:

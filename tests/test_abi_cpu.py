@@ -52,10 +52,10 @@ def test_host_word_and_bin_rules_match_oracle():
     fs = 200e6
     for f in list(r.uniform(-1.5 * fs, 1.5 * fs, 200)) + [0.0, fs / 4, -fs / 2, 40e3, 99.99e6]:
         assert rfr.freq_to_word(f, fs) == oracle.freq_to_word(f, fs)
-    for n in (16, 64, 4096, 16384):
+    for n in (2, 3, 16, 64, 100, 4096, 16384, 10 ** 5, 10 ** 7, 2 ** 24):
         for w in r.integers(0, 2 ** 64, 300, dtype=np.uint64):
             assert rfr.word_to_bin(int(w), n) == oracle.word_to_bin(int(w), n)
-    assert rfr.word_to_bin(123, 100) == -1
+    assert rfr.word_to_bin(123, 1) == -1
 
 
 def test_status_strings(so):

@@ -1,0 +1,154 @@
+"""GPU parity of the PFB for any channel count N = 2^a 3^b 5^c 7^d up to
+2^24 (Sec. III.A: Fig. 3 channelizes with N = 10^5, the section reports up to
+10^7 bins) against the FP64 oracle, through the C ABI: the one-pass
+mixed-radix kernel (N <= 8192), the four-step two-pass form above it, and
+powers of two outside the fused kernels' range.  Same tolerance as the
+power-of-two path: relative error <= 1e-5 per tone channel and per spectrum
+channel against the RMS channel norm."""
+import numpy as np
+import pytest
+
+import oracle
+import siggen
+from helpers import TOL, rel_channels_vs_rms, rel_rows
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+def _taps(N, T, win, beta):
+    _, h32 = oracle.pfb_prototype(N, T, win, beta)
+    return h32.astype(np.float64)
+
+
+def _run(plan, x_np, n_tones, N, full=True):
+    x = torch.from_numpy(x_np).to(DEV)
+    F = plan.frames_for(x.shape[0])
+    fo = torch.zeros((F, N), dtype=torch.complex64, device=DEV) if full else None
+    to = torch.zeros((n_tones, F), dtype=torch.complex64, device=DEV) if n_tones else None
+    assert plan.push_into(x, fo, to) == F
+    torch.cuda.synchronize()
+    return (None if fo is None else fo.cpu().numpy()), (None if to is None else to.cpu().numpy())
+
+
+CASES = [
+    # N, T, window, beta, frames
+    (2, 4, "hann", 0.0, 300),             # below the fused kernels' range
+    (3, 1, "rect", 0.0, 300),
+    (8, 2, "hamming", 0.0, 300),
+    (100, 4, "hamming", 0.0, 200),
+    (1000, 8, "kaiser", 9.0, 100),
+    (2401, 3, "hann", 0.0, 60),           # 7^4: radix-7 stages only
+    (6000, 16, "blackman", 0.0, 30),
+    (6720, 4, "hann", 0.0, 40),           # 2^6 * 3 * 5 * 7
+    (10000, 4, "kaiser", 9.0, 20),        # two passes
+    (19683, 2, "hann", 0.0, 10),          # 3^9, two passes of radix-3 stages
+    (32768, 8, "kaiser", 9.0, 10),        # power of two above the fused kernels
+    (100000, 4, "hamming", 0.0, 8),       # Fig. 3's N and A_v
+]
+
+
+@pytest.mark.parametrize("N,T,win,beta,frames", CASES)
+def test_any_n_parity(lib, N, T, win, beta, frames):
+    n_tones = min(24, N)
+    extra = N // 3 + 1                     # ragged tail (residue, no frame)
+    case = siggen.pfb_case(N * frames + extra, N, n_tones, seed=4000 + N + T,
+                           amp=(200.0, 1500.0), sigma=8.0)
+    plan = lib.Plan(N, T, window=win, beta=beta, words=case["words"], full=True, tones=True)
+    bins = plan.bins()
+    assert np.array_equal(bins, [oracle.word_to_bin(int(w), N) for w in case["words"]])
+    h64p, h32p = plan.taps_table()
+    h64o, h32o = oracle.pfb_prototype(N, T, win, beta)
+    assert np.abs(h32p.view(np.int32).astype(np.int64) - h32o.view(np.int32).astype(np.int64)).max() <= 1
+    full, tones = _run(plan, case["x"], n_tones, N)
+    assert full.shape[0] == frames
+    ref = oracle.pfb(case["x"], N, T, h32o.astype(np.float64), bins=bins)
+    e_t = rel_rows(tones, ref["tones"])
+    e_f = rel_channels_vs_rms(full, ref["full"])
+    print(f"N={N} T={T}: max tone rel err {e_t.max():.3e}, max channel err {e_f.max():.3e}")
+    assert e_t.max() < TOL, e_t.max()
+    assert e_f.max() < TOL, e_f.max()
+    assert np.array_equal(tones, full[:, bins].T)     # the gather is an exact copy
+
+
+@pytest.mark.parametrize("N,T,frames", [(10 ** 7, 4, 2), (1 << 24, 2, 2)])
+def test_largest_n_parity(lib, N, T, frames):
+    """The section's largest channel count (10^7) and the largest N accepted
+    (2^24): two frames against the oracle's FIR and length-N FFT; tones in
+    full, the spectrum on every 997th channel plus the tone bins."""
+    n_tones = 16
+    case = siggen.pfb_case(N * frames + 7, N, n_tones, seed=91 + T, amp=(500.0, 2000.0), sigma=8.0)
+    plan = lib.Plan(N, T, window="hann", words=case["words"], full=True, tones=True)
+    full, tones = _run(plan, case["x"], n_tones, N)
+    ref = oracle.pfb(case["x"], N, T, _taps(N, T, "hann", 0.0), bins=plan.bins())
+    e_t = rel_rows(tones, ref["tones"])
+    assert e_t.max() < TOL, e_t.max()
+    cols = np.union1d(np.arange(0, N, 997), plan.bins())
+    e_f = rel_channels_vs_rms(full[:, cols], ref["full"][:, cols])
+    print(f"N={N}: max tone rel err {e_t.max():.3e}, sampled channel err {e_f.max():.3e}")
+    assert e_f.max() < TOL, e_f.max()
+
+
+def test_paper_fig3_crossover_on_gpu(lib):
+    """Fig. 3 on the GPU path: N = 10^5, A_v = 4, Hamming; a tone half-way
+    between channels b and b+1 shows in both at about -6 dB of a
+    channel-centred tone of the same amplitude (int16 input)."""
+    N, T, b, A = 100000, 4, 31415, 6000.0
+    m = np.arange(N * (T + 2), dtype=np.float64)
+
+    def q(z):
+        return np.stack([np.rint(z.real), np.rint(z.imag)], axis=1).astype(np.int16)
+
+    centred = q(A * np.exp(2j * np.pi * ((b * m) % N) / N))
+    half = q(A * np.exp(2j * np.pi * (((2 * b + 1) * m) % (2 * N)) / (2 * N)))
+    out = []
+    for x in (centred, half):
+        plan = lib.Plan(N, T, window="hamming", words=[], full=True, tones=False)
+        full, _ = _run(plan, x, 0, N)
+        out.append(np.abs(full[T + 1]))
+    ref = out[0][b]
+    for c in (b, b + 1):
+        db = 20 * np.log10(out[1][c] / ref)
+        assert abs(db + 6.0) < 0.25, (c, db)
+
+
+@pytest.mark.parametrize("N,T", [(1000, 8), (10000, 4)])
+def test_any_n_streamed_and_resumed_bit_exact(lib, N, T):
+    """Random push sizes, and a state export / import half-way, give the
+    same frames bit for bit as one push of the whole stream."""
+    rng = np.random.default_rng(N)
+    frames = 40 if N <= 1000 else 12
+    case = siggen.pfb_case(N * frames + 11, N, 6, seed=5 + N)
+    x = torch.from_numpy(case["x"]).to(DEV)
+    one = lib.Plan(N, T, window="hann", words=case["words"], full=True, tones=True)
+    f1, t1 = _run(one, case["x"], 6, N)
+    F = f1.shape[0]
+    fo = torch.zeros((F, N), dtype=torch.complex64, device=DEV)
+    to = torch.zeros((6, F), dtype=torch.complex64, device=DEV)
+    st = lib.Plan(N, T, window="hann", words=case["words"], full=True, tones=True)
+    pos = off = 0
+    n = x.shape[0]
+    half_done = False
+    while pos < n:
+        cnt = int(min(n - pos, rng.integers(1, 3 * N)))
+        off += st.push_into(x[pos:pos + cnt], fo, to, frame_offset=off)
+        pos += cnt
+        if not half_done and pos > n // 2:
+            torch.cuda.synchronize()
+            blob = st.state_export()
+            st = lib.Plan(N, T, window="hann", words=case["words"], full=True, tones=True)
+            st.state_import(blob)
+            half_done = True
+    torch.cuda.synchronize()
+    assert off == F
+    assert np.array_equal(fo.cpu().numpy(), f1) and np.array_equal(to.cpu().numpy(), t1)
+
+
+def test_unsupported_n_is_rejected(lib):
+    """N with a prime factor above 7 is refused with RFR_E_UNSUPPORTED."""
+    for N in (11, 13 * 64, 10007):
+        with pytest.raises(lib.RfrError) as e:
+            lib.Plan(N, 4, window="hann", words=[], full=True, tones=False)
+        assert e.value.status == -7
