@@ -14,7 +14,8 @@ bin-centred tones, integer phase and bin rules for any N, the paper's -6 dB
 cross-over of adjacent channels from the prototype and from a whole PFB run at
 Fig. 3's N = 10^5, Eq. 1's chirp phase checked with Python
 integers and against its FP64 formula, the zero-rate chirp equal to the NCO
-demodulator, a chirp demodulated against itself).  No function is "parity
+demodulator, a chirp demodulated against itself, the multi-tone transmit
+buffer against the library inverse FFT and its own demodulation).  No function is "parity
 unpinned".
 """
 from __future__ import annotations
@@ -75,6 +76,7 @@ def _load():
             "orc_chirp_rate_word": (u64, [dbl, dbl]),
             "orc_chirp_synth": (C.c_int, [u64, u64, dbl, i64, i64, P]),
             "orc_chirp_demod_i16": (C.c_int, [P, i64, i32, i32, P, P, P, i32, i64, i64, P]),
+            "orc_tones_synth": (C.c_int, [P, P, P, i32, i64, i64, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -234,3 +236,15 @@ def chirp_demod(x: np.ndarray, L: int, D: int, h: np.ndarray, start_words, rate_
     _check(lib.orc_chirp_demod_i16(_ptr(xi), n, L, D, _ptr(h), _ptr(sw), _ptr(rw), len(sw), k_begin,
                                    k_end, _ptr(out)), "chirp_demod")
     return out
+
+
+def tones_synth(words, amps, m0: int, n: int, phase_words=None):
+    """Multi-tone transmit samples: returns (values complex128 [n], iq int16 [n, 2])."""
+    w = np.ascontiguousarray(np.asarray(words, dtype=np.uint64))
+    a = np.ascontiguousarray(np.asarray(amps, dtype=np.float64))
+    p = None if phase_words is None else np.ascontiguousarray(np.asarray(phase_words, dtype=np.uint64))
+    val = np.empty(n, np.complex128)
+    iq = np.empty((n, 2), np.int16)
+    _check(_load().orc_tones_synth(_ptr(w), _ptr(p), _ptr(a), len(w), int(m0), int(n), _ptr(val), _ptr(iq)),
+           "tones_synth")
+    return val, iq

@@ -512,3 +512,45 @@ int orc_chirp_demod_i16(const int16_t* iq, int64_t n_samples, int32_t L, int32_t
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Transmit buffer (Sec. III: the GPU also generates the transmission       */
+/* buffer; the tones are the same NCO words the receiver demodulates)       */
+/* ------------------------------------------------------------------------ */
+
+/* Multi-tone transmit samples m0 .. m0+n-1:
+ *   s(m) = sum_t A_t exp(+i*2*pi*((w_t*m + p_t) mod 2^64)/2^64)
+ * (a tone at word w is brought to DC by the receiver's mixer exp(-i*w*m)),
+ * in FP64 with the angle formed from the exact integer phase as in
+ * orc_mixer; value[2m], value[2m+1] receive Re, Im (may be NULL), iq the
+ * round-half-even of each, clamped to int16 (may be NULL).  p may be NULL
+ * (zero phase offsets). */
+int orc_tones_synth(const uint64_t* words, const uint64_t* phase_words, const double* amps, int32_t n_tones,
+                    int64_t m0, int64_t n, double* value, int16_t* iq)
+{
+    if (n < 0 || n_tones < 0 || (n_tones > 0 && (!words || !amps))) return -1;
+    for (int64_t i = 0; i < n; ++i) {
+        const uint64_t m = (uint64_t)(m0 + i);
+        double re = 0.0, im = 0.0;
+        for (int32_t t = 0; t < n_tones; ++t) {
+            const uint64_t ph = words[t] * m + (phase_words ? phase_words[t] : 0);
+            const double a = (double)(int64_t)ph * ldexp(M_PI, -63);
+            re += amps[t] * cos(a);
+            im += amps[t] * sin(a);
+        }
+        if (value) {
+            value[2 * i] = re;
+            value[2 * i + 1] = im;
+        }
+        if (iq) {
+            double r = nearbyint(re), q = nearbyint(im);
+            if (r > 32767.0) r = 32767.0;
+            if (r < -32768.0) r = -32768.0;
+            if (q > 32767.0) q = 32767.0;
+            if (q < -32768.0) q = -32768.0;
+            iq[2 * i] = (int16_t)r;
+            iq[2 * i + 1] = (int16_t)q;
+        }
+    }
+    return 0;
+}

@@ -111,15 +111,19 @@ __device__ __forceinline__ void dft_any(float2* x) {
 
 // One Stockham stage of radix R over G = 2^gl2 interleaved transforms of
 // length n, from src to dst (points at [gpad(i*G + g)]).
+// j / Ns as umulhi(j, ns_magic) with ns_magic = ceil(2^32 / Ns) for Ns > 1:
+// exact while j * Ns < 2^32 (here j, Ns < 2^13).
 template <int R>
 __device__ __forceinline__ void gen_stage(const float2* __restrict__ src, float2* __restrict__ dst, int n, int gl2,
-                                          int Ns, const float2* __restrict__ tw) {
+                                          int Ns, uint32_t ns_magic, const float2* __restrict__ tw) {
     const int nR = n / R;
     const int nb = nR << gl2;
     const int gm = (1 << gl2) - 1;
+#pragma unroll 2
     for (int u = threadIdx.x; u < nb; u += kGThreads) {
         const int g = u & gm, j = u >> gl2;
-        const int k = j % Ns;
+        const int q = Ns == 1 ? j : static_cast<int>(__umulhi(static_cast<uint32_t>(j), ns_magic));
+        const int k = j - q * Ns;
         float2 v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = src[gpad(((j + r * nR) << gl2) + g)];
@@ -143,13 +147,13 @@ __device__ float2* gen_fft(float2* buf0, float2* buf1, const GenFft& f, int gl2,
     for (int s = 0; s < f.nst; ++s) {
         const float2* t = tw + f.tw_off[s];
         switch (f.radix[s]) {
-        case 16: gen_stage<16>(src, dst, f.n, gl2, f.ns[s], t); break;
-        case 8: gen_stage<8>(src, dst, f.n, gl2, f.ns[s], t); break;
-        case 4: gen_stage<4>(src, dst, f.n, gl2, f.ns[s], t); break;
-        case 2: gen_stage<2>(src, dst, f.n, gl2, f.ns[s], t); break;
-        case 3: gen_stage<3>(src, dst, f.n, gl2, f.ns[s], t); break;
-        case 5: gen_stage<5>(src, dst, f.n, gl2, f.ns[s], t); break;
-        default: gen_stage<7>(src, dst, f.n, gl2, f.ns[s], t); break;
+        case 16: gen_stage<16>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
+        case 8: gen_stage<8>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
+        case 4: gen_stage<4>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
+        case 2: gen_stage<2>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
+        case 3: gen_stage<3>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
+        case 5: gen_stage<5>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
+        default: gen_stage<7>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
         }
         float2* tmp = src;
         src = dst;
@@ -182,19 +186,48 @@ struct GenArgs {
     int64_t fo;             // frame offset in the caller's outputs
 };
 
-__device__ __forceinline__ float2 load_x(const GenArgs& a, int64_t vi) {
-    return iq_to_f2(vi < a.cl ? __ldg(a.carry + vi) : __ldg(a.buf + (vi - a.cl)));
-}
-
-__device__ __forceinline__ float2 fir_point(const GenArgs& a, int64_t base, int pos) {
-    float ar = 0.f, ai = 0.f;
-    for (int t = 0; t < a.T; ++t) {
-        const float hv = __ldg(a.h + static_cast<int64_t>(t) * a.N + pos);
-        const float2 x = load_x(a, base + static_cast<int64_t>(t) * a.N + pos);
-        ar = fmaf(hv, x.x, ar);
-        ai = fmaf(hv, x.y, ai);
+// FIR of the points e = tid, tid + 512, ... < E of one frame into sm: point e
+// sits at frame position pos(e) (or is zero when pos(e) < 0).  Four points
+// and four taps at a time, all 32 loads issued before the FMAs.
+template <typename Pos>
+__device__ __forceinline__ void fir_points(const GenArgs& a, int64_t base, int E, Pos pos_of, float2* sm) {
+    constexpr int P = 4, TG = 4;
+    for (int e0 = threadIdx.x; e0 < E; e0 += P * kGThreads) {
+        int pos[P];
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            const int e = e0 + q * kGThreads;
+            pos[q] = e < E ? pos_of(e) : -1;
+        }
+        float ar[P] = {0.f, 0.f, 0.f, 0.f}, ai[P] = {0.f, 0.f, 0.f, 0.f};
+        for (int t0 = 0; t0 < a.T; t0 += TG) {
+            float hv[P][TG];
+            uint32_t xw[P][TG];
+#pragma unroll
+            for (int q = 0; q < P; ++q)
+#pragma unroll
+                for (int tt = 0; tt < TG; ++tt) {
+                    const bool ok = pos[q] >= 0 && t0 + tt < a.T;
+                    const int64_t o = static_cast<int64_t>(t0 + tt) * a.N + pos[q];
+                    const int64_t vi = base + o;
+                    hv[q][tt] = ok ? __ldg(a.h + o) : 0.f;
+                    xw[q][tt] = ok ? (vi < a.cl ? __ldg(a.carry + vi) : __ldg(a.buf + (vi - a.cl))) : 0u;
+                }
+#pragma unroll
+            for (int q = 0; q < P; ++q)
+#pragma unroll
+                for (int tt = 0; tt < TG; ++tt) {
+                    const float2 x = iq_to_f2(xw[q][tt]);
+                    ar[q] = fmaf(hv[q][tt], x.x, ar[q]);
+                    ai[q] = fmaf(hv[q][tt], x.y, ai[q]);
+                }
+        }
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            const int e = e0 + q * kGThreads;
+            if (e < E) sm[gpad(e)] = make_float2(ar[q], ai[q]);
+        }
     }
-    return make_float2(ar, ai);
 }
 
 // Shared memory: two buffers of gpad(elems) points each.
@@ -206,7 +239,7 @@ __global__ void __launch_bounds__(kGThreads, 1) gen_single_kernel(const GenArgs 
     for (int64_t kk = blockIdx.x; kk < a.F; kk += gridDim.x) {
         const int64_t k = a.k0 + kk;
         const int64_t base = k * a.N;
-        for (int p = threadIdx.x; p < a.N; p += kGThreads) sm[gpad(p)] = fir_point(a, base, p);
+        fir_points(a, base, a.N, [](int e) { return e; }, sm);
         __syncthreads();
         const float2* y = gen_fft(sm, sm1, a.fb, 0, a.tw_b);
         if (a.full) {
@@ -229,10 +262,13 @@ __global__ void __launch_bounds__(kGThreads, 1) gen_pass_a_kernel(const GenArgs 
         const int64_t kk = it / groups;
         const int g0 = static_cast<int>(it - kk * groups) << a.gla;
         const int64_t base = (a.k0 + kk) * a.N;
-        for (int e = threadIdx.x; e < E; e += kGThreads) {
-            const int g = e & (GA - 1), p1 = e >> a.gla;
-            sm[gpad(e)] = g0 + g < a.N2 ? fir_point(a, base, p1 * a.N2 + g0 + g) : make_float2(0.f, 0.f);
-        }
+        const int N2 = a.N2, gla = a.gla;
+        fir_points(a, base, E,
+                   [=](int e) {
+                       const int g = e & (GA - 1);
+                       return g0 + g < N2 ? (e >> gla) * N2 + g0 + g : -1;
+                   },
+                   sm);
         __syncthreads();
         const float2* y = gen_fft(sm, sm1, a.fa, a.gla, a.tw_a);
         float2* zf = a.z + kk * a.N;
@@ -308,6 +344,7 @@ bool build_fft(int n, GenFft* f, std::vector<float2>& tw) {
         if (f->nst >= kGenMaxStages) return false;
         f->radix[f->nst] = r;
         f->ns[f->nst] = ns;
+        f->ns_magic[f->nst] = ns > 1 ? static_cast<uint32_t>(((uint64_t(1) << 32) + ns - 1) / ns) : 0u;
         f->tw_off[f->nst] = static_cast<int>(tw.size());
         if (ns > 1) {
             for (int rr = 1; rr < r; ++rr)

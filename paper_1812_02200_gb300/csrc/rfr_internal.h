@@ -57,6 +57,7 @@ struct GenFft {                 // one mixed-radix transform length
     int nst = 0;                // stages
     int radix[kGenMaxStages];
     int ns[kGenMaxStages];      // span: product of the earlier radices
+    uint32_t ns_magic[kGenMaxStages];   // ceil(2^32 / ns)
     int tw_off[kGenMaxStages];  // offset of the stage's twiddles in the table
 };
 struct GenPlan {

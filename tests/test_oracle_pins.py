@@ -390,3 +390,55 @@ def test_chirp_loopback_own_chirp_is_constant():
     th = ph.view(np.int64).astype(np.float64) * (np.pi / 2 ** 63)
     assert np.all(np.abs(x[:, 0] - amp * np.cos(th)) <= 0.5 + 1e-9)
     assert np.all(np.abs(x[:, 1] - amp * np.sin(th)) <= 0.5 + 1e-9)
+
+
+# ------------------------------------------------------- transmit buffer
+def test_tones_synth_grid_tones_equal_library_ifft():
+    """Tones on an N-point grid (words b*2^64/N, phase words q*2^64/N): one
+    period of the transmit buffer is N times the library inverse FFT of the
+    sparse spectrum A_t e^{2 pi i q_t/N} at bins b_t; the buffer repeats with
+    period N."""
+    N = 1024
+    r = np.random.default_rng(21)
+    bins = r.choice(N, 40, replace=False)
+    q = r.integers(0, N, 40)
+    amps = r.uniform(10.0, 200.0, 40)
+    words = [(int(b) << 54) for b in bins]
+    ph = [(int(v) << 54) for v in q]
+    val, iq = oracle.tones_synth(words, amps, 0, 2 * N, ph)
+    spec = np.zeros(N, complex)
+    spec[bins] = amps * np.exp(2j * np.pi * q / N)
+    ref = N * np.fft.ifft(spec)
+    assert np.allclose(val[:N], ref, rtol=0, atol=1e-9)
+    assert np.allclose(val[N:], val[:N], rtol=0, atol=1e-9)
+    assert np.array_equal(iq[:, 0], np.clip(np.rint(val.real), -32768, 32767).astype(np.int16))
+
+
+def test_tones_synth_offgrid_linearity_and_own_demodulation():
+    """Off-grid words: the buffer is the sum of its single-tone buffers, and
+    demodulating the FP64 buffer at one tone's word with a long square window
+    returns that tone's amplitude and phase (the others average out)."""
+    r = np.random.default_rng(5)
+    words = [int(w) for w in r.integers(0, 2 ** 64, 3, dtype=np.uint64)]
+    amps = [300.0, 200.0, 100.0]
+    m0, n = 12345, 4096
+    val, _ = oracle.tones_synth(words, amps, m0, n)
+    parts = sum(oracle.tones_synth([w], [a], m0, n)[0] for w, a in zip(words, amps))
+    assert np.allclose(val, parts, rtol=0, atol=1e-9)
+    # the single-tone buffer is A exp(i*2*pi*w*m/2^64) at every sample
+    from fractions import Fraction
+    for m in (m0, m0 + 1, m0 + n - 1):
+        ph = (words[0] * m) % 2 ** 64
+        ang = 2 * np.pi * float(Fraction(ph if ph < 2 ** 63 else ph - 2 ** 64, 2 ** 64))
+        v = oracle.tones_synth([words[0]], [1.0], m, 1)[0][0]
+        assert abs(v - np.exp(1j * ang)) < 1e-12
+    # demodulation of the buffer from sample 0 at tone 0's word: a square
+    # window of L samples returns A_0 (phase 0) up to the other tones' leakage
+    L = 4096
+    full, _ = oracle.tones_synth(words, amps, 0, 2 * L)
+    h = np.full(L, 1.0 / L)
+    d = oracle.demod(full, L, L, h, [words[0]])[0]
+    # Dirichlet kernel: |sin(pi L f) / (L sin(pi f))| <= 1 / (2 L |f|), |f| <= 1/2
+    dmin = min(abs(((w - words[0] + 2 ** 63) % 2 ** 64 - 2 ** 63) / 2 ** 64) for w in words[1:])
+    leak = sum(amps[1:]) / (2 * L * dmin)
+    assert np.all(np.abs(d[1:] - amps[0]) <= leak + 1e-9)
