@@ -62,6 +62,20 @@ def source_sha(paths):
     return h.hexdigest()[:16]
 
 
+def profile_value(name, paths, key):
+    """A number from a committed ncu summary taken on the current source."""
+    p = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        txt = f.read()
+    m_sha = re.search(r"source_sha:\s*([0-9a-f]+)", txt)
+    m_v = re.search(key + r":\s*([0-9.eE+]+)", txt)
+    if not m_sha or not m_v or m_sha.group(1) != source_sha(paths):
+        return None
+    return float(m_v.group(1))
+
+
 def profile_traffic(name, paths):
     """Per-launch DRAM traffic from a committed ncu summary, if it was taken
     on the current kernel source (else None)."""
@@ -366,6 +380,51 @@ def run_chirp(args, dev, stream):
                      "value": x.shape[0] / (ms_dem * 1e-3) / 1e6, "unit": UNIT, "ms": ms_dem}}
     plan.close()
     del x, out
+    return res
+
+
+# -------------------------------------------------------- transmit buffer
+TX_SOURCES = ["paper_1812_02200_gb300/csrc/tx.cu"]
+
+
+def run_tx(args, dev, stream, words):
+    """Transmit buffer (Sec. III): 2^24 complex int16 samples of the workload's
+    1000 tones at full scale (sum A = 8191 - 32), FP32 sines of the exact
+    integer phase.  ALU-bound: the roofline is the FP32 lane-issue rate
+    (152 SMs x 128 lanes x SM clock) over the instructions one tone-sample
+    takes (from the committed ncu summary of the same source, if any)."""
+    import torch
+
+    from paper_1812_02200_gb300 import rfr
+    r = siggen.rng_for(1812)
+    amps = r.uniform(0.5, 1.0, len(words))
+    amps *= (8191.0 - 32.0) / amps.sum()
+    tx = rfr.Tx(words, amps, siggen.random_words(r, len(words)))
+    n = 1 << 24
+    out = torch.empty((n, 2), dtype=torch.int16, device=dev)
+    tx.synthesize(0, out, stream=stream)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    e0.record(stream)
+    for i in range(reps):
+        tx.synthesize(i * n, out, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / reps
+    ts = n * len(words) / (ms * 1e-3)
+    res = {"workload": f"2^24 complex int16 samples of {len(words)} tones (sum A = 8159)",
+           "value": n / (ms * 1e-3) / 1e6, "unit": UNIT, "ms": ms,
+           "tone_samples_per_s": ts, "error_bound_lsb": tx.error_bound}
+    inst = profile_value("tx_synth_kernel.md", TX_SOURCES, "inst_per_tone_sample")
+    if inst:
+        peak = 152 * 128 * 2.07e9
+        res["roofline"] = {"bound": "alu", "achieved": ts * inst / 1e12, "peak": peak / 1e12,
+                           "unit": "T lane-instructions/s", "frac": ts * inst / peak,
+                           "inst_per_tone_sample": inst,
+                           "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz"}
+    tx.close()
+    del out
     return res
 
 
@@ -677,6 +736,7 @@ def run_ours(args, ws, rank, local):
     del full, tones
     torch.cuda.empty_cache()
     large_n = None if args.no_large_n else run_large_n(args, dev, stream, x, c["words"])
+    txr = None if args.no_tx else run_tx(args, dev, stream, c["words"])
     if not args.no_demod:
         demod = run_demod(args, dev, stream, rank)
     chirp = None if args.no_chirp else run_chirp(args, dev, stream)
@@ -710,6 +770,7 @@ def run_ours(args, ws, rank, local):
         "serve": serve,
         "chirp": chirp,
         "any_n_pfb": large_n,
+        "tx": txr,
         "e2e": e2e,
         "cpu_baseline": cpu,
         "clocks": clk,
@@ -732,6 +793,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-chirp", action="store_true")
     ap.add_argument("--no-large-n", action="store_true")
+    ap.add_argument("--no-tx", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-loads", default="1,5,10,20", help="offered loads, Gsamples/s")
     ap.add_argument("--serve-seconds", type=float, default=2.0)

@@ -168,12 +168,39 @@ uint64_t rfr_chirp_rate_word(double k_hz_per_s, double fs_hz);
  * GPU in real time (Sec. III.C): samples m0 .. m0+n-1 of
  *     x[m] = (round(A*cos(2*pi*p(m)/2^64)), round(A*sin(2*pi*p(m)/2^64)))
  * as complex int16 (round half to even, clamped to the int16 range) into the
- * device buffer iq_out [n][2].  Computed in FP32; samples within 0.02 of a
- * rounding tie are recomputed in FP64, so every sample is the FP64-rounded
- * value.  0 <= amplitude <= 32767.  Asynchronous on `stream`.
+ * device buffer iq_out [n][2].  Computed in FP32 on the phase reduced to a
+ * quarter turn; a component whose FP32 value lies within twice its error
+ * bound (A*(pi*2^-27 + 2^-23 + 2^-24) + |fl(A) - A|) of a rounding tie is
+ * recomputed in FP64, so every sample is the FP64-rounded value.
+ * 0 <= amplitude <= 32767.  Asynchronous on `stream`.
  */
 rfr_status rfr_chirp_synthesize(uint64_t start_word, uint64_t rate_word, double amplitude, int64_t m0,
                                 int64_t n_samples, int16_t* iq_out, void* stream);
+
+/*
+ * Transmit buffer (Sec. III: the transmission buffer is generated on the GPU
+ * from the tones the receiver demodulates).  A generator holds n_tones NCO
+ * words w_t, phase words p_t (NULL: all zero) and amplitudes A_t >= 0
+ * (sum A_t <= 10^6), copied from host arrays, and writes samples m0 .. m0+n-1
+ *     s(m) = sum_t A_t exp(+i*2*pi*((w_t*m + p_t) mod 2^64) / 2^64)
+ * as complex int16 (each component rounded half to even, clamped) into the
+ * device buffer iq_out [n][2], asynchronously on `stream`.  A tone at word w
+ * is brought to DC by the receiver's mixer for the same word.
+ *
+ * Precision: FP32 sines and cosines of the exact integer phase, FP32 sums over
+ * 32 tones, FP64 over the chunks.  Before rounding each component is within
+ * e = rfr_tx_error_bound(tx) of the exact sum, so every component whose exact
+ * value lies farther than e from a rounding tie is the exact rounding; the few
+ * within e of a tie are one of the two neighbouring integers.  Samples are
+ * computed independently: any split of [m0, m0+n) gives the same samples.
+ * Errors: RFR_E_INVALID (arguments), RFR_E_NOMEM, RFR_E_CUDA (launch).
+ */
+typedef struct rfr_tx rfr_tx;
+rfr_status rfr_tx_create(rfr_tx** tx, const uint64_t* words, const uint64_t* phase_words,
+                         const double* amplitudes, int32_t n_tones);
+rfr_status rfr_tx_synthesize(rfr_tx* tx, int64_t m0, int64_t n, int16_t* iq_out, void* stream);
+double rfr_tx_error_bound(const rfr_tx* tx);
+void rfr_tx_destroy(rfr_tx* tx);
 
 /* Frees everything the plan owns (waits for its outstanding work). */
 void rfr_plan_destroy(rfr_plan* plan);

@@ -105,6 +105,10 @@ _SIGS = {
                                         C.c_int32]),
     "rfr_chirp_rate_word": (C.c_uint64, [C.c_double, C.c_double]),
     "rfr_chirp_synthesize": (C.c_int, [C.c_uint64, C.c_uint64, C.c_double, C.c_int64, C.c_int64, _P, _P]),
+    "rfr_tx_create": (C.c_int, [C.POINTER(_P), _P, _P, _P, C.c_int32]),
+    "rfr_tx_synthesize": (C.c_int, [_P, C.c_int64, C.c_int64, _P, _P]),
+    "rfr_tx_error_bound": (C.c_double, [_P]),
+    "rfr_tx_destroy": (None, [_P]),
     "rfr_demod_noalloc": (C.c_int, [_P, C.c_int64, _P, C.c_int32, C.c_int32, _P, C.c_int32, _P, C.c_int64, _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -151,6 +155,42 @@ def chirp_synthesize(start_word: int, rate_word: int, amplitude: float, m0: int,
                                    float(amplitude), int(m0), out.shape[0], out.data_ptr(), _stream_ptr(stream))
     if st != OK:
         raise RfrError(st, "rfr_chirp_synthesize")
+
+
+class Tx:
+    """Multi-tone transmit buffer generator (rfr_tx_*): int16 [n, 2] samples of
+    sum_t A_t exp(+i 2 pi (w_t m + p_t) / 2^64)."""
+
+    def __init__(self, words, amplitudes, phase_words=None):
+        w = np.ascontiguousarray(np.asarray(words, dtype=np.uint64))
+        a = np.ascontiguousarray(np.asarray(amplitudes, dtype=np.float64))
+        p = None if phase_words is None else np.ascontiguousarray(np.asarray(phase_words, dtype=np.uint64))
+        h = _P()
+        st = _lib.rfr_tx_create(C.byref(h), w.ctypes.data, None if p is None else p.ctypes.data,
+                                a.ctypes.data, len(w))
+        if st != OK:
+            raise RfrError(st, "rfr_tx_create")
+        self._h = h
+
+    @property
+    def error_bound(self) -> float:
+        return float(_lib.rfr_tx_error_bound(self._h))
+
+    def synthesize(self, m0: int, out, stream=None):
+        st = _lib.rfr_tx_synthesize(self._h, int(m0), out.shape[0], out.data_ptr(), _stream_ptr(stream))
+        if st != OK:
+            raise RfrError(st, "rfr_tx_synthesize")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.rfr_tx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Plan:
