@@ -25,8 +25,8 @@
 // FFT stages follow the conventions of fft_dev.cuh (Stockham autosort,
 // butterfly j reads x[j + r*n/R], twiddle W_{R*Ns}^{r*k} with k = j mod Ns,
 // writes y[(j/Ns)*R*Ns + k + r*Ns]; twiddle table [(r-1)*Ns + k] per stage).
-// Stages alternate between two shared-memory buffers of the G x n <= 8192
-// points (G transforms interleaved, element (i, g) at i*G + g, padded one
+// Stages alternate between two shared-memory buffers of the G x n <= 4096
+// (256-thread CTAs) or 8192 (512-thread CTAs) points (G transforms interleaved, element (i, g) at i*G + g, padded one
 // element in 16).
 #include <cuda_runtime.h>
 
@@ -43,8 +43,15 @@ namespace rfr {
 
 namespace {
 
-constexpr int kGThreads = 512;
-constexpr int kGElems = 8192;                      // points per CTA (G * n)
+// Two CTA shapes: TH threads hold TH * 16 points (G * n): 256 threads with
+// 4096 points (three CTAs per SM), or 512 threads with 8192 points (one CTA
+// per SM, for the largest N, where 4096 points would force single-point runs).
+constexpr int kGElemsMax = 8192;
+template <int TH>
+struct GenCfg {
+    static constexpr int kElems = TH * 16;
+    static constexpr int kMinBlocks = TH == 256 ? 3 : 1;
+};
 constexpr int kTwSplit = 4096;                     // inter-pass twiddle: m = hi*4096 + lo
 
 __device__ __forceinline__ int gpad(int e) { return e + (e >> 4); }
@@ -113,14 +120,14 @@ __device__ __forceinline__ void dft_any(float2* x) {
 // length n, from src to dst (points at [gpad(i*G + g)]).
 // j / Ns as umulhi(j, ns_magic) with ns_magic = ceil(2^32 / Ns) for Ns > 1:
 // exact while j * Ns < 2^32 (here j, Ns < 2^13).
-template <int R>
+template <int R, int TH>
 __device__ __forceinline__ void gen_stage(const float2* __restrict__ src, float2* __restrict__ dst, int n, int gl2,
                                           int Ns, uint32_t ns_magic, const float2* __restrict__ tw) {
     const int nR = n / R;
     const int nb = nR << gl2;
     const int gm = (1 << gl2) - 1;
 #pragma unroll 2
-    for (int u = threadIdx.x; u < nb; u += kGThreads) {
+    for (int u = threadIdx.x; u < nb; u += TH) {
         const int g = u & gm, j = u >> gl2;
         const int q = Ns == 1 ? j : static_cast<int>(__umulhi(static_cast<uint32_t>(j), ns_magic));
         const int k = j - q * Ns;
@@ -141,19 +148,20 @@ __device__ __forceinline__ void gen_stage(const float2* __restrict__ src, float2
 
 // The whole transform: the points start in buf0; returns the buffer that
 // holds the result (buf0 or buf1, by the parity of the stage count).
+template <int TH>
 __device__ float2* gen_fft(float2* buf0, float2* buf1, const GenFft& f, int gl2, const float2* __restrict__ tw) {
     float2* src = buf0;
     float2* dst = buf1;
     for (int s = 0; s < f.nst; ++s) {
         const float2* t = tw + f.tw_off[s];
         switch (f.radix[s]) {
-        case 16: gen_stage<16>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
-        case 8: gen_stage<8>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
-        case 4: gen_stage<4>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
-        case 2: gen_stage<2>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
-        case 3: gen_stage<3>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
-        case 5: gen_stage<5>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
-        default: gen_stage<7>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
+        case 16: gen_stage<16, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
+        case 8: gen_stage<8, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
+        case 4: gen_stage<4, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
+        case 2: gen_stage<2, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
+        case 3: gen_stage<3, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
+        case 5: gen_stage<5, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
+        default: gen_stage<7, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
         }
         float2* tmp = src;
         src = dst;
@@ -186,46 +194,64 @@ struct GenArgs {
     int64_t fo;             // frame offset in the caller's outputs
 };
 
-// FIR of the points e = tid, tid + 512, ... < E of one frame into sm: point e
-// sits at frame position pos(e) (or is zero when pos(e) < 0).  Four points
-// and four taps at a time, all 32 loads issued before the FMAs.
-template <typename Pos>
+// FIR of the points e = tid, tid + TH, ... < E of one frame into sm: point e
+// sits at frame position pos(e) (or is zero when pos(e) < 0), four points at a
+// time.  A frame whose window lies entirely in the new buffer (the common
+// case) reads it through one pointer; a frame that starts in the carry takes
+// the per-sample carry / buffer select.
+template <int TH, typename Pos>
 __device__ __forceinline__ void fir_points(const GenArgs& a, int64_t base, int E, Pos pos_of, float2* sm) {
-    constexpr int P = 4, TG = 4;
-    for (int e0 = threadIdx.x; e0 < E; e0 += P * kGThreads) {
+    constexpr int P = 4;
+    const bool fast = base >= a.cl;
+    for (int e0 = threadIdx.x; e0 < E; e0 += P * TH) {
         int pos[P];
+        bool valid[P];
 #pragma unroll
         for (int q = 0; q < P; ++q) {
-            const int e = e0 + q * kGThreads;
-            pos[q] = e < E ? pos_of(e) : -1;
+            const int e = e0 + q * TH;
+            const int pp = e < E ? pos_of(e) : -1;
+            valid[q] = pp >= 0;
+            pos[q] = valid[q] ? pp : 0;        // an in-bounds dummy point, zeroed below
         }
         float ar[P] = {0.f, 0.f, 0.f, 0.f}, ai[P] = {0.f, 0.f, 0.f, 0.f};
-        for (int t0 = 0; t0 < a.T; t0 += TG) {
-            float hv[P][TG];
-            uint32_t xw[P][TG];
+        if (fast) {
+            const float* hp = a.h;
+            const uint32_t* xp = a.buf + (base - a.cl);
+#pragma unroll 4
+            for (int t = 0; t < a.T; ++t) {
+                float hv[P];
+                uint32_t xw[P];
 #pragma unroll
-            for (int q = 0; q < P; ++q)
+                for (int q = 0; q < P; ++q) {
+                    hv[q] = __ldg(hp + pos[q]);
+                    xw[q] = __ldg(xp + pos[q]);
+                }
 #pragma unroll
-                for (int tt = 0; tt < TG; ++tt) {
-                    const bool ok = pos[q] >= 0 && t0 + tt < a.T;
-                    const int64_t o = static_cast<int64_t>(t0 + tt) * a.N + pos[q];
+                for (int q = 0; q < P; ++q) {
+                    const float2 x = iq_to_f2(xw[q]);
+                    ar[q] = fmaf(hv[q], x.x, ar[q]);
+                    ai[q] = fmaf(hv[q], x.y, ai[q]);
+                }
+                hp += a.N;
+                xp += a.N;
+            }
+        } else {
+            for (int t = 0; t < a.T; ++t) {
+#pragma unroll
+                for (int q = 0; q < P; ++q) {
+                    const int64_t o = static_cast<int64_t>(t) * a.N + pos[q];
                     const int64_t vi = base + o;
-                    hv[q][tt] = ok ? __ldg(a.h + o) : 0.f;
-                    xw[q][tt] = ok ? (vi < a.cl ? __ldg(a.carry + vi) : __ldg(a.buf + (vi - a.cl))) : 0u;
+                    const float hv = __ldg(a.h + o);
+                    const float2 x = iq_to_f2(vi < a.cl ? __ldg(a.carry + vi) : __ldg(a.buf + (vi - a.cl)));
+                    ar[q] = fmaf(hv, x.x, ar[q]);
+                    ai[q] = fmaf(hv, x.y, ai[q]);
                 }
-#pragma unroll
-            for (int q = 0; q < P; ++q)
-#pragma unroll
-                for (int tt = 0; tt < TG; ++tt) {
-                    const float2 x = iq_to_f2(xw[q][tt]);
-                    ar[q] = fmaf(hv[q][tt], x.x, ar[q]);
-                    ai[q] = fmaf(hv[q][tt], x.y, ai[q]);
-                }
+            }
         }
 #pragma unroll
         for (int q = 0; q < P; ++q) {
-            const int e = e0 + q * kGThreads;
-            if (e < E) sm[gpad(e)] = make_float2(ar[q], ai[q]);
+            const int e = e0 + q * TH;
+            if (e < E) sm[gpad(e)] = valid[q] ? make_float2(ar[q], ai[q]) : make_float2(0.f, 0.f);
         }
     }
 }
@@ -233,26 +259,28 @@ __device__ __forceinline__ void fir_points(const GenArgs& a, int64_t base, int E
 // Shared memory: two buffers of gpad(elems) points each.
 __device__ __forceinline__ float2* second_buffer(float2* sm, int elems) { return sm + gpad(elems) + 1; }
 
-__global__ void __launch_bounds__(kGThreads, 1) gen_single_kernel(const GenArgs a) {
+template <int TH>
+__global__ void __launch_bounds__(TH, GenCfg<TH>::kMinBlocks) gen_single_kernel(const GenArgs a) {
     extern __shared__ float2 sm[];
     float2* sm1 = second_buffer(sm, a.N);
     for (int64_t kk = blockIdx.x; kk < a.F; kk += gridDim.x) {
         const int64_t k = a.k0 + kk;
         const int64_t base = k * a.N;
-        fir_points(a, base, a.N, [](int e) { return e; }, sm);
+        fir_points<TH>(a, base, a.N, [](int e) { return e; }, sm);
         __syncthreads();
-        const float2* y = gen_fft(sm, sm1, a.fb, 0, a.tw_b);
+        const float2* y = gen_fft<TH>(sm, sm1, a.fb, 0, a.tw_b);
         if (a.full) {
             float2* row = a.full + (a.fo + k) * a.full_ld;
-            for (int c = threadIdx.x; c < a.N; c += kGThreads) row[c] = y[gpad(c)];
+            for (int c = threadIdx.x; c < a.N; c += TH) row[c] = y[gpad(c)];
         }
-        for (int t = threadIdx.x; t < a.n_tones; t += kGThreads)
+        for (int t = threadIdx.x; t < a.n_tones; t += TH)
             a.tones[t * a.tones_ld + a.fo + k] = y[gpad(__ldg(a.bins + t))];
         __syncthreads();
     }
 }
 
-__global__ void __launch_bounds__(kGThreads, 1) gen_pass_a_kernel(const GenArgs a) {
+template <int TH>
+__global__ void __launch_bounds__(TH, GenCfg<TH>::kMinBlocks) gen_pass_a_kernel(const GenArgs a) {
     extern __shared__ float2 sm[];
     const int GA = 1 << a.gla;
     const int groups = (a.N2 + GA - 1) >> a.gla;
@@ -263,16 +291,16 @@ __global__ void __launch_bounds__(kGThreads, 1) gen_pass_a_kernel(const GenArgs 
         const int g0 = static_cast<int>(it - kk * groups) << a.gla;
         const int64_t base = (a.k0 + kk) * a.N;
         const int N2 = a.N2, gla = a.gla;
-        fir_points(a, base, E,
+        fir_points<TH>(a, base, E,
                    [=](int e) {
                        const int g = e & (GA - 1);
                        return g0 + g < N2 ? (e >> gla) * N2 + g0 + g : -1;
                    },
                    sm);
         __syncthreads();
-        const float2* y = gen_fft(sm, sm1, a.fa, a.gla, a.tw_a);
+        const float2* y = gen_fft<TH>(sm, sm1, a.fa, a.gla, a.tw_a);
         float2* zf = a.z + kk * a.N;
-        for (int e = threadIdx.x; e < E; e += kGThreads) {
+        for (int e = threadIdx.x; e < E; e += TH) {
             const int g = e & (GA - 1), c1 = e >> a.gla, p2 = g0 + g;
             if (p2 < a.N2) {
                 const int m = p2 * c1;                       // < N1*N2 = N
@@ -284,7 +312,8 @@ __global__ void __launch_bounds__(kGThreads, 1) gen_pass_a_kernel(const GenArgs 
     }
 }
 
-__global__ void __launch_bounds__(kGThreads, 1) gen_pass_b_kernel(const GenArgs a) {
+template <int TH>
+__global__ void __launch_bounds__(TH, GenCfg<TH>::kMinBlocks) gen_pass_b_kernel(const GenArgs a) {
     extern __shared__ float2 sm[];
     const int GB = 1 << a.glb;
     const int groups = (a.N1 + GB - 1) >> a.glb;
@@ -296,21 +325,21 @@ __global__ void __launch_bounds__(kGThreads, 1) gen_pass_b_kernel(const GenArgs 
         const float2* zf = a.z + kk * a.N;
         for (int g = 0; g < GB; ++g) {
             const int c1 = c0 + g;
-            for (int p2 = threadIdx.x; p2 < a.N2; p2 += kGThreads)
+            for (int p2 = threadIdx.x; p2 < a.N2; p2 += TH)
                 sm[gpad((p2 << a.glb) + g)] =
                     c1 < a.N1 ? zf[static_cast<int64_t>(c1) * a.N2 + p2] : make_float2(0.f, 0.f);
         }
         __syncthreads();
-        const float2* y = gen_fft(sm, sm1, a.fb, a.glb, a.tw_b);
+        const float2* y = gen_fft<TH>(sm, sm1, a.fb, a.glb, a.tw_b);
         const int64_t k = a.k0 + kk;
         if (a.full) {
             float2* row = a.full + (a.fo + k) * a.full_ld;
-            for (int e = threadIdx.x; e < E; e += kGThreads) {
+            for (int e = threadIdx.x; e < E; e += TH) {
                 const int g = e & (GB - 1), c2 = e >> a.glb;
                 if (c0 + g < a.N1) row[c0 + g + static_cast<int64_t>(a.N1) * c2] = y[gpad(e)];
             }
         }
-        for (int t = threadIdx.x; t < a.n_tones; t += kGThreads) {
+        for (int t = threadIdx.x; t < a.n_tones; t += TH) {
             const int b = __ldg(a.bins + t);
             const int c1 = b % a.N1;
             if (c1 >= c0 && c1 < c0 + GB)
@@ -391,20 +420,16 @@ cudaError_t gen_plan_init(GenPlan* g, int N, int64_t z_budget_bytes) {
     if (!gen_supported(N)) return cudaErrorInvalidValue;
     g->N = N;
     std::vector<float2> tw;
-    if (N <= kGElems) {
-        g->N1 = 1;
-        g->N2 = N;
-        if (!build_fft(N, &g->fb, tw)) return cudaErrorInvalidValue;
-    } else {
-        // N = N1*N2 with N1, N2 <= 8192; pick the split with the largest
-        // min(GA, GB) (the longest contiguous runs), then the more balanced.
+    // the best N = N1*N2 split for CTAs of `elems` points: largest
+    // min(GA, GB) (the longest contiguous runs), then the more balanced
+    auto best_split = [&](int elems, int* n1o, int* n2o, int* score_o) {
         int best = -1, best_score = -1, best_bal = 0;
-        for (int n2 = 2; n2 <= kGElems; ++n2) {
+        for (int n2 = 2; n2 <= elems; ++n2) {
             if (N % n2 != 0) continue;
             const int n1 = N / n2;
-            if (n1 < 2 || n1 > kGElems) continue;
-            const int ga = std::min(16, 1 << floor_log2(kGElems / n1));
-            const int gb = std::min(16, 1 << floor_log2(kGElems / n2));
+            if (n1 < 2 || n1 > elems) continue;
+            const int ga = std::min(16, 1 << floor_log2(elems / n1));
+            const int gb = std::min(16, 1 << floor_log2(elems / n2));
             const int score = std::min(ga, gb), bal = -std::abs(n1 - n2);
             if (score > best_score || (score == best_score && bal > best_bal)) {
                 best = n2;
@@ -412,11 +437,28 @@ cudaError_t gen_plan_init(GenPlan* g, int N, int64_t z_budget_bytes) {
                 best_bal = bal;
             }
         }
-        if (best < 0) return cudaErrorInvalidValue;
-        g->N2 = best;
-        g->N1 = N / best;
-        g->gla = floor_log2(std::min(16, 1 << floor_log2(kGElems / g->N1)));
-        g->glb = floor_log2(std::min(16, 1 << floor_log2(kGElems / g->N2)));
+        *n2o = best;
+        *n1o = best > 0 ? N / best : 0;
+        *score_o = best_score;
+        return best > 0;
+    };
+    if (N <= kGElemsMax) {
+        g->threads = N <= GenCfg<256>::kElems ? 256 : 512;
+        g->N1 = 1;
+        g->N2 = N;
+        if (!build_fft(N, &g->fb, tw)) return cudaErrorInvalidValue;
+    } else {
+        int n1 = 0, n2 = 0, score = 0;
+        g->threads = 256;
+        if (!best_split(GenCfg<256>::kElems, &n1, &n2, &score) || score < 4) {
+            g->threads = 512;
+            if (!best_split(GenCfg<512>::kElems, &n1, &n2, &score)) return cudaErrorInvalidValue;
+        }
+        const int elems = g->threads * 16;
+        g->N1 = n1;
+        g->N2 = n2;
+        g->gla = floor_log2(std::min(16, 1 << floor_log2(elems / g->N1)));
+        g->glb = floor_log2(std::min(16, 1 << floor_log2(elems / g->N2)));
         if (!build_fft(g->N1, &g->fa, tw)) return cudaErrorInvalidValue;
         if (!build_fft(g->N2, &g->fb, tw)) return cudaErrorInvalidValue;
     }
@@ -449,17 +491,39 @@ cudaError_t gen_plan_init(GenPlan* g, int N, int64_t z_budget_bytes) {
 namespace {
 size_t smem_bytes(int elems) { return static_cast<size_t>(2 * (elems + elems / 16 + 1)) * sizeof(float2); }
 
-template <typename K>
+template <int TH, typename K>
 cudaError_t launch_gen(K kernel, const GenArgs& a, int64_t items, int elems, int n_sms, cudaStream_t st) {
     const size_t smem = smem_bytes(elems);
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     int occ = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kGThreads, smem) != cudaSuccess || occ < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, TH, smem) != cudaSuccess || occ < 1)
         occ = 1;
     const int64_t grid = std::min<int64_t>(items, static_cast<int64_t>(n_sms) * occ);
-    kernel<<<static_cast<unsigned>(grid), kGThreads, smem, st>>>(a);
+    kernel<<<static_cast<unsigned>(grid), TH, smem, st>>>(a);
     return cudaGetLastError();
+}
+}  // namespace
+
+namespace {
+template <int TH>
+cudaError_t gen_run(GenArgs a, const PfbLaunch& L, const GenPlan& g, cudaStream_t st) {
+    if (g.N1 == 1) {
+        a.F = L.F;
+        a.k0 = 0;
+        return launch_gen<TH>(gen_single_kernel<TH>, a, L.F, g.N, L.n_sms, st);
+    }
+    const int ga = 1 << g.gla, gb = 1 << g.glb;
+    const int64_t groups_a = (g.N2 + ga - 1) / ga, groups_b = (g.N1 + gb - 1) / gb;
+    for (int64_t k0 = 0; k0 < L.F; k0 += g.z_frames) {
+        a.k0 = k0;
+        a.F = std::min<int64_t>(g.z_frames, L.F - k0);
+        cudaError_t e = launch_gen<TH>(gen_pass_a_kernel<TH>, a, a.F * groups_a, g.N1 * ga, L.n_sms, st);
+        if (e != cudaSuccess) return e;
+        e = launch_gen<TH>(gen_pass_b_kernel<TH>, a, a.F * groups_b, g.N2 * gb, L.n_sms, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 }  // namespace
 
@@ -490,22 +554,7 @@ cudaError_t gen_pfb_launch(const PfbLaunch& L, const GenPlan& g, cudaStream_t st
     a.tones = static_cast<float2*>(L.tones);
     a.tones_ld = L.tones_ld;
     a.fo = L.frame_offset;
-    if (g.N1 == 1) {
-        a.F = L.F;
-        a.k0 = 0;
-        return launch_gen(gen_single_kernel, a, L.F, g.N, L.n_sms, st);
-    }
-    const int ga = 1 << g.gla, gb = 1 << g.glb;
-    const int64_t groups_a = (g.N2 + ga - 1) / ga, groups_b = (g.N1 + gb - 1) / gb;
-    for (int64_t k0 = 0; k0 < L.F; k0 += g.z_frames) {
-        a.k0 = k0;
-        a.F = std::min<int64_t>(g.z_frames, L.F - k0);
-        cudaError_t e = launch_gen(gen_pass_a_kernel, a, a.F * groups_a, g.N1 * ga, L.n_sms, st);
-        if (e != cudaSuccess) return e;
-        e = launch_gen(gen_pass_b_kernel, a, a.F * groups_b, g.N2 * gb, L.n_sms, st);
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    return g.threads == 256 ? gen_run<256>(a, L, g, st) : gen_run<512>(a, L, g, st);
 }
 
 }  // namespace rfr
