@@ -184,6 +184,7 @@ struct GenArgs {
     const float2* th;       // W_N^{4096*i}
     const float2* tl;       // W_N^{i}, i < 4096
     int N1, N2, gla, glb;
+    uint32_t n2_magic;      // ceil(2^32 / N2): f / N2 = umulhi(f, n2_magic) for f < GB*N2
     float2* z;              // [F][N1][N2]
     const int32_t* bins;
     int n_tones;
@@ -195,13 +196,13 @@ struct GenArgs {
 };
 
 // FIR of the points e = tid, tid + TH, ... < E of one frame into sm: point e
-// sits at frame position pos(e) (or is zero when pos(e) < 0), four points at a
-// time.  A frame whose window lies entirely in the new buffer (the common
+// sits at frame position pos(e) (or is zero when pos(e) < 0), eight points
+// at a time.  A frame whose window lies entirely in the new buffer (the common
 // case) reads it through one pointer; a frame that starts in the carry takes
 // the per-sample carry / buffer select.
 template <int TH, typename Pos>
 __device__ __forceinline__ void fir_points(const GenArgs& a, int64_t base, int E, Pos pos_of, float2* sm) {
-    constexpr int P = 4;
+    constexpr int P = 8;
     const bool fast = base >= a.cl;
     for (int e0 = threadIdx.x; e0 < E; e0 += P * TH) {
         int pos[P];
@@ -213,7 +214,9 @@ __device__ __forceinline__ void fir_points(const GenArgs& a, int64_t base, int E
             valid[q] = pp >= 0;
             pos[q] = valid[q] ? pp : 0;        // an in-bounds dummy point, zeroed below
         }
-        float ar[P] = {0.f, 0.f, 0.f, 0.f}, ai[P] = {0.f, 0.f, 0.f, 0.f};
+        float ar[P], ai[P];
+#pragma unroll
+        for (int q = 0; q < P; ++q) ar[q] = ai[q] = 0.f;
         if (fast) {
             const float* hp = a.h;
             const uint32_t* xp = a.buf + (base - a.cl);
@@ -322,12 +325,15 @@ __global__ void __launch_bounds__(TH, GenCfg<TH>::kMinBlocks) gen_pass_b_kernel(
     for (int64_t it = blockIdx.x; it < a.F * groups; it += gridDim.x) {
         const int64_t kk = it / groups;
         const int c0 = static_cast<int>(it - kk * groups) << a.glb;
-        const float2* zf = a.z + kk * a.N;
-        for (int g = 0; g < GB; ++g) {
-            const int c1 = c0 + g;
-            for (int p2 = threadIdx.x; p2 < a.N2; p2 += TH)
-                sm[gpad((p2 << a.glb) + g)] =
-                    c1 < a.N1 ? zf[static_cast<int64_t>(c1) * a.N2 + p2] : make_float2(0.f, 0.f);
+        // rows c0 .. c0+GB-1 of Z are one contiguous block of GB*N2 points
+        const float2* zf = a.z + kk * a.N + static_cast<int64_t>(c0) * a.N2;
+        const int rows = min(GB, a.N1 - c0);
+        const int cnt = rows * a.N2;
+#pragma unroll 4
+        for (int f = threadIdx.x; f < E; f += TH) {
+            const int g = static_cast<int>(__umulhi(static_cast<uint32_t>(f), a.n2_magic));   // f / N2
+            const int p2 = f - g * a.N2;
+            sm[gpad((p2 << a.glb) + g)] = f < cnt ? zf[f] : make_float2(0.f, 0.f);
         }
         __syncthreads();
         const float2* y = gen_fft<TH>(sm, sm1, a.fb, a.glb, a.tw_b);
@@ -544,6 +550,7 @@ cudaError_t gen_pfb_launch(const PfbLaunch& L, const GenPlan& g, cudaStream_t st
     a.tl = g.d_tl;
     a.N1 = g.N1;
     a.N2 = g.N2;
+    a.n2_magic = static_cast<uint32_t>(((uint64_t(1) << 32) + g.N2 - 1) / g.N2);
     a.gla = g.gla;
     a.glb = g.glb;
     a.z = g.d_z;
