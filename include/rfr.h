@@ -261,8 +261,26 @@ rfr_status rfr_state_export(rfr_plan* plan, void* host, size_t* bytes);
 rfr_status rfr_state_import(rfr_plan* plan, const void* host, size_t bytes);
 
 /*
- * rfr_plan_set_accum_chunk -- demodulation only: how many 32-tap K blocks
- * (1..64, default 2) the tensor cores accumulate in TMEM before the epilogue
+ * rfr_plan_set_demod_products -- demodulation only: the form of the tensor-
+ * core contraction.  4: the real embedding of the complex product (four real
+ * products per complex multiply-add).  3 (the default wherever D % 64 == 0,
+ * 4 otherwise): the Gauss form
+ *   P1 = sum ((xr+xi)/2) cr, P2 = sum xr (ci-cr), P3 = sum xi (cr+ci),
+ *   Re = 2 P1 - P3, Im = 2 P1 + P2
+ * (three real products; the same definition, Sec. III.B, rounded
+ * differently), which needs D % 64 == 0 (RFR_E_UNSUPPORTED otherwise) and
+ * builds its tap planes on the first switch (allocates, synchronises the
+ * device).  Either switch resets the accumulation chunk to the form's
+ * default (2 blocks: 64 taps in the four-product form, 128 in the three-
+ * product form, which reaches the same accuracy).  Set it before the first
+ * push of a stream.
+ */
+rfr_status rfr_plan_set_demod_products(rfr_plan* plan, int32_t products);
+
+/*
+ * rfr_plan_set_accum_chunk -- demodulation only: how many K blocks (32 taps
+ * each in the four-product form, 64 in the three-product form; 1..64,
+ * default 2) the tensor cores accumulate in TMEM before the epilogue
  * adds the partial sums into FP32 registers.  Longer chunks are slightly
  * faster and less accurate (the tensor cores' internal accumulation error
  * grows with the partial sums); the default keeps the weakest tones of the

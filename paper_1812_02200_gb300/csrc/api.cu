@@ -123,7 +123,19 @@ rfr_status check_status(rfr_plan* p) {
 }
 
 rfr_status ensure_demod_scratch(rfr_plan* p, int64_t F, int64_t F0) {
-    const int64_t rows = static_cast<int64_t>(rfr::demod_xs_rows(F, p->Lpad, p->D));
+    if (p->demod_products == 3) {
+        // six fp16 planes [rows][D] of the Gauss three-product form
+        const int64_t rows3 = static_cast<int64_t>(rfr::demod3_xs_rows(F, p->Lpad3, p->D));
+        if (rows3 > p->xs3_rows_cap) {
+            cudaDeviceSynchronize();
+            dev_free(p->d_xs3);
+            p->d_xs3 = nullptr;
+            p->xs3_rows_cap = 0;
+            RFR_CUDA(p, dev_alloc(&p->d_xs3, static_cast<size_t>(rows3) * 6 * p->D * sizeof(uint16_t)));
+            p->xs3_rows_cap = rows3;
+        }
+    }
+    const int64_t rows = p->demod_products == 3 ? 0 : static_cast<int64_t>(rfr::demod_xs_rows(F, p->Lpad, p->D));
     if (rows > p->xs_rows_cap) {
         cudaDeviceSynchronize();
         dev_free(p->d_xs_hi);
@@ -135,8 +147,8 @@ rfr_status ensure_demod_scratch(rfr_plan* p, int64_t F, int64_t F0) {
         RFR_CUDA(p, dev_alloc(&p->d_xs_lo, bytes));
         p->xs_rows_cap = rows;
     }
-    const int64_t rot = static_cast<int64_t>(rfr::demod_anchor_rows(F0, F)) * p->ntp +
-                        static_cast<int64_t>(p->ntp) * rfr::kDemodBM;
+    const int64_t ntp = p->demod_products == 3 ? p->ntp3 : p->ntp;
+    const int64_t rot = static_cast<int64_t>(rfr::demod_anchor_rows(F0, F)) * ntp + ntp * rfr::kDemodBM;
     if (rot > p->rot_cap) {
         cudaDeviceSynchronize();
         dev_free(p->d_rot);
@@ -248,7 +260,19 @@ rfr_status push_core(rfr_plan* p, const int16_t* iq, int64_t n, const rfr_output
                 L.n_sms = p->n_sms;
                 L.kchunk = p->accum_chunk;
                 L.raster_group = p->tune.demod_raster;
-                RFR_CUDA(p, rfr::demod_launch(L, st));
+                if (p->demod_products == 3) {
+                    L.Lpad = p->Lpad3;
+                    L.ntp = p->ntp3;
+                    L.b_hi = p->d_b3;
+                    L.b_lo = nullptr;
+                    L.inv_scale = std::ldexp(1.0, -p->tap_exp3);
+                    L.xs_hi = p->d_xs3;
+                    L.xs_lo = nullptr;
+                    L.xs_rows = p->xs3_rows_cap;
+                    RFR_CUDA(p, rfr::demod3_launch(L, st));
+                } else {
+                    RFR_CUDA(p, rfr::demod_launch(L, st));
+                }
             }
         }
     }
@@ -291,7 +315,7 @@ void destroy(rfr_plan* p) {
     for (void* q : {static_cast<void*>(p->d_h), p->d_tw, static_cast<void*>(p->d_bins),
                     static_cast<void*>(p->d_words), static_cast<void*>(p->d_rates), static_cast<void*>(p->d_h32), p->d_c32, p->d_bhi, p->d_blo,
                     static_cast<void*>(p->d_status), static_cast<void*>(p->d_carry[0]),
-                    static_cast<void*>(p->d_carry[1]), p->d_xs_hi, p->d_xs_lo, p->d_rot, p->d_qfull,
+                    static_cast<void*>(p->d_carry[1]), p->d_xs_hi, p->d_xs_lo, p->d_rot, p->d_qfull, p->d_b3, p->d_xs3,
                     p->d_qtones})
         dev_free(q);
     for (int i = 0; i < 2; ++i) {
@@ -477,6 +501,10 @@ rfr_status rfr_plan_create(rfr_plan** out, int32_t channels, int32_t taps, const
         (e = dev_alloc(&p->d_carry[1], static_cast<size_t>(p->carry_cap) * 4)) != cudaSuccess)
         return bad(cuda_fail(p, e, "plan alloc"));
     if (reset_state(p) != RFR_OK) return bad(RFR_E_CUDA);
+    // demodulation: the Gauss three-product form wherever D allows it
+    if (p->mode == RFR_MODE_DEMOD && !p->words.empty() && p->D % 64 == 0 &&
+        rfr_plan_set_demod_products(p, 3) != RFR_OK)
+        return bad(RFR_E_CUDA);
     e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return bad(cuda_fail(p, e, "plan create"));
     *out = p;
@@ -756,6 +784,40 @@ rfr_status rfr_plan_seek(rfr_plan* p, int64_t start_sample, const int16_t* histo
         if (want > 0)
             RFR_CUDA(p, cudaMemcpy(dst + zeros * 4, history, static_cast<size_t>(want) * 4, cudaMemcpyDefault));
     }
+    return RFR_OK;
+}
+
+rfr_status rfr_plan_set_demod_products(rfr_plan* p, int32_t products) {
+    if (!p || p->mode != RFR_MODE_DEMOD || (products != 3 && products != 4)) return RFR_E_INVALID;
+    if (products == 4) {
+        p->demod_products = 4;
+        p->accum_chunk = 2;
+        return RFR_OK;
+    }
+    if (p->D % 64 != 0) return fail(p, RFR_E_UNSUPPORTED, "the three-product form needs D % 64 == 0");
+    if (p->words.empty()) return fail(p, RFR_E_INVALID, "no tones");
+    if (!p->d_b3) {
+        const int nt = static_cast<int>(p->words.size());
+        p->Lpad3 = (p->L + 63) / 64 * 64;
+        p->ntp3 = (nt + 127) / 128 * 128;
+        p->tap_exp3 = p->tap_exp - 1;      // |ci -+ cr| <= sqrt(2) max|h|
+        const size_t plane = static_cast<size_t>(p->ntp3) * p->Lpad3;
+        double* d_h64 = nullptr;
+        cudaError_t e = dev_alloc(&p->d_b3, plane * 6 * sizeof(uint16_t));
+        if (e == cudaSuccess) e = dev_alloc(&d_h64, static_cast<size_t>(p->L) * 8);
+        if (e == cudaSuccess) e = cudaMemcpy(d_h64, p->h64.data(), static_cast<size_t>(p->L) * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = rfr::demod3_build_taps(d_h64, p->d_words, nt, p->ntp3, p->L, p->Lpad3, p->tap_exp3, p->d_b3, nullptr);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        dev_free(d_h64);
+        if (e != cudaSuccess) {
+            dev_free(p->d_b3);
+            p->d_b3 = nullptr;
+            return cuda_fail(p, e, "three-product tap build");
+        }
+    }
+    p->demod_products = 3;
+    p->accum_chunk = 2;
     return RFR_OK;
 }
 

@@ -30,6 +30,8 @@
 //                           samples (the Toeplitz view's 2-D tensor).
 //   gemm        (per push)  TMA -> smem (128B swizzle) -> tcgen05.mma -> TMEM
 //                           -> register sums -> rotation -> [tone][frame] out.
+//   *3 variants             the Gauss three-product form (see below), a plan
+//                           option (rfr_plan_set_demod_products).
 #include <cuda.h>
 #include <cuda_fp16.h>
 #include <cudaTypedefs.h>
@@ -341,6 +343,280 @@ demod_gemm_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constan
     }
 }
 
+// ---------------------------------------------- Gauss three-product form
+//
+// With x = xr + i xi and C = cr + i ci, the three real contractions
+//   P1 = sum ((xr + xi)/2) cr,   P2 = sum xr (ci - cr),   P3 = sum xi (cr + ci)
+// give Re(x.C) = 2 P1 - P3 and Im(x.C) = 2 P1 + P2: three real products per
+// complex multiply-add instead of the four of the real embedding.  Each A
+// plane ((xr+xi)/2, xr, xi) and B plane (cr, ci-cr, cr+ci) is split into FP16
+// hi/lo as above ((xr+xi)/2 has at most 17 significant bits, exact as hi+lo);
+// each product again takes the three MMAs hi.hi + hi.lo + lo.hi.
+//
+// Tile: 128 frames x 128 tones, K-blocks of 64 complex taps (one plane per
+// TMA stage: A hi, lo 128x64 and B hi, lo 128x64, 64 KB; three stages).  The
+// three products of an accumulation chunk run one after the other, each into
+// one of four 128-column TMEM slots taken in rotation, so the epilogue drains
+// a slot while the MMAs fill the others and every slot is drained three
+// product phases before it is reused.  Sixteen epilogue warps (four per TMEM
+// lane quadrant, 32 tones each) drain a slot with one 32-column load each,
+// adding 2 P1 to both sums, P2 to the imaginary and -P3 to the real sum.
+constexpr int G3_BT = 128;                                 // tones per tile
+constexpr int G3_BK = 64;                                  // complex taps per K-block
+constexpr uint32_t G3_A_BYTES = BM * G3_BK * 2;
+constexpr uint32_t G3_B_BYTES = G3_BT * G3_BK * 2;
+constexpr uint32_t G3_STAGE_BYTES = 2 * G3_A_BYTES + 2 * G3_B_BYTES;
+constexpr int G3_STAGES = 3;
+constexpr int G3_SLOTS = 4;
+constexpr size_t G3_SMEM = 1024 + G3_STAGES * G3_STAGE_BYTES + 256;
+constexpr int G3_EPI_WARPS = 16;          // 4 lane quadrants x 4 groups of 32 tones
+constexpr int G3_THREADS = (G3_EPI_WARPS + 2) * 32;
+
+struct G3Maps {
+    CUtensorMap a[6];   // (x sum/2, xr, xi) x (hi, lo): [rows][D] fp16, Toeplitz view
+    CUtensorMap b[6];   // (cr, ci - cr, cr + ci) x (hi, lo): [ntp][Lpad] fp16, K-major
+};
+
+__global__ void build_taps3_kernel(const double* __restrict__ h, const uint64_t* __restrict__ words,
+                                   int n_tones, int ntp, int L, int Lpad, double scale,
+                                   __half* __restrict__ planes) {
+    const int64_t total = static_cast<int64_t>(ntp) * Lpad;
+    for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
+         idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int t = static_cast<int>(idx / Lpad);
+        const int n = static_cast<int>(idx - static_cast<int64_t>(t) * Lpad);
+        double cr = 0.0, ci = 0.0;
+        if (t < n_tones && n < L) {
+            const uint64_t ph = words[t] * static_cast<uint64_t>(n);
+            const double xs = static_cast<double>(static_cast<int64_t>(ph)) * 0x1p-63;
+            double sn, cs;
+            sincospi(xs, &sn, &cs);
+            const double a = h[n] * scale;
+            cr = a * cs;
+            ci = -a * sn;
+        }
+        const double v[3] = {cr, ci - cr, cr + ci};
+#pragma unroll
+        for (int q = 0; q < 3; ++q) split_store(planes + (2 * q) * total, planes + (2 * q + 1) * total, idx, v[q]);
+    }
+}
+
+// Sample s of [carry | buffer] -> the six planes ((xr+xi)/2, xr, xi) x (hi, lo).
+__global__ void presplit3_kernel(const uint32_t* __restrict__ carry, int64_t cl, const uint32_t* __restrict__ buf,
+                                 int64_t lv, int64_t total, __half* __restrict__ planes) {
+    for (int64_t s = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; s < total;
+         s += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        uint32_t w = 0;
+        if (s < lv) w = s < cl ? carry[s] : buf[s - cl];
+        const float2 f = iq_to_f2(w);
+        const float v[3] = {0.5f * (f.x + f.y), f.x, f.y};      // exact in FP32
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const __half hv = __float2half_rn(v[q]);
+            planes[(2 * q) * total + s] = hv;
+            planes[(2 * q + 1) * total + s] = __float2half_rn(v[q] - __half2float(hv));
+        }
+    }
+}
+
+__global__ void __launch_bounds__(G3_THREADS, 1)
+demod3m_gemm_kernel(const __grid_constant__ G3Maps mp, const GemmArgs g) {
+    extern __shared__ unsigned char smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    unsigned char* smem = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + G3_STAGES * G3_STAGE_BYTES);
+    uint64_t* empty = full + G3_STAGES;
+    uint64_t* sfull = empty + G3_STAGES;
+    uint64_t* sempty = sfull + G3_SLOTS;
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(sempty + G3_SLOTS);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < G3_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < G3_SLOTS; ++b) {
+            mbar_init(&sfull[b], 1);
+            mbar_init(&sempty[b], G3_EPI_WARPS * 32);
+        }
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == G3_EPI_WARPS + 1) {
+        umma::alloc(tmem_holder, TMEM_COLS);
+        umma::relinquish();
+    }
+    if (warp == G3_EPI_WARPS && lane == 0) {
+        for (int i = 0; i < 6; ++i) {
+            tma_prefetch_desc(&mp.a[i]);
+            tma_prefetch_desc(&mp.b[i]);
+        }
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = *tmem_holder;
+    const int n_tiles = g.n_mt * g.n_nt;
+    constexpr uint32_t IDESC = umma::idesc_f16_f32(BM, G3_BT);
+
+    if (warp == G3_EPI_WARPS) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            uint32_t it = 0;
+            bool stop = false;
+            for (int tile = blockIdx.x; tile < n_tiles && !stop; tile += gridDim.x) {
+                int tm, tn;
+                tile_coords(g, tile, tm, tn);
+                const int m0 = tm * BM, n0 = tn * G3_BT;
+                for (int kb0 = 0; kb0 < g.KB && !stop; kb0 += g.kchunk) {
+                    const int kb1 = min(kb0 + g.kchunk, g.KB);
+                    for (int q = 0; q < 3 && !stop; ++q) {
+                        for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                            const int s = it % G3_STAGES;
+                            const uint32_t ph = (it / G3_STAGES) & 1;
+                            if (*abort_flag || !mbar_wait(&empty[s], ph ^ 1, g.status)) {
+                                *abort_flag = 1;
+                                stop = true;
+                                break;
+                            }
+                            unsigned char* st = smem + s * G3_STAGE_BYTES;
+                            mbar_arrive_expect_tx(&full[s], G3_STAGE_BYTES);
+                            const int kt = kb * G3_BK;
+                            const int c0 = kt % g.two_d, c1 = m0 + kt / g.two_d;
+                            tma_load_2d(st, &mp.a[2 * q], c0, c1, &full[s]);
+                            tma_load_2d(st + G3_A_BYTES, &mp.a[2 * q + 1], c0, c1, &full[s]);
+                            tma_load_2d(st + 2 * G3_A_BYTES, &mp.b[2 * q], kt, n0, &full[s]);
+                            tma_load_2d(st + 2 * G3_A_BYTES + G3_B_BYTES, &mp.b[2 * q + 1], kt, n0, &full[s]);
+                        }
+                    }
+                }
+            }
+            // wait for the copies still in flight before leaving
+            for (uint32_t k = 0; k < G3_STAGES && it > 0; ++k) {
+                const uint32_t j = it - 1 - k;
+                if (static_cast<int32_t>(j) < 0) break;
+                mbar_wait(&full[j % G3_STAGES], (j / G3_STAGES) & 1, g.status);
+            }
+        }
+    } else if (warp == G3_EPI_WARPS + 1) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            uint32_t it = 0, phase = 0;
+            bool stop = false;
+            for (int tile = blockIdx.x; tile < n_tiles && !stop; tile += gridDim.x) {
+                for (int kb0 = 0; kb0 < g.KB && !stop; kb0 += g.kchunk) {
+                    const int kb1 = min(kb0 + g.kchunk, g.KB);
+                    for (int q = 0; q < 3 && !stop; ++q, ++phase) {
+                        const uint32_t slot = phase % G3_SLOTS, use = phase / G3_SLOTS;
+                        if (*abort_flag || !mbar_wait(&sempty[slot], (use & 1) ^ 1, g.status)) {
+                            *abort_flag = 1;
+                            stop = true;
+                            break;
+                        }
+                        umma::fence_after_sync();
+                        const uint32_t d_tmem = tmem + slot * G3_BT;
+                        for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                            const int s = it % G3_STAGES;
+                            const uint32_t ph = (it / G3_STAGES) & 1;
+                            if (!mbar_wait(&full[s], ph, g.status)) {
+                                *abort_flag = 1;
+                                stop = true;
+                                break;
+                            }
+                            umma::fence_after_sync();
+                            const uint32_t sa = smem_u32(smem + s * G3_STAGE_BYTES);
+                            const uint32_t ah = sa, al = sa + G3_A_BYTES;
+                            const uint32_t bh = sa + 2 * G3_A_BYTES, bl = bh + G3_B_BYTES;
+#pragma unroll
+                            for (int k = 0; k < G3_BK / 16; ++k) {
+                                const uint32_t off = k * 32;
+                                const uint32_t acc = (kb > kb0 || k > 0) ? 1u : 0u;
+                                umma::mma_f16(d_tmem, umma::desc_k_sw128(ah + off), umma::desc_k_sw128(bh + off), IDESC, acc);
+                                umma::mma_f16(d_tmem, umma::desc_k_sw128(ah + off), umma::desc_k_sw128(bl + off), IDESC, 1u);
+                                umma::mma_f16(d_tmem, umma::desc_k_sw128(al + off), umma::desc_k_sw128(bh + off), IDESC, 1u);
+                            }
+                            umma::commit(&empty[s]);
+                        }
+                        umma::commit(&sfull[slot]);
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------ epilogue (16 warps)
+        const int qd = warp & 3, grp = warp >> 2;          // lane quadrant, 32-tone group
+        const int row = qd * 32 + lane;
+        uint32_t phase = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+            int mt, tn;
+            tile_coords(g, tile, mt, tn);
+            const int m0 = mt * BM, n0 = tn * G3_BT;
+            float re[32], im[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) re[i] = im[i] = 0.f;
+            for (int kb0 = 0; kb0 < g.KB && ok; kb0 += g.kchunk) {
+                for (int q = 0; q < 3; ++q, ++phase) {
+                    const uint32_t slot = phase % G3_SLOTS, use = phase / G3_SLOTS;
+                    if (*abort_flag || !mbar_wait(&sfull[slot], use & 1, g.status)) {
+                        *abort_flag = 1;
+                        ok = false;
+                        break;
+                    }
+                    umma::fence_after_sync();
+                    uint32_t r[32];
+                    umma::ld_32x32b_x32(tmem + (static_cast<uint32_t>(qd * 32) << 16) + slot * G3_BT + grp * 32, r);
+                    umma::wait_ld();
+                    umma::fence_before_sync();
+                    mbar_arrive(&sempty[slot]);
+                    if (q == 0) {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) {
+                            const float v = 2.f * __uint_as_float(r[i]);
+                            re[i] += v;
+                            im[i] += v;
+                        }
+                    } else if (q == 1) {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) im[i] += __uint_as_float(r[i]);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) re[i] -= __uint_as_float(r[i]);
+                    }
+                }
+            }
+            if (!ok) break;
+            const int64_t k = static_cast<int64_t>(m0) + row;
+            if (k < g.F) {
+                const int tb = n0 + grp * 32;
+                const int64_t K = g.F0 + k;
+                const int64_t arow = K / BM - g.F0 / BM;
+                const int si = static_cast<int>(K % BM);
+#pragma unroll
+                for (int tl = 0; tl < 32; ++tl) {
+                    const int t = tb + tl;
+                    if (t < g.n_tones) {
+                        const float2 an = __ldg(g.anchors + arow * g.ntp + t);
+                        const float2 sp = __ldg(g.steps + static_cast<int64_t>(t) * BM + si);
+                        const float2 rot = cmul(an, sp);
+                        const float2 acc = make_float2(re[tl] * g.inv_scale, im[tl] * g.inv_scale);
+                        g.out[static_cast<int64_t>(t) * g.ld + g.fo + k] = cmul(acc, rot);
+                    }
+                }
+            }
+        }
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == G3_EPI_WARPS + 1) {
+        umma::fence_after_sync();
+        umma::dealloc(tmem, TMEM_COLS);
+    }
+}
+
 // ------------------------------------------------------------ host side
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -383,6 +659,8 @@ size_t demod_xs_rows(int64_t F, int Lpad, int D) {
     // frame F-1 reads rows F-1 .. F-1 + (Lpad-1)/D
     return static_cast<size_t>(F + (Lpad - 1) / D);
 }
+
+size_t demod3_xs_rows(int64_t F, int Lpad, int D) { return static_cast<size_t>(F + (Lpad - 1) / D); }
 
 cudaError_t demod_build_taps(const double* d_h, const uint64_t* d_words, int n_tones, int ntp, int L,
                              int Lpad, int e, void* b_hi, void* b_lo, cudaStream_t st) {
@@ -443,6 +721,66 @@ cudaError_t demod_launch(const DemodLaunch& L, cudaStream_t st) {
     const int tiles = n_mt * n_nt;
     const int grid = std::min(tiles, L.n_sms);
     demod_gemm_kernel<<<grid, GEMM_THREADS, GEMM_SMEM, st>>>(mAh, mAl, mBh, mBl, g);
+    return cudaGetLastError();
+}
+
+cudaError_t demod3_build_taps(const double* d_h, const uint64_t* d_words, int n_tones, int ntp, int L, int Lpad,
+                              int e, void* planes, cudaStream_t st) {
+    const int64_t total = static_cast<int64_t>(ntp) * Lpad;
+    build_taps3_kernel<<<grid_for(total, 152), 256, 0, st>>>(d_h, d_words, n_tones, ntp, L, Lpad, std::ldexp(1.0, e),
+                                                              static_cast<__half*>(planes));
+    return cudaGetLastError();
+}
+
+cudaError_t demod3_launch(const DemodLaunch& L, cudaStream_t st) {
+    if (L.F <= 0) return cudaSuccess;
+    if (L.D % G3_BK != 0 || L.Lpad % G3_BK != 0 || L.ntp % G3_BT != 0) return cudaErrorInvalidValue;
+    const int64_t rows = static_cast<int64_t>(demod3_xs_rows(L.F, L.Lpad, L.D));
+    if (rows > L.xs_rows) return cudaErrorInvalidValue;
+    const int n_mt = static_cast<int>((L.F + BM - 1) / BM);
+    const int n_nt = L.ntp / G3_BT;
+    const int n_anch = demod_anchor_rows(L.F0, L.F);
+    float2* anchors = static_cast<float2*>(L.rot);
+    float2* steps = anchors + static_cast<int64_t>(n_anch) * L.ntp;
+    const int64_t nrot = static_cast<int64_t>(n_anch) * L.ntp + static_cast<int64_t>(L.ntp) * BM;
+    rot_kernel<<<grid_for(nrot, L.n_sms), 256, 0, st>>>(L.words, L.n_tones, L.ntp, L.F0 / BM, L.L, L.D, n_anch,
+                                                         anchors, steps);
+    const int64_t total = rows * L.D;
+    __half* xp = static_cast<__half*>(L.xs_hi);
+    presplit3_kernel<<<grid_for(total, L.n_sms), 256, 0, st>>>(
+        reinterpret_cast<const uint32_t*>(L.carry), L.cl, reinterpret_cast<const uint32_t*>(L.buf), L.cl + L.n,
+        total, xp);
+    G3Maps mp;
+    const __half* bp = static_cast<const __half*>(L.b_hi);
+    const int64_t bplane = static_cast<int64_t>(L.ntp) * L.Lpad;
+    for (int i = 0; i < 6; ++i) {
+        if (!make_map(&mp.a[i], xp + i * total, static_cast<uint64_t>(L.D), static_cast<uint64_t>(rows), BM) ||
+            !make_map(&mp.b[i], bp + i * bplane, static_cast<uint64_t>(L.Lpad), static_cast<uint64_t>(L.ntp), G3_BT))
+            return cudaErrorInvalidValue;
+    }
+    GemmArgs g{};
+    g.raster = L.raster_group;
+    g.F = L.F;
+    g.F0 = L.F0;
+    g.n_tones = L.n_tones;
+    g.ntp = L.ntp;
+    g.KB = L.Lpad / G3_BK;
+    g.kchunk = L.kchunk > 0 ? L.kchunk : 1;
+    g.two_d = L.D;                 // columns of a Toeplitz source row (one plane)
+    g.n_mt = n_mt;
+    g.n_nt = n_nt;
+    g.anchors = anchors;
+    g.steps = steps;
+    g.inv_scale = static_cast<float>(L.inv_scale);
+    g.out = static_cast<float2*>(L.tones);
+    g.ld = L.tones_ld;
+    g.fo = L.frame_offset;
+    g.status = L.status;
+    cudaError_t e = cudaFuncSetAttribute(demod3m_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(G3_SMEM));
+    if (e != cudaSuccess) return e;
+    const int grid = std::min(n_mt * n_nt, L.n_sms);
+    demod3m_gemm_kernel<<<grid, G3_THREADS, G3_SMEM, st>>>(mp, g);
     return cudaGetLastError();
 }
 

@@ -113,6 +113,13 @@ cudaError_t demod_build_taps(const double* d_h, const uint64_t* d_words, int n_t
                              int L, int Lpad, int e, void* b_hi, void* b_lo, cudaStream_t st);
 cudaError_t demod_launch(const DemodLaunch& L, cudaStream_t st);
 size_t demod_xs_rows(int64_t F, int Lpad, int D);
+// Gauss three-product form: B planes (cr, ci - cr, cr + ci) x (hi, lo), each
+// [ntp][Lpad] fp16 (ntp a multiple of 128, Lpad of 64); the launch takes them
+// in b_hi, and the six [rows][D] source planes in xs_hi (D % 64 == 0).
+cudaError_t demod3_build_taps(const double* d_h, const uint64_t* d_words, int n_tones, int ntp, int L, int Lpad,
+                              int e, void* planes, cudaStream_t st);
+cudaError_t demod3_launch(const DemodLaunch& L, cudaStream_t st);
+size_t demod3_xs_rows(int64_t F, int Lpad, int D);
 int demod_anchor_rows(int64_t F0, int64_t F);
 
 // -------------------------------------------------------------- chirp
@@ -192,6 +199,11 @@ struct rfr_plan {
     int32_t ntp = 0;               // demod tones padded
     int tap_exp = 0;               // demod power-of-two tap scale exponent
     int accum_chunk = 2;           // demod: K blocks per TMEM accumulation chunk
+    int demod_products = 4;        // demod GEMM form: 4 (real embedding) or 3 (Gauss)
+    void* d_b3 = nullptr;          // three-product form: six tap planes
+    void* d_xs3 = nullptr;         // three-product form: six source planes
+    int64_t xs3_rows_cap = 0;
+    int32_t Lpad3 = 0, ntp3 = 0, tap_exp3 = 0;
     int* d_status = nullptr;
 
     // stream state

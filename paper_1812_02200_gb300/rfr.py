@@ -100,6 +100,7 @@ _SIGS = {
     "rfr_now_us": (C.c_double, []),
     "rfr_plan_seek": (C.c_int, [_P, C.c_int64, _P, C.c_int64]),
     "rfr_plan_set_accum_chunk": (C.c_int, [_P, C.c_int32]),
+    "rfr_plan_set_demod_products": (C.c_int, [_P, C.c_int32]),
     "rfr_wait_selftest": (C.c_int, [C.c_int64, C.POINTER(C.c_int32)]),
     "rfr_plan_create_chirp": (C.c_int, [C.POINTER(_P), C.c_int32, C.POINTER(Window), _P, _P, C.c_int32,
                                         C.c_int32]),
@@ -327,6 +328,10 @@ class Plan:
 
     def set_accum_chunk(self, k_blocks: int):
         self._check(_lib.rfr_plan_set_accum_chunk(self._h, int(k_blocks)), "set_accum_chunk")
+
+    def set_demod_products(self, products: int):
+        """Demodulation GEMM form: 4 (real embedding, default) or 3 (Gauss)."""
+        self._check(_lib.rfr_plan_set_demod_products(self._h, int(products)), "set_demod_products")
 
     def seek(self, start_sample: int, history=None):
         """Start at absolute sample `start_sample` (a multiple of the hop) with

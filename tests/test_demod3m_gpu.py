@@ -1,0 +1,149 @@
+"""GPU parity of the Gauss three-product form of the tensor-core
+demodulation (Sec. III.B; rfr_plan_set_demod_products(plan, 3)) against the
+FP64 oracle, through the C ABI: the same definition as the four-product
+form with three real contractions per complex multiply-add, the same
+tolerance (relative RMS error <= 1e-5 per tone)."""
+import numpy as np
+import pytest
+
+import oracle
+import siggen
+from helpers import TOL, rel_rows
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+FC = 40e3 / 200e6
+
+
+def _plan3(lib, L, D, words, win="blackman", fc=FC, beta=0.0):
+    p = lib.Plan(0, L, window=win, beta=beta, cutoff=fc, words=words, decimation=D)
+    p.set_demod_products(3)
+    return p
+
+
+def _run(plan, x_np, n_tones):
+    x = torch.from_numpy(x_np).to(DEV)
+    F = plan.frames_for(x.shape[0])
+    out = torch.zeros((n_tones, F), dtype=torch.complex64, device=DEV)
+    assert plan.push_into(x, tones=out) == F
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+SHAPES = [
+    # L, D, tones, frames, window, cutoff
+    (256, 64, 8, 200, "blackman", 0.01),
+    (1000, 512, 130, 140, "hann", 0.002),       # L not a multiple of 64; 2 tone tiles
+    (4096, 2048, 160, 130, "blackman", 2e-4),   # the workload's filter
+    (4096, 512, 40, 150, "kaiser", 1e-3),       # L = 8 D
+    (1024, 2048, 50, 160, "hamming", 1e-3),     # L < D
+    (512, 512, 30, 260, "rect", 0.0),           # moving average, D = L
+    (3000, 448, 300, 90, "hann", 1e-3),         # 3 tone tiles, D = 7 * 64
+]
+
+
+@pytest.mark.parametrize("L,D,nt,frames,win,fc", SHAPES)
+def test_demod3m_parity_shapes(lib, L, D, nt, frames, win, fc):
+    beta = 9.0 if win == "kaiser" else 0.0
+    case = siggen.demod_case(frames * D + D // 3, nt, seed=3000 + L + D + nt)
+    plan = _plan3(lib, L, D, case["words"], win, fc, beta)
+    got = _run(plan, case["x"], nt)
+    assert got.shape[1] == frames
+    ref = oracle.demod(case["x"], L, D, oracle.lowpass(win, L, fc, beta), case["words"])
+    e = rel_rows(got, ref)
+    print(f"3M L={L} D={D} tones={nt}: max rel err {e.max():.3e}")
+    assert e.max() < TOL
+
+
+def test_demod3m_weak_tones_workload_statistics(lib):
+    c = siggen.c3(n=1 << 21)
+    L, D = 4096, 2048
+    plan = _plan3(lib, L, D, c["words"])
+    got = _run(plan, c["x"], 2048)
+    h = oracle.lowpass("blackman", L, FC)
+    sel = np.concatenate([np.argsort(c["amps"])[:8], np.random.default_rng(1).choice(2048, 8, replace=False)])
+    frames = np.unique(np.linspace(0, got.shape[1] - 1, 64).astype(int))
+    errs = []
+    for s in sel:
+        ref = np.concatenate([oracle.demod(c["x"], L, D, h, [c["words"][s]], k, k + 1)[0] for k in frames])
+        errs.append(np.linalg.norm(got[s, frames] - ref) / np.linalg.norm(ref))
+    errs = np.array(errs)
+    print(f"3M weakest-tone rel err {errs[:8].max():.3e}, random {errs[8:].max():.3e}")
+    assert errs.max() < TOL
+
+
+def test_demod3m_c3_full_size_sampled(lib):
+    c = siggen.c3()
+    L, D = 4096, 2048
+    plan = _plan3(lib, L, D, c["words"])
+    got = _run(plan, c["x"], 2048)
+    assert got.shape == (2048, 65536)
+    h = oracle.lowpass("blackman", L, FC)
+    sel = np.concatenate([np.argsort(c["amps"])[:4], [0, 1000, 2047]])
+    for a, b in [(0, 8), (32760, 32768), (65528, 65536)]:
+        ref = oracle.demod(c["x"], L, D, h, c["words"][sel], a, b)
+        e = np.linalg.norm(got[sel, a:b] - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        assert e.max() < TOL, (a, e.max())
+
+
+def test_demod3m_full_range_int16(lib):
+    """Samples over the whole int16 range (xr + xi up to 65534, beyond the
+    largest FP16 number without the halving of the sum)."""
+    r = np.random.default_rng(17)
+    L, D, nt, frames = 1024, 512, 40, 80
+    x = r.integers(-32768, 32768, size=(frames * D, 2)).astype(np.int16)
+    x[::7] = 32767
+    x[3::11] = -32768
+    words = siggen.random_words(r, nt)
+    plan = _plan3(lib, L, D, words)
+    got = _run(plan, x, nt)
+    ref = oracle.demod(x, L, D, oracle.lowpass("blackman", L, FC), words)
+    e = rel_rows(got, ref)
+    print(f"3M full-range: max rel err {e.max():.3e}")
+    assert np.isfinite(got).all() and e.max() < TOL
+
+
+def test_demod3m_streamed_equals_one_shot_bit_exact(lib):
+    L, D, nt = 1024, 512, 150
+    case = siggen.demod_case(D * 400 + 77, nt, seed=31)
+    ref = _run(_plan3(lib, L, D, case["words"]), case["x"], nt)
+    st = _plan3(lib, L, D, case["words"])
+    x = torch.from_numpy(case["x"]).to(DEV)
+    F = ref.shape[1]
+    out = torch.zeros((nt, F), dtype=torch.complex64, device=DEV)
+    rng = np.random.default_rng(8)
+    pos = off = 0
+    while pos < x.shape[0]:
+        cnt = int(min(x.shape[0] - pos, rng.integers(1, 40 * D)))
+        off += st.push_into(x[pos:pos + cnt], tones=out, frame_offset=off)
+        pos += cnt
+    torch.cuda.synchronize()
+    assert off == F and np.array_equal(out.cpu().numpy(), ref)
+
+
+def test_demod3m_switching_forms(lib):
+    """A fresh plan with D % 64 == 0 is in the three-product form; switching
+    4 -> 3 -> 4 gives each form's results again bit for bit; D % 64 != 0 is
+    refused for the three-product form."""
+    L, D, nt = 1024, 512, 20
+    case = siggen.demod_case(D * 50, nt, seed=5)
+    p = lib.Plan(0, L, window="blackman", cutoff=FC, words=case["words"], decimation=D)
+    default = _run(p, case["x"], nt)
+    p.reset()
+    p.set_demod_products(4)
+    four = _run(p, case["x"], nt)
+    p.reset()
+    p.set_demod_products(3)
+    three = _run(p, case["x"], nt)
+    p.reset()
+    p.set_demod_products(4)
+    again = _run(p, case["x"], nt)
+    assert np.array_equal(four, again)
+    assert np.array_equal(three, default)
+    assert rel_rows(three, four).max() < TOL
+    q = lib.Plan(0, L, window="blackman", cutoff=FC, words=case["words"], decimation=96)
+    with pytest.raises(lib.RfrError) as e:
+        q.set_demod_products(3)
+    assert e.value.status == -7

@@ -17,8 +17,12 @@ pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 
 
-def _plan(lib, L, D, words, win="blackman", fc=40e3 / 200e6, beta=0.0):
-    return lib.Plan(0, L, window=win, beta=beta, cutoff=fc, words=words, decimation=D)
+def _plan(lib, L, D, words, win="blackman", fc=40e3 / 200e6, beta=0.0, products=4):
+    """A demodulation plan in the four-product form (the three-product form,
+    the default wherever D % 64 == 0, has its own test file)."""
+    p = lib.Plan(0, L, window=win, beta=beta, cutoff=fc, words=words, decimation=D)
+    p.set_demod_products(products)
+    return p
 
 
 def _run(plan, x_np, n_tones):
