@@ -318,7 +318,7 @@ void destroy(rfr_plan* p) {
                     static_cast<void*>(p->d_carry[1]), p->d_xs_hi, p->d_xs_lo, p->d_rot, p->d_qfull, p->d_b3, p->d_xs3,
                     p->d_qtones})
         dev_free(q);
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < rfr_plan::kStageBufs; ++i) {
         dev_free(p->d_stage_in[i]);
         dev_free(p->d_stage_full[i]);
         dev_free(p->d_stage_tones[i]);
@@ -687,14 +687,14 @@ rfr_status rfr_process_host(rfr_plan* p, const int16_t* iq_host, int64_t n, rfr_
     const int64_t fmax = chunk / p->H + 2;
     if (p->stage_samples < chunk) {
         cudaDeviceSynchronize();
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < rfr_plan::kStageBufs; ++i) {
             dev_free(p->d_stage_in[i]);
             dev_free(p->d_stage_full[i]);
             dev_free(p->d_stage_tones[i]);
             p->d_stage_in[i] = p->d_stage_full[i] = p->d_stage_tones[i] = nullptr;
         }
         p->stage_samples = 0;
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < rfr_plan::kStageBufs; ++i) {
             RFR_CUDA(p, dev_alloc(&p->d_stage_in[i], static_cast<size_t>(chunk) * 4));
             if (want_full) RFR_CUDA(p, dev_alloc(&p->d_stage_full[i], static_cast<size_t>(fmax) * p->N * 8));
             if (want_tones) RFR_CUDA(p, dev_alloc(&p->d_stage_tones[i], static_cast<size_t>(fmax) * nt * 8));
@@ -709,7 +709,7 @@ rfr_status rfr_process_host(rfr_plan* p, const int16_t* iq_host, int64_t n, rfr_
     cudaEvent_t prev = nullptr;
     while (done < n) {
         const int64_t cnt = std::min(chunk, n - done);
-        const int s = i & 1;
+        const int s = i % rfr_plan::kStageBufs;
         cudaStream_t st = p->stage_st[s];
         RFR_CUDA(p, cudaMemcpyAsync(p->d_stage_in[s], iq_host + 2 * done, static_cast<size_t>(cnt) * 4,
                                     cudaMemcpyHostToDevice, st));
@@ -740,8 +740,8 @@ rfr_status rfr_process_host(rfr_plan* p, const int16_t* iq_host, int64_t n, rfr_
         done += cnt;
         ++i;
     }
-    for (int s = 0; s < 2; ++s) RFR_CUDA(p, cudaStreamSynchronize(p->stage_st[s]));
-    p->last_stream = p->stage_st[(i + 1) & 1];
+    for (int s = 0; s < rfr_plan::kStageBufs; ++s) RFR_CUDA(p, cudaStreamSynchronize(p->stage_st[s]));
+    p->last_stream = p->stage_st[(i + rfr_plan::kStageBufs - 1) % rfr_plan::kStageBufs];
     out->frames = fo - out->frame_offset;
     return check_status(p);
 }

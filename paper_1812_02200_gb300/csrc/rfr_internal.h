@@ -229,12 +229,13 @@ struct rfr_plan {
     cudaStream_t last_stream = nullptr;
 
     // host-staging (rfr_process_host)
-    void* d_stage_in[2] = {nullptr, nullptr};
-    void* d_stage_full[2] = {nullptr, nullptr};
-    void* d_stage_tones[2] = {nullptr, nullptr};
+    static constexpr int kStageBufs = 3;       // chunks in flight (copy in, compute, copy out)
+    void* d_stage_in[kStageBufs] = {};
+    void* d_stage_full[kStageBufs] = {};
+    void* d_stage_tones[kStageBufs] = {};
     int64_t stage_samples = 0;
-    cudaStream_t stage_st[2] = {nullptr, nullptr};
-    cudaEvent_t stage_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaStream_t stage_st[kStageBufs] = {};
+    cudaEvent_t stage_ev[kStageBufs] = {};
 
     // plain-form scratch
     void* plain_scratch = nullptr;
