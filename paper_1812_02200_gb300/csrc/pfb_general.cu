@@ -20,8 +20,12 @@
 // FP64-built table entries), Z stored in runs of GA points.  Pass B: one CTA
 // per (frame, GB consecutive c1): GB rows of Z, GB interleaved FFTs of length
 // N2, the spectrum stored in runs of GB points, and the tone channels.  Z
-// holds a batch of frames small enough to stay in L2 between the passes.
+// holds a batch of frames (1 GB) between the passes.
 //
+// Each sub-transform runs the fewest Stockham passes of radices up to 25:
+// 16, 8, 4, 2 from fft_dev.cuh, 3, 5, 7 from their definitions, and the
+// composites 6 ... 25 as register DFTs of two factors with their inner
+// twiddles from a constant table.
 // FFT stages follow the conventions of fft_dev.cuh (Stockham autosort,
 // butterfly j reads x[j + r*n/R], twiddle W_{R*Ns}^{r*k} with k = j mod Ns,
 // writes y[(j/Ns)*R*Ns + k + r*Ns]; twiddle table [(r-1)*Ns + k] per stage).
@@ -53,6 +57,7 @@ struct GenCfg {
     static constexpr int kMinBlocks = TH == 256 ? 3 : 1;
 };
 constexpr int kTwSplit = 4096;                     // inter-pass twiddle: m = hi*4096 + lo
+constexpr int kGMax = 64;                          // transforms interleaved per CTA
 
 __device__ __forceinline__ int gpad(int e) { return e + (e >> 4); }
 
@@ -110,10 +115,108 @@ __device__ __forceinline__ void dft_odd(float2* x) {
     for (int r = 0; r < R; ++r) x[r] = out[r];
 }
 
+
+// Inner twiddles of the composite radices (registers-only DFTs of R = A*B):
+// exp(-2*pi*i*e/R) for e < R, FP64 cos/sin rounded to FP32, R in
+// {6, 9, 10, 12, 15, 20, 25} back to back.
+__constant__ float2 c_inner_tw[97] = {
+    {1.0f, -0.0f}, {0.5f, -0.8660253882408142f}, {-0.5f, -0.8660253882408142f},
+    {-1.0f, -1.2246468525851679e-16f}, {-0.5f, 0.8660253882408142f}, {0.5f, 0.8660253882408142f},
+    {1.0f, -0.0f}, {0.7660444378852844f, -0.6427876353263855f}, {0.1736481785774231f, -0.9848077297210693f},
+    {-0.5f, -0.8660253882408142f}, {-0.9396926164627075f, -0.3420201539993286f}, {-0.9396926164627075f, 0.3420201539993286f},
+    {-0.5f, 0.8660253882408142f}, {0.1736481785774231f, 0.9848077297210693f}, {0.7660444378852844f, 0.6427876353263855f},
+    {1.0f, -0.0f}, {0.80901700258255f, -0.5877852439880371f}, {0.30901700258255005f, -0.9510565400123596f},
+    {-0.30901700258255005f, -0.9510565400123596f}, {-0.80901700258255f, -0.5877852439880371f}, {-1.0f, -1.2246468525851679e-16f},
+    {-0.80901700258255f, 0.5877852439880371f}, {-0.30901700258255005f, 0.9510565400123596f}, {0.30901700258255005f, 0.9510565400123596f},
+    {0.80901700258255f, 0.5877852439880371f}, {1.0f, -0.0f}, {0.8660253882408142f, -0.5f},
+    {0.5f, -0.8660253882408142f}, {6.123234262925839e-17f, -1.0f}, {-0.5f, -0.8660253882408142f},
+    {-0.8660253882408142f, -0.5f}, {-1.0f, -1.2246468525851679e-16f}, {-0.8660253882408142f, 0.5f},
+    {-0.5f, 0.8660253882408142f}, {-1.8369701465288538e-16f, 1.0f}, {0.5f, 0.8660253882408142f},
+    {0.8660253882408142f, 0.5f}, {1.0f, -0.0f}, {0.9135454297065735f, -0.4067366421222687f},
+    {0.6691306233406067f, -0.7431448101997375f}, {0.30901700258255005f, -0.9510565400123596f}, {-0.10452846437692642f, -0.9945219159126282f},
+    {-0.5f, -0.8660253882408142f}, {-0.80901700258255f, -0.5877852439880371f}, {-0.9781476259231567f, -0.2079116851091385f},
+    {-0.9781476259231567f, 0.2079116851091385f}, {-0.80901700258255f, 0.5877852439880371f}, {-0.5f, 0.8660253882408142f},
+    {-0.10452846437692642f, 0.9945219159126282f}, {0.30901700258255005f, 0.9510565400123596f}, {0.6691306233406067f, 0.7431448101997375f},
+    {0.9135454297065735f, 0.4067366421222687f}, {1.0f, -0.0f}, {0.9510565400123596f, -0.30901700258255005f},
+    {0.80901700258255f, -0.5877852439880371f}, {0.5877852439880371f, -0.80901700258255f}, {0.30901700258255005f, -0.9510565400123596f},
+    {6.123234262925839e-17f, -1.0f}, {-0.30901700258255005f, -0.9510565400123596f}, {-0.5877852439880371f, -0.80901700258255f},
+    {-0.80901700258255f, -0.5877852439880371f}, {-0.9510565400123596f, -0.30901700258255005f}, {-1.0f, -1.2246468525851679e-16f},
+    {-0.9510565400123596f, 0.30901700258255005f}, {-0.80901700258255f, 0.5877852439880371f}, {-0.5877852439880371f, 0.80901700258255f},
+    {-0.30901700258255005f, 0.9510565400123596f}, {-1.8369701465288538e-16f, 1.0f}, {0.30901700258255005f, 0.9510565400123596f},
+    {0.5877852439880371f, 0.80901700258255f}, {0.80901700258255f, 0.5877852439880371f}, {0.9510565400123596f, 0.30901700258255005f},
+    {1.0f, -0.0f}, {0.9685831665992737f, -0.24868988990783691f}, {0.8763066530227661f, -0.4817536771297455f},
+    {0.728968620300293f, -0.6845471262931824f}, {0.5358268022537231f, -0.8443279266357422f}, {0.30901700258255005f, -0.9510565400123596f},
+    {0.06279052048921585f, -0.9980267286300659f}, {-0.187381312251091f, -0.9822872281074524f}, {-0.4257792830467224f, -0.9048270583152771f},
+    {-0.6374239921569824f, -0.7705132365226746f}, {-0.80901700258255f, -0.5877852439880371f}, {-0.9297764897346497f, -0.3681245446205139f},
+    {-0.9921147227287292f, -0.12533323466777802f}, {-0.9921147227287292f, 0.12533323466777802f}, {-0.9297764897346497f, 0.3681245446205139f},
+    {-0.80901700258255f, 0.5877852439880371f}, {-0.6374239921569824f, 0.7705132365226746f}, {-0.4257792830467224f, 0.9048270583152771f},
+    {-0.187381312251091f, 0.9822872281074524f}, {0.06279052048921585f, 0.9980267286300659f}, {0.30901700258255005f, 0.9510565400123596f},
+    {0.5358268022537231f, 0.8443279266357422f}, {0.728968620300293f, 0.6845471262931824f}, {0.8763066530227661f, 0.4817536771297455f},
+    {0.9685831665992737f, 0.24868988990783691f}};
+
+template <int R>
+__host__ __device__ constexpr int inner_off() {
+    if (R == 6) return 0;
+    if (R == 9) return 6;
+    if (R == 10) return 15;
+    if (R == 12) return 25;
+    if (R == 15) return 37;
+    if (R == 20) return 52;
+    if (R == 25) return 72;
+    return -1;
+}
+
+// R = A*B with A the power-of-two part (when R has one and R/A > 1), else the
+// smallest odd prime factor.
+template <int R>
+__host__ __device__ constexpr int split_a() {
+    if (R % 16 == 0 && R > 16) return 16;
+    if (R % 8 == 0 && R > 8) return 8;
+    if (R % 4 == 0 && R > 4) return 4;
+    if (R % 2 == 0 && R > 2) return 2;
+    if (R % 3 == 0 && R > 3) return 3;
+    if (R % 5 == 0 && R > 5) return 5;
+    return 7;
+}
+
+// Length-R DFT in registers, natural order.  Composite R = A*B, input index
+// n = n1 + A*n2 and output index k = B*k1 + k2:
+//   X[B*k1 + k2] = sum_{n1} W_A^{n1*k1} W_R^{n1*k2} sum_{n2} x[n1 + A*n2] W_B^{n2*k2}.
+template <int R>
+__device__ __forceinline__ void dft_reg(float2* x) {
+    if constexpr (R == 2 || R == 4 || R == 8 || R == 16) {
+        dft_small<R>(x);
+    } else if constexpr (R == 3 || R == 5 || R == 7) {
+        dft_odd<R>(x);
+    } else {
+        constexpr int A = split_a<R>(), B = R / A;
+        static_assert(inner_off<R>() >= 0, "composite radix without an inner twiddle table");
+        float2 y[R];
+#pragma unroll
+        for (int n1 = 0; n1 < A; ++n1) {
+            float2 t[B];
+#pragma unroll
+            for (int n2 = 0; n2 < B; ++n2) t[n2] = x[n1 + A * n2];
+            dft_reg<B>(t);
+#pragma unroll
+            for (int k2 = 0; k2 < B; ++k2)
+                y[n1 * B + k2] = (n1 == 0 || k2 == 0) ? t[k2] : cmul(t[k2], c_inner_tw[inner_off<R>() + n1 * k2]);
+        }
+#pragma unroll
+        for (int k2 = 0; k2 < B; ++k2) {
+            float2 t[A];
+#pragma unroll
+            for (int n1 = 0; n1 < A; ++n1) t[n1] = y[n1 * B + k2];
+            dft_reg<A>(t);
+#pragma unroll
+            for (int k1 = 0; k1 < A; ++k1) x[B * k1 + k2] = t[k1];
+        }
+    }
+}
+
 template <int R>
 __device__ __forceinline__ void dft_any(float2* x) {
-    if constexpr (R == 3 || R == 5 || R == 7) dft_odd<R>(x);
-    else dft_small<R>(x);
+    dft_reg<R>(x);
 }
 
 // One Stockham stage of radix R over G = 2^gl2 interleaved transforms of
@@ -156,12 +259,20 @@ __device__ float2* gen_fft(float2* buf0, float2* buf1, const GenFft& f, int gl2,
         const float2* t = tw + f.tw_off[s];
         switch (f.radix[s]) {
         case 16: gen_stage<16, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
+        case 25: gen_stage<25, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
+        case 20: gen_stage<20, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
+        case 15: gen_stage<15, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
+        case 12: gen_stage<12, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
+        case 10: gen_stage<10, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
+        case 9: gen_stage<9, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
         case 8: gen_stage<8, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
-        case 4: gen_stage<4, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
-        case 2: gen_stage<2, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
-        case 3: gen_stage<3, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
+        case 7: gen_stage<7, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
+        case 6: gen_stage<6, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
         case 5: gen_stage<5, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
-        default: gen_stage<7, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
+        case 4: gen_stage<4, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
+        case 3: gen_stage<3, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
+        case 2: gen_stage<2, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
+        default: break;
         }
         float2* tmp = src;
         src = dst;
@@ -368,7 +479,7 @@ int floor_log2(int v) {
     return l;
 }
 
-// Radices of a length-n transform (16s first, then one 8/4/2, then 3, 5, 7),
+// Radices of a length-n transform (the fewest passes of register DFTs),
 // stage spans and twiddle-table offsets; appends the FP64-built twiddles to
 // `tw` (offsets are absolute positions in `tw`).
 bool build_fft(int n, GenFft* f, std::vector<float2>& tw) {
@@ -393,20 +504,18 @@ bool build_fft(int n, GenFft* f, std::vector<float2>& tw) {
         ns *= r;
         return true;
     };
-    while (m % 16 == 0) {
-        if (!add(16)) return false;
-        m /= 16;
+    // fewest passes: the largest radix of the register DFTs that divides
+    // what is left (16 = 2^4 and the composites up to 25)
+    while (m > 1) {
+        int r = 0;
+        for (int c : {25, 20, 16, 15, 12, 10, 9, 8, 7, 6, 5, 4, 3, 2})
+            if (m % c == 0) {
+                r = c;
+                break;
+            }
+        if (r == 0 || !add(r)) return false;
+        m /= r;
     }
-    for (int r : {8, 4, 2})
-        if (m % r == 0) {
-            if (!add(r)) return false;
-            m /= r;
-        }
-    for (int r : {3, 5, 7})
-        while (m % r == 0) {
-            if (!add(r)) return false;
-            m /= r;
-        }
     return m == 1;
 }
 
@@ -434,8 +543,8 @@ cudaError_t gen_plan_init(GenPlan* g, int N, int64_t z_budget_bytes) {
             if (N % n2 != 0) continue;
             const int n1 = N / n2;
             if (n1 < 2 || n1 > elems) continue;
-            const int ga = std::min(16, 1 << floor_log2(elems / n1));
-            const int gb = std::min(16, 1 << floor_log2(elems / n2));
+            const int ga = std::min(kGMax, 1 << floor_log2(elems / n1));
+            const int gb = std::min(kGMax, 1 << floor_log2(elems / n2));
             const int score = std::min(ga, gb), bal = -std::abs(n1 - n2);
             if (score > best_score || (score == best_score && bal > best_bal)) {
                 best = n2;
@@ -463,8 +572,8 @@ cudaError_t gen_plan_init(GenPlan* g, int N, int64_t z_budget_bytes) {
         const int elems = g->threads * 16;
         g->N1 = n1;
         g->N2 = n2;
-        g->gla = floor_log2(std::min(16, 1 << floor_log2(elems / g->N1)));
-        g->glb = floor_log2(std::min(16, 1 << floor_log2(elems / g->N2)));
+        g->gla = floor_log2(std::min(kGMax, 1 << floor_log2(elems / g->N1)));
+        g->glb = floor_log2(std::min(kGMax, 1 << floor_log2(elems / g->N2)));
         if (!build_fft(g->N1, &g->fa, tw)) return cudaErrorInvalidValue;
         if (!build_fft(g->N2, &g->fb, tw)) return cudaErrorInvalidValue;
     }
