@@ -170,9 +170,11 @@ uint64_t rfr_chirp_rate_word(double k_hz_per_s, double fs_hz);
  * as complex int16 (round half to even, clamped to the int16 range) into the
  * device buffer iq_out [n][2].  Computed in FP32 on the phase reduced to a
  * quarter turn; a component whose FP32 value lies within twice its error
- * bound (A*(pi*2^-27 + 2^-23 + 2^-24) + |fl(A) - A|) of a rounding tie is
+ * bound (A*(pi*(2^-27 + 2^-31) + 2^-23) + |fl(A) - A|) of a rounding tie is
  * recomputed in FP64, so every sample is the FP64-rounded value.
- * 0 <= amplitude <= 32767.  Asynchronous on `stream`.
+ * 0 <= amplitude <= 32767.  Asynchronous on `stream`; the first call on a
+ * device uploads a small table synchronously (make it outside stream
+ * capture).
  */
 rfr_status rfr_chirp_synthesize(uint64_t start_word, uint64_t rate_word, double amplitude, int64_t m0,
                                 int64_t n_samples, int16_t* iq_out, void* stream);
