@@ -407,6 +407,22 @@ def run_chirp(args, dev, stream):
                                       "frac": 4.0 * n / (ms_syn * 1e-3) / 1e9 / hbm_peak}},
            "demod": {"workload": "2^26 samples against 8 chirps, L=4096 Blackman-sinc, D=2048",
                      "value": x.shape[0] / (ms_dem * 1e-3) / 1e6, "unit": UNIT, "ms": ms_dem}}
+    lane_peak = 152 * 128 * 2.07e9
+    i_syn = profile_value("chirp_kernels.md", CHIRP_SOURCES, "inst_per_sample_synth")
+    i_dem = profile_value("chirp_kernels.md", CHIRP_SOURCES, "inst_per_tap_chirp_demod")
+    if i_syn:
+        a = n / (ms_syn * 1e-3) * i_syn
+        res["synthesis"]["roofline_alu"] = {"bound": "alu", "achieved": a / 1e12, "peak": lane_peak / 1e12,
+                                            "unit": "T lane-instructions/s", "frac": a / lane_peak,
+                                            "inst_per_sample": i_syn,
+                                            "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz"}
+    if i_dem:
+        evals = x.shape[0] * 8 * DEMOD_L / DEMOD_D
+        a = evals / (ms_dem * 1e-3) * i_dem
+        res["demod"]["roofline"] = {"bound": "alu", "achieved": a / 1e12, "peak": lane_peak / 1e12,
+                                    "unit": "T lane-instructions/s", "frac": a / lane_peak,
+                                    "inst_per_mixer_evaluation": i_dem,
+                                    "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz"}
     plan.close()
     del x, out
     return res
@@ -414,6 +430,7 @@ def run_chirp(args, dev, stream):
 
 # -------------------------------------------------------- transmit buffer
 TX_SOURCES = ["paper_1812_02200_gb300/csrc/tx.cu"]
+CHIRP_SOURCES = ["paper_1812_02200_gb300/csrc/chirp.cu"]
 
 
 def run_tx(args, dev, stream, words):
