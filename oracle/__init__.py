@@ -77,6 +77,7 @@ def _load():
             "orc_chirp_synth": (C.c_int, [u64, u64, dbl, i64, i64, P]),
             "orc_chirp_demod_i16": (C.c_int, [P, i64, i32, i32, P, P, P, i32, i64, i64, P]),
             "orc_tones_synth": (C.c_int, [P, P, P, i32, i64, i64, P, P]),
+            "orc_pfb_hop_i16": (C.c_int, [P, i64, i32, i32, i32, P, i64, i64, P, P, i32, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -177,6 +178,31 @@ def pfb(x: np.ndarray, n_chan: int, taps: int, h: np.ndarray, k_begin: int = 0,
         if want_v:
             out["v"] = v
     _check(rc, "pfb")
+    if want_full:
+        out["full"] = full
+    if nb:
+        out["tones"] = tones
+    return out
+
+
+def pfb_hop(x: np.ndarray, n_chan: int, taps: int, hop: int, h: np.ndarray, k_begin: int = 0,
+            k_end: int | None = None, bins=None, want_full: bool = True):
+    """PFB with `hop` samples between frames on an int16 [n, 2] stream (frames
+    end at (k+1)*hop - 1; channels keep the absolute time origin's phase).
+    Returns a dict with 'full' [nk, N] and 'tones' [n_bins, nk]."""
+    h = np.ascontiguousarray(h, np.float64)
+    xi = np.ascontiguousarray(x, np.int16)
+    n = xi.shape[0]
+    if k_end is None:
+        k_end = n // hop
+    nk = k_end - k_begin
+    bins_a = None if bins is None else np.ascontiguousarray(bins, np.int32)
+    nb = 0 if bins_a is None else len(bins_a)
+    full = np.empty((nk, n_chan), np.complex128) if want_full else None
+    tones = np.empty((nb, nk), np.complex128) if nb else None
+    _check(_load().orc_pfb_hop_i16(_ptr(xi), n, n_chan, taps, hop, _ptr(h), k_begin, k_end, _ptr(full),
+                                   _ptr(bins_a), nb, _ptr(tones)), "pfb_hop")
+    out = {}
     if want_full:
         out["full"] = full
     if nb:

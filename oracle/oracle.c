@@ -373,6 +373,68 @@ int orc_pfb_i16(const int16_t* iq, int64_t n_samples, int32_t n_chan, int32_t ta
     return rc;
 }
 
+/* PFB with a hop of H samples between frames (H = N: the critically sampled
+ * PFB above; H < N: oversampled), on the complex int16 stream, each sample
+ * promoted to FP64 exactly.  Frame k uses the M = N*T samples that end at
+ * sample (k+1)*H - 1, i.e. start at s_k = (k+1)*H - M (samples before 0 are
+ * zero), and its channels keep the phase of the absolute time origin:
+ *   v_k[p] = sum_{t<T} h[t*N + p] * x[s_k + t*N + p]
+ *   y_k[c] = sum_p v_k[p] exp(-2*pi*i*c*(s_k + p)/N)
+ * so channel c is the stream mixed down by exp(-2*pi*i*c*m/N) and filtered,
+ * exactly as the direct demodulator gives it for the bin-centred word (for
+ * H = N, s_k is a multiple of N and the factor is 1).  The exponent depends
+ * on (s_k + p) mod N only, so y_k is the FFT of v_k circularly shifted by
+ * s_k mod N: u[(p + s) mod N] = v_k[p]. */
+int orc_pfb_hop_i16(const int16_t* iq, int64_t n_samples, int32_t n_chan, int32_t taps, int32_t hop,
+                    const double* h, int64_t k_begin, int64_t k_end,
+                    double* full, const int32_t* bins, int32_t n_bins, double* tones)
+{
+    if (!iq || n_chan <= 0 || taps <= 0 || hop <= 0 || !h || k_begin < 0 || k_end < k_begin) return -1;
+    if (k_end * (int64_t)hop > n_samples) return -1;
+    if (n_bins > 0 && (!bins || !tones)) return -1;
+    for (int32_t s = 0; s < n_bins; ++s)
+        if (bins[s] < 0 || bins[s] >= n_chan) return -1;
+    const int64_t n = n_chan, m = n * taps, nk = k_end - k_begin;
+    double* v = (double*)malloc(sizeof(double) * 2 * (size_t)n);
+    double* u = (double*)malloc(sizeof(double) * 2 * (size_t)n);
+    if (!v || !u) {
+        free(v);
+        free(u);
+        return -2;
+    }
+    int rc = 0;
+    for (int64_t k = k_begin; k < k_end && rc == 0; ++k) {
+        const int64_t start = (k + 1) * (int64_t)hop - m;
+        for (int64_t p = 0; p < n; ++p) {
+            double ar = 0.0, ai = 0.0;
+            for (int64_t t = 0; t < taps; ++t) {
+                const int64_t idx = start + t * n + p;
+                if (idx < 0) continue;                /* zero history */
+                ar += h[t * n + p] * (double)iq[2 * idx];
+                ai += h[t * n + p] * (double)iq[2 * idx + 1];
+            }
+            v[2 * p] = ar;
+            v[2 * p + 1] = ai;
+        }
+        const int64_t sh = ((start % n) + n) % n;
+        for (int64_t p = 0; p < n; ++p) {
+            const int64_t q = (p + sh) % n;
+            u[2 * q] = v[2 * p];
+            u[2 * q + 1] = v[2 * p + 1];
+        }
+        rc = orc_fft((int32_t)n, u);
+        if (rc != 0) break;
+        if (full) memcpy(full + 2 * (k - k_begin) * n, u, sizeof(double) * 2 * (size_t)n);
+        for (int32_t s = 0; s < n_bins; ++s) {
+            tones[2 * ((int64_t)s * nk + (k - k_begin))] = u[2 * bins[s]];
+            tones[2 * ((int64_t)s * nk + (k - k_begin)) + 1] = u[2 * bins[s] + 1];
+        }
+    }
+    free(v);
+    free(u);
+    return rc;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Direct multi-tone demodulation (Sec. III.B)                               */
 /* ------------------------------------------------------------------------ */

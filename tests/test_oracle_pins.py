@@ -442,3 +442,59 @@ def test_tones_synth_offgrid_linearity_and_own_demodulation():
     dmin = min(abs(((w - words[0] + 2 ** 63) % 2 ** 64 - 2 ** 63) / 2 ** 64) for w in words[1:])
     leak = sum(amps[1:]) / (2 * L * dmin)
     assert np.all(np.abs(d[1:] - amps[0]) <= leak + 1e-9)
+
+
+# ----------------------------------------------------- oversampled PFB
+def _i16(n, seed, amp=3000):
+    r = np.random.default_rng(seed)
+    return r.integers(-amp, amp, size=(n, 2)).astype(np.int16)
+
+
+def test_pfb_hop_n_is_the_critically_sampled_pfb():
+    N, T = 64, 4
+    _, h32 = oracle.pfb_prototype(N, T, "hann")
+    h = h32.astype(np.float64)
+    x = _i16(N * 30, 1)
+    a = oracle.pfb(x, N, T, h)["full"]
+    b = oracle.pfb_hop(x, N, T, N, h)["full"]
+    assert np.allclose(a, b, rtol=1e-13, atol=1e-9)
+
+
+def test_pfb_hop_brute_force():
+    """Tiny case against the definition written out with Python loops:
+    y_k[c] = sum_p v_k[p] exp(-2 pi i c (s_k + p) / N), s_k = (k+1) H - N T."""
+    N, T, H = 6, 2, 4
+    h = np.linspace(0.3, 1.7, N * T)
+    x = _i16(40, 2)
+    xc = x[:, 0].astype(float) + 1j * x[:, 1]
+    got = oracle.pfb_hop(x, N, T, H, h)["full"]
+    for k in range(got.shape[0]):
+        s = (k + 1) * H - N * T
+        v = [sum(h[t * N + p] * (xc[s + t * N + p] if s + t * N + p >= 0 else 0) for t in range(T))
+             for p in range(N)]
+        for c in range(N):
+            ref = sum(v[p] * np.exp(-2j * np.pi * c * (s + p) / N) for p in range(N))
+            assert abs(got[k, c] - ref) < 1e-9 * (1 + abs(ref))
+
+
+@pytest.mark.parametrize("N,T,H", [(64, 4, 32), (64, 4, 16), (32, 8, 24)])
+def test_pfb_hop_channel_is_the_demodulator(N, T, H):
+    """Channel c of the oversampled PFB equals direct demodulation at the
+    bin-centred word c 2^64/N with L = N T and D = H (same taps)."""
+    h64, _ = oracle.pfb_prototype(N, T, "kaiser", 9.0)
+    x = _i16(N * 40, 3)
+    y = oracle.pfb_hop(x, N, T, H, h64)["full"]
+    for c in (0, 1, N // 3, N - 1):
+        w = (c << (64 - int(np.log2(N)))) % 2 ** 64
+        d = oracle.demod(x, N * T, H, h64, [w])[0]
+        assert np.allclose(d[: y.shape[0]], y[:, c], rtol=1e-11, atol=1e-7)
+
+
+def test_pfb_half_hop_odd_frames_are_the_critically_sampled_frames():
+    N, T = 100, 4
+    _, h32 = oracle.pfb_prototype(N, T, "hamming")
+    h = h32.astype(np.float64)
+    x = _i16(N * 20, 4)
+    crit = oracle.pfb(x, N, T, h)["full"]
+    half = oracle.pfb_hop(x, N, T, N // 2, h)["full"]
+    assert np.allclose(half[1::2][: crit.shape[0]], crit[: half[1::2].shape[0]], rtol=1e-12, atol=1e-8)
