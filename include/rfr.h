@@ -130,8 +130,13 @@ typedef struct {
  *   window     prototype window and cut-off (see rfr_window).
  *   tones      NCO words of the readout tones (0 <= count <= 65536).  PFB:
  *              tone s is read from bin rfr_word_to_bin(words[s], N).
- *   decimation PFB: must equal N (critically sampled).  Demodulation: D >= 1
- *              and D a multiple of 32 for the tensor-core path.
+ *   decimation PFB: the hop H between frames, 1 <= H <= N (H = N: critically
+ *              sampled, the paper's PFB; H < N: oversampled, frame k ending
+ *              at sample (k+1)*H - 1, each channel keeping the phase of the
+ *              absolute time origin, so channel c equals the demodulator's
+ *              output for the bin-centred word; oversampled plans run the
+ *              mixed-radix kernels).  Demodulation: D >= 1 and D a multiple
+ *              of 32 for the tensor-core path.
  *   out_flags  PFB: any non-empty combination of RFR_OUT_FULL, RFR_OUT_TONES
  *              (RFR_OUT_TONES needs count > 0).  Demodulation: RFR_OUT_TONES.
  * Allocates the plan's device tables and stream state on the current device.
@@ -297,7 +302,7 @@ rfr_status rfr_plan_set_accum_chunk(rfr_plan* plan, int32_t k_blocks);
  * it had been pushed: the next push's first frame is frame start_sample/hop,
  * with NCO phases taken from the absolute sample index.  `history` (device or
  * host) holds the n_history = min(H, start_sample) samples just before
- * start_sample, H = (T-1)*N for the PFB and max(L - D, 0) for demodulation;
+ * start_sample, H = N*T - hop for the PFB and max(L - D, 0) for demodulation;
  * earlier samples count as zero.  This is how a
  * long stream is split along time across plans or GPUs: each shard gets its
  * slice plus this halo, and the shards' frames concatenate to the one-shot

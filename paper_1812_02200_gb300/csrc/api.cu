@@ -209,6 +209,8 @@ rfr_status push_core(rfr_plan* p, const int16_t* iq, int64_t n, const rfr_output
             L.n_sms = p->n_sms;
             L.max_smem = p->max_smem;
             L.lookahead = p->tune.pfb_lookahead;
+            L.hop = static_cast<int>(p->H);
+            L.a0 = p->samples - p->cl;
             RFR_CUDA(p, p->gen ? rfr::gen_pfb_launch(L, p->gplan, st) : rfr::pfb_launch(L, st));
         } else if (p->mode == RFR_MODE_CHIRP) {
             rfr::ChirpLaunch L{};
@@ -399,16 +401,17 @@ rfr_status rfr_plan_create(rfr_plan** out, int32_t channels, int32_t taps, const
     if (channels > 0) {
         // ------------------------------------------------------------- PFB
         if (channels < 2 || channels > (1 << 24)) return bad(RFR_E_INVALID);
-        if (taps < 1 || taps > 16 || decimation != channels) return bad(RFR_E_INVALID);
+        if (taps < 1 || taps > 16 || decimation < 1 || decimation > channels) return bad(RFR_E_INVALID);
         if (out_flags == 0 || (out_flags & ~uint32_t(RFR_OUT_FULL | RFR_OUT_TONES)) != 0) return bad(RFR_E_INVALID);
         if ((out_flags & RFR_OUT_TONES) && nt == 0) return bad(RFR_E_INVALID);
         const bool pow2 = (channels & (channels - 1)) == 0;
         p->mode = RFR_MODE_PFB;
         p->N = channels;
         p->T = taps;
-        // powers of two from 16 to 16384: the fused single-CTA kernels;
-        // every other N = 2^a 3^b 5^c 7^d up to 2^24: the mixed-radix kernels
-        p->gen = !pow2 || channels < 16 || channels > 16384;
+        // powers of two from 16 to 16384, critically sampled: the fused
+        // single-CTA kernels; every other N = 2^a 3^b 5^c 7^d up to 2^24 and
+        // every hop < N (oversampled): the mixed-radix kernels
+        p->gen = !pow2 || channels < 16 || channels > 16384 || decimation != channels;
         if (p->gen && !rfr::gen_supported(channels)) return bad(RFR_E_UNSUPPORTED);
         if (p->gen) {
             p->Tk = taps;
@@ -430,7 +433,7 @@ rfr_status rfr_plan_create(rfr_plan** out, int32_t channels, int32_t taps, const
         std::vector<float> tw = p->gen ? std::vector<float>() : make_twiddles(p->log2n);
         p->tw_count = static_cast<int>(tw.size() / 2);
         p->W = static_cast<int64_t>(p->Tk) * channels;
-        p->H = channels;
+        p->H = decimation;
         p->carry_cap = p->W;
         cudaError_t e = cudaSuccess;
         if ((e = dev_alloc(&p->d_h, hk.size() * 4)) != cudaSuccess ||
@@ -765,9 +768,9 @@ rfr_status rfr_wait_selftest(int64_t limit_ns, int32_t* device_status) {
 rfr_status rfr_plan_seek(rfr_plan* p, int64_t start_sample, const int16_t* history, int64_t n_history) {
     if (!p || start_sample < 0 || start_sample % p->H != 0 || n_history < 0) return RFR_E_INVALID;
     const int64_t halo = p->W - p->H;                 // internal window minus hop
-    // history the caller provides: (T-1)*N (PFB) or L - D (demodulation); the
-    // kernel's zero-padded extra taps (if any) see zeros, which they ignore
-    const int64_t user_halo = p->mode == RFR_MODE_PFB ? static_cast<int64_t>(p->T - 1) * p->N
+    // history the caller provides: N*T - hop (PFB) or L - D (demodulation);
+    // the kernel's zero-padded extra taps (if any) see zeros, which they ignore
+    const int64_t user_halo = p->mode == RFR_MODE_PFB ? static_cast<int64_t>(p->T) * p->N - p->H
                                                       : static_cast<int64_t>(p->L) - p->D;
     const int64_t want = std::min<int64_t>(std::max<int64_t>(user_halo, 0), start_sample);
     if (n_history != want || (want > 0 && !history))

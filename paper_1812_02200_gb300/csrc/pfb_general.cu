@@ -1,10 +1,15 @@
 // pfb_general.cu -- the PFB of Sec. III.A for channel counts that are not a
 // power of two, or too large for one CTA (Fig. 3 channelizes with N = 10^5;
 // the section reports up to 10^7 bins): any N = 2^a 3^b 5^c 7^d with
-// 2 <= N <= 2^24, T <= 16 taps per channel, critically sampled (hop N).
+// 2 <= N <= 2^24, T <= 16 taps per channel, any hop 1 <= H <= N between frames.
 //
 // Frame k of the virtual stream [carry | buffer] uses the T*N samples from
-// k*N on:  v_k[p] = sum_{t<T} h[t*N + p] * x[k*N + t*N + p],  y_k = DFT_N(v_k).
+// k*H on (H = hop, N when critically sampled):
+//   v_k[p] = sum_{t<T} h[t*N + p] * x[k*H + t*N + p],
+//   y_k[c] = sum_p v_k[p] exp(-2*pi*i*c*(A_k + p)/N),
+// A_k the absolute index of the window's first sample (a multiple of N when
+// H = N, so y_k = DFT_N(v_k)); the factor is a circular shift of the FFT
+// input by A_k mod N, folded into the FIR's placement.
 //
 // Single pass (N <= 8192): one CTA per frame computes the FIR straight into
 // shared memory, runs an in-place mixed-radix Stockham FFT there and writes
@@ -288,6 +293,8 @@ struct GenArgs {
     int64_t F;              // frames in this launch
     int64_t k0;             // index of the launch's first frame within the push
     int N, T;
+    int hop;                // samples between frames
+    int64_t a0;             // absolute sample index of the virtual stream's first sample
     const float* h;         // [T*N]
     GenFft fa, fb;          // pass A (length N1) and pass B / single (length N2 = N)
     const float2* tw_a;
@@ -370,6 +377,15 @@ __device__ __forceinline__ void fir_points(const GenArgs& a, int64_t base, int E
     }
 }
 
+// Frames keep the phase of the absolute time origin: the FFT input index q
+// holds the window position (q - s) mod N, s = (absolute index of the
+// window's first sample) mod N, so that channel c is the stream mixed down by
+// exp(-2*pi*i*c*m/N) for every hop (s = 0 whenever the hop is N).
+__device__ __forceinline__ int frame_shift(const GenArgs& a, int64_t base) {
+    const int64_t s = (a.a0 + base) % a.N;
+    return static_cast<int>(s < 0 ? s + a.N : s);
+}
+
 // Shared memory: two buffers of gpad(elems) points each.
 __device__ __forceinline__ float2* second_buffer(float2* sm, int elems) { return sm + gpad(elems) + 1; }
 
@@ -379,8 +395,10 @@ __global__ void __launch_bounds__(TH, GenCfg<TH>::kMinBlocks) gen_single_kernel(
     float2* sm1 = second_buffer(sm, a.N);
     for (int64_t kk = blockIdx.x; kk < a.F; kk += gridDim.x) {
         const int64_t k = a.k0 + kk;
-        const int64_t base = k * a.N;
-        fir_points<TH>(a, base, a.N, [](int e) { return e; }, sm);
+        const int64_t base = k * a.hop;
+        const int sh = frame_shift(a, base);
+        const int N = a.N;
+        fir_points<TH>(a, base, a.N, [=](int e) { return e >= sh ? e - sh : e - sh + N; }, sm);
         __syncthreads();
         const float2* y = gen_fft<TH>(sm, sm1, a.fb, 0, a.tw_b);
         if (a.full) {
@@ -403,12 +421,15 @@ __global__ void __launch_bounds__(TH, GenCfg<TH>::kMinBlocks) gen_pass_a_kernel(
     for (int64_t it = blockIdx.x; it < a.F * groups; it += gridDim.x) {
         const int64_t kk = it / groups;
         const int g0 = static_cast<int>(it - kk * groups) << a.gla;
-        const int64_t base = (a.k0 + kk) * a.N;
-        const int N2 = a.N2, gla = a.gla;
+        const int64_t base = (a.k0 + kk) * a.hop;
+        const int sh = frame_shift(a, base);
+        const int N2 = a.N2, gla = a.gla, N = a.N;
         fir_points<TH>(a, base, E,
                    [=](int e) {
                        const int g = e & (GA - 1);
-                       return g0 + g < N2 ? (e >> gla) * N2 + g0 + g : -1;
+                       if (g0 + g >= N2) return -1;
+                       const int q = (e >> gla) * N2 + g0 + g;          // FFT input index
+                       return q >= sh ? q - sh : q - sh + N;            // window position
                    },
                    sm);
         __syncthreads();
@@ -650,6 +671,8 @@ cudaError_t gen_pfb_launch(const PfbLaunch& L, const GenPlan& g, cudaStream_t st
     a.buf = reinterpret_cast<const uint32_t*>(L.buf);
     a.N = g.N;
     a.T = L.taps_kernel;
+    a.hop = L.hop > 0 ? L.hop : g.N;
+    a.a0 = L.a0;
     a.h = L.h;
     a.fa = g.fa;
     a.fb = g.fb;

@@ -46,6 +46,8 @@ struct PfbLaunch {
     int max_smem;
     int lookahead;      // ring super-blocks fetched ahead (0 = as many as fit, <= 3)
     int variant;        // 0 = best available, 1 = shared-memory int16 ring only
+    int hop;            // samples between frames (N: critically sampled)
+    int64_t a0;         // absolute sample index of the virtual stream's first sample
 };
 bool pfb_uses_ring(int log2n, int taps);
 

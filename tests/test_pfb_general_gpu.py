@@ -152,3 +152,69 @@ def test_unsupported_n_is_rejected(lib):
         with pytest.raises(lib.RfrError) as e:
             lib.Plan(N, 4, window="hann", words=[], full=True, tones=False)
         assert e.value.status == -7
+
+
+# ------------------------------------------------------ oversampled (hop < N)
+OVERSAMPLED = [
+    # N, T, hop, window, frames
+    (1024, 8, 512, "kaiser", 200),       # power of two, half hop
+    (4096, 8, 1024, "kaiser", 60),       # the workload's N, quarter hop
+    (1000, 4, 250, "hann", 120),
+    (64, 4, 48, "hamming", 300),         # a hop that does not divide N
+    (10000, 4, 5000, "kaiser", 16),      # four-step form
+]
+
+
+@pytest.mark.parametrize("N,T,hop,win,frames", OVERSAMPLED)
+def test_oversampled_parity(lib, N, T, hop, win, frames):
+    beta = 9.0 if win == "kaiser" else 0.0
+    n_tones = min(16, N)
+    case = siggen.pfb_case(hop * frames + N * T, N, n_tones, seed=600 + N + hop, amp=(200.0, 1500.0))
+    plan = lib.Plan(N, T, window=win, beta=beta, words=case["words"], decimation=hop, full=True, tones=True)
+    full, tones = _run(plan, case["x"], n_tones, N)
+    ref = oracle.pfb_hop(case["x"], N, T, hop, _taps(N, T, win, beta), k_end=full.shape[0], bins=plan.bins())
+    e_t = rel_rows(tones, ref["tones"])
+    e_f = rel_channels_vs_rms(full, ref["full"])
+    print(f"N={N} T={T} hop={hop}: max tone rel err {e_t.max():.3e}, max channel err {e_f.max():.3e}")
+    assert e_t.max() < TOL and e_f.max() < TOL
+
+
+def test_oversampled_channel_is_the_gpu_demodulator(lib):
+    """Channel c of the oversampled PFB (hop 512, N = 1024, T = 8) and the
+    tensor-core demodulator at the bin-centred word c 2^64/N with L = N T,
+    D = hop and the same FP32 taps agree within the tolerance."""
+    N, T, hop = 1024, 8, 512
+    case = siggen.pfb_case(hop * 160 + N * T, N, 6, seed=17, amp=(300.0, 2000.0))
+    pfb = lib.Plan(N, T, window="hann", words=case["words"], decimation=hop, full=False, tones=True)
+    _, tp = _run(pfb, case["x"], 6, N, full=False)
+    dem = lib.Plan(0, N * T, window="hann", cutoff=0.5 / N, words=case["words"], decimation=hop)
+    h64p, _ = pfb.taps_table()
+    h64d, _ = dem.taps_table()
+    assert np.allclose(h64p, h64d, rtol=1e-12, atol=1e-18)
+    x = torch.from_numpy(case["x"]).to(DEV)
+    td = torch.zeros((6, dem.frames_for(x.shape[0])), dtype=torch.complex64, device=DEV)
+    dem.push_into(x, tones=td)
+    torch.cuda.synchronize()
+    F = min(tp.shape[1], td.shape[1])
+    assert rel_rows(tp[:, :F], td.cpu().numpy()[:, :F]).max() < TOL
+
+
+@pytest.mark.parametrize("N,hop", [(1000, 250), (1024, 512)])
+def test_oversampled_streamed_equals_one_shot(lib, N, hop):
+    rng = np.random.default_rng(N + hop)
+    case = siggen.pfb_case(hop * 150 + 5, N, 6, seed=9 + N)
+    x = torch.from_numpy(case["x"]).to(DEV)
+    mk = lambda: lib.Plan(N, 4, window="hann", words=case["words"], decimation=hop, full=True, tones=True)
+    f1, t1 = _run(mk(), case["x"], 6, N)
+    F = f1.shape[0]
+    fo = torch.zeros((F, N), dtype=torch.complex64, device=DEV)
+    to = torch.zeros((6, F), dtype=torch.complex64, device=DEV)
+    st = mk()
+    pos = off = 0
+    while pos < x.shape[0]:
+        cnt = int(min(x.shape[0] - pos, rng.integers(1, 3 * hop)))
+        off += st.push_into(x[pos:pos + cnt], fo, to, frame_offset=off)
+        pos += cnt
+    torch.cuda.synchronize()
+    assert off == F
+    assert np.array_equal(fo.cpu().numpy(), f1) and np.array_equal(to.cpu().numpy(), t1)

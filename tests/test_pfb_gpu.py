@@ -222,7 +222,7 @@ def test_invalid_plans(lib):
     w = np.array([1 << 60], np.uint64)
     bad = [dict(channels=1, taps=4), dict(channels=64, taps=0), dict(channels=64, taps=17),
            dict(channels=-3, taps=4, decimation=64), dict(channels=1 << 25, taps=2),
-           dict(channels=64, taps=4, decimation=32), dict(channels=100, taps=4, decimation=50)]
+           dict(channels=64, taps=4, decimation=65), dict(channels=100, taps=4, decimation=0)]
     for kw in bad:
         with pytest.raises(lib.RfrError) as ei:
             lib.Plan(window="hann", words=w, **kw)

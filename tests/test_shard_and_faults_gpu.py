@@ -12,13 +12,14 @@ pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 
 
-@pytest.mark.parametrize("kind", ["pfb", "pfb_padded", "demod", "demod_short"])
+@pytest.mark.parametrize("kind", ["pfb", "pfb_padded", "pfb_oversampled", "demod", "demod_short"])
 def test_two_shards_concatenate_to_one_shot(lib, kind):
     if kind.startswith("pfb"):
-        N, T = (1024, 8) if kind == "pfb" else (512, 3)       # T=3 runs with zero-padded taps
+        N, T = {"pfb": (1024, 8), "pfb_padded": (512, 3), "pfb_oversampled": (1000, 4)}[kind]
+        hop = N // 4 if kind == "pfb_oversampled" else N      # T=3 runs with zero-padded taps
         c = siggen.pfb_case(N * 300 + 17, N, 12, seed=81)
-        mk = lambda: lib.Plan(N, T, window="hann", words=c["words"])
-        hop, halo = N, (T - 1) * N
+        mk = lambda: lib.Plan(N, T, window="hann", words=c["words"], decimation=hop)
+        halo = T * N - hop
     else:
         L, D = (4096, 1024) if kind == "demod" else (1024, 2048)
         c = siggen.demod_case(D * 200 + 33, 90, seed=82)
