@@ -173,6 +173,7 @@ rfr_status push_check(rfr_plan* p, const int16_t* iq, int64_t n, const rfr_outpu
 
 rfr_status ensure_scratch(rfr_plan* p, int64_t n) {
     const int64_t F = frames_for_len(p, p->cl + n);
+    if (p->mode == RFR_MODE_PFB && p->gen && F > 0) RFR_CUDA(p, rfr::gen_plan_reserve(&p->gplan, F));
     if (p->mode == RFR_MODE_DEMOD && F > 0 && !p->words.empty()) return ensure_demod_scratch(p, F, p->frames);
     return RFR_OK;
 }
@@ -211,6 +212,15 @@ rfr_status push_core(rfr_plan* p, const int16_t* iq, int64_t n, const rfr_output
             L.lookahead = p->tune.pfb_lookahead;
             L.hop = static_cast<int>(p->H);
             L.a0 = p->samples - p->cl;
+            if (p->gen && p->gplan.N1 > 1 && p->gplan.z_frames < std::min(F, p->gplan.z_cap_frames)) {
+                // grow the between-pass buffer, unless the stream is being
+                // captured (then the frames go through the buffer in batches)
+                cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+                RFR_CUDA(p, cudaStreamIsCapturing(st, &cs));
+                if (cs == cudaStreamCaptureStatusNone) RFR_CUDA(p, rfr::gen_plan_reserve(&p->gplan, F));
+                else if (p->gplan.z_frames < 1)
+                    return fail(p, RFR_E_INVALID, "reserve scratch (a push outside capture) before capturing");
+            }
             RFR_CUDA(p, p->gen ? rfr::gen_pfb_launch(L, p->gplan, st) : rfr::pfb_launch(L, st));
         } else if (p->mode == RFR_MODE_CHIRP) {
             rfr::ChirpLaunch L{};

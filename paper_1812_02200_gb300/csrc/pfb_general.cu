@@ -551,6 +551,20 @@ void gen_plan_free(GenPlan* g) {
     *g = GenPlan{};
 }
 
+cudaError_t gen_plan_reserve(GenPlan* g, int64_t frames) {
+    if (g->N1 <= 1) return cudaSuccess;                       // one pass: no Z
+    const int64_t want = std::max<int64_t>(1, std::min<int64_t>(frames, g->z_cap_frames));
+    if (want <= g->z_frames) return cudaSuccess;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return e;
+    if (g->d_z) cudaFree(g->d_z);
+    g->d_z = nullptr;
+    g->z_frames = 0;
+    if ((e = cudaMalloc(&g->d_z, static_cast<size_t>(want) * g->N * 8)) != cudaSuccess) return e;
+    g->z_frames = want;
+    return cudaSuccess;
+}
+
 cudaError_t gen_plan_init(GenPlan* g, int N, int64_t z_budget_bytes) {
     *g = GenPlan{};
     if (!gen_supported(N)) return cudaErrorInvalidValue;
@@ -618,8 +632,8 @@ cudaError_t gen_plan_init(GenPlan* g, int N, int64_t z_budget_bytes) {
             (e = cudaMemcpy(g->d_th, th.data(), nh * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess ||
             (e = cudaMemcpy(g->d_tl, tl.data(), kTwSplit * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
             return e;
-        g->z_frames = std::max<int64_t>(1, z_budget_bytes / (static_cast<int64_t>(N) * 8));
-        if ((e = cudaMalloc(&g->d_z, static_cast<size_t>(g->z_frames) * N * 8)) != cudaSuccess) return e;
+        // Z is allocated by gen_plan_reserve, sized by the pushes (up to the budget)
+        g->z_cap_frames = std::max<int64_t>(1, z_budget_bytes / (static_cast<int64_t>(N) * 8));
     }
     return cudaSuccess;
 }
@@ -649,6 +663,7 @@ cudaError_t gen_run(GenArgs a, const PfbLaunch& L, const GenPlan& g, cudaStream_
         a.k0 = 0;
         return launch_gen<TH>(gen_single_kernel<TH>, a, L.F, g.N, L.n_sms, st);
     }
+    if (g.z_frames < 1 || !g.d_z) return cudaErrorInvalidValue;   // gen_plan_reserve first
     const int ga = 1 << g.gla, gb = 1 << g.glb;
     const int64_t groups_a = (g.N2 + ga - 1) / ga, groups_b = (g.N1 + gb - 1) / gb;
     for (int64_t k0 = 0; k0 < L.F; k0 += g.z_frames) {

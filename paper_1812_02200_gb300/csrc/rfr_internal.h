@@ -72,9 +72,13 @@ struct GenPlan {
     float2* d_tl = nullptr;     // W_N^i, i < 4096
     float2* d_z = nullptr;      // between-pass buffer, z_frames x N
     int64_t z_frames = 0;
+    int64_t z_cap_frames = 0;   // the most frames Z grows to
 };
 bool gen_supported(int64_t n);
 cudaError_t gen_plan_init(GenPlan* g, int N, int64_t z_budget_bytes);
+// Grow Z to min(frames, z_cap_frames) (allocates and synchronises the device;
+// never during stream capture).
+cudaError_t gen_plan_reserve(GenPlan* g, int64_t frames);
 void gen_plan_free(GenPlan* g);
 int pfb_kernel_taps(int log2n, int taps);
 cudaError_t pfb_launch(const PfbLaunch& L, cudaStream_t st);
