@@ -3,11 +3,14 @@
  *
  * The library turns a software radio's complex int16 ADC stream into
  * per-tone baseband timestreams, in the two forms of arXiv:1812.02200:
- *   - a critically sampled polyphase filter bank (PFB, Sec. III.A): a windowed
- *     polyphase FIR over N channels x T taps, an N-point FFT per frame, and
- *     the full spectrum and/or a gather of the bins that hold the tones;
+ *   - a polyphase filter bank (PFB, Sec. III.A): a windowed polyphase FIR
+ *     over N channels x T taps, an N-point FFT per frame, and the full
+ *     spectrum and/or a gather of the bins that hold the tones (critically
+ *     sampled as in the paper, or oversampled with a hop below N);
  *   - direct multi-tone demodulation (Sec. III.B): a per-tone NCO mix, a
- *     low-pass FIR and decimation by D.
+ *     low-pass FIR and decimation by D;
+ * plus the chirped readout (Sec. III.C) and the GPU-generated transmit
+ * buffers (a chirp; a multi-tone comb).
  *
  * Conventions shared by every call:
  *   - Samples are complex int16, I then Q interleaved (4 bytes per sample),
@@ -16,8 +19,10 @@
  *   - The stream starts at sample 0 with zero history.  Frame k is computed
  *     from the W samples that end at sample (k+1)*hop - 1 (W = N*T, hop = N
  *     for the PFB; W = L, hop = D for demodulation); samples before 0 are 0.
- *   - The PFB output of channel c is y_k[c] = sum_p v_k[p] exp(-2*pi*i*c*p/N),
- *     natural bin order, no 1/N factor (the taps sum to 1 instead).
+ *   - The PFB output of channel c is y_k[c] = sum_p v_k[p] exp(-2*pi*i*c*p/N)
+ *     (for a hop below N, exp(-2*pi*i*c*(A_k + p)/N) with A_k the absolute
+ *     index of the frame's first sample), natural bin order, no 1/N factor
+ *     (the taps sum to 1 instead).
  *   - A tone is an NCO word w: a uint64 phase increment per sample in units
  *     of 2*pi/2^64.  Its phase at absolute sample m is w*m mod 2^64 (exact
  *     integer arithmetic); the mixer is exp(-i*phase).
@@ -25,6 +30,11 @@
  *     is a cudaStream_t passed as void* (NULL = the legacy default stream).
  *   - Every call returns an rfr_status; nothing is thrown across the ABI.
  *     rfr_last_error() gives a message for the last failure of a plan.
+ *   - Tracing: the calls that enqueue GPU work open NVTX ranges named after
+ *     themselves.  RFR_DEBUG=1 in the environment (read once per process)
+ *     makes them synchronise their stream after enqueueing, unless it is
+ *     being captured, and return the first CUDA or device-status error at
+ *     the call that caused it; results are unchanged.
  *
  * Thread safety: a plan is used by one host thread at a time.  Different
  * plans are independent.

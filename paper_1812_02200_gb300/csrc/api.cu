@@ -13,6 +13,7 @@
 #include "dev_common.cuh"
 #include "fft_dev.cuh"
 #include "rfr_internal.h"
+#include "trace.h"
 
 using rfr::DEV_OK;
 using rfr::DEV_TIMEOUT;
@@ -120,6 +121,15 @@ rfr_status check_status(rfr_plan* p) {
     if (st == DEV_TIMEOUT) return fail(p, RFR_E_TIMEOUT, "a device-side wait timed out");
     if (st != DEV_OK) return fail(p, RFR_E_CUDA, "device status error");
     return RFR_OK;
+}
+
+// RFR_DEBUG: wait for the call's work and report its errors at the call.
+rfr_status debug_check(rfr_plan* p, cudaStream_t st, const char* what) {
+    if (!rfr::debug_sync_allowed(st)) return RFR_OK;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(p, e, what);
+    return check_status(p);
 }
 
 rfr_status ensure_demod_scratch(rfr_plan* p, int64_t F, int64_t F0) {
@@ -585,11 +595,13 @@ uint64_t rfr_chirp_rate_word(double k_hz_per_s, double fs_hz) {
 
 rfr_status rfr_chirp_synthesize(uint64_t start_word, uint64_t rate_word, double amplitude, int64_t m0,
                                 int64_t n, int16_t* iq_out, void* stream) {
+    rfr::TraceRange tr("rfr_chirp_synthesize");
     if (n < 0 || (n > 0 && !iq_out) || !(amplitude >= 0.0) || amplitude > 32767.0) return RFR_E_INVALID;
-    return rfr::chirp_synth(start_word, rate_word, amplitude, m0, n, iq_out, static_cast<cudaStream_t>(stream)) ==
-                   cudaSuccess
-               ? RFR_OK
-               : RFR_E_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (rfr::chirp_synth(start_word, rate_word, amplitude, m0, n, iq_out, st) != cudaSuccess) return RFR_E_CUDA;
+    if (rfr::debug_sync_allowed(st) && (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess))
+        return RFR_E_CUDA;
+    return RFR_OK;
 }
 
 void rfr_plan_destroy(rfr_plan* p) { destroy(p); }
@@ -616,14 +628,17 @@ rfr_status rfr_frames_for(const rfr_plan* p, int64_t n, int64_t* frames) {
 }
 
 rfr_status rfr_push_into(rfr_plan* p, const int16_t* iq, int64_t n, rfr_output* out, void* stream) {
+    rfr::TraceRange tr("rfr_push_into");
     if (!p || !out) return RFR_E_INVALID;
     int64_t F = 0;
     rfr_status s = push_core(p, iq, n, out, &F, static_cast<cudaStream_t>(stream));
+    if (s == RFR_OK) s = debug_check(p, static_cast<cudaStream_t>(stream), "rfr_push_into");
     out->frames = (s == RFR_OK) ? F : 0;
     return s;
 }
 
 rfr_status rfr_push(rfr_plan* p, const int16_t* iq, int64_t n, void* stream) {
+    rfr::TraceRange tr("rfr_push");
     if (!p) return RFR_E_INVALID;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int64_t F = frames_for_len(p, p->cl + n);
@@ -661,10 +676,12 @@ rfr_status rfr_push(rfr_plan* p, const int16_t* iq, int64_t n, void* stream) {
     int64_t got = 0;
     rfr_status s = push_core(p, iq, n, &o, &got, st);
     if (s == RFR_OK) p->q_frames += got;
+    if (s == RFR_OK) s = debug_check(p, st, "rfr_push");
     return s;
 }
 
 rfr_status rfr_pull(rfr_plan* p, rfr_output* out) {
+    rfr::TraceRange tr("rfr_pull");
     if (!p || !out) return RFR_E_INVALID;
     const int64_t F = p->q_frames;
     out->frames = 0;
@@ -690,6 +707,7 @@ rfr_status rfr_pull(rfr_plan* p, rfr_output* out) {
 }
 
 rfr_status rfr_process_host(rfr_plan* p, const int16_t* iq_host, int64_t n, rfr_output* out) {
+    rfr::TraceRange tr("rfr_process_host");
     if (!p || !out || n < 0 || (n > 0 && !iq_host)) return RFR_E_INVALID;
     const int64_t Ftot = frames_for_len(p, p->cl + n);
     if (!out_ok(p, out, Ftot)) return fail(p, RFR_E_SHORT, "process_host: output too small");
@@ -920,6 +938,7 @@ rfr_status rfr_plan_get_bins(const rfr_plan* p, int32_t* bins, int32_t* count) {
 }
 
 rfr_status rfr_plain_oneshot(rfr_plan* p, const int16_t* iq, int64_t n, rfr_output* out, void* stream) {
+    rfr::TraceRange tr("rfr_plain_oneshot");
     if (!p || !out || n < 0 || (n > 0 && !iq)) return RFR_E_INVALID;
     if (p->mode == RFR_MODE_CHIRP) return fail(p, RFR_E_UNSUPPORTED, "no plain form for chirp plans");
     cudaStream_t st = static_cast<cudaStream_t>(stream);

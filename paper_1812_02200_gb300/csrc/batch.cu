@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "rfr_internal.h"
+#include "trace.h"
 
 struct rfr_batch {
     std::vector<rfr_plan*> plans;
@@ -144,6 +145,7 @@ void rfr_batch_destroy(rfr_batch* b) {
 
 rfr_status rfr_batch_push(rfr_batch* b, const int16_t* const* bufs, const int64_t* n_samples,
                           rfr_output* outs, void* stream) {
+    rfr::TraceRange tr("rfr_batch_push");
     if (!b || !bufs || !n_samples || !outs) return RFR_E_INVALID;
     const int n = static_cast<int>(b->plans.size());
     // 1. validate and grow scratch outside of any capture
@@ -203,6 +205,8 @@ rfr_status rfr_batch_push(rfr_batch* b, const int16_t* const* bufs, const int64_
     if (cudaGraphLaunch(b->exec, st) != cudaSuccess) return batch_fail(b, RFR_E_CUDA, "graph launch");
     for (auto* p : b->plans) p->last_stream = st;
     ++b->steps;
+    if (rfr::debug_sync_allowed(st) && (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess))
+        return batch_fail(b, RFR_E_CUDA, "RFR_DEBUG: batch step failed on the device");
     return RFR_OK;
 }
 
@@ -218,6 +222,7 @@ rfr_status rfr_batch_stats(const rfr_batch* b, int64_t* steps, int64_t* graph_up
 const char* rfr_batch_last_error(const rfr_batch* b) { return b ? b->last_error.c_str() : ""; }
 
 rfr_status rfr_plan_autotune(rfr_plan* p, int64_t n_samples, int32_t use_cache, double* best_ms) {
+    rfr::TraceRange tr("rfr_plan_autotune");
     if (!p || n_samples < 1 || n_samples > (int64_t(1) << 31)) return RFR_E_INVALID;
     const std::string key = tune_key(p, n_samples);
     if (use_cache) {

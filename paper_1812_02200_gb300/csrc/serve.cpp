@@ -35,6 +35,7 @@
 #include <vector>
 
 #include "rfr_internal.h"
+#include "trace.h"
 
 namespace {
 
@@ -193,6 +194,7 @@ void worker_loop(rfr_server* s) {
             f.bytes = need;
             f.frames = F;
             f.t_admit = now_us();
+            rfr::TraceRange tr("rfr_server_admit");
             f.ev = s->event_pool.back();
             s->event_pool.pop_back();
             cudaStream_t st = s->streams[rq.readout];

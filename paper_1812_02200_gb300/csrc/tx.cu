@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "../../include/rfr.h"
+#include "trace.h"
 
 namespace {
 
@@ -170,13 +171,18 @@ rfr_status rfr_tx_create(rfr_tx** out, const uint64_t* words, const uint64_t* ph
 }
 
 rfr_status rfr_tx_synthesize(rfr_tx* t, int64_t m0, int64_t n, int16_t* iq_out, void* stream) {
+    rfr::TraceRange tr("rfr_tx_synthesize");
     if (!t || n < 0 || (n > 0 && !iq_out)) return RFR_E_INVALID;
     if (n == 0) return RFR_OK;
     const int64_t tiles = (n + kTxTile - 1) / kTxTile;
     const int64_t blocks = std::min<int64_t>(tiles, static_cast<int64_t>(t->n_sms) * 8);
     tx_synth_kernel<<<static_cast<unsigned>(blocks), kTxThreads, 0, static_cast<cudaStream_t>(stream)>>>(
         t->d_words, t->d_phases, t->d_amps, t->n_tones, m0, n, reinterpret_cast<short2*>(iq_out));
-    return cudaGetLastError() == cudaSuccess ? RFR_OK : RFR_E_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return RFR_E_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (rfr::debug_sync_allowed(st) && (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess))
+        return RFR_E_CUDA;
+    return RFR_OK;
 }
 
 double rfr_tx_error_bound(const rfr_tx* t) { return t ? t->error_bound : -1.0; }
