@@ -503,11 +503,23 @@ def run_large_n(args, dev, stream, x, words):
         ms = e0.elapsed_time(e1) / reps
         bps = 4.0 + 8.0 + 8.0 * len(words) / N
         gbs = bps * n / (ms * 1e-3) / 1e9
-        out.append({"workload": f"PFB N={N} T=4 Hamming, 2^{int(np.log2(n))} complex int16 samples, "
-                                f"full spectrum + {len(words)} tones",
-                    "value": n / (ms * 1e-3) / 1e6, "unit": UNIT, "ms": ms, "frames": F,
-                    "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
-                                 "frac": gbs / hbm_peak, "bytes_per_sample": bps}})
+        res = {"workload": f"PFB N={N} T=4 Hamming, 2^{int(np.log2(n))} complex int16 samples, "
+                           f"full spectrum + {len(words)} tones",
+               "value": n / (ms * 1e-3) / 1e6, "unit": UNIT, "ms": ms, "frames": F,
+               "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                            "frac": gbs / hbm_peak, "bytes_per_sample": bps}}
+        if not args.no_plain and N <= 100000:
+            # the plain FP32 form on the same stream: FP32 FIR kernel + cuFFT + gather
+            plan.plain_oneshot(x, full, tones, stream=stream)
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            plan.plain_oneshot(x, full, tones, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            pms = e0.elapsed_time(e1)
+            res["plain_fp32"] = {"value": n / (pms * 1e-3) / 1e6, "unit": UNIT, "ms": pms,
+                                 "form": "FP32 FIR kernel + cuFFT C2C batched + gather kernel"}
+        out.append(res)
         plan.close()
         del full, tones
         torch.cuda.empty_cache()

@@ -941,6 +941,8 @@ rfr_status rfr_plain_oneshot(rfr_plan* p, const int16_t* iq, int64_t n, rfr_outp
     rfr::TraceRange tr("rfr_plain_oneshot");
     if (!p || !out || n < 0 || (n > 0 && !iq)) return RFR_E_INVALID;
     if (p->mode == RFR_MODE_CHIRP) return fail(p, RFR_E_UNSUPPORTED, "no plain form for chirp plans");
+    if (p->mode == RFR_MODE_PFB && p->H != p->N)
+        return fail(p, RFR_E_UNSUPPORTED, "the plain form is critically sampled only");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // zero history: frame k uses samples ((k+1)*hop - W, (k+1)*hop]
     const int64_t W = p->mode == RFR_MODE_PFB ? static_cast<int64_t>(p->N) * p->T : p->L;

@@ -254,36 +254,74 @@ __device__ __forceinline__ void gen_stage(const float2* __restrict__ src, float2
     __syncthreads();
 }
 
-// The whole transform: the points start in buf0; returns the buffer that
-// holds the result (buf0 or buf1, by the parity of the stage count).
-template <int TH>
-__device__ float2* gen_fft(float2* buf0, float2* buf1, const GenFft& f, int gl2, const float2* __restrict__ tw) {
+// The last stage of a transform: the same butterflies, each output point
+// handed to sink(e, value) (e = c*G + g: output c of transform g) instead of
+// being written back to shared memory.
+template <int R, int TH, typename Sink>
+__device__ __forceinline__ void gen_stage_out(const float2* __restrict__ src, int n, int gl2, int Ns,
+                                              uint32_t ns_magic, const float2* __restrict__ tw, Sink& sink) {
+    const int nR = n / R;
+    const int nb = nR << gl2;
+    const int gm = (1 << gl2) - 1;
+    for (int u = threadIdx.x; u < nb; u += TH) {
+        const int g = u & gm, j = u >> gl2;
+        const int q = Ns == 1 ? j : static_cast<int>(__umulhi(static_cast<uint32_t>(j), ns_magic));
+        const int k = j - q * Ns;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = src[gpad(((j + r * nR) << gl2) + g)];
+        if (Ns > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], __ldg(tw + (r - 1) * Ns + k));
+        }
+        dft_any<R>(v);
+        const int base = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) sink(((base + r * Ns) << gl2) + g, v[r]);
+    }
+}
+
+// The whole transform with its output points delivered to `sink` by the
+// last stage; the points start in buf0.  Returns the buffer the last stage
+// did not read (free for the caller).
+template <int TH, typename Sink>
+__device__ float2* gen_fft_to(float2* buf0, float2* buf1, const GenFft& f, int gl2, const float2* __restrict__ tw,
+                              Sink sink) {
     float2* src = buf0;
     float2* dst = buf1;
     for (int s = 0; s < f.nst; ++s) {
         const float2* t = tw + f.tw_off[s];
+        const bool last = s == f.nst - 1;
+#define RFR_GEN_CASE(RR)                                                                              \
+    case RR:                                                                                          \
+        if (last) gen_stage_out<RR, TH>(src, f.n, gl2, f.ns[s], f.ns_magic[s], t, sink);              \
+        else gen_stage<RR, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t);                        \
+        break;
         switch (f.radix[s]) {
-        case 16: gen_stage<16, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
-        case 25: gen_stage<25, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
-        case 20: gen_stage<20, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
-        case 15: gen_stage<15, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
-        case 12: gen_stage<12, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
-        case 10: gen_stage<10, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
-        case 9: gen_stage<9, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
-        case 8: gen_stage<8, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
-        case 7: gen_stage<7, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
-        case 6: gen_stage<6, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
-        case 5: gen_stage<5, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
-        case 4: gen_stage<4, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
-        case 3: gen_stage<3, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
-        case 2: gen_stage<2, TH>(src, dst, f.n, gl2, f.ns[s], f.ns_magic[s], t); break;
+            RFR_GEN_CASE(16)
+            RFR_GEN_CASE(25)
+            RFR_GEN_CASE(20)
+            RFR_GEN_CASE(15)
+            RFR_GEN_CASE(12)
+            RFR_GEN_CASE(10)
+            RFR_GEN_CASE(9)
+            RFR_GEN_CASE(8)
+            RFR_GEN_CASE(7)
+            RFR_GEN_CASE(6)
+            RFR_GEN_CASE(5)
+            RFR_GEN_CASE(4)
+            RFR_GEN_CASE(3)
+            RFR_GEN_CASE(2)
         default: break;
         }
-        float2* tmp = src;
-        src = dst;
-        dst = tmp;
+#undef RFR_GEN_CASE
+        if (!last) {
+            float2* tmp = src;
+            src = dst;
+            dst = tmp;
+        }
     }
-    return src;
+    return dst;
 }
 
 struct GenArgs {
@@ -400,13 +438,20 @@ __global__ void __launch_bounds__(TH, GenCfg<TH>::kMinBlocks) gen_single_kernel(
         const int N = a.N;
         fir_points<TH>(a, base, a.N, [=](int e) { return e >= sh ? e - sh : e - sh + N; }, sm);
         __syncthreads();
-        const float2* y = gen_fft<TH>(sm, sm1, a.fb, 0, a.tw_b);
-        if (a.full) {
-            float2* row = a.full + (a.fo + k) * a.full_ld;
-            for (int c = threadIdx.x; c < a.N; c += TH) row[c] = y[gpad(c)];
+        float2* row = a.full ? a.full + (a.fo + k) * a.full_ld : nullptr;
+        const bool keep = a.n_tones > 0;
+        float2* const freebuf = (a.fb.nst & 1) ? sm1 : sm;   // the buffer the last stage does not read
+        // the last stage writes the spectrum row and, for the tone gather, a
+        // copy into the free shared-memory buffer
+        gen_fft_to<TH>(sm, sm1, a.fb, 0, a.tw_b, [=](int c, float2 v) {
+            if (row) row[c] = v;
+            if (keep) freebuf[gpad(c)] = v;
+        });
+        if (keep) {
+            __syncthreads();
+            for (int t = threadIdx.x; t < a.n_tones; t += TH)
+                a.tones[t * a.tones_ld + a.fo + k] = freebuf[gpad(__ldg(a.bins + t))];
         }
-        for (int t = threadIdx.x; t < a.n_tones; t += TH)
-            a.tones[t * a.tones_ld + a.fo + k] = y[gpad(__ldg(a.bins + t))];
         __syncthreads();
     }
 }
@@ -433,16 +478,18 @@ __global__ void __launch_bounds__(TH, GenCfg<TH>::kMinBlocks) gen_pass_a_kernel(
                    },
                    sm);
         __syncthreads();
-        const float2* y = gen_fft<TH>(sm, sm1, a.fa, a.gla, a.tw_a);
+        // the last stage multiplies by W_N^{p2*c1} and stores Z directly
         float2* zf = a.z + kk * a.N;
-        for (int e = threadIdx.x; e < E; e += TH) {
-            const int g = e & (GA - 1), c1 = e >> a.gla, p2 = g0 + g;
-            if (p2 < a.N2) {
+        const float2* th = a.th;
+        const float2* tl = a.tl;
+        gen_fft_to<TH>(sm, sm1, a.fa, a.gla, a.tw_a, [=](int e, float2 v) {
+            const int g = e & (GA - 1), c1 = e >> gla, p2 = g0 + g;
+            if (p2 < N2) {
                 const int m = p2 * c1;                       // < N1*N2 = N
-                const float2 w = cmul(__ldg(a.th + (m / kTwSplit)), __ldg(a.tl + (m % kTwSplit)));
-                zf[static_cast<int64_t>(c1) * a.N2 + p2] = cmul(y[gpad(e)], w);
+                const float2 w = cmul(__ldg(th + (m / kTwSplit)), __ldg(tl + (m % kTwSplit)));
+                zf[static_cast<int64_t>(c1) * N2 + p2] = cmul(v, w);
             }
-        }
+        });
         __syncthreads();
     }
 }
@@ -468,20 +515,26 @@ __global__ void __launch_bounds__(TH, GenCfg<TH>::kMinBlocks) gen_pass_b_kernel(
             sm[gpad((p2 << a.glb) + g)] = f < cnt ? zf[f] : make_float2(0.f, 0.f);
         }
         __syncthreads();
-        const float2* y = gen_fft<TH>(sm, sm1, a.fb, a.glb, a.tw_b);
         const int64_t k = a.k0 + kk;
-        if (a.full) {
-            float2* row = a.full + (a.fo + k) * a.full_ld;
-            for (int e = threadIdx.x; e < E; e += TH) {
-                const int g = e & (GB - 1), c2 = e >> a.glb;
-                if (c0 + g < a.N1) row[c0 + g + static_cast<int64_t>(a.N1) * c2] = y[gpad(e)];
+        // the last stage stores the spectrum (runs of GB points) and, for the
+        // tone gather, a copy in the free shared-memory buffer
+        float2* row = a.full ? a.full + (a.fo + k) * a.full_ld : nullptr;
+        const bool keep = a.n_tones > 0;
+        float2* const freebuf = (a.fb.nst & 1) ? sm1 : sm;
+        const int glb = a.glb, N1 = a.N1;
+        gen_fft_to<TH>(sm, sm1, a.fb, a.glb, a.tw_b, [=](int e, float2 v) {
+            const int g = e & (GB - 1), c2 = e >> glb;
+            if (row && c0 + g < N1) row[c0 + g + static_cast<int64_t>(N1) * c2] = v;
+            if (keep) freebuf[gpad(e)] = v;
+        });
+        if (keep) {
+            __syncthreads();
+            for (int t = threadIdx.x; t < a.n_tones; t += TH) {
+                const int b = __ldg(a.bins + t);
+                const int c1 = b % a.N1;
+                if (c1 >= c0 && c1 < c0 + GB)
+                    a.tones[t * a.tones_ld + a.fo + k] = freebuf[gpad(((b / a.N1) << a.glb) + c1 - c0)];
             }
-        }
-        for (int t = threadIdx.x; t < a.n_tones; t += TH) {
-            const int b = __ldg(a.bins + t);
-            const int c1 = b % a.N1;
-            if (c1 >= c0 && c1 < c0 + GB)
-                a.tones[t * a.tones_ld + a.fo + k] = y[gpad(((b / a.N1) << a.glb) + c1 - c0)];
         }
         __syncthreads();
     }
@@ -503,7 +556,7 @@ int floor_log2(int v) {
 // Radices of a length-n transform (the fewest passes of register DFTs),
 // stage spans and twiddle-table offsets; appends the FP64-built twiddles to
 // `tw` (offsets are absolute positions in `tw`).
-bool build_fft(int n, GenFft* f, std::vector<float2>& tw) {
+bool build_fft(int n, GenFft* f, std::vector<float2>& tw, int rmax) {
     *f = GenFft{};
     f->n = n;
     int m = n, ns = 1;
@@ -526,11 +579,13 @@ bool build_fft(int n, GenFft* f, std::vector<float2>& tw) {
         return true;
     };
     // fewest passes: the largest radix of the register DFTs that divides
-    // what is left (16 = 2^4 and the composites up to 25)
+    // what is left (16 = 2^4 and the composites up to 25), at most rmax
+    // (primes up to 7 always allowed).  Fewer passes measured faster than
+    // smaller radices that keep every thread of the CTA busy.
     while (m > 1) {
         int r = 0;
         for (int c : {25, 20, 16, 15, 12, 10, 9, 8, 7, 6, 5, 4, 3, 2})
-            if (m % c == 0) {
+            if (m % c == 0 && (c <= rmax || c <= 7)) {
                 r = c;
                 break;
             }
@@ -596,7 +651,7 @@ cudaError_t gen_plan_init(GenPlan* g, int N, int64_t z_budget_bytes) {
         g->threads = N <= GenCfg<256>::kElems ? 256 : 512;
         g->N1 = 1;
         g->N2 = N;
-        if (!build_fft(N, &g->fb, tw)) return cudaErrorInvalidValue;
+        if (!build_fft(N, &g->fb, tw, 25)) return cudaErrorInvalidValue;
     } else {
         int n1 = 0, n2 = 0, score = 0;
         g->threads = 256;
@@ -609,8 +664,8 @@ cudaError_t gen_plan_init(GenPlan* g, int N, int64_t z_budget_bytes) {
         g->N2 = n2;
         g->gla = floor_log2(std::min(kGMax, 1 << floor_log2(elems / g->N1)));
         g->glb = floor_log2(std::min(kGMax, 1 << floor_log2(elems / g->N2)));
-        if (!build_fft(g->N1, &g->fa, tw)) return cudaErrorInvalidValue;
-        if (!build_fft(g->N2, &g->fb, tw)) return cudaErrorInvalidValue;
+        if (!build_fft(g->N1, &g->fa, tw, 25)) return cudaErrorInvalidValue;
+        if (!build_fft(g->N2, &g->fb, tw, 25)) return cudaErrorInvalidValue;
     }
     cudaError_t e;
     const size_t twn = std::max<size_t>(tw.size(), 1);
