@@ -343,11 +343,14 @@ void destroy(rfr_plan* p) {
     for (int i = 0; i < rfr_plan::kStageBufs; ++i) {
         dev_free(p->d_stage_in[i]);
         dev_free(p->d_stage_full[i]);
-        dev_free(p->d_stage_tones[i]);
         if (p->stage_st[i]) cudaStreamDestroy(p->stage_st[i]);
     }
     for (auto& e : p->stage_ev)
         if (e) cudaEventDestroy(e);
+    for (int g = 0; g < rfr_plan::kToneGroups; ++g) {
+        dev_free(p->d_tgroup[g]);
+        if (p->tgroup_ev[g]) cudaEventDestroy(p->tgroup_ev[g]);
+    }
     rfr::plain_release(p->plain_scratch, p->plain_fft);
     rfr::gen_plan_free(&p->gplan);
     delete p;
@@ -717,28 +720,52 @@ rfr_status rfr_process_host(rfr_plan* p, const int16_t* iq_host, int64_t n, rfr_
     // chunk: a multiple of the hop, about 2^24 samples
     const int64_t chunk = std::max<int64_t>(p->H, (int64_t(1) << 24) / p->H * p->H);
     const int64_t fmax = chunk / p->H + 2;
-    if (p->stage_samples < chunk) {
+    // A strided device-to-host copy runs at the link's rate only with rows of
+    // about 128 KB or more (32 KB rows reach about half of it), so the tone
+    // rows of several chunks collect in one group buffer of >= 16384 frames
+    // (within 256 MB) and leave in one copy.
+    int64_t gcap = fmax;
+    if (want_tones) {
+        const int64_t by_rows = (16384 + fmax - 1) / fmax;
+        const int64_t by_mem = std::max<int64_t>(1, (int64_t(256) << 20) / (static_cast<int64_t>(nt) * 8 * fmax));
+        gcap = fmax * std::min(by_rows, by_mem);
+    }
+    if (p->stage_samples < chunk || (want_tones && p->tgroup_cap < gcap)) {
         cudaDeviceSynchronize();
         for (int i = 0; i < rfr_plan::kStageBufs; ++i) {
             dev_free(p->d_stage_in[i]);
             dev_free(p->d_stage_full[i]);
-            dev_free(p->d_stage_tones[i]);
-            p->d_stage_in[i] = p->d_stage_full[i] = p->d_stage_tones[i] = nullptr;
+            p->d_stage_in[i] = p->d_stage_full[i] = nullptr;
+        }
+        for (auto& g : p->d_tgroup) {
+            dev_free(g);
+            g = nullptr;
         }
         p->stage_samples = 0;
+        p->tgroup_cap = 0;
         for (int i = 0; i < rfr_plan::kStageBufs; ++i) {
             RFR_CUDA(p, dev_alloc(&p->d_stage_in[i], static_cast<size_t>(chunk) * 4));
             if (want_full) RFR_CUDA(p, dev_alloc(&p->d_stage_full[i], static_cast<size_t>(fmax) * p->N * 8));
-            if (want_tones) RFR_CUDA(p, dev_alloc(&p->d_stage_tones[i], static_cast<size_t>(fmax) * nt * 8));
             if (!p->stage_st[i]) RFR_CUDA(p, cudaStreamCreateWithFlags(&p->stage_st[i], cudaStreamNonBlocking));
         }
         for (auto& e : p->stage_ev)
             if (!e) RFR_CUDA(p, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        if (want_tones) {
+            for (int g = 0; g < rfr_plan::kToneGroups; ++g) {
+                RFR_CUDA(p, dev_alloc(&p->d_tgroup[g], static_cast<size_t>(gcap) * nt * 8));
+                if (!p->tgroup_ev[g]) RFR_CUDA(p, cudaEventCreateWithFlags(&p->tgroup_ev[g], cudaEventDisableTiming));
+            }
+            p->tgroup_cap = gcap;
+        }
         p->stage_samples = chunk;
     }
+    gcap = want_tones ? p->tgroup_cap : gcap;
     int64_t done = 0, fo = out->frame_offset;
     int i = 0;
     cudaEvent_t prev = nullptr;
+    int g = 0;                       // tone group being filled
+    int64_t gused = 0, gfo = fo;     // its frames so far, its first output frame
+    bool g_out[rfr_plan::kToneGroups] = {};   // a copy out of the group buffer is in flight
     while (done < n) {
         const int64_t cnt = std::min(chunk, n - done);
         const int s = i % rfr_plan::kStageBufs;
@@ -746,30 +773,38 @@ rfr_status rfr_process_host(rfr_plan* p, const int16_t* iq_host, int64_t n, rfr_
         RFR_CUDA(p, cudaMemcpyAsync(p->d_stage_in[s], iq_host + 2 * done, static_cast<size_t>(cnt) * 4,
                                     cudaMemcpyHostToDevice, st));
         if (prev) RFR_CUDA(p, cudaStreamWaitEvent(st, prev, 0));   // pushes stay in stream order
+        if (want_tones && gused == 0 && g_out[g]) RFR_CUDA(p, cudaStreamWaitEvent(st, p->tgroup_ev[g], 0));
         rfr_output o{};
         o.full = p->d_stage_full[s];
         o.full_ld = p->N;
         o.full_cap = fmax;
-        o.tones = p->d_stage_tones[s];
-        o.tones_ld = fmax;
-        o.tones_cap = fmax;
+        if (want_tones) {
+            o.tones = static_cast<char*>(p->d_tgroup[g]) + gused * 8;
+            o.tones_ld = gcap;
+            o.tones_cap = gcap - gused;
+        }
         int64_t F = 0;
         rfr_status rs = push_core(p, static_cast<const int16_t*>(p->d_stage_in[s]), cnt, &o, &F, st);
         if (rs != RFR_OK) return rs;
         RFR_CUDA(p, cudaEventRecord(p->stage_ev[s], st));
         prev = p->stage_ev[s];
-        if (F > 0) {
-            if (want_full)
-                RFR_CUDA(p, cudaMemcpy2DAsync(static_cast<char*>(out->full) + fo * out->full_ld * 8,
-                                              out->full_ld * 8, p->d_stage_full[s], p->N * 8, p->N * 8, F,
-                                              cudaMemcpyDeviceToHost, st));
-            if (want_tones)
-                RFR_CUDA(p, cudaMemcpy2DAsync(static_cast<char*>(out->tones) + fo * 8, out->tones_ld * 8,
-                                              p->d_stage_tones[s], fmax * 8, F * 8, nt,
-                                              cudaMemcpyDeviceToHost, st));
-        }
+        if (F > 0 && want_full)
+            RFR_CUDA(p, cudaMemcpy2DAsync(static_cast<char*>(out->full) + fo * out->full_ld * 8, out->full_ld * 8,
+                                          p->d_stage_full[s], p->N * 8, p->N * 8, F, cudaMemcpyDeviceToHost, st));
         fo += F;
         done += cnt;
+        gused += F;
+        // the group leaves when the next chunk might not fit, or at the end;
+        // every earlier push into it precedes this one in stream order
+        if (want_tones && gused > 0 && (gused + fmax > gcap || done == n)) {
+            RFR_CUDA(p, cudaMemcpy2DAsync(static_cast<char*>(out->tones) + gfo * 8, out->tones_ld * 8,
+                                          p->d_tgroup[g], gcap * 8, gused * 8, nt, cudaMemcpyDeviceToHost, st));
+            RFR_CUDA(p, cudaEventRecord(p->tgroup_ev[g], st));
+            g_out[g] = true;
+            g = (g + 1) % rfr_plan::kToneGroups;
+            gused = 0;
+            gfo = fo;
+        }
         ++i;
     }
     for (int s = 0; s < rfr_plan::kStageBufs; ++s) RFR_CUDA(p, cudaStreamSynchronize(p->stage_st[s]));

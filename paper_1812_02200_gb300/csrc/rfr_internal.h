@@ -238,10 +238,15 @@ struct rfr_plan {
     static constexpr int kStageBufs = 3;       // chunks in flight (copy in, compute, copy out)
     void* d_stage_in[kStageBufs] = {};
     void* d_stage_full[kStageBufs] = {};
-    void* d_stage_tones[kStageBufs] = {};
     int64_t stage_samples = 0;
     cudaStream_t stage_st[kStageBufs] = {};
     cudaEvent_t stage_ev[kStageBufs] = {};
+    // tone rows leave the device in groups of chunks (long rows for the
+    // strided device-to-host copy); two group buffers alternate
+    static constexpr int kToneGroups = 2;
+    void* d_tgroup[kToneGroups] = {};
+    int64_t tgroup_cap = 0;        // frames per row of a group buffer
+    cudaEvent_t tgroup_ev[kToneGroups] = {};
 
     // plain-form scratch
     void* plain_scratch = nullptr;

@@ -330,7 +330,8 @@ class Plan:
         self._check(_lib.rfr_plan_set_accum_chunk(self._h, int(k_blocks)), "set_accum_chunk")
 
     def set_demod_products(self, products: int):
-        """Demodulation GEMM form: 4 (real embedding, default) or 3 (Gauss)."""
+        """Demodulation GEMM form: 3 (Gauss; the default where D % 64 == 0) or
+        4 (real embedding of the complex product)."""
         self._check(_lib.rfr_plan_set_demod_products(self._h, int(products)), "set_demod_products")
 
     def seek(self, start_sample: int, history=None):

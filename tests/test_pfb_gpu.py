@@ -183,6 +183,29 @@ def test_push_pull_queue_and_host_path(lib):
     assert np.array_equal(th.numpy(), t1)
 
 
+def test_process_host_tone_groups(lib):
+    """Host-staged run long enough that tone rows leave the device in several
+    groups of chunks and a group buffer is reused (9 chunks of 2^24 samples
+    and a ragged tail, 4 chunks per group); a second call continues the
+    stream.  Equal, bit for bit, to one device push of the same samples."""
+    N, T, nt = 4096, 8, 48
+    rng = siggen.rng_for(77)
+    words = siggen.bin_words(siggen.distinct_bins(rng, N, nt), N)
+    n1, n2 = 9 * (1 << 24) + 12345, (1 << 24) + 777
+    g = torch.Generator().manual_seed(78)
+    xh = torch.randint(-2000, 2000, (n1 + n2, 2), dtype=torch.int16, generator=g).pin_memory()
+    ref = _plan(lib, N, T, "kaiser", 9.0, words, full=False)
+    F = ref.frames_for(n1 + n2)
+    tr = torch.zeros((nt, F), dtype=torch.complex64, device=DEV)
+    assert ref.push_into(xh.to(DEV), None, tr) == F
+    h = _plan(lib, N, T, "kaiser", 9.0, words, full=False)
+    th = torch.full((nt, F), float("nan"), dtype=torch.complex64).pin_memory()
+    F1 = h.frames_for(n1)
+    assert h.process_host(xh[:n1], None, th) == F1
+    assert F1 + h.process_host(xh[n1:], None, th, frame_offset=F1) == F
+    assert np.array_equal(th.numpy(), tr.cpu().numpy())
+
+
 def test_tones_only_and_full_only(lib):
     N, T = 512, 4
     case = siggen.pfb_case(N * 90, N, 10, seed=21)
