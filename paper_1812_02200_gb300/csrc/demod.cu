@@ -47,6 +47,20 @@
 
 namespace rfr {
 
+// cuTensorMapEncodeTiled from the driver, looked up once (nullptr if absent)
+void* tmap_encode_tiled_fn() {
+    static void* fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = p;
+    });
+    return fn;
+}
+
 namespace {
 
 constexpr int BM = kDemodBM, BN = kDemodBN, BK = kDemodBK;
@@ -619,16 +633,7 @@ demod3m_gemm_kernel(const __grid_constant__ G3Maps mp, const GemmArgs g) {
 
 // ------------------------------------------------------------ host side
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess && q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    });
-    return fn;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tmap_encode_tiled_fn());
 }
 
 // 2-D fp16 tensor [rows][cols] (cols contiguous), box [box_rows][64], 128B swizzle.

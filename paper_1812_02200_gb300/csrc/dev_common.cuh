@@ -93,6 +93,14 @@ __device__ __forceinline__ void tma_bulk_s2g(void* dst, const void* src, uint32_
     asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
                  ::"l"(dst), "r"(smem_u32(src)), "r"(bytes) : "memory");
 }
+// 2-D tiled tensor copy shared -> global (bulk async-group completion); the
+// box is the tensor map's, (c0, c1) its origin: c0 the innermost coordinate
+// in elements (c0 * element size a multiple of 16 bytes), c1 the row, both
+// >= 0.  Elements outside the tensor's extent are not written.
+__device__ __forceinline__ void tma_store_2d(const void* tmap, int32_t c0, int32_t c1, const void* src) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];"
+                 ::"l"(tmap), "r"(c0), "r"(c1), "r"(smem_u32(src)) : "memory");
+}
 __device__ __forceinline__ void bulk_commit() {
     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }

@@ -24,8 +24,12 @@
 // Both run the same in-CTA FFT (fft_dev.cuh) and write
 //   full[(frame_offset + j) * full_ld + c]      (natural bin order)
 //   tones[s * tones_ld + frame_offset + j] = y_j[bin[s]].
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <cstdio>
+#include <cstring>
 
 #include "dev_common.cuh"
 #include "fft_dev.cuh"
@@ -55,8 +59,8 @@ struct PfbArgs {
     int64_t tones_ld;
     int64_t frame_offset;
     int use_tma;
-    int tones_vec;           // tones rows/offsets 16-byte aligned for grouped stores
-    int nb_smem;             // TMEM variant: tones whose bins and values are staged in smem (0 or n_tones)
+    int tones_tma;           // TMEM variant: whole tone groups leave by 2-D TMA stores
+    int nb_smem;             // TMEM variant: tones staged in smem (0 or n_tones)
     int full_bulk;           // TMEM variant: full rows written by one TMA bulk store each
     int* status;
     int64_t q_lo, q_hi;      // iteration range
@@ -241,35 +245,56 @@ __global__ void __launch_bounds__(kRingThreads, 1) pfb_ring_kernel(const PfbArgs
 // (t = 0..T-1 from zero), so results are bit-identical to them.
 constexpr int kTmemStage = 4;        // staging slots (blocks of 4096 samples)
 constexpr int kTmemSlots = 8;        // delay-line blocks held in TMEM
-constexpr int kToneGroup = 4;        // frames of tone values staged before one store
+constexpr int kToneGroup = 4;        // output frames per tone group (32 bytes of each tone row)
+constexpr int kToneBox = 256;        // tone rows per TMA store box
+constexpr int kTonesPerThread = 5;   // tones in shared memory: at most 5 * 256
 
-__host__ __device__ constexpr size_t tmem_smem_bytes(int tw_count, int n_bins_smem) {
-    return static_cast<size_t>(kTmemStage) * 4096 * 4 + static_cast<size_t>(2) * (4096 + 256) * 8 +
-           static_cast<size_t>((tw_count + 1) & ~1) * 8 + static_cast<size_t>((n_bins_smem + 1) & ~1) * 4 +
-           static_cast<size_t>(kToneGroup) * n_bins_smem * 8 + kTmemStage * 8 + 16;
+// Shared memory of the TMEM variant: int16 staging ring, two exchange
+// buffers, twiddles; with the tones in shared memory also their bins and the
+// tone tile [rows][kToneGroup] (rows = tones rounded up to the store box,
+// 1 KiB aligned); then the mbarriers and the TMEM address.
+struct TmemLayout {
+    size_t xb, tw, bins, tile, bars, total;
+};
+__host__ __device__ __forceinline__ TmemLayout tmem_layout(int tw_count, int nb) {
+    TmemLayout L{};
+    L.xb = static_cast<size_t>(kTmemStage) * 4096 * 4;
+    L.tw = L.xb + static_cast<size_t>(2) * (4096 + 256) * 8;
+    size_t o = L.tw + static_cast<size_t>((tw_count + 1) & ~1) * 8;
+    L.bins = o;
+    o = (o + static_cast<size_t>(nb) * 4 + 1023) / 1024 * 1024;
+    L.tile = o;
+    o += static_cast<size_t>((nb + kToneBox - 1) / kToneBox * kToneBox) * kToneGroup * 8;
+    L.bars = o;
+    L.total = o + kTmemStage * 8 + 16;
+    return L;
 }
 
 template <int T>
-__global__ void __launch_bounds__(kRingThreads, 1) pfb_tmem_kernel(const PfbArgs a) {
-    constexpr int LOG2N = 12, N = 4096, NT = 256;
+__global__ void __launch_bounds__(kRingThreads, 1)
+    pfb_tmem_kernel(const PfbArgs a, const __grid_constant__ CUtensorMap tm_tones) {
+    constexpr int N = 4096, NT = 256;
     static_assert(T <= kTmemSlots, "delay line fits in TMEM");
     extern __shared__ __align__(1024) unsigned char smem[];
+    const int nb_smem = a.nb_smem;
+    const TmemLayout lay = tmem_layout(a.tw_count, nb_smem);
     uint32_t* stage = reinterpret_cast<uint32_t*>(smem);
     // two exchange buffers used alternately (frame parity), so consecutive
     // passes and frames need only three barriers per frame
-    float2* const xb0 = reinterpret_cast<float2*>(smem + static_cast<size_t>(kTmemStage) * N * 4);
+    float2* const xb0 = reinterpret_cast<float2*>(smem + lay.xb);
     float2* const xb1 = xb0 + (N + N / 16);
-    float2* tw = xb1 + (N + N / 16);
-    const int nb_smem = a.nb_smem;
-    int32_t* sbins = reinterpret_cast<int32_t*>(tw + ((a.tw_count + 1) & ~1));
-    // tone values of kToneGroup frames: tstage[q * nb_smem + t]
-    float2* tstage = reinterpret_cast<float2*>(sbins + ((nb_smem + 1) & ~1));
-    uint64_t* bars = reinterpret_cast<uint64_t*>(tstage + static_cast<size_t>(kToneGroup) * nb_smem);
+    float2* tw = reinterpret_cast<float2*>(smem + lay.tw);
+    int32_t* sbins = reinterpret_cast<int32_t*>(smem + lay.bins);
+    float2* tile = reinterpret_cast<float2*>(smem + lay.tile);   // tone t, group frame q at t*kToneGroup + q
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + lay.bars);
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + kTmemStage);
 
     const int tid = threadIdx.x, warp = tid >> 5, tf = tid;
-    const int64_t ja = static_cast<int64_t>(blockIdx.x) * a.iters_per_cta;
-    const int64_t jb = min_i64(a.F, ja + a.iters_per_cta);
+    // CTA ranges start on whole tone groups of OUTPUT frames (frame_offset + j
+    // a multiple of kToneGroup), so every TMA store origin is 32-byte aligned
+    const int64_t shift = a.frame_offset & (kToneGroup - 1);
+    const int64_t ja = max_i64(0, static_cast<int64_t>(blockIdx.x) * a.iters_per_cta - shift);
+    const int64_t jb = min_i64(a.F, static_cast<int64_t>(blockIdx.x + 1) * a.iters_per_cta - shift);
     if (ja >= jb) return;
     const int64_t b0 = ja, b1 = jb + T - 1;                     // blocks [b0, b1)
     const int64_t need = (a.F + T - 1) * static_cast<int64_t>(N);
@@ -351,7 +376,9 @@ __global__ void __launch_bounds__(kRingThreads, 1) pfb_tmem_kernel(const PfbArgs
         dft16(v);
 #pragma unroll
         for (int r = 0; r < 16; ++r) P[fpad(16 * tf + r)] = v[r];
-        if (a.full_bulk && tid == 0) bulk_wait_read_all();     // previous row left Q (= this P's twin)
+        // the previous frame's bulk stores have read the spectrum row (now Q's
+        // twin) and the tone tile before either is written again
+        if (tid == 0) bulk_wait_read_all();
         __syncthreads();                                         // (A) pass 0 written, staging read
         if (tid == 0 && b + kTmemStage < b1)
             issue_sb_tma(a, b + kTmemStage, need, stage + s * N, &bars[s]);
@@ -374,8 +401,14 @@ __global__ void __launch_bounds__(kRingThreads, 1) pfb_tmem_kernel(const PfbArgs
             for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], tw[240 + (r - 1) * 256 + tf]);
             dft16(v);                                            // v[r] = bin tf + 256 r
         }
-        // spectrum -> P: unpadded natural order when the full row goes out by
-        // one bulk store, padded otherwise (only the tone gather reads it)
+        // Outputs.  The spectrum goes to P (unpadded natural order when the
+        // full row leaves by one bulk store, padded when only the tones read
+        // it).  Tones in shared memory: thread tid gathers tones tid + 256 k
+        // into the tone tile (all bins, then all values, then all stores, so
+        // the loads overlap); a group of kToneGroup output frames leaves by
+        // 2-D TMA stores (whole groups) or plain stores (a CTA's partial
+        // first or last group, unaligned rows).  More tones: each is gathered
+        // from P and stored per frame.
         const bool bulk = a.full_bulk != 0;
         if (a.full && !bulk) {
             float2* row = a.full + (a.frame_offset + j) * a.full_ld;
@@ -386,58 +419,58 @@ __global__ void __launch_bounds__(kRingThreads, 1) pfb_tmem_kernel(const PfbArgs
 #pragma unroll
             for (int i = 0; i < 16; ++i) P[tf + i * NT] = v[i];
             fence_proxy_async_smem();
-        }
-        if (bulk || a.n_tones > 0) {
-            if (!bulk) {
+        } else if (a.n_tones > 0) {
 #pragma unroll
-                for (int i = 0; i < 16; ++i) P[fpad(tf + i * NT)] = v[i];
-            }
-            __syncthreads();                                     // (C) spectrum in P
-            if (bulk && tid == 0) {
-                tma_bulk_s2g(a.full + (a.frame_offset + j) * a.full_ld, P, N * 8);
-                bulk_commit();
-            }
+            for (int i = 0; i < 16; ++i) P[fpad(tf + i * NT)] = v[i];
         }
-        if (a.n_tones > 0) {
-            if (nb_smem == a.n_tones) {
-                // stage this frame's tone values; store kToneGroup frames per
-                // tone at once (full 32-byte sectors instead of 8-byte pieces)
-                const int q = static_cast<int>((j - ja) % kToneGroup);
-                for (int t = tid; t < nb_smem; t += NT)
-                    tstage[q * nb_smem + t] = P[bulk ? sbins[t] : fpad(sbins[t])];
-                if (q == kToneGroup - 1 || j == jb - 1) {
-                    __syncthreads();
-                    const int64_t j0 = j - q;                    // first frame of the group
-                    const int nq = q + 1;
-                    float2* base = a.tones + a.frame_offset + j0;
-                    if (a.tones_vec && nq == kToneGroup) {
-                        // 2 threads per tone, 16 bytes (2 frames) each
-                        for (int it = tid; it < 2 * nb_smem; it += NT) {
-                            const int t = it >> 1, h = it & 1;
-                            const float2 v0 = tstage[(2 * h) * nb_smem + t];
-                            const float2 v1 = tstage[(2 * h + 1) * nb_smem + t];
-                            *reinterpret_cast<float4*>(base + static_cast<int64_t>(t) * a.tones_ld + 2 * h) =
-                                make_float4(v0.x, v0.y, v1.x, v1.y);
-                        }
-                    } else {
-                        for (int it = tid; it < nq * nb_smem; it += NT) {
-                            const int t = it / nq, qq = it - t * nq;
-                            base[static_cast<int64_t>(t) * a.tones_ld + qq] = tstage[qq * nb_smem + t];
-                        }
+        __syncthreads();                                         // (C) spectrum in P; Q reads done
+        if (bulk && tid == 0) {
+            tma_bulk_s2g(a.full + (a.frame_offset + j) * a.full_ld, P, N * 8);
+            bulk_commit();
+        }
+        if (nb_smem > 0) {
+            const int q = static_cast<int>((a.frame_offset + j) & (kToneGroup - 1));
+            int bk[kTonesPerThread];
+#pragma unroll
+            for (int k = 0; k < kTonesPerThread; ++k) bk[k] = tid + k * NT < nb_smem ? sbins[tid + k * NT] : -1;
+            float2 tv[kTonesPerThread];
+#pragma unroll
+            for (int k = 0; k < kTonesPerThread; ++k)
+                if (bk[k] >= 0) tv[k] = P[bulk ? bk[k] : fpad(bk[k])];
+#pragma unroll
+            for (int k = 0; k < kTonesPerThread; ++k)
+                if (bk[k] >= 0) tile[(tid + k * NT) * kToneGroup + q] = tv[k];
+            if (q == kToneGroup - 1 || j == jb - 1) {
+                const bool gtma = a.tones_tma && q == kToneGroup - 1 && j - q >= ja;
+                if (gtma) fence_proxy_async_smem();
+                __syncthreads();                                 // tile complete
+                if (gtma) {
+                    if (tid == 0) {
+                        const int32_t x0 = static_cast<int32_t>(a.frame_offset + j - q);
+                        for (int r0 = 0; r0 < nb_smem; r0 += kToneBox)
+                            tma_store_2d(&tm_tones, x0, r0, tile + static_cast<size_t>(r0) * kToneGroup);
+                        bulk_commit();
+                    }
+                } else {
+                    // frames j - q .. j of the group that this CTA produced
+                    const int q0 = static_cast<int>(max_i64(0, ja - (j - q)));
+                    const int nq = q + 1 - q0;
+                    float2* base = a.tones + a.frame_offset + (j - q);
+                    for (int it = tid; it < nq * nb_smem; it += NT) {
+                        const int t = it / nq, qq = q0 + (it - t * nq);
+                        base[static_cast<int64_t>(t) * a.tones_ld + qq] = tile[t * kToneGroup + qq];
                     }
                 }
-            } else {
-                float2* col = a.tones + a.frame_offset + j;
-                for (int t = tid; t < a.n_tones; t += NT) {
-                    const int bin = __ldg(a.bins + t);
-                    col[t * a.tones_ld] = P[bulk ? bin : fpad(bin)];
-                }
             }
-        } else if (!bulk) {
-            __syncthreads();   // pass-2 reads of Q done before the next frame writes it
+        } else if (a.n_tones > 0) {
+            float2* col = a.tones + a.frame_offset + j;
+            for (int t = tid; t < a.n_tones; t += NT) {
+                const int bin = __ldg(a.bins + t);
+                col[t * a.tones_ld] = P[bulk ? bin : fpad(bin)];
+            }
         }
     }
-    if (a.full_bulk && tid == 0) bulk_wait_all();
+    if (tid == 0) bulk_wait_all();
     (void)ok;
     umma::fence_before_sync();
     __syncthreads();
@@ -540,22 +573,39 @@ cudaError_t launch_direct(PfbArgs a, int n_sms, int max_smem, cudaStream_t st) {
 
 template <int T>
 cudaError_t launch_tmem(PfbArgs a, int n_sms, int max_smem, cudaStream_t st) {
-    a.nb_smem = (a.n_tones > 0 && tmem_smem_bytes(a.tw_count, a.n_tones) <= static_cast<size_t>(max_smem))
+    a.nb_smem = (a.n_tones > 0 && a.n_tones <= kTonesPerThread * kRingThreads &&
+                 tmem_layout(a.tw_count, a.n_tones).total <= static_cast<size_t>(max_smem))
                     ? a.n_tones : 0;
-    const size_t smem = tmem_smem_bytes(a.tw_count, a.nb_smem);
+    const size_t smem = tmem_layout(a.tw_count, a.nb_smem).total;
     if (smem > static_cast<size_t>(max_smem)) return cudaErrorInvalidConfiguration;
+    // whole tone groups per CTA (of output frames, see the kernel)
+    const int64_t shift = a.frame_offset & (kToneGroup - 1);
     const int64_t grid = std::min<int64_t>(a.F, n_sms);
-    // whole tone groups per CTA, so every CTA's groups start on an even frame
-    a.iters_per_cta = ((a.F + grid - 1) / grid + kToneGroup - 1) / kToneGroup * kToneGroup;
-    const int64_t grid2 = (a.F + a.iters_per_cta - 1) / a.iters_per_cta;
-    a.tones_vec = (a.tones != nullptr && (reinterpret_cast<uintptr_t>(a.tones) % 16) == 0 &&
-                   (a.tones_ld % 2) == 0 && (a.frame_offset % 2) == 0) ? 1 : 0;
+    a.iters_per_cta = ((a.F + shift + grid - 1) / grid + kToneGroup - 1) / kToneGroup * kToneGroup;
+    const int64_t grid2 = (a.F + shift + a.iters_per_cta - 1) / a.iters_per_cta;
     a.full_bulk = (a.full != nullptr && (reinterpret_cast<uintptr_t>(a.full) % 16) == 0 &&
                    (a.full_ld % 2) == 0) ? 1 : 0;
+    // tone rows as a 2-D tensor of 8-byte elements [n_tones][frame_offset + F]
+    // (row pitch tones_ld * 8 bytes, a multiple of 16); box kToneGroup x kToneBox
+    CUtensorMap tm;
+    std::memset(&tm, 0, sizeof tm);
+    a.tones_tma = 0;
+    auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tmap_encode_tiled_fn());
+    if (a.nb_smem > 0 && enc && (reinterpret_cast<uintptr_t>(a.tones) % 16) == 0 && (a.tones_ld % 2) == 0 &&
+        a.frame_offset + a.F < (int64_t(1) << 31)) {
+        cuuint64_t dims[2] = {static_cast<cuuint64_t>(a.frame_offset + a.F), static_cast<cuuint64_t>(a.n_tones)};
+        cuuint64_t strides[1] = {static_cast<cuuint64_t>(a.tones_ld) * 8};
+        cuuint32_t box[2] = {kToneGroup, kToneBox};
+        cuuint32_t estr[2] = {1, 1};
+        if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, a.tones, dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+            a.tones_tma = 1;
+    }
     auto k = pfb_tmem_kernel<T>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<static_cast<unsigned>(grid2), kRingThreads, smem, st>>>(a);
+    k<<<static_cast<unsigned>(grid2), kRingThreads, smem, st>>>(a, tm);
     return cudaGetLastError();
 }
 

@@ -50,6 +50,8 @@ struct PfbLaunch {
     int64_t a0;         // absolute sample index of the virtual stream's first sample
 };
 bool pfb_uses_ring(int log2n, int taps);
+// cuTensorMapEncodeTiled (PFN_cuTensorMapEncodeTiled_v12000) or nullptr
+void* tmap_encode_tiled_fn();
 
 // PFB for any N = 2^a 3^b 5^c 7^d <= 2^24 (pfb_general.cu): mixed-radix
 // in-CTA FFT, one pass for N <= 16384, the four-step split N = N1*N2 above.
