@@ -353,18 +353,33 @@ __global__ void __launch_bounds__(kRingThreads, 1)
         float are[16], aim[16];
 #pragma unroll
         for (int r = 0; r < 16; ++r) are[r] = aim[r] = 0.f;
+        // taps in order t = 0..T-1; each slot read as two 16-column halves,
+        // the next half's load in flight while this half's FMAs issue
+        uint32_t xa[16], xb[16];
+        umma::ld_32x32b_x16(tbase + 32u * static_cast<uint32_t>(j % kTmemSlots), xa);
+        umma::wait_ld_regs(xa);
 #pragma unroll
         for (int t = 0; t < T; ++t) {
-            uint32_t x[32];
-            umma::ld_32x32b_x32(tbase + 32u * static_cast<uint32_t>((j + t) % kTmemSlots), x);
-            umma::wait_ld();
+            const uint32_t col = tbase + 32u * static_cast<uint32_t>((j + t) % kTmemSlots);
+            umma::ld_32x32b_x16(col + 16u, xb);
 #pragma unroll
-            for (int r = 0; r < 16; r += 2) {
-                ffma2(are[r], are[r + 1], hr[t][r], hr[t][r + 1], __uint_as_float(x[2 * r]),
-                      __uint_as_float(x[2 * r + 1]));
-                ffma2(aim[r], aim[r + 1], hr[t][r], hr[t][r + 1], __uint_as_float(x[2 * r + 2]),
-                      __uint_as_float(x[2 * r + 3]));
+            for (int r = 0; r < 8; r += 2) {
+                ffma2(are[r], are[r + 1], hr[t][r], hr[t][r + 1], __uint_as_float(xa[2 * r]),
+                      __uint_as_float(xa[2 * r + 1]));
+                ffma2(aim[r], aim[r + 1], hr[t][r], hr[t][r + 1], __uint_as_float(xa[2 * r + 2]),
+                      __uint_as_float(xa[2 * r + 3]));
             }
+            umma::wait_ld_regs(xb);
+            if (t + 1 < T)
+                umma::ld_32x32b_x16(tbase + 32u * static_cast<uint32_t>((j + t + 1) % kTmemSlots), xa);
+#pragma unroll
+            for (int r = 8; r < 16; r += 2) {
+                ffma2(are[r], are[r + 1], hr[t][r], hr[t][r + 1], __uint_as_float(xb[2 * r - 16]),
+                      __uint_as_float(xb[2 * r - 15]));
+                ffma2(aim[r], aim[r + 1], hr[t][r], hr[t][r + 1], __uint_as_float(xb[2 * r - 14]),
+                      __uint_as_float(xb[2 * r - 13]));
+            }
+            if (t + 1 < T) umma::wait_ld_regs(xa);
         }
         float2 v[16];
 #pragma unroll
