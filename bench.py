@@ -25,6 +25,7 @@ import os
 import re
 import subprocess
 import sys
+import tempfile
 import threading
 import time
 
@@ -548,8 +549,7 @@ def run_batch(args, dev, stream):
     seq_plans = [make_spec_plan(rfr, sp, c["words"]) for sp, c in zip(specs, cases)]
     # tune each stream shape once; the sequential comparison loads the same
     # choices from the cache file
-    os.environ.setdefault("RFR_TUNE_CACHE", os.path.join(ROOT, "gpurun_out", "rfr_tune_cache.json")
-                          if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/rfr_tune_cache.json")
+    os.environ.setdefault("RFR_TUNE_CACHE", os.path.join(tempfile.gettempdir(), "rfr_tune_cache.json"))
     for p, q, x in zip(plans, seq_plans, xs):
         p.autotune(x.shape[0], use_cache=True)
         q.autotune(x.shape[0], use_cache=True)

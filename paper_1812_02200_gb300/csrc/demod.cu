@@ -47,7 +47,7 @@
 
 namespace rfr {
 
-// cuTensorMapEncodeTiled from the driver, looked up once (nullptr if absent)
+// the CUDA driver API's cuTensorMapEncodeTiled, looked up once (nullptr if absent)
 void* tmap_encode_tiled_fn() {
     static void* fn = nullptr;
     static std::once_flag once;
