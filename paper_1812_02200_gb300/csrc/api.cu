@@ -467,7 +467,8 @@ rfr_status rfr_plan_create(rfr_plan** out, int32_t channels, int32_t taps, const
         // the between-pass buffer of the two-pass form: 1 GB of frames (at
         // least one); large batches keep the launches few and their tails
         // short, which costs more here than Z's round trip through HBM
-        if (p->gen && (e = rfr::gen_plan_init(&p->gplan, channels, int64_t(1024) << 20)) != cudaSuccess)
+        if (p->gen && ((e = rfr::gen_plan_init(&p->gplan, channels, int64_t(1024) << 20)) != cudaSuccess ||
+                       (e = rfr::gen_plan_set_tones(&p->gplan, p->bins.data(), nt)) != cudaSuccess))
             return bad(cuda_fail(p, e, "plan alloc"));
         cudaMemcpy(p->d_h, hk.data(), hk.size() * 4, cudaMemcpyHostToDevice);
         cudaMemcpy(p->d_h32, p->h32.data(), p->h32.size() * 4, cudaMemcpyHostToDevice);

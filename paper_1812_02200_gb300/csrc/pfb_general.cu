@@ -21,8 +21,9 @@
 //   y[c1 + N1*c2] = sum_{p2} Z[c1][p2] W_{N2}^{p2*c2}                     (pass B)
 // with W_L = exp(-2*pi*i/L).  Pass A: one CTA per (frame, GA consecutive p2):
 // the FIR of its N1 x GA points (input read in runs of GA samples), GA
-// interleaved FFTs of length N1, the twiddle W_N^{p2*c1} (the product of two
-// FP64-built table entries), Z stored in runs of GA points.  Pass B: one CTA
+// interleaved FFTs of length N1, the twiddle W_N^{p2*c1} (the product of
+// three FP64-built entries, one per 8-bit digit of p2*c1, from tables in
+// shared memory), Z stored in runs of GA points.  Pass B: one CTA
 // per (frame, GB consecutive c1): GB rows of Z, GB interleaved FFTs of length
 // N2, the spectrum stored in runs of GB points, and the tone channels.  Z
 // holds a batch of frames (1 GB) between the passes.
@@ -61,7 +62,7 @@ struct GenCfg {
     static constexpr int kElems = TH * 16;
     static constexpr int kMinBlocks = TH == 256 ? 3 : 1;
 };
-constexpr int kTwSplit = 4096;                     // inter-pass twiddle: m = hi*4096 + lo
+constexpr int kTwDigit = 256;                      // inter-pass twiddle tables: 3 x 256 entries
 constexpr int kGMax = 64;                          // transforms interleaved per CTA
 
 __device__ __forceinline__ int gpad(int e) { return e + (e >> 4); }
@@ -337,13 +338,14 @@ struct GenArgs {
     GenFft fa, fb;          // pass A (length N1) and pass B / single (length N2 = N)
     const float2* tw_a;
     const float2* tw_b;
-    const float2* th;       // W_N^{4096*i}
-    const float2* tl;       // W_N^{i}, i < 4096
+    const float2* tw3;      // [3][256]: W_N^{i}, W_N^{256 i}, W_N^{65536 i}
     int N1, N2, gla, glb;
     uint32_t n2_magic;      // ceil(2^32 / N2): f / N2 = umulhi(f, n2_magic) for f < GB*N2
     float2* z;              // [F][N1][N2]
     const int32_t* bins;
     int n_tones;
+    const int2* gtone;      // pass B: tones per group (see GenPlan)
+    const int* goff;
     float2* full;
     int64_t full_ld;
     float2* tones;
@@ -463,6 +465,9 @@ __global__ void __launch_bounds__(TH, GenCfg<TH>::kMinBlocks) gen_pass_a_kernel(
     const int groups = (a.N2 + GA - 1) >> a.gla;
     const int E = a.N1 << a.gla;
     float2* sm1 = second_buffer(sm, E);
+    // the digit tables of W_N^m, m = a*65536 + b*256 + c (N <= 2^24)
+    float2* stw = sm + 2 * (gpad(E) + 1);
+    for (int i = threadIdx.x; i < 3 * kTwDigit; i += TH) stw[i] = __ldg(a.tw3 + i);
     for (int64_t it = blockIdx.x; it < a.F * groups; it += gridDim.x) {
         const int64_t kk = it / groups;
         const int g0 = static_cast<int>(it - kk * groups) << a.gla;
@@ -480,13 +485,11 @@ __global__ void __launch_bounds__(TH, GenCfg<TH>::kMinBlocks) gen_pass_a_kernel(
         __syncthreads();
         // the last stage multiplies by W_N^{p2*c1} and stores Z directly
         float2* zf = a.z + kk * a.N;
-        const float2* th = a.th;
-        const float2* tl = a.tl;
         gen_fft_to<TH>(sm, sm1, a.fa, a.gla, a.tw_a, [=](int e, float2 v) {
             const int g = e & (GA - 1), c1 = e >> gla, p2 = g0 + g;
             if (p2 < N2) {
                 const int m = p2 * c1;                       // < N1*N2 = N
-                const float2 w = cmul(__ldg(th + (m / kTwSplit)), __ldg(tl + (m % kTwSplit)));
+                const float2 w = cmul(cmul(stw[m & 255], stw[kTwDigit + ((m >> 8) & 255)]), stw[2 * kTwDigit + (m >> 16)]);
                 zf[static_cast<int64_t>(c1) * N2 + p2] = cmul(v, w);
             }
         });
@@ -529,11 +532,11 @@ __global__ void __launch_bounds__(TH, GenCfg<TH>::kMinBlocks) gen_pass_b_kernel(
         });
         if (keep) {
             __syncthreads();
-            for (int t = threadIdx.x; t < a.n_tones; t += TH) {
-                const int b = __ldg(a.bins + t);
-                const int c1 = b % a.N1;
-                if (c1 >= c0 && c1 < c0 + GB)
-                    a.tones[t * a.tones_ld + a.fo + k] = freebuf[gpad(((b / a.N1) << a.glb) + c1 - c0)];
+            const int gi = c0 >> a.glb;
+            const int i1 = __ldg(a.goff + gi + 1);
+            for (int i = __ldg(a.goff + gi) + threadIdx.x; i < i1; i += TH) {
+                const int2 te = __ldg(a.gtone + i);
+                a.tones[te.x * a.tones_ld + a.fo + k] = freebuf[gpad(te.y)];
             }
         }
         __syncthreads();
@@ -599,9 +602,31 @@ bool build_fft(int n, GenFft* f, std::vector<float2>& tw, int rmax) {
 
 bool gen_supported(int64_t n) { return n >= 2 && n <= (int64_t(1) << 24) && smooth7(n); }
 
+cudaError_t gen_plan_set_tones(GenPlan* g, const int32_t* bins, int n_tones) {
+    if (g->N1 <= 1 || n_tones <= 0) return cudaSuccess;
+    const int gb = 1 << g->glb;
+    const int groups = (g->N1 + gb - 1) / gb;
+    std::vector<int> off(groups + 1, 0);
+    for (int t = 0; t < n_tones; ++t) ++off[(bins[t] % g->N1) / gb + 1];
+    for (int i = 0; i < groups; ++i) off[i + 1] += off[i];
+    std::vector<int2> list(n_tones);
+    std::vector<int> fill(off.begin(), off.end() - 1);
+    for (int t = 0; t < n_tones; ++t) {
+        const int c1 = bins[t] % g->N1, c2 = bins[t] / g->N1, gi = c1 / gb;
+        list[fill[gi]++] = make_int2(t, (c2 << g->glb) + c1 - gi * gb);
+    }
+    cudaError_t e;
+    if ((e = cudaMalloc(&g->d_gtone, list.size() * sizeof(int2))) != cudaSuccess ||
+        (e = cudaMalloc(&g->d_goff, off.size() * sizeof(int))) != cudaSuccess ||
+        (e = cudaMemcpy(g->d_gtone, list.data(), list.size() * sizeof(int2), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(g->d_goff, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return e;
+    return cudaSuccess;
+}
+
 void gen_plan_free(GenPlan* g) {
-    for (void* q : {static_cast<void*>(g->d_tw), static_cast<void*>(g->d_th), static_cast<void*>(g->d_tl),
-                    static_cast<void*>(g->d_z)})
+    for (void* q : {static_cast<void*>(g->d_tw), static_cast<void*>(g->d_tw3),
+                    static_cast<void*>(g->d_z), static_cast<void*>(g->d_gtone), static_cast<void*>(g->d_goff)})
         if (q) cudaFree(q);
     *g = GenPlan{};
 }
@@ -674,18 +699,18 @@ cudaError_t gen_plan_init(GenPlan* g, int N, int64_t z_budget_bytes) {
         (e = cudaMemcpy(g->d_tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
         return e;
     if (g->N1 > 1) {
-        const int nh = (N + kTwSplit - 1) / kTwSplit;
-        std::vector<float2> th(nh), tl(kTwSplit);
+        std::vector<float2> t3(3 * kTwDigit);
         auto w = [&](int64_t m) {
             const double a = -2.0 * 3.14159265358979323846 * static_cast<double>(m % N) / static_cast<double>(N);
             return make_float2(static_cast<float>(std::cos(a)), static_cast<float>(std::sin(a)));
         };
-        for (int i = 0; i < nh; ++i) th[i] = w(static_cast<int64_t>(i) * kTwSplit);
-        for (int i = 0; i < kTwSplit; ++i) tl[i] = w(i);
-        if ((e = cudaMalloc(&g->d_th, nh * sizeof(float2))) != cudaSuccess ||
-            (e = cudaMalloc(&g->d_tl, kTwSplit * sizeof(float2))) != cudaSuccess ||
-            (e = cudaMemcpy(g->d_th, th.data(), nh * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess ||
-            (e = cudaMemcpy(g->d_tl, tl.data(), kTwSplit * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
+        for (int i = 0; i < kTwDigit; ++i) {
+            t3[i] = w(i);
+            t3[kTwDigit + i] = w(static_cast<int64_t>(i) << 8);
+            t3[2 * kTwDigit + i] = w(static_cast<int64_t>(i) << 16);
+        }
+        if ((e = cudaMalloc(&g->d_tw3, t3.size() * sizeof(float2))) != cudaSuccess ||
+            (e = cudaMemcpy(g->d_tw3, t3.data(), t3.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
             return e;
         // Z is allocated by gen_plan_reserve, sized by the pushes (up to the budget)
         g->z_cap_frames = std::max<int64_t>(1, z_budget_bytes / (static_cast<int64_t>(N) * 8));
@@ -697,8 +722,9 @@ namespace {
 size_t smem_bytes(int elems) { return static_cast<size_t>(2 * (elems + elems / 16 + 1)) * sizeof(float2); }
 
 template <int TH, typename K>
-cudaError_t launch_gen(K kernel, const GenArgs& a, int64_t items, int elems, int n_sms, cudaStream_t st) {
-    const size_t smem = smem_bytes(elems);
+cudaError_t launch_gen(K kernel, const GenArgs& a, int64_t items, int elems, int n_sms, cudaStream_t st,
+                       size_t extra_smem = 0) {
+    const size_t smem = smem_bytes(elems) + extra_smem;
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     int occ = 1;
@@ -724,7 +750,8 @@ cudaError_t gen_run(GenArgs a, const PfbLaunch& L, const GenPlan& g, cudaStream_
     for (int64_t k0 = 0; k0 < L.F; k0 += g.z_frames) {
         a.k0 = k0;
         a.F = std::min<int64_t>(g.z_frames, L.F - k0);
-        cudaError_t e = launch_gen<TH>(gen_pass_a_kernel<TH>, a, a.F * groups_a, g.N1 * ga, L.n_sms, st);
+        cudaError_t e = launch_gen<TH>(gen_pass_a_kernel<TH>, a, a.F * groups_a, g.N1 * ga, L.n_sms, st,
+                                       3 * kTwDigit * sizeof(float2));
         if (e != cudaSuccess) return e;
         e = launch_gen<TH>(gen_pass_b_kernel<TH>, a, a.F * groups_b, g.N2 * gb, L.n_sms, st);
         if (e != cudaSuccess) return e;
@@ -748,8 +775,7 @@ cudaError_t gen_pfb_launch(const PfbLaunch& L, const GenPlan& g, cudaStream_t st
     a.fb = g.fb;
     a.tw_a = g.d_tw;               // stage offsets of fa and fb index the one table
     a.tw_b = g.d_tw;
-    a.th = g.d_th;
-    a.tl = g.d_tl;
+    a.tw3 = g.d_tw3;
     a.N1 = g.N1;
     a.N2 = g.N2;
     a.n2_magic = static_cast<uint32_t>(((uint64_t(1) << 32) + g.N2 - 1) / g.N2);
@@ -758,6 +784,8 @@ cudaError_t gen_pfb_launch(const PfbLaunch& L, const GenPlan& g, cudaStream_t st
     a.z = g.d_z;
     a.bins = L.bins;
     a.n_tones = L.n_tones;
+    a.gtone = g.d_gtone;
+    a.goff = g.d_goff;
     a.full = static_cast<float2*>(L.full);
     a.full_ld = L.full_ld;
     a.tones = static_cast<float2*>(L.tones);

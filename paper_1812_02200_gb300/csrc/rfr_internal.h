@@ -70,17 +70,23 @@ struct GenPlan {
     int threads = 256;          // CTA shape: 256 threads x 4096 points or 512 x 8192
     GenFft fa{}, fb{};          // lengths N1 (pass A) and N2 (pass B / single pass)
     float2* d_tw = nullptr;     // stage twiddles of fa and fb (absolute tw_off)
-    float2* d_th = nullptr;     // W_N^(4096 i)
-    float2* d_tl = nullptr;     // W_N^i, i < 4096
+    float2* d_tw3 = nullptr;    // [3][256]: W_N^i, W_N^(256 i), W_N^(65536 i)
     float2* d_z = nullptr;      // between-pass buffer, z_frames x N
     int64_t z_frames = 0;
     int64_t z_cap_frames = 0;   // the most frames Z grows to
+    // pass B's tone lists: the tones of pass-B group i (bins with c1 in
+    // [i*GB, (i+1)*GB)) are d_gtone[d_goff[i] .. d_goff[i+1]), each {tone,
+    // its index (c2 << glb) + c1 - i*GB in the group's spectrum}
+    int2* d_gtone = nullptr;
+    int* d_goff = nullptr;
 };
 bool gen_supported(int64_t n);
 cudaError_t gen_plan_init(GenPlan* g, int N, int64_t z_budget_bytes);
 // Grow Z to min(frames, z_cap_frames) (allocates and synchronises the device;
 // never during stream capture).
 cudaError_t gen_plan_reserve(GenPlan* g, int64_t frames);
+// The tone lists of pass B from the tones' bins (two-pass plans; no-op otherwise).
+cudaError_t gen_plan_set_tones(GenPlan* g, const int32_t* bins, int n_tones);
 void gen_plan_free(GenPlan* g);
 int pfb_kernel_taps(int log2n, int taps);
 cudaError_t pfb_launch(const PfbLaunch& L, cudaStream_t st);
