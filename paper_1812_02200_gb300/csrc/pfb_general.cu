@@ -351,6 +351,8 @@ struct GenArgs {
     float2* tones;
     int64_t tones_ld;
     int64_t fo;             // frame offset in the caller's outputs
+    int zbulk;              // pass B reads its Z rows by one bulk copy (16-byte aligned rows)
+    int* status;            // device status word (bounded waits)
 };
 
 // FIR of the points e = tid, tid + TH, ... < E of one frame into sm: point e
@@ -504,6 +506,16 @@ __global__ void __launch_bounds__(TH, GenCfg<TH>::kMinBlocks) gen_pass_b_kernel(
     const int groups = (a.N1 + GB - 1) >> a.glb;
     const int E = a.N2 << a.glb;
     float2* sm1 = second_buffer(sm, E);
+    // the bulk copy lands 16-byte aligned in the second buffer (one spare
+    // element at its end); its mbarrier follows the two buffers
+    float2* zst = sm1 + ((reinterpret_cast<uintptr_t>(sm1) & 8) ? 1 : 0);
+    uint64_t* zbar = reinterpret_cast<uint64_t*>(sm + 2 * (gpad(E) + 1));
+    if (a.zbulk && threadIdx.x == 0) {
+        mbar_init(zbar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t zphase = 0;
     for (int64_t it = blockIdx.x; it < a.F * groups; it += gridDim.x) {
         const int64_t kk = it / groups;
         const int c0 = static_cast<int>(it - kk * groups) << a.glb;
@@ -511,11 +523,19 @@ __global__ void __launch_bounds__(TH, GenCfg<TH>::kMinBlocks) gen_pass_b_kernel(
         const float2* zf = a.z + kk * a.N + static_cast<int64_t>(c0) * a.N2;
         const int rows = min(GB, a.N1 - c0);
         const int cnt = rows * a.N2;
+        if (a.zbulk) {
+            if (threadIdx.x == 0) {
+                mbar_arrive_expect_tx(zbar, static_cast<uint32_t>(cnt) * 8u);
+                tma_bulk_g2s(zst, zf, static_cast<uint32_t>(cnt) * 8u, zbar);
+            }
+            if (!mbar_wait(zbar, zphase, a.status)) return;
+            zphase ^= 1u;
+        }
 #pragma unroll 4
         for (int f = threadIdx.x; f < E; f += TH) {
             const int g = static_cast<int>(__umulhi(static_cast<uint32_t>(f), a.n2_magic));   // f / N2
             const int p2 = f - g * a.N2;
-            sm[gpad((p2 << a.glb) + g)] = f < cnt ? zf[f] : make_float2(0.f, 0.f);
+            sm[gpad((p2 << a.glb) + g)] = f < cnt ? (a.zbulk ? zst[f] : zf[f]) : make_float2(0.f, 0.f);
         }
         __syncthreads();
         const int64_t k = a.k0 + kk;
@@ -539,6 +559,7 @@ __global__ void __launch_bounds__(TH, GenCfg<TH>::kMinBlocks) gen_pass_b_kernel(
                 a.tones[te.x * a.tones_ld + a.fo + k] = freebuf[gpad(te.y)];
             }
         }
+        fence_proxy_async_smem();   // shared-memory reads done before the next bulk copy writes
         __syncthreads();
     }
 }
@@ -753,7 +774,7 @@ cudaError_t gen_run(GenArgs a, const PfbLaunch& L, const GenPlan& g, cudaStream_
         cudaError_t e = launch_gen<TH>(gen_pass_a_kernel<TH>, a, a.F * groups_a, g.N1 * ga, L.n_sms, st,
                                        3 * kTwDigit * sizeof(float2));
         if (e != cudaSuccess) return e;
-        e = launch_gen<TH>(gen_pass_b_kernel<TH>, a, a.F * groups_b, g.N2 * gb, L.n_sms, st);
+        e = launch_gen<TH>(gen_pass_b_kernel<TH>, a, a.F * groups_b, g.N2 * gb, L.n_sms, st, 16);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -786,6 +807,10 @@ cudaError_t gen_pfb_launch(const PfbLaunch& L, const GenPlan& g, cudaStream_t st
     a.n_tones = L.n_tones;
     a.gtone = g.d_gtone;
     a.goff = g.d_goff;
+    // Z rows start on 16-byte boundaries when N and N2 are even (Z itself is
+    // 256-byte aligned), and every copy is then a multiple of 16 bytes
+    a.zbulk = (g.N % 2 == 0 && g.N2 % 2 == 0) ? 1 : 0;
+    a.status = L.status;
     a.full = static_cast<float2*>(L.full);
     a.full_ld = L.full_ld;
     a.tones = static_cast<float2*>(L.tones);
