@@ -38,11 +38,14 @@
 // Stages alternate between two shared-memory buffers of the G x n <= 4096
 // (256-thread CTAs) or 8192 (512-thread CTAs) points (G transforms interleaved, element (i, g) at i*G + g, padded one
 // element in 16).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 #include <vector>
 
 #include "dev_common.cuh"
@@ -353,6 +356,11 @@ struct GenArgs {
     int64_t fo;             // frame offset in the caller's outputs
     int zbulk;              // pass B reads its Z rows by one bulk copy (16-byte aligned rows)
     int* status;            // device status word (bounded waits)
+    // FIR ahead of pass A (see GenPlan::vtma): V [frames][N], and pass A's
+    // boxes of it (vboxes boxes of vbox_rows rows x GA points, vsstride
+    // points apart in shared memory)
+    float2* v;
+    int vtma, vbox_rows, vboxes, vsstride;
 };
 
 // FIR of the points e = tid, tid + TH, ... < E of one frame into sm: point e
@@ -460,8 +468,86 @@ __global__ void __launch_bounds__(TH, GenCfg<TH>::kMinBlocks) gen_single_kernel(
     }
 }
 
+// The FIR of the two-pass form ahead of pass A: v[k][q] for the launch's
+// frames k and every FFT input index q (window position (q - s) mod N), into
+// V in natural order.  One CTA per (frame, kFirThreads * kFirPts points);
+// consecutive threads take consecutive points, so every load and store is
+// coalesced, and the small register footprint leaves many warps in flight.
+// Taps are summed in the same order as fir_points (t = 0.. T-1 from zero).
+constexpr int kFirThreads = 256, kFirPts = 4;
+// TC > 0: T == TC known at compile time, so every load of a thread (2 TC
+// kFirPts) is issued before the first use; TC == 0: any T.
+template <int TC>
+__global__ void __launch_bounds__(kFirThreads) gen_fir_kernel(const GenArgs a) {
+    const int64_t kk = blockIdx.y;
+    const int64_t base = (a.k0 + kk) * a.hop;
+    const int sh = frame_shift(a, base);
+    const int N = a.N;
+    const int T = TC > 0 ? TC : a.T;
+    const int qb = static_cast<int>(blockIdx.x) * (kFirThreads * kFirPts) + static_cast<int>(threadIdx.x);
+    int pos[kFirPts];
+    float ar[kFirPts], ai[kFirPts];
+#pragma unroll
+    for (int j = 0; j < kFirPts; ++j) {
+        const int q = qb + j * kFirThreads;
+        pos[j] = q < N ? (q >= sh ? q - sh : q - sh + N) : 0;
+        ar[j] = ai[j] = 0.f;
+    }
+    if (base >= a.cl) {
+        const uint32_t* xp = a.buf + (base - a.cl);
+        if constexpr (TC > 0) {
+            float hv[TC][kFirPts];
+            uint32_t xw[TC][kFirPts];
+#pragma unroll
+            for (int t = 0; t < TC; ++t)
+#pragma unroll
+                for (int j = 0; j < kFirPts; ++j) {
+                    hv[t][j] = __ldg(a.h + (t * N + pos[j]));
+                    xw[t][j] = __ldg(xp + (t * N + pos[j]));
+                }
+#pragma unroll
+            for (int t = 0; t < TC; ++t)
+#pragma unroll
+                for (int j = 0; j < kFirPts; ++j) {
+                    const float2 x = iq_to_f2(xw[t][j]);
+                    ar[j] = fmaf(hv[t][j], x.x, ar[j]);
+                    ai[j] = fmaf(hv[t][j], x.y, ai[j]);
+                }
+        } else {
+            for (int t = 0; t < T; ++t) {
+#pragma unroll
+                for (int j = 0; j < kFirPts; ++j) {
+                    const float hv = __ldg(a.h + (t * N + pos[j]));
+                    const float2 x = iq_to_f2(__ldg(xp + (t * N + pos[j])));
+                    ar[j] = fmaf(hv, x.x, ar[j]);
+                    ai[j] = fmaf(hv, x.y, ai[j]);
+                }
+            }
+        }
+    } else {
+        for (int t = 0; t < T; ++t) {
+#pragma unroll
+            for (int j = 0; j < kFirPts; ++j) {
+                const int64_t o = static_cast<int64_t>(t) * N + pos[j];
+                const int64_t vi = base + o;
+                const float hv = __ldg(a.h + o);
+                const float2 x = iq_to_f2(vi < a.cl ? __ldg(a.carry + vi) : __ldg(a.buf + (vi - a.cl)));
+                ar[j] = fmaf(hv, x.x, ar[j]);
+                ai[j] = fmaf(hv, x.y, ai[j]);
+            }
+        }
+    }
+    float2* vrow = a.v + kk * N;
+#pragma unroll
+    for (int j = 0; j < kFirPts; ++j) {
+        const int q = qb + j * kFirThreads;
+        if (q < N) vrow[q] = make_float2(ar[j], ai[j]);
+    }
+}
+
 template <int TH>
-__global__ void __launch_bounds__(TH, GenCfg<TH>::kMinBlocks) gen_pass_a_kernel(const GenArgs a) {
+__global__ void __launch_bounds__(TH, GenCfg<TH>::kMinBlocks)
+    gen_pass_a_kernel(const GenArgs a, const __grid_constant__ CUtensorMap tmv) {
     extern __shared__ float2 sm[];
     const int GA = 1 << a.gla;
     const int groups = (a.N2 + GA - 1) >> a.gla;
@@ -470,20 +556,48 @@ __global__ void __launch_bounds__(TH, GenCfg<TH>::kMinBlocks) gen_pass_a_kernel(
     // the digit tables of W_N^m, m = a*65536 + b*256 + c (N <= 2^24)
     float2* stw = sm + 2 * (gpad(E) + 1);
     for (int i = threadIdx.x; i < 3 * kTwDigit; i += TH) stw[i] = __ldg(a.tw3 + i);
+    // V's boxes land 128-byte aligned in the second buffer; mbarrier after the tables
+    float2* vst = reinterpret_cast<float2*>((reinterpret_cast<uintptr_t>(sm1) + 127) & ~uintptr_t(127));
+    uint64_t* vbar = reinterpret_cast<uint64_t*>(stw + 3 * kTwDigit);
+    if (a.vtma && threadIdx.x == 0) {
+        mbar_init(vbar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t vphase = 0;
     for (int64_t it = blockIdx.x; it < a.F * groups; it += gridDim.x) {
         const int64_t kk = it / groups;
         const int g0 = static_cast<int>(it - kk * groups) << a.gla;
-        const int64_t base = (a.k0 + kk) * a.hop;
-        const int sh = frame_shift(a, base);
-        const int N2 = a.N2, gla = a.gla, N = a.N;
-        fir_points<TH>(a, base, E,
-                   [=](int e) {
-                       const int g = e & (GA - 1);
-                       if (g0 + g >= N2) return -1;
-                       const int q = (e >> gla) * N2 + g0 + g;          // FFT input index
-                       return q >= sh ? q - sh : q - sh + N;            // window position
-                   },
-                   sm);
+        const int N2 = a.N2, gla = a.gla;
+        if (a.vtma) {
+            // points p1*GA + g = V[kk][p1*N2 + g0 + g]: boxes of rows of V
+            // viewed as [frames*N1][N2] (columns past N2 read as zero)
+            if (threadIdx.x == 0) {
+                mbar_arrive_expect_tx(vbar, static_cast<uint32_t>(a.vboxes * a.vbox_rows * GA * 8));
+                for (int b = 0; b < a.vboxes; ++b)
+                    tma_load_2d(vst + b * a.vsstride, &tmv, g0,
+                                static_cast<int32_t>(kk * a.N1 + b * a.vbox_rows), vbar);
+            }
+            if (!mbar_wait(vbar, vphase, a.status)) return;
+            vphase ^= 1u;
+            for (int b = 0; b < a.vboxes; ++b) {
+                const int rows = min(a.vbox_rows, a.N1 - b * a.vbox_rows);
+                const int o = b * a.vbox_rows * GA;
+                for (int e = threadIdx.x; e < rows * GA; e += TH) sm[gpad(o + e)] = vst[b * a.vsstride + e];
+            }
+        } else {
+            const int64_t base = (a.k0 + kk) * a.hop;
+            const int sh = frame_shift(a, base);
+            const int N = a.N;
+            fir_points<TH>(a, base, E,
+                       [=](int e) {
+                           const int g = e & (GA - 1);
+                           if (g0 + g >= N2) return -1;
+                           const int q = (e >> gla) * N2 + g0 + g;          // FFT input index
+                           return q >= sh ? q - sh : q - sh + N;            // window position
+                       },
+                       sm);
+        }
         __syncthreads();
         // the last stage multiplies by W_N^{p2*c1} and stores Z directly
         float2* zf = a.z + kk * a.N;
@@ -495,6 +609,7 @@ __global__ void __launch_bounds__(TH, GenCfg<TH>::kMinBlocks) gen_pass_a_kernel(
                 zf[static_cast<int64_t>(c1) * N2 + p2] = cmul(v, w);
             }
         });
+        fence_proxy_async_smem();   // shared-memory reads done before the next box lands
         __syncthreads();
     }
 }
@@ -647,7 +762,8 @@ cudaError_t gen_plan_set_tones(GenPlan* g, const int32_t* bins, int n_tones) {
 
 void gen_plan_free(GenPlan* g) {
     for (void* q : {static_cast<void*>(g->d_tw), static_cast<void*>(g->d_tw3),
-                    static_cast<void*>(g->d_z), static_cast<void*>(g->d_gtone), static_cast<void*>(g->d_goff)})
+                    static_cast<void*>(g->d_z), static_cast<void*>(g->d_gtone), static_cast<void*>(g->d_goff),
+                    static_cast<void*>(g->d_v)})
         if (q) cudaFree(q);
     *g = GenPlan{};
 }
@@ -659,9 +775,11 @@ cudaError_t gen_plan_reserve(GenPlan* g, int64_t frames) {
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return e;
     if (g->d_z) cudaFree(g->d_z);
-    g->d_z = nullptr;
+    if (g->d_v) cudaFree(g->d_v);
+    g->d_z = g->d_v = nullptr;
     g->z_frames = 0;
     if ((e = cudaMalloc(&g->d_z, static_cast<size_t>(want) * g->N * 8)) != cudaSuccess) return e;
+    if (g->vtma && (e = cudaMalloc(&g->d_v, static_cast<size_t>(want) * g->N * 8)) != cudaSuccess) return e;
     g->z_frames = want;
     return cudaSuccess;
 }
@@ -733,8 +851,24 @@ cudaError_t gen_plan_init(GenPlan* g, int N, int64_t z_budget_bytes) {
         if ((e = cudaMalloc(&g->d_tw3, t3.size() * sizeof(float2))) != cudaSuccess ||
             (e = cudaMemcpy(g->d_tw3, t3.data(), t3.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
             return e;
-        // Z is allocated by gen_plan_reserve, sized by the pushes (up to the budget)
+        // Z (and V) are allocated by gen_plan_reserve, sized by the pushes (up to the budget)
         g->z_cap_frames = std::max<int64_t>(1, z_budget_bytes / (static_cast<int64_t>(N) * 8));
+        // V by 2-D TMA: rows of N2 points (8 bytes each) need a 16-byte
+        // multiple as pitch, and each box's first column g0 (a multiple of
+        // GA) a 16-byte offset, so GA >= 2; pass A's N1 x GA points come in
+        // boxes of at most 256 rows, each box 128-byte aligned in the second
+        // buffer
+        const int ga = 1 << g->gla;
+        const int elems = g->N1 * ga;
+        const int nb = (g->N1 + 255) / 256, rows = (g->N1 + nb - 1) / nb;
+        const int sstride = (rows * ga + 15) / 16 * 16;
+        if (g->N2 % 2 == 0 && ga >= 2 && tmap_encode_tiled_fn() != nullptr &&
+            (nb - 1) * sstride + rows * ga + 16 <= elems + elems / 16 + 1) {
+            g->vtma = 1;
+            g->vboxes = nb;
+            g->vbox_rows = rows;
+            g->vsstride = sstride;
+        }
     }
     return cudaSuccess;
 }
@@ -742,9 +876,9 @@ cudaError_t gen_plan_init(GenPlan* g, int N, int64_t z_budget_bytes) {
 namespace {
 size_t smem_bytes(int elems) { return static_cast<size_t>(2 * (elems + elems / 16 + 1)) * sizeof(float2); }
 
-template <int TH, typename K>
-cudaError_t launch_gen(K kernel, const GenArgs& a, int64_t items, int elems, int n_sms, cudaStream_t st,
-                       size_t extra_smem = 0) {
+template <int TH, typename K, typename... Args>
+cudaError_t launch_gen(K kernel, int64_t items, int elems, int n_sms, cudaStream_t st, size_t extra_smem,
+                       const Args&... args) {
     const size_t smem = smem_bytes(elems) + extra_smem;
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
@@ -752,7 +886,7 @@ cudaError_t launch_gen(K kernel, const GenArgs& a, int64_t items, int elems, int
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, TH, smem) != cudaSuccess || occ < 1)
         occ = 1;
     const int64_t grid = std::min<int64_t>(items, static_cast<int64_t>(n_sms) * occ);
-    kernel<<<static_cast<unsigned>(grid), TH, smem, st>>>(a);
+    kernel<<<static_cast<unsigned>(grid), TH, smem, st>>>(args...);
     return cudaGetLastError();
 }
 }  // namespace
@@ -763,18 +897,47 @@ cudaError_t gen_run(GenArgs a, const PfbLaunch& L, const GenPlan& g, cudaStream_
     if (g.N1 == 1) {
         a.F = L.F;
         a.k0 = 0;
-        return launch_gen<TH>(gen_single_kernel<TH>, a, L.F, g.N, L.n_sms, st);
+        return launch_gen<TH>(gen_single_kernel<TH>, L.F, g.N, L.n_sms, st, 0, a);
     }
     if (g.z_frames < 1 || !g.d_z) return cudaErrorInvalidValue;   // gen_plan_reserve first
     const int ga = 1 << g.gla, gb = 1 << g.glb;
     const int64_t groups_a = (g.N2 + ga - 1) / ga, groups_b = (g.N1 + gb - 1) / gb;
+    // V as [z_frames * N1 rows][N2 points] of 8-byte elements, box GA x vbox_rows
+    CUtensorMap tmv;
+    std::memset(&tmv, 0, sizeof tmv);
+    if (a.vtma) {
+        if (!g.d_v) return cudaErrorInvalidValue;
+        auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tmap_encode_tiled_fn());
+        cuuint64_t dims[2] = {static_cast<cuuint64_t>(g.N2), static_cast<cuuint64_t>(g.z_frames) * g.N1};
+        cuuint64_t strides[1] = {static_cast<cuuint64_t>(g.N2) * 8};
+        cuuint32_t box[2] = {static_cast<cuuint32_t>(ga), static_cast<cuuint32_t>(g.vbox_rows)};
+        cuuint32_t estr[2] = {1, 1};
+        if (!enc || enc(&tmv, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, g.d_v, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
     for (int64_t k0 = 0; k0 < L.F; k0 += g.z_frames) {
         a.k0 = k0;
         a.F = std::min<int64_t>(g.z_frames, L.F - k0);
-        cudaError_t e = launch_gen<TH>(gen_pass_a_kernel<TH>, a, a.F * groups_a, g.N1 * ga, L.n_sms, st,
-                                       3 * kTwDigit * sizeof(float2));
+        cudaError_t e;
+        if (a.vtma) {
+            const dim3 fg(static_cast<unsigned>((g.N + kFirThreads * kFirPts - 1) / (kFirThreads * kFirPts)),
+                          static_cast<unsigned>(a.F));
+            switch (a.T) {
+            case 1: gen_fir_kernel<1><<<fg, kFirThreads, 0, st>>>(a); break;
+            case 2: gen_fir_kernel<2><<<fg, kFirThreads, 0, st>>>(a); break;
+            case 3: gen_fir_kernel<3><<<fg, kFirThreads, 0, st>>>(a); break;
+            case 4: gen_fir_kernel<4><<<fg, kFirThreads, 0, st>>>(a); break;
+            case 8: gen_fir_kernel<8><<<fg, kFirThreads, 0, st>>>(a); break;
+            default: gen_fir_kernel<0><<<fg, kFirThreads, 0, st>>>(a); break;
+            }
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+        e = launch_gen<TH>(gen_pass_a_kernel<TH>, a.F * groups_a, g.N1 * ga, L.n_sms, st,
+                           3 * kTwDigit * sizeof(float2) + 16, a, tmv);
         if (e != cudaSuccess) return e;
-        e = launch_gen<TH>(gen_pass_b_kernel<TH>, a, a.F * groups_b, g.N2 * gb, L.n_sms, st, 16);
+        e = launch_gen<TH>(gen_pass_b_kernel<TH>, a.F * groups_b, g.N2 * gb, L.n_sms, st, 16, a);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -811,6 +974,11 @@ cudaError_t gen_pfb_launch(const PfbLaunch& L, const GenPlan& g, cudaStream_t st
     // 256-byte aligned), and every copy is then a multiple of 16 bytes
     a.zbulk = (g.N % 2 == 0 && g.N2 % 2 == 0) ? 1 : 0;
     a.status = L.status;
+    a.v = g.d_v;
+    a.vtma = g.vtma;
+    a.vbox_rows = g.vbox_rows;
+    a.vboxes = g.vboxes;
+    a.vsstride = g.vsstride;
     a.full = static_cast<float2*>(L.full);
     a.full_ld = L.full_ld;
     a.tones = static_cast<float2*>(L.tones);

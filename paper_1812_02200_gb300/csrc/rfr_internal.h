@@ -79,6 +79,11 @@ struct GenPlan {
     // its index (c2 << glb) + c1 - i*GB in the group's spectrum}
     int2* d_gtone = nullptr;
     int* d_goff = nullptr;
+    // vtma: the FIR runs as its own kernel into V (z_frames x N, natural
+    // order) and pass A fetches its points by 2-D TMA boxes of V (N2 even,
+    // boxes fit the CTA's second buffer); else pass A computes the FIR
+    int vtma = 0, vbox_rows = 0, vboxes = 0, vsstride = 0;
+    float2* d_v = nullptr;
 };
 bool gen_supported(int64_t n);
 cudaError_t gen_plan_init(GenPlan* g, int N, int64_t z_budget_bytes);
