@@ -790,20 +790,23 @@ cudaError_t gen_plan_init(GenPlan* g, int N, int64_t z_budget_bytes) {
     g->N = N;
     std::vector<float2> tw;
     // the best N = N1*N2 split for CTAs of `elems` points: largest
-    // min(GA, GB) (the longest contiguous runs), then the more balanced
+    // min(GA, GB) (the longest contiguous runs), then the more balanced, then
+    // an even N2 (16-byte aligned rows: V and Z move by TMA)
     auto best_split = [&](int elems, int* n1o, int* n2o, int* score_o) {
-        int best = -1, best_score = -1, best_bal = 0;
+        int best = -1, best_score = -1, best_bal = 0, best_even = 0;
         for (int n2 = 2; n2 <= elems; ++n2) {
             if (N % n2 != 0) continue;
             const int n1 = N / n2;
             if (n1 < 2 || n1 > elems) continue;
             const int ga = std::min(kGMax, 1 << floor_log2(elems / n1));
             const int gb = std::min(kGMax, 1 << floor_log2(elems / n2));
-            const int score = std::min(ga, gb), bal = -std::abs(n1 - n2);
-            if (score > best_score || (score == best_score && bal > best_bal)) {
+            const int score = std::min(ga, gb), bal = -std::abs(n1 - n2), even = n2 % 2 == 0;
+            if (score > best_score || (score == best_score && bal > best_bal) ||
+                (score == best_score && bal == best_bal && even > best_even)) {
                 best = n2;
                 best_score = score;
                 best_bal = bal;
+                best_even = even;
             }
         }
         *n2o = best;
