@@ -47,6 +47,9 @@ CASES = [
     (19683, 2, "hann", 0.0, 10),          # 3^9, two passes of radix-3 stages
     (32768, 8, "kaiser", 9.0, 10),        # power of two above the fused kernels
     (100000, 4, "hamming", 0.0, 8),       # Fig. 3's N and A_v
+    (20000, 5, "hann", 0.0, 12),          # two passes, FIR ahead with any T
+    (30000, 3, "blackman", 0.0, 10),      # two passes, T = 3
+    (40000, 1, "rect", 0.0, 10),          # two passes, T = 1
 ]
 
 
