@@ -19,14 +19,18 @@
 // p = N2*p1 + p2 and output index c = c1 + N1*c2,
 //   Z[c1][p2]     = W_N^{p2*c1} * sum_{p1} v[N2*p1 + p2] W_{N1}^{p1*c1}   (pass A)
 //   y[c1 + N1*c2] = sum_{p2} Z[c1][p2] W_{N2}^{p2*c2}                     (pass B)
-// with W_L = exp(-2*pi*i/L).  Pass A: one CTA per (frame, GA consecutive p2):
-// the FIR of its N1 x GA points (input read in runs of GA samples), GA
-// interleaved FFTs of length N1, the twiddle W_N^{p2*c1} (the product of
-// three FP64-built entries, one per 8-bit digit of p2*c1, from tables in
-// shared memory), Z stored in runs of GA points.  Pass B: one CTA
-// per (frame, GB consecutive c1): GB rows of Z, GB interleaved FFTs of length
-// N2, the spectrum stored in runs of GB points, and the tone channels.  Z
-// holds a batch of frames (1 GB) between the passes.
+// with W_L = exp(-2*pi*i/L).  When N2 is even and a pass-A CTA holds at
+// least two transforms (the common case), the FIR runs first as its own
+// coalesced kernel into V [frames][N] and pass A takes its N1 x GA points as
+// 2-D TMA boxes of V; otherwise pass A computes the FIR of its points itself
+// (input read in runs of GA samples).  Pass A: one CTA per (frame, GA
+// consecutive p2): GA interleaved FFTs of length N1, the twiddle W_N^{p2*c1}
+// (the product of three FP64-built entries, one per 8-bit digit of p2*c1,
+// from tables in shared memory), Z stored in runs of GA points.  Pass B: one
+// CTA per (frame, GB consecutive c1): GB rows of Z (one bulk copy when N2 is
+// even), GB interleaved FFTs of length N2, the spectrum stored in runs of GB
+// points, and the group's tones from a list built on the host.  V and Z hold
+// a batch of frames (1 GB each) between the launches.
 //
 // Each sub-transform runs the fewest Stockham passes of radices up to 25:
 // 16, 8, 4, 2 from fft_dev.cuh, 3, 5, 7 from their definitions, and the

@@ -11,7 +11,10 @@
 //     y_j[c] = sum_p v_j[p] exp(-2*pi*i*c*p/N)
 // which is frame (F0 + j) of the stream, F0 the frames before this push.
 //
-// Two variants:
+// Three variants:
+//  TMEM   (N = 4096, T <= 8, 16-byte aligned pushes): the FP32 delay line in
+//         tensor memory, int16 blocks by 1-D TMA, spectrum rows by TMA bulk
+//         stores and tone groups by 2-D TMA tensor stores (see below).
 //  RING   (N <= 4096, T <= 8 after padding): each CTA owns a contiguous run
 //         of "super-blocks" (4096 samples = G = 4096/N frames' worth of new
 //         samples).  A ring of super-blocks in shared memory is filled by
@@ -21,7 +24,8 @@
 //  DIRECT (any other N <= 16384, T <= 16): no ring; the T samples of every
 //         branch are read from global memory (L2 serves the T-fold reuse)
 //         and the taps with __ldg.
-// Both run the same in-CTA FFT (fft_dev.cuh) and write
+// RING and DIRECT run the in-CTA FFT of fft_dev.cuh (TMEM the same passes
+// written out for N = 4096); all write
 //   full[(frame_offset + j) * full_ld + c]      (natural bin order)
 //   tones[s * tones_ld + frame_offset + j] = y_j[bin[s]].
 #include <cuda.h>
