@@ -341,6 +341,7 @@ struct GenArgs {
     int N, T;
     int hop;                // samples between frames
     int64_t a0;             // absolute sample index of the virtual stream's first sample
+    int sh_fixed;           // the frames' shift when hop == N (the same for all), else -1
     const float* h;         // [T*N]
     GenFft fa, fb;          // pass A (length N1) and pass B / single (length N2 = N)
     const float2* tw_a;
@@ -436,6 +437,7 @@ __device__ __forceinline__ void fir_points(const GenArgs& a, int64_t base, int E
 // window's first sample) mod N, so that channel c is the stream mixed down by
 // exp(-2*pi*i*c*m/N) for every hop (s = 0 whenever the hop is N).
 __device__ __forceinline__ int frame_shift(const GenArgs& a, int64_t base) {
+    if (a.sh_fixed >= 0) return a.sh_fixed;
     const int64_t s = (a.a0 + base) % a.N;
     return static_cast<int>(s < 0 ? s + a.N : s);
 }
@@ -961,6 +963,8 @@ cudaError_t gen_pfb_launch(const PfbLaunch& L, const GenPlan& g, cudaStream_t st
     a.T = L.taps_kernel;
     a.hop = L.hop > 0 ? L.hop : g.N;
     a.a0 = L.a0;
+    // frame starts a0 + k*N: one shift for every frame
+    a.sh_fixed = a.hop == g.N ? static_cast<int>(((L.a0 % g.N) + g.N) % g.N) : -1;
     a.h = L.h;
     a.fa = g.fa;
     a.fb = g.fb;
