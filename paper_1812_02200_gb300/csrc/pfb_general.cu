@@ -480,7 +480,7 @@ __global__ void __launch_bounds__(TH, GenCfg<TH>::kMinBlocks) gen_single_kernel(
 // consecutive threads take consecutive points, so every load and store is
 // coalesced, and the small register footprint leaves many warps in flight.
 // Taps are summed in the same order as fir_points (t = 0.. T-1 from zero).
-constexpr int kFirThreads = 256, kFirPts = 4;
+constexpr int kFirThreads = 256, kFirPts = 8;
 // TC > 0: T == TC known at compile time, so every load of a thread (2 TC
 // kFirPts) is issued before the first use; TC == 0: any T.
 template <int TC>
