@@ -477,18 +477,21 @@ def run_tx(args, dev, stream, words):
 
 # ----------------------------------------------------------- any-N PFB
 def run_large_n(args, dev, stream, x, words):
-    """PFB at channel counts that are not powers of two (Sec. III.A): Fig. 3's
-    N = 10^5 and the section's largest, 10^7, with A_v = T = 4 and a Hamming
-    window, on the workload's 2^28-sample stream, full spectrum + its 1000
-    tones (mixed-radix kernels: four-step two-pass form at these N)."""
+    """PFB beyond the fused kernels (Sec. III.A): Fig. 3's N = 10^5 and the
+    section's largest, 10^7, with A_v = T = 4 and a Hamming window (four-step
+    two-pass form), and the workload's N = 4096, T = 8 Kaiser(9) oversampled
+    4x (hop 1024, the mixed-radix one-pass form); each on the workload's
+    2^28-sample stream, full spectrum + its 1000 tones."""
     import torch
 
     from paper_1812_02200_gb300 import rfr
     hbm_peak = measured_peaks()[0]
     out = []
     n = x.shape[0]
-    for N, reps in ((100000, 5), (10 ** 7, 3)):
-        plan = rfr.Plan(N, 4, window="hamming", words=words, full=True, tones=True)
+    for N, T, win, hop, reps in ((100000, 4, "hamming", 100000, 5), (10 ** 7, 4, "hamming", 10 ** 7, 3),
+                                 (4096, 8, "kaiser", 1024, 3)):
+        plan = rfr.Plan(N, T, window=win, beta=BETA if win == "kaiser" else 0.0, words=words, full=True,
+                        tones=True, decimation=hop)
         F = plan.frames_for(n)
         # pushes after the first may complete one more frame (residue)
         full = torch.empty((F + 1, N), dtype=torch.complex64, device=dev)
@@ -502,14 +505,15 @@ def run_large_n(args, dev, stream, x, words):
         e1.record(stream)
         torch.cuda.synchronize(dev)
         ms = e0.elapsed_time(e1) / reps
-        bps = 4.0 + 8.0 + 8.0 * len(words) / N
+        bps = 4.0 + (8.0 * N + 8.0 * len(words)) / hop
         gbs = bps * n / (ms * 1e-3) / 1e9
-        res = {"workload": f"PFB N={N} T=4 Hamming, 2^{int(np.log2(n))} complex int16 samples, "
-                           f"full spectrum + {len(words)} tones",
+        wname = "Kaiser(9)" if win == "kaiser" else win.capitalize()
+        res = {"workload": f"PFB N={N} T={T} {wname}" + (f" hop {hop}" if hop != N else "") +
+                           f", 2^{int(np.log2(n))} complex int16 samples, full spectrum + {len(words)} tones",
                "value": n / (ms * 1e-3) / 1e6, "unit": UNIT, "ms": ms, "frames": F,
                "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                             "frac": gbs / hbm_peak, "bytes_per_sample": bps}}
-        if not args.no_plain and N <= 100000:
+        if not args.no_plain and N <= 100000 and hop == N:
             # the plain FP32 form on the same stream: FP32 FIR kernel + cuFFT + gather
             plan.plain_oneshot(x, full, tones, stream=stream)
             torch.cuda.synchronize(dev)

@@ -340,6 +340,7 @@ struct GenArgs {
     int64_t k0;             // index of the launch's first frame within the push
     int N, T;
     int hop;                // samples between frames
+    int gls;                // one-pass form: log2 of the frames per CTA iteration
     int64_t a0;             // absolute sample index of the virtual stream's first sample
     int sh_fixed;           // the frames' shift when hop == N (the same for all), else -1
     const float* h;         // [T*N]
@@ -445,30 +446,114 @@ __device__ __forceinline__ int frame_shift(const GenArgs& a, int64_t base) {
 // Shared memory: two buffers of gpad(elems) points each.
 __device__ __forceinline__ float2* second_buffer(float2* sm, int elems) { return sm + gpad(elems) + 1; }
 
+// FIR of G = 2^gls consecutive frames (the first at stream position base0,
+// frame g at base0 + g*hop with shift shs[g]) into sm, interleaved: point e =
+// i*G + g is FFT input i of frame g; frames g >= nf are zero.  Eight points
+// at a time per thread, taps summed as in fir_points.
+template <int TH>
+__device__ __forceinline__ void fir_frames(const GenArgs& a, int64_t base0, int E, int gls, int nf,
+                                           const int* shs, float2* sm) {
+    constexpr int P = 8;
+    const int G = 1 << gls, N = a.N;
+    const bool fast = base0 >= a.cl;
+    for (int e0 = threadIdx.x; e0 < E; e0 += P * TH) {
+        int hoff[P], xoff[P];
+        bool valid[P];
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            const int e = e0 + q * TH;
+            const int g = e & (G - 1), i = e >> gls;
+            valid[q] = e < E && g < nf;
+            const int sh = valid[q] ? shs[g] : 0;
+            const int pos = i >= sh ? i - sh : i - sh + N;
+            hoff[q] = valid[q] ? pos : 0;                     // in-bounds dummy, zeroed below
+            xoff[q] = valid[q] ? g * a.hop + pos : 0;
+        }
+        float ar[P], ai[P];
+#pragma unroll
+        for (int q = 0; q < P; ++q) ar[q] = ai[q] = 0.f;
+        if (fast) {
+            const float* hp = a.h;
+            const uint32_t* xp = a.buf + (base0 - a.cl);
+#pragma unroll 4
+            for (int t = 0; t < a.T; ++t) {
+                float hv[P];
+                uint32_t xw[P];
+#pragma unroll
+                for (int q = 0; q < P; ++q) {
+                    hv[q] = __ldg(hp + hoff[q]);
+                    xw[q] = __ldg(xp + xoff[q]);
+                }
+#pragma unroll
+                for (int q = 0; q < P; ++q) {
+                    const float2 x = iq_to_f2(xw[q]);
+                    ar[q] = fmaf(hv[q], x.x, ar[q]);
+                    ai[q] = fmaf(hv[q], x.y, ai[q]);
+                }
+                hp += N;
+                xp += N;
+            }
+        } else {
+            for (int t = 0; t < a.T; ++t) {
+#pragma unroll
+                for (int q = 0; q < P; ++q) {
+                    const float hv = __ldg(a.h + static_cast<int64_t>(t) * N + hoff[q]);
+                    const int64_t vi = base0 + static_cast<int64_t>(t) * N + xoff[q];
+                    const float2 x = iq_to_f2(vi < a.cl ? __ldg(a.carry + vi) : __ldg(a.buf + (vi - a.cl)));
+                    ar[q] = fmaf(hv, x.x, ar[q]);
+                    ai[q] = fmaf(hv, x.y, ai[q]);
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            const int e = e0 + q * TH;
+            if (e < E) sm[gpad(e)] = valid[q] ? make_float2(ar[q], ai[q]) : make_float2(0.f, 0.f);
+        }
+    }
+}
+
+// One pass (N <= 8192): G = 2^gls consecutive frames per CTA iteration,
+// interleaved (point i of frame g at i*G + g), so that a small N still gives
+// every thread of the CTA butterflies in each stage.
 template <int TH>
 __global__ void __launch_bounds__(TH, GenCfg<TH>::kMinBlocks) gen_single_kernel(const GenArgs a) {
     extern __shared__ float2 sm[];
-    float2* sm1 = second_buffer(sm, a.N);
-    for (int64_t kk = blockIdx.x; kk < a.F; kk += gridDim.x) {
-        const int64_t k = a.k0 + kk;
-        const int64_t base = k * a.hop;
-        const int sh = frame_shift(a, base);
-        const int N = a.N;
-        fir_points<TH>(a, base, a.N, [=](int e) { return e >= sh ? e - sh : e - sh + N; }, sm);
+    const int gls = a.gls, G = 1 << gls, N = a.N;
+    const int E = N << gls;
+    float2* sm1 = second_buffer(sm, E);
+    int* shs = reinterpret_cast<int*>(sm + 2 * (gpad(E) + 1));    // the G frames' shifts
+    const int64_t iters = (a.F + G - 1) >> gls;
+    for (int64_t it = blockIdx.x; it < iters; it += gridDim.x) {
+        const int64_t kk0 = it << gls;
+        const int nf = a.F - kk0 < G ? static_cast<int>(a.F - kk0) : G;
+        const int64_t k0 = a.k0 + kk0;                       // the first frame's index in the push
+        if (static_cast<int>(threadIdx.x) < G) shs[threadIdx.x] = frame_shift(a, (k0 + threadIdx.x) * a.hop);
         __syncthreads();
-        float2* row = a.full ? a.full + (a.fo + k) * a.full_ld : nullptr;
+        if (gls == 0) {
+            const int sh = shs[0];
+            fir_points<TH>(a, k0 * a.hop, N, [=](int e) { return e >= sh ? e - sh : e - sh + N; }, sm);
+        } else {
+            fir_frames<TH>(a, k0 * a.hop, E, gls, nf, shs, sm);
+        }
+        __syncthreads();
+        float2* rows = a.full ? a.full + (a.fo + k0) * a.full_ld : nullptr;
+        const int64_t ld = a.full_ld;
         const bool keep = a.n_tones > 0;
         float2* const freebuf = (a.fb.nst & 1) ? sm1 : sm;   // the buffer the last stage does not read
-        // the last stage writes the spectrum row and, for the tone gather, a
+        // the last stage writes the spectrum rows and, for the tone gather, a
         // copy into the free shared-memory buffer
-        gen_fft_to<TH>(sm, sm1, a.fb, 0, a.tw_b, [=](int c, float2 v) {
-            if (row) row[c] = v;
-            if (keep) freebuf[gpad(c)] = v;
+        gen_fft_to<TH>(sm, sm1, a.fb, gls, a.tw_b, [=](int e, float2 v) {
+            const int g = e & (G - 1);
+            if (rows && g < nf) rows[g * ld + (e >> gls)] = v;
+            if (keep) freebuf[gpad(e)] = v;
         });
         if (keep) {
             __syncthreads();
-            for (int t = threadIdx.x; t < a.n_tones; t += TH)
-                a.tones[t * a.tones_ld + a.fo + k] = freebuf[gpad(__ldg(a.bins + t))];
+            for (int i = threadIdx.x; i < (a.n_tones << gls); i += TH) {
+                const int t = i >> gls, g = i & (G - 1);
+                if (g < nf) a.tones[t * a.tones_ld + a.fo + k0 + g] = freebuf[gpad((__ldg(a.bins + t) << gls) + g)];
+            }
         }
         __syncthreads();
     }
@@ -824,6 +909,8 @@ cudaError_t gen_plan_init(GenPlan* g, int N, int64_t z_budget_bytes) {
         g->threads = N <= GenCfg<256>::kElems ? 256 : 512;
         g->N1 = 1;
         g->N2 = N;
+        // frames per CTA iteration: as many as fill the CTA's points (<= 64)
+        g->gls = floor_log2(std::min(kGMax, g->threads * 16 / N));
         if (!build_fft(N, &g->fb, tw, 25)) return cudaErrorInvalidValue;
     } else {
         int n1 = 0, n2 = 0, score = 0;
@@ -906,7 +993,8 @@ cudaError_t gen_run(GenArgs a, const PfbLaunch& L, const GenPlan& g, cudaStream_
     if (g.N1 == 1) {
         a.F = L.F;
         a.k0 = 0;
-        return launch_gen<TH>(gen_single_kernel<TH>, L.F, g.N, L.n_sms, st, 0, a);
+        return launch_gen<TH>(gen_single_kernel<TH>, (L.F + (1 << g.gls) - 1) >> g.gls, g.N << g.gls, L.n_sms, st,
+                              (size_t(1) << g.gls) * sizeof(int), a);
     }
     if (g.z_frames < 1 || !g.d_z) return cudaErrorInvalidValue;   // gen_plan_reserve first
     const int ga = 1 << g.gla, gb = 1 << g.glb;
@@ -962,6 +1050,7 @@ cudaError_t gen_pfb_launch(const PfbLaunch& L, const GenPlan& g, cudaStream_t st
     a.N = g.N;
     a.T = L.taps_kernel;
     a.hop = L.hop > 0 ? L.hop : g.N;
+    a.gls = g.gls;
     a.a0 = L.a0;
     // frame starts a0 + k*N: one shift for every frame
     a.sh_fixed = a.hop == g.N ? static_cast<int>(((L.a0 % g.N) + g.N) % g.N) : -1;

@@ -67,6 +67,7 @@ struct GenFft {                 // one mixed-radix transform length
 struct GenPlan {
     int N = 0, N1 = 1, N2 = 0;  // N1 == 1: single pass
     int gla = 0, glb = 0;       // log2 of the transforms per CTA in pass A / B
+    int gls = 0;                // one pass: log2 of the frames per CTA iteration
     int threads = 256;          // CTA shape: 256 threads x 4096 points or 512 x 8192
     GenFft fa{}, fb{};          // lengths N1 (pass A) and N2 (pass B / single pass)
     float2* d_tw = nullptr;     // stage twiddles of fa and fb (absolute tw_off)
