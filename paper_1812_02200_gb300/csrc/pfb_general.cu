@@ -232,6 +232,34 @@ __device__ __forceinline__ void dft_any(float2* x) {
     dft_reg<R>(x);
 }
 
+// The R points x0 + r*s (r < R) of a padded buffer: when s is a multiple of
+// 16, gpad(x0 + r*s) = gpad(x0) + r*(s + s/16) exactly, so one padded index
+// and a constant step replace R of them.
+template <int R>
+__device__ __forceinline__ void load_strided(float2 (&v)[R], const float2* __restrict__ src, int x0, int s) {
+    if ((s & 15) == 0) {
+        const float2* p = src + gpad(x0);
+        const int st = s + (s >> 4);
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = p[r * st];
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = src[gpad(x0 + r * s)];
+    }
+}
+template <int R>
+__device__ __forceinline__ void store_strided(const float2 (&v)[R], float2* __restrict__ dst, int x0, int s) {
+    if ((s & 15) == 0) {
+        float2* p = dst + gpad(x0);
+        const int st = s + (s >> 4);
+#pragma unroll
+        for (int r = 0; r < R; ++r) p[r * st] = v[r];
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[gpad(x0 + r * s)] = v[r];
+    }
+}
+
 // One Stockham stage of radix R over G = 2^gl2 interleaved transforms of
 // length n, from src to dst (points at [gpad(i*G + g)]).
 // j / Ns as umulhi(j, ns_magic) with ns_magic = ceil(2^32 / Ns) for Ns > 1:
@@ -248,16 +276,14 @@ __device__ __forceinline__ void gen_stage(const float2* __restrict__ src, float2
         const int q = Ns == 1 ? j : static_cast<int>(__umulhi(static_cast<uint32_t>(j), ns_magic));
         const int k = j - q * Ns;
         float2 v[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = src[gpad(((j + r * nR) << gl2) + g)];
+        load_strided<R>(v, src, u, nb);                      // points (j + r*nR)*G + g
         if (Ns > 1) {
 #pragma unroll
             for (int r = 1; r < R; ++r) v[r] = cmul(v[r], __ldg(tw + (r - 1) * Ns + k));
         }
         dft_any<R>(v);
         const int base = (j - k) * R + k;
-#pragma unroll
-        for (int r = 0; r < R; ++r) dst[gpad(((base + r * Ns) << gl2) + g)] = v[r];
+        store_strided<R>(v, dst, (base << gl2) + g, Ns << gl2);   // points (base + r*Ns)*G + g
     }
     __syncthreads();
 }
@@ -276,8 +302,7 @@ __device__ __forceinline__ void gen_stage_out(const float2* __restrict__ src, in
         const int q = Ns == 1 ? j : static_cast<int>(__umulhi(static_cast<uint32_t>(j), ns_magic));
         const int k = j - q * Ns;
         float2 v[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = src[gpad(((j + r * nR) << gl2) + g)];
+        load_strided<R>(v, src, u, nb);                      // points (j + r*nR)*G + g
         if (Ns > 1) {
 #pragma unroll
             for (int r = 1; r < R; ++r) v[r] = cmul(v[r], __ldg(tw + (r - 1) * Ns + k));
