@@ -672,6 +672,11 @@ def run_serve(args, dev):
         slot = [0] * len(specs)
         base = rfr.now_us()
         for tag, ((t, r), n) in enumerate(zip(arr, sizes)):
+            # sleep until just before the arrival, then spin: the submitting
+            # thread leaves the host cores to the server's worker and poller
+            ahead = t * 1e6 - (rfr.now_us() - base)
+            if ahead > 300.0:
+                time.sleep((ahead - 200.0) * 1e-6)
             while rfr.now_us() - base < t * 1e6:
                 pass
             # four rotating output regions per readout, each large enough for

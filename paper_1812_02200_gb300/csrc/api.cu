@@ -132,6 +132,7 @@ rfr_status debug_check(rfr_plan* p, cudaStream_t st, const char* what) {
     return check_status(p);
 }
 
+// F0 < 0: size the rotation table for the worst alignment of the first frame
 rfr_status ensure_demod_scratch(rfr_plan* p, int64_t F, int64_t F0) {
     if (p->demod_products == 3) {
         // six fp16 planes [rows][D] of the Gauss three-product form
@@ -158,7 +159,8 @@ rfr_status ensure_demod_scratch(rfr_plan* p, int64_t F, int64_t F0) {
         p->xs_rows_cap = rows;
     }
     const int64_t ntp = p->demod_products == 3 ? p->ntp3 : p->ntp;
-    const int64_t rot = static_cast<int64_t>(rfr::demod_anchor_rows(F0, F)) * ntp + ntp * rfr::kDemodBM;
+    const int64_t anchors = F0 >= 0 ? rfr::demod_anchor_rows(F0, F) : (F + rfr::kDemodBM - 2) / rfr::kDemodBM + 1;
+    const int64_t rot = anchors * ntp + ntp * rfr::kDemodBM;
     if (rot > p->rot_cap) {
         cudaDeviceSynchronize();
         dev_free(p->d_rot);
@@ -182,9 +184,13 @@ rfr_status push_check(rfr_plan* p, const int16_t* iq, int64_t n, const rfr_outpu
 }
 
 rfr_status ensure_scratch(rfr_plan* p, int64_t n) {
-    const int64_t F = frames_for_len(p, p->cl + n);
+    // the most frames a push of n samples can complete whatever the stream's
+    // state (a carried residue adds up to hop - 1 samples: the carry holds at
+    // most W - 1), with the rotation table sized for any first frame, so that
+    // later pushes of up to n samples never allocate (nor synchronise)
+    const int64_t F = frames_for_len(p, std::max<int64_t>(p->cl, p->W - 1) + n);
     if (p->mode == RFR_MODE_PFB && p->gen && F > 0) RFR_CUDA(p, rfr::gen_plan_reserve(&p->gplan, F));
-    if (p->mode == RFR_MODE_DEMOD && F > 0 && !p->words.empty()) return ensure_demod_scratch(p, F, p->frames);
+    if (p->mode == RFR_MODE_DEMOD && F > 0 && !p->words.empty()) return ensure_demod_scratch(p, F, -1);
     return RFR_OK;
 }
 
