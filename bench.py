@@ -635,13 +635,15 @@ def run_serve(args, dev):
         outs.append(torch.empty((max(p.n_tones, 1), 4 * f), dtype=torch.complex64).pin_memory())
     log(f"[bench] serve setup {time.time() - t0:.1f}s")
     srv = rfr.Server(plans, 40 << 30, max_n)
-    # warm-up, outside the statistics: one buffer per readout through the
-    # server (first launches of every plan's kernels, first-use setup)
+    # warm-up, outside the statistics: a small and a full-size buffer per
+    # readout through the server (first launches of every plan's kernels,
+    # first-use setup at both ends of the size range)
     for r in range(len(specs)):
         srv.submit(r, host_x[r][: 1 << 18], tones=outs[r], frame_offset=0, tag=(1 << 40) + r)
+        srv.submit(r, host_x[r], tones=outs[r], frame_offset=outs[r].shape[1] // 4, tag=(1 << 41) + r)
     got = 0
     t_w = time.time()
-    while got < len(specs) and time.time() - t_w < 120:
+    while got < 2 * len(specs) and time.time() - t_w < 120:
         got += len(srv.poll(1024, wait_ms=20))
     loads = [float(v) for v in args.serve_loads.split(",") if v]
     rng = np.random.default_rng(55)
