@@ -61,3 +61,24 @@ def test_reference_arm_other_ranks_exit_quietly(capsys, monkeypatch):
         steps, warmup, ref_frames = 1, 0, 16
     bench.run_reference(A, 2, 1)
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_rank0_prints_the_contract_line():
+    """`bench.py --impl reference` on one process: the oracle timed on a host
+    core, one JSON line with the contract's keys (runs without a GPU)."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "2", "--warmup", "1",
+                        "--ref-frames", "16"], cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["steps"] == 2 and d["warmup"] == 3   # W >= 3 enforced
+    for k in ("metric", "value", "unit", "n_gpus", "ms_per_step", "higher_is_better", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
