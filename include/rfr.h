@@ -150,6 +150,12 @@ typedef struct {
  *   out_flags  PFB: any non-empty combination of RFR_OUT_FULL, RFR_OUT_TONES
  *              (RFR_OUT_TONES needs count > 0).  Demodulation: RFR_OUT_TONES.
  * Allocates the plan's device tables and stream state on the current device.
+ * Two-pass PFB plans (N > 8192 and not a power of two up to 16384) also hold
+ * between-pass buffers for a batch of frames: Z, and (when the split of N has
+ * an even second factor) the FIR outputs V, each up to 1 GB, allocated by the
+ * first push that needs them (rfr_batch_push grows them before capturing its
+ * graph; rfr_server_create sizes them for its largest buffer, so serving
+ * never allocates).
  * Errors: RFR_E_INVALID (parameters), RFR_E_NOMEM, RFR_E_CUDA.
  */
 rfr_status rfr_plan_create(rfr_plan** plan, int32_t channels, int32_t taps,
