@@ -133,43 +133,44 @@ __device__ __forceinline__ void fft_frame(float2 (&v)[16], float2* buf, int tf,
     static_assert(LOG2N >= 4, "N >= 16");
 
     dft16(v);  // pass 0, span 1
-    if constexpr (P16 == 1 && RF == 1) return;
-    // write y[16*tf + r]
+    if constexpr (P16 > 1 || RF > 1) {   // N = 16: one pass only
+        // write y[16*tf + r]
 #pragma unroll
-    for (int r = 0; r < 16; ++r) buf[fpad(16 * tf + r)] = v[r];
-    int tw_off = 0;
+        for (int r = 0; r < 16; ++r) buf[fpad(16 * tf + r)] = v[r];
+        int tw_off = 0;
 #pragma unroll
-    for (int s = 1; s < P16; ++s) {
-        const int ns = 1 << (4 * s);
-        __syncthreads();
-#pragma unroll
-        for (int r = 0; r < 16; ++r) v[r] = buf[fpad(tf + r * NT)];
-        const int k = tf & (ns - 1);
-#pragma unroll
-        for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], tw_load<TW_SMEM>(tw, tw_off + (r - 1) * ns + k));
-        tw_off += 15 * ns;
-        dft16(v);
-        const bool last = (s == P16 - 1) && (RF == 1);
-        if (!last) {
+        for (int s = 1; s < P16; ++s) {
+            const int ns = 1 << (4 * s);
             __syncthreads();
-            const int base = (tf / ns) * 16 * ns + k;
 #pragma unroll
-            for (int r = 0; r < 16; ++r) buf[fpad(base + r * ns)] = v[r];
+            for (int r = 0; r < 16; ++r) v[r] = buf[fpad(tf + r * NT)];
+            const int k = tf & (ns - 1);
+#pragma unroll
+            for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], tw_load<TW_SMEM>(tw, tw_off + (r - 1) * ns + k));
+            tw_off += 15 * ns;
+            dft16(v);
+            const bool last = (s == P16 - 1) && (RF == 1);
+            if (!last) {
+                __syncthreads();
+                const int base = (tf / ns) * 16 * ns + k;
+#pragma unroll
+                for (int r = 0; r < 16; ++r) buf[fpad(base + r * ns)] = v[r];
+            }
         }
-    }
-    if constexpr (RF > 1) {
-        constexpr int NB = 16 / RF;      // butterflies per thread
-        constexpr int SPAN = N / RF;     // Ns of the final pass
-        __syncthreads();
+        if constexpr (RF > 1) {
+            constexpr int NB = 16 / RF;      // butterflies per thread
+            constexpr int SPAN = N / RF;     // Ns of the final pass
+            __syncthreads();
 #pragma unroll
-        for (int q = 0; q < NB; ++q) {
-            const int j = tf + q * NT;
+            for (int q = 0; q < NB; ++q) {
+                const int j = tf + q * NT;
 #pragma unroll
-            for (int r = 0; r < RF; ++r) v[q * RF + r] = buf[fpad(j + r * SPAN)];
+                for (int r = 0; r < RF; ++r) v[q * RF + r] = buf[fpad(j + r * SPAN)];
 #pragma unroll
-            for (int r = 1; r < RF; ++r)
-                v[q * RF + r] = cmul(v[q * RF + r], tw_load<TW_SMEM>(tw, tw_off + (r - 1) * SPAN + j));
-            dft_small<RF>(v + q * RF);
+                for (int r = 1; r < RF; ++r)
+                    v[q * RF + r] = cmul(v[q * RF + r], tw_load<TW_SMEM>(tw, tw_off + (r - 1) * SPAN + j));
+                dft_small<RF>(v + q * RF);
+            }
         }
     }
 }
