@@ -165,6 +165,7 @@ OVERSAMPLED = [
     (1000, 4, 250, "hann", 120),
     (64, 4, 48, "hamming", 300),         # a hop that does not divide N
     (10000, 4, 5000, "kaiser", 16),      # four-step form
+    (20000, 4, 7000, "hann", 12),        # four-step form, hop not dividing N (a shift per frame)
 ]
 
 
@@ -221,3 +222,22 @@ def test_oversampled_streamed_equals_one_shot(lib, N, hop):
     torch.cuda.synchronize()
     assert off == F
     assert np.array_equal(fo.cpu().numpy(), f1) and np.array_equal(to.cpu().numpy(), t1)
+
+
+@pytest.mark.parametrize("N,T,hop", [(100000, 4, 100000),     # two passes, FIR ahead (V by TMA)
+                                     (19683, 2, 19683),       # two passes, FIR inside pass A
+                                     (1000, 8, 1000),         # one pass, 4 frames per CTA iteration
+                                     (20000, 4, 7000)])       # two passes, oversampled
+def test_any_n_output_subsets_bit_exact(lib, N, T, hop):
+    """Tones-only and full-only plans (other branches of the output stages)
+    give, bit for bit, the tones and the spectrum of a full + tones plan."""
+    n_tones = 20
+    frames = 10
+    case = siggen.pfb_case(hop * frames + N * T, N, n_tones, seed=700 + N + hop, amp=(200.0, 1500.0))
+    mk = lambda full, tones: lib.Plan(N, T, window="hann", words=case["words"], decimation=hop,
+                                      full=full, tones=tones)
+    f1, t1 = _run(mk(True, True), case["x"], n_tones, N)
+    _, t2 = _run(mk(False, True), case["x"], n_tones, N, full=False)
+    f3, _ = _run(mk(True, False), case["x"], 0, N)
+    assert np.array_equal(t2, t1)
+    assert np.array_equal(f3, f1)
