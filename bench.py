@@ -198,6 +198,81 @@ def aggregate_rate(ws, steps, samples_per_rank_step, ms_max):
 
 
 # ------------------------------------------------------------------- oracle
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the ISA)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip().lower() == "model name":
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+_POOL = None
+
+
+def oracle_pool():
+    """Process pool over every host core for the oracle (spawned processes:
+    safe after the parent has touched the GPU)."""
+    global _POOL
+    if _POOL is None:
+        import multiprocessing as mp
+
+        import oracle
+        oracle.build()                     # once, before the workers load it
+        _POOL = mp.get_context("spawn").Pool(os.cpu_count() or 1)
+        _POOL.map(_w_noop, range(4 * (os.cpu_count() or 1)))
+    return _POOL
+
+
+def _w_noop(_):
+    return 0
+
+
+def _w_demod(a):
+    import oracle
+    x, m0, L, D, h, words, k0, k1 = a
+    return oracle.demod(x, L, D, h, words, k0, k1, m0=m0)
+
+
+def _w_pfb_time(a):
+    import oracle
+    x, N, T, h, k0, k1, bins = a
+    t0 = time.perf_counter()
+    oracle.pfb(x, N, T, h, k_begin=k0, k_end=k1, bins=bins)
+    return time.perf_counter() - t0
+
+
+def oracle_pfb_rate_all_cores(frames_per_core: int, c):
+    """The FP64 oracle on disjoint frame ranges of the workload, one range per
+    host core, all at once; returns (Ms/s, wall seconds, samples, cores)."""
+    pool = oracle_pool()
+    cores = os.cpu_count() or 1
+    _, h32 = __import__("oracle").pfb_prototype(N_CHAN, TAPS, "kaiser", BETA)
+    h = h32.astype(np.float64)
+    bins = np.array([__import__("oracle").word_to_bin(int(w), N_CHAN) for w in c["words"]], np.int32)
+    tasks = []
+    for i in range(cores):
+        k0 = TAPS - 1 + i * frames_per_core
+        s0 = (k0 + 1 - TAPS) * N_CHAN
+        x = np.ascontiguousarray(c["x"][s0:(k0 + frames_per_core) * N_CHAN])
+        tasks.append((x, N_CHAN, TAPS, h, TAPS - 1, TAPS - 1 + frames_per_core, bins))
+    t0 = time.perf_counter()
+    pool.map(_w_pfb_time, tasks, chunksize=1)
+    dt = time.perf_counter() - t0
+    samples = cores * frames_per_core * N_CHAN
+    return samples / dt / 1e6, dt, samples, cores
+
+
 def oracle_pfb_rate(sample_frames: int, c=None):
     """FP64 oracle on the first `sample_frames` frames of the workload, one
     host core; returns (Ms/s, seconds, samples)."""
@@ -215,6 +290,33 @@ def oracle_pfb_rate(sample_frames: int, c=None):
     dt = time.perf_counter() - t0
     samples = sample_frames * N_CHAN
     return samples / dt / 1e6, dt, samples
+
+
+def pfb_full_spectrum_error(c, full, F, bins, h, slices=8, frames=32):
+    """Full-spectrum error of the timed configuration against the FP64 oracle
+    on `slices` runs of `frames` frames spread over the stream, per channel c
+    over those frames: strict ||y_c - y*_c|| / ||y*_c|| (maxima over the tone
+    channels and over the noise-only channels) and the same divided by
+    max(own, RMS channel norm)."""
+    import oracle
+    got, ref = [], []
+    for i in range(slices):
+        a = min(F - frames, i * (F // slices))
+        ref.append(oracle.pfb(c["x"], N_CHAN, TAPS, h, k_begin=a, k_end=a + frames)["full"])
+        got.append(full[a:a + frames].cpu().numpy())
+    g, r = np.concatenate(got), np.concatenate(ref)
+    num = np.linalg.norm(g - r, axis=0)
+    own = np.maximum(np.linalg.norm(r, axis=0), 1e-300)
+    rms = np.sqrt(np.mean(own ** 2))
+    tone = np.zeros(N_CHAN, bool)
+    tone[np.asarray(bins, int)] = True
+    strict = num / own
+    return {"frames_checked": slices * frames, "channels": N_CHAN,
+            "strict_tone_max": float(strict[tone].max()), "strict_noise_max": float(strict[~tone].max()),
+            "strict_noise_median": float(np.median(strict[~tone])),
+            "rms_norm_max": float((num / np.maximum(own, rms)).max()),
+            "note": "strict per-channel ratio; noise-only channels are ~1e-3 of the tone power, so FP32 "
+                    "rounding of the strong channels dominates their strict ratio"}
 
 
 def run_reference(args, ws, rank):
@@ -276,6 +378,9 @@ def run_demod(args, dev, stream, rank):
         got = np.concatenate([out[sel, a:b].cpu().numpy() for a, b in fr], axis=1)
         ref = np.concatenate(refs, axis=1)
         rel = float(np.max(np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)))
+    all_tones = None
+    if rank == 0 and not args.no_check and not args.no_cpu:
+        all_tones = demod_all_tones_error(c, out, F, args.demod_check_slices)
     for _ in range(2):
         plan.push_into(x, tones=out, stream=stream)
     torch.cuda.synchronize(dev)
@@ -297,6 +402,7 @@ def run_demod(args, dev, stream, rank):
            "tune": plan.tune(),
            "value": samples / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms,
            "rel_err_max_checked_tones": rel,
+           "rel_err_all_tones": all_tones,
            "roofline": {"bound": "tensor", "achieved": achieved, "peak": bf16_peak,
                         "unit": "TFLOP/s", "frac": achieved / bf16_peak,
                         "traffic": profile_traffic("demod3m_gemm_kernel_c3.md", DEMOD_SOURCES),
@@ -360,6 +466,38 @@ def run_demod(args, dev, stream, rank):
     del out, x
     plan.close()
     return res
+
+
+def demod_all_tones_error(c, out, F, slices, frames=4):
+    """Per-tone relative RMS error of ALL tones of the demodulation workload
+    against the FP64 oracle, over `slices` runs of `frames` frames spread
+    across the stream, the oracle spread over every host core (each task one
+    frame run x 256 tones, given only the samples it reads, at their absolute
+    origin)."""
+    import oracle
+    h = oracle.lowpass("blackman", DEMOD_L, DEMOD_FC)
+    pool = oracle_pool()
+    starts = [min(F - frames, i * (F // slices)) for i in range(slices)]
+    tasks, keys = [], []
+    nt = len(c["words"])
+    for a in starts:
+        m0 = max(0, (a + 1) * DEMOD_D - DEMOD_L)
+        xs = np.ascontiguousarray(c["x"][m0:(a + frames) * DEMOD_D])
+        for t0 in range(0, nt, 256):
+            tasks.append((xs, m0, DEMOD_L, DEMOD_D, h, c["words"][t0:t0 + 256], a, a + frames))
+            keys.append((a, t0))
+    t_0 = time.perf_counter()
+    res = pool.map(_w_demod, tasks, chunksize=1)
+    dt = time.perf_counter() - t_0
+    ref = np.zeros((nt, slices * frames), np.complex128)
+    for (a, t0), r in zip(keys, res):
+        j = starts.index(a)
+        ref[t0:t0 + r.shape[0], j * frames:(j + 1) * frames] = r
+    got = np.concatenate([out[:, a:a + frames].cpu().numpy() for a in starts], axis=1)
+    e = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    return {"tones": nt, "frames_checked": slices * frames, "max": float(e.max()),
+            "median": float(np.median(e)), "p99": float(np.percentile(e, 99)),
+            "oracle_seconds": dt, "cores": os.cpu_count() or 1}
 
 
 # ------------------------------------------------------------------- chirp
@@ -538,6 +676,34 @@ def make_spec_plan(rfr, spec, words, full=False):
     return rfr.Plan(0, spec["L"], window="blackman", cutoff=DEMOD_FC, words=words, decimation=spec["D"])
 
 
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12     # FMA lanes x 2 flops x max SM clock
+
+
+def batch_roofline(specs, ns, ms):
+    """Roof time of the batched step = the sum over streams of each stream's
+    own roof time: the larger of its HBM time (algorithmic bytes: 4 B in plus
+    8 B per output value) and its compute time (PFB: 4T FIR + 5 log2 N FFT
+    flops per sample at the FP32 FMA rate; demodulation: 8 L tones / D flops
+    per sample at the measured dense bf16 rate)."""
+    hbm, bf16, _, kind = measured_peaks()
+    tot, parts = 0.0, {"pfb_hbm": 0.0, "pfb_fp32": 0.0, "demod_hbm": 0.0, "demod_tensor": 0.0}
+    for sp, n in zip(specs, ns):
+        if sp["kind"] == "pfb":
+            t_b = n * (4.0 + 8.0 * sp["tones"] / sp["N"]) / (hbm * 1e9)
+            t_c = n * (4.0 * sp["T"] + 5.0 * np.log2(sp["N"])) / (FP32_PEAK_TFLOPS * 1e12)
+            parts["pfb_hbm" if t_b >= t_c else "pfb_fp32"] += max(t_b, t_c)
+        else:
+            t_b = n * (4.0 + 8.0 * sp["tones"] / sp["D"]) / (hbm * 1e9)
+            t_c = n * 8.0 * sp["L"] * sp["tones"] / sp["D"] / (bf16 * 1e12)
+            parts["demod_hbm" if t_b >= t_c else "demod_tensor"] += max(t_b, t_c)
+        tot += max(t_b, t_c)
+    return {"bound": "mixed", "roof_ms": tot * 1e3, "achieved_ms": ms, "frac": tot * 1e3 / ms,
+            "roof_ms_by_bound": {k: v * 1e3 for k, v in parts.items()},
+            "peak": {"hbm_gbs": hbm, "bf16_tflops": bf16, "fp32_tflops": FP32_PEAK_TFLOPS, "kind": kind},
+            "note": "sum over streams of max(algorithmic bytes / HBM peak, algorithmic flops / compute "
+                    "peak); frac = roof time / measured step time"}
+
+
 def run_batch(args, dev, stream):
     """Workload 4: 24 mixed PFB / demodulation streams of 2^22..2^26 samples
     per step, one CUDA-graph launch per step, launch choices autotuned."""
@@ -596,13 +762,16 @@ def run_batch(args, dev, stream):
         torch.cuda.synchronize(dev)
         ms_plain = e0.elapsed_time(e1)
     st = batch.stats()
+    roof = batch_roofline(specs, [x.shape[0] for x in xs], ms_batch)
     res = {"workload": "24 streams of 2^22..2^26 samples (log-uniform), 16 PFB "
                        "(N in {256..16384}, T in {4,8,16}, tones out) + 8 demodulation "
                        "(64..4096 tones, L in {1024,4096}, D in {512,2048})",
            "samples_per_step": samples,
            "value": samples / (ms_batch * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms_batch,
            "graph": st,
-           "sequential_fused": {"value": samples / (ms_seq * 1e-3) / 1e6, "ms_per_step": ms_seq},
+           "roofline": roof,
+           "sequential_fused": {"value": samples / (ms_seq * 1e-3) / 1e6, "ms_per_step": ms_seq,
+                                "batch_speedup": ms_seq / ms_batch},
            "plain_fp32_per_stream": None if ms_plain is None else
            {"value": samples / (ms_plain * 1e-3) / 1e6, "ms_per_step": ms_plain},
            "tune": [p.tune() for p in plans][:4] + ["..."]}
@@ -614,9 +783,13 @@ def run_batch(args, dev, stream):
 # ------------------------------------------------------------------- serve
 def run_serve(args, dev):
     """Workload 5: 32 readouts (plans drawn as in the batched workload),
-    buffers of 1..32 MB arriving as Poisson processes, host-resident input and
-    output (pinned), admission under a 40 GB device budget; p50/p99 latency
-    from submit to completion and the sustained rate per offered load."""
+    buffers of 1..32 MB arriving as Poisson processes, admission under a 40 GB
+    device budget; p50/p99 latency from submit to completion and the
+    sustained rate per offered load.  Two modes: host-resident input and
+    output (pinned; the copies are part of each request) and device-resident
+    (inputs and outputs already in device memory).  Each load point runs for
+    args.serve_seconds of arrivals and is repeated; the spread of p99 over the
+    repeats is reported."""
     import threading as th
 
     import torch
@@ -625,31 +798,36 @@ def run_serve(args, dev):
     specs = siggen.c5_specs()
     max_n = 8 << 20                      # 32 MB of complex int16
     t0 = time.time()
-    host_x, plans, outs = [], [], []
+    host_x, dev_x, plans, outs, dev_outs = [], [], [], [], []
     for sp in specs:
         c = siggen.spec_input(sp, n=max_n)
         host_x.append(torch.from_numpy(c["x"]).pin_memory())
+        dev_x.append(torch.from_numpy(c["x"]).to(dev))
         plans.append(make_spec_plan(rfr, sp, c["words"]))
     for p in plans:
         f = p.frames_for(max_n) + 2
         outs.append(torch.empty((max(p.n_tones, 1), 4 * f), dtype=torch.complex64).pin_memory())
+        dev_outs.append(torch.empty((max(p.n_tones, 1), 4 * f), dtype=torch.complex64, device=dev))
     log(f"[bench] serve setup {time.time() - t0:.1f}s")
     srv = rfr.Server(plans, 40 << 30, max_n)
     # warm-up, outside the statistics: a small and a full-size buffer per
-    # readout through the server (first launches of every plan's kernels,
-    # first-use setup at both ends of the size range)
+    # readout through the server in each mode (first launches of every plan's
+    # kernels, first-use setup at both ends of the size range)
+    n_warm = 0
     for r in range(len(specs)):
-        srv.submit(r, host_x[r][: 1 << 18], tones=outs[r], frame_offset=0, tag=(1 << 40) + r)
-        srv.submit(r, host_x[r], tones=outs[r], frame_offset=outs[r].shape[1] // 4, tag=(1 << 41) + r)
+        for xs, os_ in ((host_x, outs), (dev_x, dev_outs)):
+            srv.submit(r, xs[r][: 1 << 18], tones=os_[r], frame_offset=0, tag=(1 << 40) + n_warm)
+            srv.submit(r, xs[r], tones=os_[r], frame_offset=os_[r].shape[1] // 4, tag=(1 << 41) + n_warm)
+            n_warm += 2
     got = 0
     t_w = time.time()
-    while got < 2 * len(specs) and time.time() - t_w < 120:
+    while got < n_warm and time.time() - t_w < 180:
         got += len(srv.poll(1024, wait_ms=20))
     loads = [float(v) for v in args.serve_loads.split(",") if v]
     rng = np.random.default_rng(55)
-    points = []
-    for load in loads:
-        mean_n = float(np.mean(siggen.c5_buffer_samples(rng, 4096)))
+    mean_n = float(np.mean(siggen.c5_buffer_samples(np.random.default_rng(1), 1 << 16)))
+
+    def one_point(load, xs, os_):
         rate = load * 1e9 / mean_n / len(specs)          # buffers/s per readout
         dur = args.serve_seconds
         arr = []
@@ -683,25 +861,52 @@ def run_serve(args, dev):
                 pass
             # four rotating output regions per readout, each large enough for
             # the frames of the largest buffer
-            off = (slot[r] % 4) * (outs[r].shape[1] // 4)
+            off = (slot[r] % 4) * (os_[r].shape[1] // 4)
             slot[r] += 1
-            srv.submit(r, host_x[r][: int(n)], tones=outs[r], frame_offset=off, tag=tag)
+            srv.submit(r, xs[r][: int(n)], tones=os_[r], frame_offset=off, tag=tag)
+        t_sub_end = rfr.now_us() - base
         stop[0] = True
-        pt.join(timeout=120)
+        pt.join(timeout=180)
         lat = np.array([d["t_done_us"] - d["t_submit_us"] for d in done]) / 1e3
         t_first = min(d["t_submit_us"] for d in done)
         t_last = max(d["t_done_us"] for d in done)
         tot = float(sum(d["samples"] for d in done))
-        points.append({"offered_gsps": load, "buffers": len(done),
-                       "sustained_gsps": tot / ((t_last - t_first) * 1e-6) / 1e9,
-                       "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                       "max_ms": float(lat.max())})
-        log(f"[bench] serve load {load}: {points[-1]}")
+        bad = sum(1 for d in done if d["status"] != 0)
+        return {"buffers": len(done), "failed": bad,
+                "offered_realised_gsps": tot / (t_sub_end * 1e-6) / 1e9,
+                "sustained_gsps": tot / ((t_last - t_first) * 1e-6) / 1e9,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "max_ms": float(lat.max())}
+
+    modes = {}
+    for mode, xs, os_, reps in (("host_pinned", host_x, outs, args.serve_reps),
+                                ("device_resident", dev_x, dev_outs, args.serve_reps_device)):
+        pts = []
+        for load in loads:
+            runs = [one_point(load, xs, os_) for _ in range(max(1, reps))]
+            p99 = [r["p99_ms"] for r in runs]
+            pt = {"offered_gsps": load, "repeats": len(runs),
+                  "buffers": int(sum(r["buffers"] for r in runs)),
+                  "failed": int(sum(r["failed"] for r in runs)),
+                  "offered_realised_gsps": float(np.mean([r["offered_realised_gsps"] for r in runs])),
+                  "sustained_gsps": float(np.mean([r["sustained_gsps"] for r in runs])),
+                  "p50_ms": float(np.median([r["p50_ms"] for r in runs])),
+                  "p99_ms": float(np.median(p99)), "p99_ms_min": float(min(p99)),
+                  "p99_ms_max": float(max(p99)), "max_ms": float(max(r["max_ms"] for r in runs))}
+            pts.append(pt)
+            log(f"[bench] serve {mode} load {load}: {pt}")
+        modes[mode] = pts
     st = srv.stats()
     srv.close()
     return {"workload": "32 readouts (plans as the batched workload), Poisson arrivals, "
-                        "buffers log-uniform 1..32 MB, pinned host in/out, 40 GB budget",
-            "points": points, "peak_device_bytes": st["peak_bytes"], "seconds_per_point": args.serve_seconds}
+                        "buffers log-uniform 1..32 MB, 40 GB budget",
+            "points": modes["host_pinned"], "device_resident": modes["device_resident"],
+            "peak_device_bytes": st["peak_bytes"], "seconds_per_point": args.serve_seconds,
+            "note": "points: pinned host input and output (the copies are part of each request); "
+                    "device_resident: inputs and outputs in device memory.  offered_realised is the "
+                    "submitted samples over the submission window (Poisson draws make it differ from "
+                    "the nominal load); sustained is the completed samples from first submit to last "
+                    "completion, which includes the last buffer's latency."}
 
 
 # --------------------------------------------------------------------- ours
@@ -726,6 +931,7 @@ def run_ours(args, ws, rank, local):
     plan.push_into(x, full, tones, stream=stream)
     torch.cuda.synchronize(dev)
     rel_err = None
+    full_err = None
     if rank == 0 and not args.no_check:
         import oracle
         _, h32 = oracle.pfb_prototype(N_CHAN, TAPS, "kaiser", BETA)
@@ -738,6 +944,7 @@ def run_ours(args, ws, rank, local):
             errs.append(float(np.max(np.linalg.norm(got - ref, axis=1) /
                                      np.linalg.norm(ref, axis=1))))
         rel_err = max(errs)
+        full_err = pfb_full_spectrum_error(c, full, F, plan.bins(), h32.astype(np.float64))
 
     # -- timed region: K pushes (the stream continues; each push = F frames)
     for _ in range(args.warmup):
@@ -801,13 +1008,20 @@ def run_ours(args, ws, rank, local):
                "d2h_bytes_per_step": int(fh.numel() * 8 + th.numel() * 8),
                "call": "rfr_process_host (pinned host in/out, chunked copies overlapped)"}
 
-    # -- oracle on the host cores, bounded sample (rank 0 only)
+    # -- oracle on the host cores, bounded sample (rank 0 only): one core,
+    # then every core on disjoint frame ranges
     cpu = None
     if rank == 0 and not args.no_cpu:
         nf = min(args.cpu_frames, F - TAPS)
         v, dt, s = oracle_pfb_rate(nf, c)
+        cores = os.cpu_count() or 1
+        fpc = max(16, min(args.cpu_frames_per_core, (F - TAPS) // cores))
+        va, dta, sa, na = oracle_pfb_rate_all_cores(fpc, c)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{nf} frames ({s} samples) of the workload, {dt:.1f} s"}
+               "sample": f"{nf} frames ({s} samples) of the workload, {dt:.1f} s",
+               "value_all_cores": va, "cores_all": na,
+               "sample_all_cores": f"{na} processes x {fpc} disjoint frames ({sa} samples), {dta:.1f} s wall",
+               "cpu_model": cpu_model(), "nproc": cores}
 
     demod = None
     del full, tones
@@ -834,6 +1048,9 @@ def run_ours(args, ws, rank, local):
                    "l2": "inputs and outputs larger than L2 (no flush)",
                    "parallelism": f"replicas x{ws}"},
         "rel_err_max_tone": rel_err,
+        "rel_err_full_strict": None if full_err is None else full_err["strict_noise_max"],
+        "rel_err_full_rms": None if full_err is None else full_err["rms_norm_max"],
+        "full_spectrum_error": full_err,
         "gpu_launches": 2 * args.steps,
         "gpu_launches_note": "fused PFB kernel + carry-update kernel per step",
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
@@ -867,16 +1084,20 @@ def main():
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-demod", action="store_true")
     ap.add_argument("--demod-log2-samples", type=int, default=27)
+    ap.add_argument("--demod-check-slices", type=int, default=16)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-chirp", action="store_true")
     ap.add_argument("--no-large-n", action="store_true")
     ap.add_argument("--no-tx", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--serve-loads", default="1,5,10,20", help="offered loads, Gsamples/s")
-    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-loads", default="0.5,1,2,5,10,15,20", help="offered loads, Gsamples/s")
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-reps", type=int, default=3)
+    ap.add_argument("--serve-reps-device", type=int, default=1)
     ap.add_argument("--log2-samples", type=int, default=28,
                     help="stream length (28 = the workload; smaller only for profiling)")
     ap.add_argument("--cpu-frames", type=int, default=32768)
+    ap.add_argument("--cpu-frames-per-core", type=int, default=4096)
     ap.add_argument("--ref-frames", type=int, default=2048)
     args = ap.parse_args()
     if args.warmup < 3:

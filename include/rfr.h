@@ -155,7 +155,11 @@ typedef struct {
  * an even second factor) the FIR outputs V, each up to 1 GB, allocated by the
  * first push that needs them (rfr_batch_push grows them before capturing its
  * graph; rfr_server_create sizes them for its largest buffer, so serving
- * never allocates).
+ * never allocates).  Demodulation plans likewise allocate their per-push
+ * scratch (the FP16 split of the stream and the rotation tables) on the first
+ * push of a given size, which synchronises the device; inside a stream
+ * capture such a push fails with RFR_E_INVALID instead, so push once at the
+ * largest size outside capture first.
  * Errors: RFR_E_INVALID (parameters), RFR_E_NOMEM, RFR_E_CUDA.
  */
 rfr_status rfr_plan_create(rfr_plan** plan, int32_t channels, int32_t taps,
@@ -270,15 +274,22 @@ rfr_status rfr_pull(rfr_plan* plan, rfr_output* out);
 rfr_status rfr_process_host(rfr_plan* plan, const int16_t* iq_host, int64_t n_samples,
                             rfr_output* out_host);
 
-/* Zero history, residue and stream position (and drop pending frames). */
+/* Zero history, residue and stream position (and drop pending frames): the
+ * plan starts a new stream at sample 0, as after rfr_plan_create (the
+ * buffered Rx stream of Sec. III restarted).  Synchronises the device.
+ * Errors: RFR_E_INVALID (NULL plan), RFR_E_CUDA. */
 rfr_status rfr_reset(rfr_plan* plan);
 
 /*
- * Checkpoint / resume of the stream state (history, residue, position).
- * Export with host == NULL stores the needed size in *bytes.  Import needs a
- * plan created with the same parameters; it restores the state exactly, so
- * the next push continues the stream bit-identically.  Both synchronise with
- * the plan's outstanding work.
+ * Checkpoint / resume of the stream state (history, residue, position) of the
+ * buffered Rx stream of Sec. III: the state a push carries to the next one.
+ * Export with host == NULL stores the needed size in *bytes; otherwise *bytes
+ * is the capacity of `host` (RFR_E_SHORT if too small) and receives the size
+ * written.  Import needs a plan created with the same parameters
+ * (RFR_E_INVALID otherwise, state unchanged); it restores the state exactly,
+ * so the next push continues the stream bit-identically.  Both synchronise
+ * with the plan's outstanding work; the blob is plain host memory owned by
+ * the caller.
  */
 rfr_status rfr_state_export(rfr_plan* plan, void* host, size_t* bytes);
 rfr_status rfr_state_import(rfr_plan* plan, const void* host, size_t bytes);
@@ -328,6 +339,17 @@ rfr_status rfr_plan_seek(rfr_plan* plan, int64_t start_sample, const int16_t* hi
                          int64_t n_history);
 
 /*
+ * rfr_plan_inject_device_status -- failure injection on the host: writes the
+ * plan's device status word exactly as a kernel whose bounded wait gave up
+ * would (status 1 = timeout; 0 clears it), so that callers and tests can
+ * exercise their RFR_E_TIMEOUT handling without faulting or hanging a GPU.
+ * Kernels of a later push that find the word set leave their waits early.
+ * Synchronises the device.  Errors: RFR_E_INVALID (status not 0, 1 or 2),
+ * RFR_E_CUDA.
+ */
+rfr_status rfr_plan_inject_device_status(rfr_plan* plan, int32_t status);
+
+/*
  * rfr_wait_selftest -- launch a kernel whose bounded device-side wait can
  * never be satisfied and check that it gives up after limit_ns (1 us .. 2 s)
  * with the library's timeout status: returns RFR_E_TIMEOUT (and the device
@@ -337,9 +359,11 @@ rfr_status rfr_plan_seek(rfr_plan* plan, int64_t start_sample, const int16_t* hi
 rfr_status rfr_wait_selftest(int64_t limit_ns, int32_t* device_status);
 
 /*
- * Prototype taps (host memory): h64 in FP64 (may be NULL), h32 the FP32
+ * Prototype taps (host memory, caller-owned): the windowed-sinc low-pass of
+ * Sec. III.A (PFB, length N*T, oldest sample first) or the demodulator's
+ * filter of Sec. III.B (length L).  h64 in FP64 (may be NULL), h32 the FP32
  * values the PFB kernels use (may be NULL).  *n receives the length (N*T or
- * L); with both pointers NULL only *n is set.
+ * L); with both pointers NULL only *n is set.  Errors: RFR_E_INVALID.
  */
 rfr_status rfr_plan_get_taps(const rfr_plan* plan, double* h64, float* h32, int64_t* n);
 
@@ -458,6 +482,10 @@ rfr_status rfr_server_poll(rfr_server* server, rfr_completion* done, int32_t cap
                            int32_t wait_ms);
 rfr_status rfr_server_get_stats(const rfr_server* server, rfr_server_stats* stats);
 
+/* A completion's status is RFR_E_TIMEOUT when a bounded device-side wait of
+ * that request's kernels gave up (the plan's device status word is copied
+ * after each request and cleared), RFR_E_CUDA on a CUDA error. */
+
 /* Finishes every submitted request, then frees the server. */
 void rfr_server_destroy(rfr_server* server);
 
@@ -497,13 +525,27 @@ rfr_status rfr_demod_noalloc(const int16_t* iq, int64_t n_samples, const double*
                              int32_t D, const uint64_t* words, int32_t n_tones, void* tones,
                              int64_t tones_ld, void* stream);
 
-/* Frequency f_hz at sample rate fs_hz -> NCO word: f/fs wrapped into
- * [-1/2, 1/2), times 2^64, rounded to nearest (two's complement). */
+/*
+ * rfr_demod_noalloc_status -- the device status word of the last
+ * rfr_demod_noalloc call (it lives in the same shared static array, so it
+ * belongs to whichever call ran last on this device).  Waits for `stream`
+ * (pass the stream of that call), then copies the word into *device_status
+ * (may be NULL) without allocating.  Returns RFR_E_TIMEOUT when a bounded
+ * device-side wait of the call's GEMM gave up (its output is then incomplete),
+ * RFR_E_CUDA for a CUDA error or any other non-zero word, RFR_OK otherwise.
+ * (The paper has no counterpart.)
+ */
+rfr_status rfr_demod_noalloc_status(void* stream, int32_t* device_status);
+
+/* The per-tone NCO of Sec. III.B (the mixer of each readout tone): frequency
+ * f_hz at sample rate fs_hz -> NCO word, f/fs wrapped into [-1/2, 1/2), times
+ * 2^64, rounded to nearest (two's complement).  Pure function, no device work. */
 uint64_t rfr_freq_to_word(double f_hz, double fs_hz);
 
-/* Bin of an NCO word in an n-channel PFB: round(word*n/2^64) mod n, ties
- * up, i.e. floor((word*n + 2^63) / 2^64) mod n in exact 128-bit integer
- * arithmetic, for any n >= 2; -1 if n < 2. */
+/* The user-selected channels of Sec. III.A (the PFB bins that hold the
+ * readout tones): bin of an NCO word in an n-channel PFB, round(word*n/2^64)
+ * mod n, ties up, i.e. floor((word*n + 2^63) / 2^64) mod n in exact 128-bit
+ * integer arithmetic, for any n >= 2; -1 if n < 2.  Pure function. */
 int32_t rfr_word_to_bin(uint64_t word, int32_t n);
 
 const char* rfr_status_string(rfr_status status);

@@ -71,13 +71,13 @@ def _load():
             "orc_pfb_f64": (C.c_int, [P, i64, i32, i32, P, i64, i64, P, P, P, i32, P]),
             "orc_pfb_i16": (C.c_int, [P, i64, i32, i32, P, i64, i64, P, P, i32, P]),
             "orc_demod_f64": (C.c_int, [P, i64, i32, i32, P, P, i32, i64, i64, P]),
-            "orc_demod_i16": (C.c_int, [P, i64, i32, i32, P, P, i32, i64, i64, P]),
+            "orc_demod_i16": (C.c_int, [P, i64, i64, i32, i32, P, P, i32, i64, i64, P]),
             "orc_chirp_phase": (u64, [u64, u64, i64]),
             "orc_chirp_rate_word": (u64, [dbl, dbl]),
             "orc_chirp_synth": (C.c_int, [u64, u64, dbl, i64, i64, P]),
-            "orc_chirp_demod_i16": (C.c_int, [P, i64, i32, i32, P, P, P, i32, i64, i64, P]),
+            "orc_chirp_demod_i16": (C.c_int, [P, i64, i64, i32, i32, P, P, P, i32, i64, i64, P]),
             "orc_tones_synth": (C.c_int, [P, P, P, i32, i64, i64, P, P]),
-            "orc_pfb_hop_i16": (C.c_int, [P, i64, i32, i32, i32, P, i64, i64, P, P, i32, P]),
+            "orc_pfb_hop_i16": (C.c_int, [P, i64, i64, i32, i32, i32, P, i64, i64, P, P, i32, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -186,21 +186,23 @@ def pfb(x: np.ndarray, n_chan: int, taps: int, h: np.ndarray, k_begin: int = 0,
 
 
 def pfb_hop(x: np.ndarray, n_chan: int, taps: int, hop: int, h: np.ndarray, k_begin: int = 0,
-            k_end: int | None = None, bins=None, want_full: bool = True):
+            k_end: int | None = None, bins=None, want_full: bool = True, m0: int = 0):
     """PFB with `hop` samples between frames on an int16 [n, 2] stream (frames
     end at (k+1)*hop - 1; channels keep the absolute time origin's phase).
+    x[i] is the sample at absolute index m0 + i (earlier samples are zero) and
+    k_begin, k_end are absolute frame indices.
     Returns a dict with 'full' [nk, N] and 'tones' [n_bins, nk]."""
     h = np.ascontiguousarray(h, np.float64)
     xi = np.ascontiguousarray(x, np.int16)
     n = xi.shape[0]
     if k_end is None:
-        k_end = n // hop
+        k_end = (m0 + n) // hop
     nk = k_end - k_begin
     bins_a = None if bins is None else np.ascontiguousarray(bins, np.int32)
     nb = 0 if bins_a is None else len(bins_a)
     full = np.empty((nk, n_chan), np.complex128) if want_full else None
     tones = np.empty((nb, nk), np.complex128) if nb else None
-    _check(_load().orc_pfb_hop_i16(_ptr(xi), n, n_chan, taps, hop, _ptr(h), k_begin, k_end, _ptr(full),
+    _check(_load().orc_pfb_hop_i16(_ptr(xi), n, int(m0), n_chan, taps, hop, _ptr(h), k_begin, k_end, _ptr(full),
                                    _ptr(bins_a), nb, _ptr(tones)), "pfb_hop")
     out = {}
     if want_full:
@@ -211,19 +213,23 @@ def pfb_hop(x: np.ndarray, n_chan: int, taps: int, hop: int, h: np.ndarray, k_be
 
 
 def demod(x: np.ndarray, L: int, D: int, h: np.ndarray, words, k_begin: int = 0,
-          k_end: int | None = None) -> np.ndarray:
-    """Direct demodulation; returns complex128 [n_words, nk]."""
+          k_end: int | None = None, m0: int = 0) -> np.ndarray:
+    """Direct demodulation; returns complex128 [n_words, nk].  For an int16
+    stream, x[i] is the sample at absolute index m0 + i (earlier samples are
+    zero) and k_begin, k_end are absolute frame indices."""
     lib = _load()
     h = np.ascontiguousarray(h, np.float64)
     w = np.ascontiguousarray(np.asarray(words, dtype=np.uint64))
     n = x.shape[0]
+    if m0 and x.dtype != np.int16:
+        raise ValueError("an absolute origin m0 is supported for int16 streams")
     if k_end is None:
-        k_end = n // D
+        k_end = (m0 + n) // D
     nk = k_end - k_begin
     out = np.empty((len(w), nk), np.complex128)
     if x.dtype == np.int16:
         xi = np.ascontiguousarray(x)
-        rc = lib.orc_demod_i16(_ptr(xi), n, L, D, _ptr(h), _ptr(w), len(w), k_begin, k_end, _ptr(out))
+        rc = lib.orc_demod_i16(_ptr(xi), n, int(m0), L, D, _ptr(h), _ptr(w), len(w), k_begin, k_end, _ptr(out))
     else:
         xc = np.ascontiguousarray(x, np.complex128)
         rc = lib.orc_demod_f64(_ptr(xc), n, L, D, _ptr(h), _ptr(w), len(w), k_begin, k_end, _ptr(out))
@@ -248,18 +254,20 @@ def chirp_synth(start_word: int, rate_word: int, amp: float, m0: int, n: int) ->
 
 
 def chirp_demod(x: np.ndarray, L: int, D: int, h: np.ndarray, start_words, rate_words,
-                k_begin: int = 0, k_end: int | None = None) -> np.ndarray:
-    """Demodulation against chirps; x int16 [n, 2]; returns complex128 [n_chirps, nk]."""
+                k_begin: int = 0, k_end: int | None = None, m0: int = 0) -> np.ndarray:
+    """Demodulation against chirps; x int16 [n, 2], x[i] the sample at absolute
+    index m0 + i (earlier samples zero), absolute frame indices; returns
+    complex128 [n_chirps, nk]."""
     lib = _load()
     h = np.ascontiguousarray(h, np.float64)
     sw = np.ascontiguousarray(np.asarray(start_words, dtype=np.uint64))
     rw = np.ascontiguousarray(np.asarray(rate_words, dtype=np.uint64))
     n = x.shape[0]
     if k_end is None:
-        k_end = n // D
+        k_end = (m0 + n) // D
     out = np.empty((len(sw), k_end - k_begin), np.complex128)
     xi = np.ascontiguousarray(x, np.int16)
-    _check(lib.orc_chirp_demod_i16(_ptr(xi), n, L, D, _ptr(h), _ptr(sw), _ptr(rw), len(sw), k_begin,
+    _check(lib.orc_chirp_demod_i16(_ptr(xi), n, int(m0), L, D, _ptr(h), _ptr(sw), _ptr(rw), len(sw), k_begin,
                                    k_end, _ptr(out)), "chirp_demod")
     return out
 

@@ -375,9 +375,11 @@ int orc_pfb_i16(const int16_t* iq, int64_t n_samples, int32_t n_chan, int32_t ta
 
 /* PFB with a hop of H samples between frames (H = N: the critically sampled
  * PFB above; H < N: oversampled), on the complex int16 stream, each sample
- * promoted to FP64 exactly.  Frame k uses the M = N*T samples that end at
- * sample (k+1)*H - 1, i.e. start at s_k = (k+1)*H - M (samples before 0 are
- * zero), and its channels keep the phase of the absolute time origin:
+ * promoted to FP64 exactly.  iq[i] is the sample at ABSOLUTE stream index
+ * m0 + i (m0 = 0: the stream start); samples before m0 are zero.  Frame k
+ * (an absolute frame index) uses the M = N*T samples that end at sample
+ * (k+1)*H - 1, i.e. start at s_k = (k+1)*H - M, and its channels keep the
+ * phase of the absolute time origin:
  *   v_k[p] = sum_{t<T} h[t*N + p] * x[s_k + t*N + p]
  *   y_k[c] = sum_p v_k[p] exp(-2*pi*i*c*(s_k + p)/N)
  * so channel c is the stream mixed down by exp(-2*pi*i*c*m/N) and filtered,
@@ -385,12 +387,12 @@ int orc_pfb_i16(const int16_t* iq, int64_t n_samples, int32_t n_chan, int32_t ta
  * H = N, s_k is a multiple of N and the factor is 1).  The exponent depends
  * on (s_k + p) mod N only, so y_k is the FFT of v_k circularly shifted by
  * s_k mod N: u[(p + s) mod N] = v_k[p]. */
-int orc_pfb_hop_i16(const int16_t* iq, int64_t n_samples, int32_t n_chan, int32_t taps, int32_t hop,
-                    const double* h, int64_t k_begin, int64_t k_end,
+int orc_pfb_hop_i16(const int16_t* iq, int64_t n_samples, int64_t m0, int32_t n_chan, int32_t taps,
+                    int32_t hop, const double* h, int64_t k_begin, int64_t k_end,
                     double* full, const int32_t* bins, int32_t n_bins, double* tones)
 {
     if (!iq || n_chan <= 0 || taps <= 0 || hop <= 0 || !h || k_begin < 0 || k_end < k_begin) return -1;
-    if (k_end * (int64_t)hop > n_samples) return -1;
+    if (m0 < 0 || k_end * (int64_t)hop - m0 > n_samples) return -1;
     if (n_bins > 0 && (!bins || !tones)) return -1;
     for (int32_t s = 0; s < n_bins; ++s)
         if (bins[s] < 0 || bins[s] >= n_chan) return -1;
@@ -409,9 +411,9 @@ int orc_pfb_hop_i16(const int16_t* iq, int64_t n_samples, int32_t n_chan, int32_
             double ar = 0.0, ai = 0.0;
             for (int64_t t = 0; t < taps; ++t) {
                 const int64_t idx = start + t * n + p;
-                if (idx < 0) continue;                /* zero history */
-                ar += h[t * n + p] * (double)iq[2 * idx];
-                ai += h[t * n + p] * (double)iq[2 * idx + 1];
+                if (idx < m0) continue;               /* zero before the first sample */
+                ar += h[t * n + p] * (double)iq[2 * (idx - m0)];
+                ai += h[t * n + p] * (double)iq[2 * (idx - m0) + 1];
             }
             v[2 * p] = ar;
             v[2 * p + 1] = ai;
@@ -472,13 +474,17 @@ int orc_demod_f64(const double* x, int64_t n_samples, int32_t L, int32_t D,
     return 0;
 }
 
-/* The same on a complex int16 stream (exact promotion of the samples). */
-int orc_demod_i16(const int16_t* iq, int64_t n_samples, int32_t L, int32_t D,
+/* The same on a complex int16 stream (exact promotion of the samples) that
+ * starts at ABSOLUTE sample index m0 >= 0: iq[i] is sample m0 + i, samples
+ * before m0 are zero, frame indices k are absolute (b_k = (k+1)*D - L) and
+ * the NCO phase is w * (absolute index) mod 2^64.  m0 = 0 is the stream
+ * start with zero history. */
+int orc_demod_i16(const int16_t* iq, int64_t n_samples, int64_t m0, int32_t L, int32_t D,
                   const double* h, const uint64_t* words, int32_t n_sel,
                   int64_t k_begin, int64_t k_end, double* out)
 {
-    if (!iq || L <= 0 || D <= 0 || k_end < k_begin) return -1;
-    if (k_end * (int64_t)D > n_samples) return -1;
+    if (!iq || L <= 0 || D <= 0 || m0 < 0 || k_begin < 0 || k_end < k_begin) return -1;
+    if (k_end * (int64_t)D - m0 > n_samples) return -1;
     if (n_sel > 0 && (!words || !out)) return -1;
     const int64_t nk = k_end - k_begin;
     for (int32_t s = 0; s < n_sel; ++s) {
@@ -487,10 +493,10 @@ int orc_demod_i16(const int16_t* iq, int64_t n_samples, int32_t L, int32_t D,
             double ar = 0.0, ai = 0.0;
             for (int64_t n = 0; n < L; ++n) {
                 const int64_t m = b + n;
-                if (m < 0) continue;
+                if (m < m0) continue;
                 double cr, ci;
                 orc_mixer(orc_nco_phase(words[s], (uint64_t)m), &cr, &ci);
-                const double xr = (double)iq[2 * m], xi = (double)iq[2 * m + 1];
+                const double xr = (double)iq[2 * (m - m0)], xi = (double)iq[2 * (m - m0) + 1];
                 ar += h[n] * (xr * cr - xi * ci);
                 ai += h[n] * (xr * ci + xi * cr);
             }
@@ -544,15 +550,17 @@ int orc_chirp_synth(uint64_t start_word, uint64_t rate_word, double amp, int64_t
     return 0;
 }
 
-/* Demodulation against chirps (Sec. III.C, "using the algorithm outlined in
- * section III.B"): as orc_demod_i16 with the linear NCO phase replaced by the
- * chirp phase p(m): for each chirp s and frame k, b_k = (k+1)*D - L,
+/* Demodulation against chirps (Sec. III.C, demodulated by the method of
+ * Sec. III.B): as orc_demod_i16 (same absolute origin m0) with the linear NCO
+ * phase replaced by the chirp phase p(m): for each chirp s and frame k,
+ * b_k = (k+1)*D - L,
  *   out[s][k] = sum_{n<L} h[n] * x[b_k+n] * exp(-i*2*pi*p_s(b_k+n)/2^64). */
-int orc_chirp_demod_i16(const int16_t* iq, int64_t n_samples, int32_t L, int32_t D, const double* h,
-                        const uint64_t* start_words, const uint64_t* rate_words, int32_t n_sel,
-                        int64_t k_begin, int64_t k_end, double* out)
+int orc_chirp_demod_i16(const int16_t* iq, int64_t n_samples, int64_t m0, int32_t L, int32_t D,
+                        const double* h, const uint64_t* start_words, const uint64_t* rate_words,
+                        int32_t n_sel, int64_t k_begin, int64_t k_end, double* out)
 {
-    if (!iq || L <= 0 || D <= 0 || k_end < k_begin || k_end * (int64_t)D > n_samples) return -1;
+    if (!iq || L <= 0 || D <= 0 || m0 < 0 || k_begin < 0 || k_end < k_begin) return -1;
+    if (k_end * (int64_t)D - m0 > n_samples) return -1;
     if (n_sel > 0 && (!start_words || !rate_words || !out)) return -1;
     const int64_t nk = k_end - k_begin;
     for (int32_t s = 0; s < n_sel; ++s) {
@@ -561,10 +569,10 @@ int orc_chirp_demod_i16(const int16_t* iq, int64_t n_samples, int32_t L, int32_t
             double ar = 0.0, ai = 0.0;
             for (int64_t n = 0; n < L; ++n) {
                 const int64_t m = b + n;
-                if (m < 0) continue;
+                if (m < m0) continue;
                 double cr, ci;
                 orc_mixer(orc_chirp_phase(start_words[s], rate_words[s], m), &cr, &ci);
-                const double xr = (double)iq[2 * m], xi = (double)iq[2 * m + 1];
+                const double xr = (double)iq[2 * (m - m0)], xi = (double)iq[2 * (m - m0) + 1];
                 ar += h[n] * (xr * cr - xi * ci);
                 ai += h[n] * (xr * ci + xi * cr);
             }

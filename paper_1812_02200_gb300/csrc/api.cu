@@ -132,8 +132,32 @@ rfr_status debug_check(rfr_plan* p, cudaStream_t st, const char* what) {
     return check_status(p);
 }
 
-// F0 < 0: size the rotation table for the worst alignment of the first frame
-rfr_status ensure_demod_scratch(rfr_plan* p, int64_t F, int64_t F0) {
+// Growth synchronises the device and allocates, which a stream capture
+// cannot contain: refused (RFR_E_INVALID) while `st` is being captured.
+rfr_status refuse_growth_in_capture(rfr_plan* p, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    RFR_CUDA(p, cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone)
+        return fail(p, RFR_E_INVALID,
+                    "demodulation scratch must grow for this push size: push once outside stream capture first");
+    return RFR_OK;
+}
+
+// F0 < 0: size the rotation table for the worst alignment of the first frame.
+// st: the stream of the push that needs the scratch (checked for capture).
+rfr_status ensure_demod_scratch(rfr_plan* p, int64_t F, int64_t F0, cudaStream_t st) {
+    {
+        const int64_t rows3 = p->demod_products == 3
+                                  ? static_cast<int64_t>(rfr::demod3_xs_rows(F, p->Lpad3, p->D)) : 0;
+        const int64_t rows = p->demod_products == 3 ? 0 : static_cast<int64_t>(rfr::demod_xs_rows(F, p->Lpad, p->D));
+        const int64_t ntp = p->demod_products == 3 ? p->ntp3 : p->ntp;
+        const int64_t anchors = F0 >= 0 ? rfr::demod_anchor_rows(F0, F) : (F + rfr::kDemodBM - 2) / rfr::kDemodBM + 1;
+        const int64_t rot = anchors * ntp + ntp * rfr::kDemodBM;
+        if (rows3 > p->xs3_rows_cap || rows > p->xs_rows_cap || rot > p->rot_cap) {
+            const rfr_status rs = refuse_growth_in_capture(p, st);
+            if (rs != RFR_OK) return rs;
+        }
+    }
     if (p->demod_products == 3) {
         // six fp16 planes [rows][D] of the Gauss three-product form
         const int64_t rows3 = static_cast<int64_t>(rfr::demod3_xs_rows(F, p->Lpad3, p->D));
@@ -190,7 +214,7 @@ rfr_status ensure_scratch(rfr_plan* p, int64_t n) {
     // later pushes of up to n samples never allocate (nor synchronise)
     const int64_t F = frames_for_len(p, std::max<int64_t>(p->cl, p->W - 1) + n);
     if (p->mode == RFR_MODE_PFB && p->gen && F > 0) RFR_CUDA(p, rfr::gen_plan_reserve(&p->gplan, F));
-    if (p->mode == RFR_MODE_DEMOD && F > 0 && !p->words.empty()) return ensure_demod_scratch(p, F, -1);
+    if (p->mode == RFR_MODE_DEMOD && F > 0 && !p->words.empty()) return ensure_demod_scratch(p, F, -1, nullptr);
     return RFR_OK;
 }
 
@@ -258,7 +282,7 @@ rfr_status push_core(rfr_plan* p, const int16_t* iq, int64_t n, const rfr_output
             RFR_CUDA(p, rfr::chirp_demod_launch(L, st));
         } else {
             if (!p->words.empty()) {
-                rfr_status rs = ensure_demod_scratch(p, F, p->frames);
+                rfr_status rs = ensure_demod_scratch(p, F, p->frames, st);
                 if (rs != RFR_OK) return rs;
                 rfr::DemodLaunch L{};
                 L.carry = carry;
@@ -833,6 +857,14 @@ rfr_status rfr_wait_selftest(int64_t limit_ns, int32_t* device_status) {
     if (e1 != cudaSuccess || e2 != cudaSuccess) return RFR_E_CUDA;
     if (device_status) *device_status = st;
     return st == DEV_TIMEOUT ? RFR_E_TIMEOUT : RFR_OK;
+}
+
+rfr_status rfr_plan_inject_device_status(rfr_plan* p, int32_t status) {
+    if (!p || status < DEV_OK || status > rfr::DEV_BADARG) return RFR_E_INVALID;
+    RFR_CUDA(p, cudaDeviceSynchronize());
+    const int v = status;
+    RFR_CUDA(p, cudaMemcpy(p->d_status, &v, sizeof(int), cudaMemcpyHostToDevice));
+    return RFR_OK;
 }
 
 rfr_status rfr_plan_seek(rfr_plan* p, int64_t start_sample, const int16_t* history, int64_t n_history) {

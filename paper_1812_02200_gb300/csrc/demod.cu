@@ -938,3 +938,17 @@ extern "C" rfr_status rfr_demod_noalloc(const int16_t* iq, int64_t n_samples, co
     demod_gemm_kernel<<<std::min(n_mt * g.n_nt, std::max(n_sms, 1)), GEMM_THREADS, GEMM_SMEM, st>>>(mAh, mAl, mBh, mBl, g);
     return cudaGetLastError() == cudaSuccess ? RFR_OK : RFR_E_CUDA;
 }
+
+extern "C" rfr_status rfr_demod_noalloc_status(void* stream, int32_t* device_status) {
+    using namespace rfr;
+    unsigned char* base = nullptr;
+    if (na_scratch(&base) != cudaSuccess) return RFR_E_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int v = 0;
+    if (cudaMemcpyAsync(&v, base + kNaStatus, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return RFR_E_CUDA;
+    if (device_status) *device_status = v;
+    if (v == DEV_TIMEOUT) return RFR_E_TIMEOUT;
+    return v == DEV_OK ? RFR_OK : RFR_E_CUDA;
+}

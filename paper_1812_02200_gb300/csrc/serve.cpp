@@ -17,7 +17,10 @@
 //     in order because they share one stream, which also keeps its filter
 //     history and NCO phase consistent on the device;
 //   - completions (event done) release their memory and are reported through
-//     rfr_server_poll with submit/admit/done timestamps.
+//     rfr_server_poll with submit/admit/done timestamps; each request also
+//     copies its plan's device status word to pinned host memory (and clears
+//     it) before its event, so a device-side wait that gave up during that
+//     request is reported as that request's RFR_E_TIMEOUT.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -34,6 +37,7 @@
 #include <thread>
 #include <vector>
 
+#include "dev_common.cuh"
 #include "rfr_internal.h"
 #include "trace.h"
 
@@ -116,7 +120,7 @@ struct Request {
 struct InFlight {
     Request rq;
     size_t off = 0, bytes = 0;
-    cudaEvent_t ev = nullptr;
+    int slot = -1;          // index of its completion event and status snapshot
     int64_t frames = 0;
     double t_admit = 0;
 };
@@ -135,7 +139,9 @@ struct rfr_server {
     std::deque<rfr_completion> done;        // guarded by mu
     std::deque<Request> waiting;            // worker only
     std::vector<InFlight> in_flight;        // worker only
-    std::vector<cudaEvent_t> event_pool;    // worker only
+    std::vector<cudaEvent_t> events;        // one per slot
+    int* h_status = nullptr;                // pinned: device status word per slot
+    std::vector<int> free_slots;            // worker only
     std::atomic<bool> stop{false};
     std::thread worker;
     std::atomic<int64_t> n_submitted{0}, n_admitted{0}, n_completed{0}, n_queued{0}, n_inflight{0};
@@ -180,7 +186,7 @@ void worker_loop(rfr_server* s) {
             }
         }
         // admission in arrival order while memory allows
-        while (!s->waiting.empty() && !s->event_pool.empty()) {
+        while (!s->waiting.empty() && !s->free_slots.empty()) {
             Request& rq = s->waiting.front();
             rfr_plan* p = s->plans[rq.readout];
             const bool host_in = rq.n > 0 && host_pointer(rq.iq);
@@ -195,8 +201,8 @@ void worker_loop(rfr_server* s) {
             f.frames = F;
             f.t_admit = now_us();
             rfr::TraceRange tr("rfr_server_admit");
-            f.ev = s->event_pool.back();
-            s->event_pool.pop_back();
+            f.slot = s->free_slots.back();
+            s->free_slots.pop_back();
             cudaStream_t st = s->streams[rq.readout];
             char* cur = s->arena.ptr(off);
             const int16_t* dev_in = rq.iq;
@@ -236,7 +242,11 @@ void worker_loop(rfr_server* s) {
                 s->error = rs;
                 s->last_error = p->last_error;
             }
-            cudaEventRecord(f.ev, st);
+            // this request's device status (a bounded wait that gave up),
+            // then cleared so the readout's next request starts clean
+            cudaMemcpyAsync(&s->h_status[f.slot], p->d_status, sizeof(int), cudaMemcpyDeviceToHost, st);
+            cudaMemsetAsync(p->d_status, 0, sizeof(int), st);
+            cudaEventRecord(s->events[f.slot], st);
             f.frames = rs == RFR_OK ? got : 0;
             s->in_flight.push_back(f);
             s->waiting.pop_front();
@@ -246,7 +256,7 @@ void worker_loop(rfr_server* s) {
         // completions
         for (size_t i = 0; i < s->in_flight.size();) {
             InFlight& f = s->in_flight[i];
-            const cudaError_t q = cudaEventQuery(f.ev);
+            const cudaError_t q = cudaEventQuery(s->events[f.slot]);
             if (q == cudaErrorNotReady) {
                 ++i;
                 continue;
@@ -256,13 +266,16 @@ void worker_loop(rfr_server* s) {
             c.readout = f.rq.readout;
             c.status = q == cudaSuccess ? RFR_OK : RFR_E_CUDA;
             if (q != cudaSuccess) cudaGetLastError();
+            const int dev_status = s->h_status[f.slot];
+            if (c.status == RFR_OK && dev_status == rfr::DEV_TIMEOUT) c.status = RFR_E_TIMEOUT;
+            else if (c.status == RFR_OK && dev_status != rfr::DEV_OK) c.status = RFR_E_CUDA;
             c.frames = f.frames;
             c.samples = f.rq.n;
             c.t_submit_us = f.rq.t_submit;
             c.t_admit_us = f.t_admit;
             c.t_done_us = now_us();
             s->arena.release(f.off, f.bytes);
-            s->event_pool.push_back(f.ev);
+            s->free_slots.push_back(f.slot);
             {
                 std::lock_guard<std::mutex> lk(s->mu);
                 s->done.push_back(c);
@@ -280,7 +293,9 @@ void server_free(rfr_server* s) {
     if (!s) return;
     for (auto st : s->streams)
         if (st) cudaStreamDestroy(st);
-    for (auto e : s->event_pool) cudaEventDestroy(e);
+    for (auto e : s->events)
+        if (e) cudaEventDestroy(e);
+    if (s->h_status) cudaFreeHost(s->h_status);
     delete s;
 }
 
@@ -322,12 +337,21 @@ rfr_status rfr_server_create(rfr_server** out, rfr_plan* const* plans, int32_t n
             server_free(s);
             return RFR_E_CUDA;
         }
-    s->event_pool.resize(static_cast<size_t>(n) * 8 + 64, nullptr);
-    for (auto& e : s->event_pool)
+    const size_t slots = static_cast<size_t>(n) * 8 + 64;
+    s->events.resize(slots, nullptr);
+    for (auto& e : s->events)
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
             server_free(s);
             return RFR_E_CUDA;
         }
+    if (cudaHostAlloc(reinterpret_cast<void**>(&s->h_status), slots * sizeof(int), cudaHostAllocDefault) !=
+        cudaSuccess) {
+        s->h_status = nullptr;
+        server_free(s);
+        return RFR_E_NOMEM;
+    }
+    std::memset(s->h_status, 0, slots * sizeof(int));
+    for (size_t i = 0; i < slots; ++i) s->free_slots.push_back(static_cast<int>(slots - 1 - i));
     s->worker = std::thread(worker_loop, s);
     *out = s;
     return RFR_OK;

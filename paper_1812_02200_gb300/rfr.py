@@ -111,6 +111,8 @@ _SIGS = {
     "rfr_tx_error_bound": (C.c_double, [_P]),
     "rfr_tx_destroy": (None, [_P]),
     "rfr_demod_noalloc": (C.c_int, [_P, C.c_int64, _P, C.c_int32, C.c_int32, _P, C.c_int32, _P, C.c_int64, _P]),
+    "rfr_demod_noalloc_status": (C.c_int, [_P, C.POINTER(C.c_int32)]),
+    "rfr_plan_inject_device_status": (C.c_int, [_P, C.c_int32]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -339,6 +341,11 @@ class Plan:
         `history` = the samples just before it (int16 [n, 2] tensor)."""
         n = 0 if history is None else history.shape[0]
         self._check(_lib.rfr_plan_seek(self._h, int(start_sample), _ptr(history), n), "seek")
+
+    def inject_device_status(self, status: int):
+        """Write the plan's device status word as a timed-out kernel would
+        (1), or clear it (0): host-side failure injection for tests."""
+        self._check(_lib.rfr_plan_inject_device_status(self._h, int(status)), "inject_device_status")
 
     def autotune(self, n_samples: int, use_cache: bool = True) -> float:
         ms = C.c_double()

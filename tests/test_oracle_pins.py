@@ -498,3 +498,97 @@ def test_pfb_half_hop_odd_frames_are_the_critically_sampled_frames():
     crit = oracle.pfb(x, N, T, h)["full"]
     half = oracle.pfb_hop(x, N, T, N // 2, h)["full"]
     assert np.allclose(half[1::2][: crit.shape[0]], crit[: half[1::2].shape[0]], rtol=1e-12, atol=1e-8)
+
+
+# ------------------------------------------------ absolute stream origin
+def _turns_to_phasor(phase_u64: int) -> complex:
+    """exp(-i 2 pi phase / 2^64) for a phase given as a Python integer."""
+    p = phase_u64 % 2 ** 64
+    s = p - 2 ** 64 if p >= 2 ** 63 else p
+    return complex(np.exp(-1j * np.pi * (s / 2 ** 63)))
+
+
+@pytest.mark.parametrize("m0", [1, 17, 96, 250])
+def test_absolute_origin_equals_zero_padded_stream(m0):
+    """A stream that starts at absolute sample m0 (zero before it) is the
+    zero-padded stream [0]*m0 + x seen from 0: the same frames, bit for bit,
+    for the demodulator, the chirp demodulator and the oversampled PFB."""
+    r = np.random.default_rng(40 + m0)
+    x = r.integers(-8192, 8192, size=(700, 2)).astype(np.int16)
+    xp = np.concatenate([np.zeros((m0, 2), np.int16), x])
+    L, D = 48, 16
+    h = oracle.lowpass("hann", L, 0.03)
+    ws = [int(v) for v in r.integers(0, 2 ** 64, 3, dtype=np.uint64)]
+    rs = [int(v) for v in r.integers(0, 2 ** 64, 3, dtype=np.uint64)]
+    k0, k1 = 2, (m0 + 700) // D
+    assert np.array_equal(oracle.demod(x, L, D, h, ws, k0, k1, m0=m0), oracle.demod(xp, L, D, h, ws, k0, k1))
+    assert np.array_equal(oracle.chirp_demod(x, L, D, h, ws, rs, k0, k1, m0=m0),
+                          oracle.chirp_demod(xp, L, D, h, ws, rs, k0, k1))
+    N, T, H = 12, 3, 8
+    hp = np.linspace(0.2, 1.1, N * T)
+    a = oracle.pfb_hop(x, N, T, H, hp, 1, (m0 + 700) // H, bins=[0, 5], m0=m0)
+    b = oracle.pfb_hop(xp, N, T, H, hp, 1, (m0 + 700) // H, bins=[0, 5])
+    assert np.array_equal(a["full"], b["full"]) and np.array_equal(a["tones"], b["tones"])
+
+
+LARGE_ORIGINS = [2 ** 31 + 3 * 64, 2 ** 40 + 5 * 64, 2 ** 62 + 7 * 64]
+
+
+@pytest.mark.parametrize("m0", LARGE_ORIGINS)
+def test_demod_far_origin_is_the_shifted_phase(m0):
+    """Time shift of the NCO (Sec. III.B mixer): the same samples placed at
+    absolute origin m0 (a multiple of D) give, frame for frame, the origin-0
+    output times exp(-i 2 pi (w m0 mod 2^64) / 2^64), the factor formed from
+    Python integers.  Checks the uint64 phase of the oracle far past 2^31,
+    2^40 and 2^62 samples."""
+    L, D = 128, 64
+    r = np.random.default_rng(m0 % 1000)
+    x = r.integers(-8192, 8192, size=(D * 12, 2)).astype(np.int16)
+    h = oracle.lowpass("blackman", L, 0.01)
+    ws = [int(v) for v in r.integers(0, 2 ** 64, 4, dtype=np.uint64)]
+    K0 = m0 // D
+    near = oracle.demod(x, L, D, h, ws, 0, 12)
+    far = oracle.demod(x, L, D, h, ws, K0, K0 + 12, m0=m0)
+    for s, w in enumerate(ws):
+        ref = near[s] * _turns_to_phasor(w * m0)
+        assert np.max(np.abs(far[s] - ref)) < 1e-11 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("m0", LARGE_ORIGINS)
+def test_chirp_far_origin_is_a_shifted_chirp(m0):
+    """Eq. 1 in sample units is quadratic: p(m0 + j) = p(m0) + (s + 2 r m0) j
+    + r j^2 (mod 2^64).  So demodulating at origin m0 against (s, r) equals
+    demodulating at 0 against (s + 2 r m0, r), times exp(-i 2 pi p(m0) / 2^64),
+    all words from Python integers."""
+    L, D = 128, 64
+    r = np.random.default_rng(m0 % 997)
+    x = r.integers(-8192, 8192, size=(D * 12, 2)).astype(np.int16)
+    h = oracle.lowpass("hann", L, 0.01)
+    ss = [int(v) for v in r.integers(0, 2 ** 64, 3, dtype=np.uint64)]
+    rr = [int(v) for v in r.integers(0, 2 ** 40, 3, dtype=np.uint64)]
+    K0 = m0 // D
+    far = oracle.chirp_demod(x, L, D, h, ss, rr, K0, K0 + 12, m0=m0)
+    for i, (s, q) in enumerate(zip(ss, rr)):
+        s2 = (s + 2 * q * m0) % 2 ** 64
+        near = oracle.chirp_demod(x, L, D, h, [s2], [q], 0, 12)[0]
+        ref = near * _turns_to_phasor(s * m0 + q * m0 * m0)
+        assert np.max(np.abs(far[i] - ref)) < 1e-11 * np.max(np.abs(ref))
+        assert oracle.chirp_phase(s, q, m0) == (s * m0 + q * m0 * m0) % 2 ** 64
+
+
+@pytest.mark.parametrize("m0", [2 ** 31 + 3 * 8, 2 ** 40 + 5 * 8, 2 ** 62 + 8 * 8])
+def test_pfb_hop_far_origin_is_the_channel_phase(m0):
+    """Channels keep the absolute time origin's phase: moving the same samples
+    to origin m0 (a multiple of the hop) multiplies channel c by
+    exp(-2 pi i c (m0 mod N) / N) (N = 12, so m0 mod N is not 0)."""
+    N, T, H = 12, 4, 8
+    assert m0 % N != 0
+    r = np.random.default_rng(m0 % 991)
+    x = r.integers(-8192, 8192, size=(H * 20, 2)).astype(np.int16)
+    h64, _ = oracle.pfb_prototype(N, T, "kaiser", 9.0)
+    K0 = m0 // H
+    near = oracle.pfb_hop(x, N, T, H, h64, 0, 20)["full"]
+    far = oracle.pfb_hop(x, N, T, H, h64, K0, K0 + 20, m0=m0)["full"]
+    c = np.arange(N)
+    ref = near * np.exp(-2j * np.pi * c * (m0 % N) / N)[None, :]
+    assert np.max(np.abs(far - ref)) < 1e-11 * np.max(np.abs(ref))

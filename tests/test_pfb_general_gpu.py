@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 import siggen
-from helpers import TOL, rel_channels_vs_rms, rel_rows
+from helpers import STRICT_NOISE_BOUND, TOL, full_spectrum_errors, rel_channels_vs_rms, rel_rows
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -70,9 +70,12 @@ def test_any_n_parity(lib, N, T, win, beta, frames):
     ref = oracle.pfb(case["x"], N, T, h32o.astype(np.float64), bins=bins)
     e_t = rel_rows(tones, ref["tones"])
     e_f = rel_channels_vs_rms(full, ref["full"])
-    print(f"N={N} T={T}: max tone rel err {e_t.max():.3e}, max channel err {e_f.max():.3e}")
+    fe = full_spectrum_errors(full, ref["full"], bins)
+    print(f"N={N} T={T}: max tone rel err {e_t.max():.3e}, max channel err {e_f.max():.3e}; strict: tone "
+          f"channels {fe['strict_tone_max']:.3e}, noise-only channels {fe['strict_noise_max']:.3e}")
     assert e_t.max() < TOL, e_t.max()
     assert e_f.max() < TOL, e_f.max()
+    assert fe["strict_tone_max"] < TOL and fe["strict_noise_max"] < STRICT_NOISE_BOUND
     assert np.array_equal(tones, full[:, bins].T)     # the gather is an exact copy
 
 

@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 import siggen
-from helpers import TOL, rel_channels_vs_rms, rel_rows
+from helpers import STRICT_NOISE_BOUND, TOL, full_spectrum_errors, rel_channels_vs_rms, rel_rows
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -53,9 +53,13 @@ def test_c1_full_size_parity(lib):
     ref = oracle.pfb(c["x"], N, T, h32o.astype(np.float64), bins=bins)
     e_t = rel_rows(tones, ref["tones"])
     e_f = rel_channels_vs_rms(full, ref["full"])
-    print(f"c1 max tone rel err {e_t.max():.3e}, max full-channel err {e_f.max():.3e}")
+    fe = full_spectrum_errors(full, ref["full"], bins)
+    print(f"c1 max tone rel err {e_t.max():.3e}, max full-channel err {e_f.max():.3e}; strict per-channel: "
+          f"tone channels {fe['strict_tone_max']:.3e}, noise-only channels max {fe['strict_noise_max']:.3e} "
+          f"(median {fe['strict_noise_median']:.3e})")
     assert e_t.max() < TOL
     assert e_f.max() < TOL
+    assert fe["strict_tone_max"] < TOL and fe["strict_noise_max"] < STRICT_NOISE_BOUND
     assert np.array_equal(tones, full[:, bins].T)   # gather is an exact copy
 
 
@@ -89,8 +93,12 @@ def test_pfb_parity_shapes(lib, N, T, win, beta, frames):
     ref = oracle.pfb(case["x"], N, T, _oracle_taps(N, T, win, beta), bins=plan.bins())
     e_t = rel_rows(tones, ref["tones"])
     e_f = rel_channels_vs_rms(full, ref["full"])
+    fe = full_spectrum_errors(full, ref["full"], plan.bins())
+    print(f"N={N} T={T}: tones {e_t.max():.3e}, full (max(own, RMS)) {e_f.max():.3e}, strict tone channels "
+          f"{fe['strict_tone_max']:.3e}, strict noise-only channels {fe['strict_noise_max']:.3e}")
     assert e_t.max() < TOL, e_t.max()
     assert e_f.max() < TOL, e_f.max()
+    assert fe["strict_tone_max"] < TOL and fe["strict_noise_max"] < STRICT_NOISE_BOUND
 
 
 @pytest.mark.parametrize("N,T", [(64, 4), (4096, 8), (1024, 16)])

@@ -141,3 +141,26 @@ def test_server_refuses_request_larger_than_budget(lib):
     with pytest.raises(lib.RfrError):
         srv.submit(5, torch.zeros((16, 2), dtype=torch.int16).pin_memory())
     srv.close()
+
+
+def test_server_reports_a_device_timeout_for_that_request_only(lib):
+    """Failure detection without a GPU fault: the plan's device status word is
+    set on the host (as a kernel whose bounded wait gave up would set it); the
+    next request completes with RFR_E_TIMEOUT, the one after it with RFR_OK."""
+    N, hop = 1024, 1024
+    c = siggen.pfb_case(N * 40, N, 8, seed=3)
+    p = lib.Plan(N, 4, window="hann", words=c["words"], full=False)
+    srv = lib.Server([p], 64 << 20, N * 20)
+    x = torch.from_numpy(c["x"]).to(DEV)
+    out = torch.zeros((8, 40), dtype=torch.complex64, device=DEV)
+    p.inject_device_status(1)
+    got = {}
+    for tag, (a, b) in enumerate([(0, N * 20), (N * 20, N * 40)]):
+        srv.submit(0, x[a:b], tones=out, frame_offset=a // hop, tag=tag)
+        while tag not in got:
+            for d in srv.poll(8, wait_ms=100):
+                got[d["tag"]] = d
+    srv.close()
+    assert got[0]["status"] == lib.E_TIMEOUT
+    assert got[1]["status"] == lib.OK
+    p.close()
