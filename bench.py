@@ -868,6 +868,7 @@ def run_serve(args, dev):
         stop[0] = True
         pt.join(timeout=180)
         lat = np.array([d["t_done_us"] - d["t_submit_us"] for d in done]) / 1e3
+        wait = np.array([d["t_admit_us"] - d["t_submit_us"] for d in done]) / 1e3
         t_first = min(d["t_submit_us"] for d in done)
         t_last = max(d["t_done_us"] for d in done)
         tot = float(sum(d["samples"] for d in done))
@@ -876,7 +877,8 @@ def run_serve(args, dev):
                 "offered_realised_gsps": tot / (t_sub_end * 1e-6) / 1e9,
                 "sustained_gsps": tot / ((t_last - t_first) * 1e-6) / 1e9,
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "max_ms": float(lat.max())}
+                "max_ms": float(lat.max()), "admit_wait_p50_ms": float(np.percentile(wait, 50)),
+                "admit_wait_p99_ms": float(np.percentile(wait, 99))}
 
     modes = {}
     for mode, xs, os_, reps in (("host_pinned", host_x, outs, args.serve_reps),
@@ -892,7 +894,9 @@ def run_serve(args, dev):
                   "sustained_gsps": float(np.mean([r["sustained_gsps"] for r in runs])),
                   "p50_ms": float(np.median([r["p50_ms"] for r in runs])),
                   "p99_ms": float(np.median(p99)), "p99_ms_min": float(min(p99)),
-                  "p99_ms_max": float(max(p99)), "max_ms": float(max(r["max_ms"] for r in runs))}
+                  "p99_ms_max": float(max(p99)), "max_ms": float(max(r["max_ms"] for r in runs)),
+                  "admit_wait_p50_ms": float(np.median([r["admit_wait_p50_ms"] for r in runs])),
+                  "admit_wait_p99_ms": float(np.median([r["admit_wait_p99_ms"] for r in runs]))}
             pts.append(pt)
             log(f"[bench] serve {mode} load {load}: {pt}")
         modes[mode] = pts

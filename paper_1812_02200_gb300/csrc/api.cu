@@ -252,6 +252,7 @@ rfr_status push_core(rfr_plan* p, const int16_t* iq, int64_t n, const rfr_output
             L.lookahead = p->tune.pfb_lookahead;
             L.hop = static_cast<int>(p->H);
             L.a0 = p->samples - p->cl;
+            L.sym_taps = p->sym_taps ? 1 : 0;
             if (p->gen && p->gplan.N1 > 1 && p->gplan.z_frames < std::min(F, p->gplan.z_cap_frames)) {
                 // grow the between-pass buffer, unless the stream is being
                 // captured (then the frames go through the buffer in batches)
@@ -476,8 +477,12 @@ rfr_status rfr_plan_create(rfr_plan** out, int32_t channels, int32_t taps, const
         p->h64.resize(M);
         const double fc = window->cutoff > 0.0 ? window->cutoff : 0.5 / channels;
         if (rfr::build_lowpass(window->kind, window->beta, fc, M, p->h64.data()) != 0) return bad(RFR_E_INVALID);
+        // FP32 taps, exactly symmetric like the prototype itself (its FP64
+        // evaluation can differ in the last bit between h[j] and h[M-1-j]):
+        // the rounding of the mean of the two, within one FP32 ulp of either
         p->h32.resize(M);
-        for (int64_t j = 0; j < M; ++j) p->h32[j] = static_cast<float>(p->h64[j]);
+        for (int64_t j = 0; j < M; ++j) p->h32[j] = static_cast<float>(0.5 * (p->h64[j] + p->h64[M - 1 - j]));
+        p->sym_taps = p->Tk == taps;
         // kernel taps: zero-padded at the oldest end to Tk*N
         std::vector<float> hk(static_cast<size_t>(p->Tk) * channels, 0.0f);
         std::copy(p->h32.begin(), p->h32.end(), hk.begin() + static_cast<size_t>(p->Tk - taps) * channels);

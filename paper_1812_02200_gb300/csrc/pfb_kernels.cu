@@ -499,6 +499,311 @@ __global__ void __launch_bounds__(kRingThreads, 1)
     }
 }
 
+// ------------------------------------------------- TMEM, symmetric taps
+// N = 4096, T = 8 with an exactly symmetric prototype, h[j] = h[8N - 1 - j]
+// (the plan builds it so).  Same stream view, TMEM delay line, sum order
+// and outputs as pfb_tmem_kernel (bit-identical results), arranged so that
+// a frame costs two CTA barriers instead of three and no twiddle traffic
+// through shared memory:
+//   - Lanes l and 31 - l of a warp own the mirrored FFT rows tf and 255 - tf
+//     (row tf = the points tf + 256 r).  A thread filters its row's points
+//     r < 8 and the mirror points (255 - tf, 15 - r), whose taps are the same
+//     values in reverse tap order, so it holds 64 tap registers instead of
+//     128; one warp shuffle per value then swaps the mirrored halves so that
+//     every thread has its whole row for the first radix-16 pass.
+//   - The 2 x 15 twiddles of passes 1 and 2 depend only on the row: they
+//     live in registers.
+//   - Three exchange buffers: pass 0 writes B0, pass 1 B1, pass 2 writes the
+//     spectrum to B2 (natural order).  The spectrum of frame j is stored (TMA
+//     bulk) and its tones gathered while pass 1 of frame j + 1 runs, so the
+//     iteration has one barrier after pass 0 and one after pass 1.
+constexpr size_t kSymXb = static_cast<size_t>(4096 + 256) * 8;
+struct SymLayout {
+    size_t b0, b1, b2, bins, tile, bars, total;
+};
+__host__ __device__ __forceinline__ SymLayout sym_layout(int nb) {
+    SymLayout L{};
+    L.b0 = static_cast<size_t>(kTmemStage) * 4096 * 4;
+    L.b1 = L.b0 + kSymXb;
+    L.b2 = L.b1 + kSymXb;
+    size_t o = L.b2 + static_cast<size_t>(4096) * 8;
+    L.bins = o;
+    o = (o + static_cast<size_t>(nb) * 4 + 1023) / 1024 * 1024;
+    L.tile = o;
+    o += static_cast<size_t>((nb + kToneBox - 1) / kToneBox * kToneBox) * kToneGroup * 8;
+    L.bars = o;
+    L.total = o + kTmemStage * 8 + 16;
+    return L;
+}
+
+__global__ void __launch_bounds__(kRingThreads, 1)
+    pfb_tmem_sym_kernel(const PfbArgs a, const __grid_constant__ CUtensorMap tm_tones) {
+    constexpr int N = 4096, NT = 256, T = 8;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int nb_smem = a.nb_smem;
+    const SymLayout lay = sym_layout(nb_smem);
+    uint32_t* stage = reinterpret_cast<uint32_t*>(smem);
+    float2* const B0 = reinterpret_cast<float2*>(smem + lay.b0);
+    float2* const B1 = reinterpret_cast<float2*>(smem + lay.b1);
+    float2* const B2 = reinterpret_cast<float2*>(smem + lay.b2);
+    int32_t* sbins = reinterpret_cast<int32_t*>(smem + lay.bins);
+    float2* tile = reinterpret_cast<float2*>(smem + lay.tile);   // tone t, group frame q at t*kToneGroup + q
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + lay.bars);
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + kTmemStage);
+    volatile int* s_ok = reinterpret_cast<volatile int*>(tmem_holder + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tf = lane < 16 ? 16 * warp + lane : 224 - 16 * warp + lane;   // partner lane 31 - l: 255 - tf
+    const int64_t shift = a.frame_offset & (kToneGroup - 1);
+    const int64_t ja = max_i64(0, static_cast<int64_t>(blockIdx.x) * a.iters_per_cta - shift);
+    const int64_t jb = min_i64(a.F, static_cast<int64_t>(blockIdx.x + 1) * a.iters_per_cta - shift);
+    if (ja >= jb) return;
+    const int64_t b0 = ja, b1 = jb + T - 1;                     // blocks [b0, b1)
+    const int64_t need = (a.F + T - 1) * static_cast<int64_t>(N);
+
+    if (warp == 0) {
+        umma::alloc(tmem_holder, 512);
+        umma::relinquish();
+    }
+    if (tid == 0) {
+        for (int s = 0; s < kTmemStage; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    for (int i = tid; i < nb_smem; i += blockDim.x) sbins[i] = __ldg(a.bins + i);
+    // taps of the own points (tf, q), q < 8; the mirror point (255-tf, 15-q)
+    // takes tap t from H[T-1-t][q]
+    float H[T][8];
+#pragma unroll
+    for (int t = 0; t < T; ++t)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) H[t][q] = __ldg(a.h + t * N + tf + q * NT);
+    float2 w1[15], w2[15];
+    {
+        const int k = tf & 15;
+#pragma unroll
+        for (int r = 1; r < 16; ++r) {
+            w1[r - 1] = __ldg(a.tw + (r - 1) * 16 + k);
+            w2[r - 1] = __ldg(a.tw + 240 + (r - 1) * 256 + tf);
+        }
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tbase = *tmem_holder + (static_cast<uint32_t>(32 * (warp & 3)) << 16) +
+                           static_cast<uint32_t>(256 * (warp >> 2));
+    if (tid == 0)
+        for (int64_t b = b0; b < min_i64(b0 + kTmemStage, b1); ++b)
+            issue_sb_tma(a, b, need, stage + (b % kTmemStage) * N, &bars[b % kTmemStage]);
+
+    // int16 block b (staging slot s) -> FP32 -> the thread's TMEM columns of
+    // slot b mod 8: points (tf, q) then the mirror points (255-tf, 15-m), as
+    // planar pairs (re_q, re_q+1, im_q, im_q+1)
+    auto ingest = [&](int64_t b, int s) {
+        // the phase completed already (thread 0 saw it before the last
+        // barrier); each thread's own wait makes the copy visible to it
+        mbar_wait(&bars[s], static_cast<uint32_t>(((b - b0) / kTmemStage) & 1), a.status);
+        uint32_t xr[32];
+        const uint32_t* sg = stage + s * N;
+#pragma unroll
+        for (int q = 0; q < 16; q += 2) {
+            const int p0 = q < 8 ? tf + q * NT : 4095 - tf - (q - 8) * NT;
+            const int p1 = q < 8 ? tf + (q + 1) * NT : 4095 - tf - (q - 7) * NT;
+            const float2 f0 = iq_to_f2(sg[p0]);
+            const float2 f1 = iq_to_f2(sg[p1]);
+            xr[2 * q] = __float_as_uint(f0.x);
+            xr[2 * q + 1] = __float_as_uint(f1.x);
+            xr[2 * q + 2] = __float_as_uint(f0.y);
+            xr[2 * q + 3] = __float_as_uint(f1.y);
+        }
+        umma::st_32x32b_x32(tbase + 32u * static_cast<uint32_t>(b % kTmemSlots), xr);
+        umma::wait_st();
+    };
+    auto stage_parity = [&](int64_t b) { return static_cast<uint32_t>(((b - b0) / kTmemStage) & 1); };
+
+    // warm-up: the T - 1 blocks before the first frame's last one
+    bool ok = true;
+    for (int64_t b = b0; b < b0 + T - 1; ++b) {
+        const int s = static_cast<int>(b % kTmemStage);
+        const bool got = mbar_wait(&bars[s], stage_parity(b), a.status);
+        if (__syncthreads_or(!got)) {
+            ok = false;
+            break;
+        }
+        ingest(b, s);
+        __syncthreads();                                         // staging slot s read by all
+        if (tid == 0 && b + kTmemStage < b1)
+            issue_sb_tma(a, b + kTmemStage, need, stage + s * N, &bars[s]);
+    }
+    if (ok) {
+        if (tid == 0) *s_ok = mbar_wait(&bars[(b0 + T - 1) % kTmemStage], stage_parity(b0 + T - 1), a.status) ? 1 : 0;
+        __syncthreads();
+        ok = *s_ok != 0;
+    }
+    const bool bulk = a.full_bulk != 0;
+    int64_t jp = -1;                                             // frame whose spectrum is in B2
+    // stores and gathers the spectrum of frame jp (in B2) into the tone tile
+    auto gather = [&](int64_t j) {
+        if (bulk && tid == 0) {
+            tma_bulk_s2g(a.full + (a.frame_offset + j) * a.full_ld, B2, N * 8);
+            bulk_commit();
+        }
+        if (nb_smem > 0) {
+            const int q = static_cast<int>((a.frame_offset + j) & (kToneGroup - 1));
+            int bk[kTonesPerThread];
+#pragma unroll
+            for (int k = 0; k < kTonesPerThread; ++k) bk[k] = tid + k * NT < nb_smem ? sbins[tid + k * NT] : -1;
+            float2 tv[kTonesPerThread];
+#pragma unroll
+            for (int k = 0; k < kTonesPerThread; ++k)
+                if (bk[k] >= 0) tv[k] = B2[bk[k]];
+#pragma unroll
+            for (int k = 0; k < kTonesPerThread; ++k)
+                if (bk[k] >= 0) tile[(tid + k * NT) * kToneGroup + q] = tv[k];
+        } else if (a.n_tones > 0) {
+            float2* col = a.tones + a.frame_offset + j;
+            for (int t = tid; t < a.n_tones; t += NT) col[t * a.tones_ld] = B2[__ldg(a.bins + t)];
+        }
+    };
+    // group of frame j complete (last of a tone group or of the CTA's range)?
+    auto closes_group = [&](int64_t j) {
+        return nb_smem > 0 && ((((a.frame_offset + j) & (kToneGroup - 1)) == kToneGroup - 1) || j == jb - 1);
+    };
+    auto tile_by_tma = [&](int64_t j) {
+        const int q = static_cast<int>((a.frame_offset + j) & (kToneGroup - 1));
+        return a.tones_tma && q == kToneGroup - 1 && j - q >= ja;
+    };
+    // writes the tone group that frame j closed (after a barrier that
+    // follows every thread's gather)
+    auto flush_group = [&](int64_t j) {
+        const int q = static_cast<int>((a.frame_offset + j) & (kToneGroup - 1));
+        if (tile_by_tma(j)) {
+            if (tid == 0) {
+                const int32_t x0 = static_cast<int32_t>(a.frame_offset + j - q);
+                for (int r0 = 0; r0 < nb_smem; r0 += kToneBox)
+                    tma_store_2d(&tm_tones, x0, r0, tile + static_cast<size_t>(r0) * kToneGroup);
+                bulk_commit();
+            }
+        } else {
+            // frames j - q .. j of the group that this CTA produced
+            const int q0 = static_cast<int>(max_i64(0, ja - (j - q)));
+            const int nq = q + 1 - q0;
+            float2* base = a.tones + a.frame_offset + (j - q);
+            for (int it = tid; it < nq * nb_smem; it += NT) {
+                const int t = it / nq, qq = q0 + (it - t * nq);
+                base[static_cast<int64_t>(t) * a.tones_ld + qq] = tile[t * kToneGroup + qq];
+            }
+        }
+    };
+
+    for (int64_t j = ja; ok && j < jb; ++j) {
+        const int64_t b = j + T - 1;                             // the block that completes frame j
+        const int s = static_cast<int>(b % kTmemStage);
+        ingest(b, s);
+        // polyphase FIR, taps in order t = 0..T-1 (slot halves: own points,
+        // then mirror points, the next load in flight during the FMAs)
+        float are[16], aim[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) are[r] = aim[r] = 0.f;
+        uint32_t xa[16], xb[16];
+        umma::ld_32x32b_x16(tbase + 32u * static_cast<uint32_t>(j % kTmemSlots), xa);
+        umma::wait_ld_regs(xa);
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const uint32_t col = tbase + 32u * static_cast<uint32_t>((j + t) % kTmemSlots);
+            umma::ld_32x32b_x16(col + 16u, xb);
+#pragma unroll
+            for (int q = 0; q < 8; q += 2) {
+                ffma2(are[q], are[q + 1], H[t][q], H[t][q + 1], __uint_as_float(xa[2 * q]),
+                      __uint_as_float(xa[2 * q + 1]));
+                ffma2(aim[q], aim[q + 1], H[t][q], H[t][q + 1], __uint_as_float(xa[2 * q + 2]),
+                      __uint_as_float(xa[2 * q + 3]));
+            }
+            umma::wait_ld_regs(xb);
+            if (t + 1 < T)
+                umma::ld_32x32b_x16(tbase + 32u * static_cast<uint32_t>((j + t + 1) % kTmemSlots), xa);
+#pragma unroll
+            for (int m = 0; m < 8; m += 2) {
+                ffma2(are[8 + m], are[9 + m], H[T - 1 - t][m], H[T - 1 - t][m + 1], __uint_as_float(xb[2 * m]),
+                      __uint_as_float(xb[2 * m + 1]));
+                ffma2(aim[8 + m], aim[9 + m], H[T - 1 - t][m], H[T - 1 - t][m + 1],
+                      __uint_as_float(xb[2 * m + 2]), __uint_as_float(xb[2 * m + 3]));
+            }
+            if (t + 1 < T) umma::wait_ld_regs(xa);
+        }
+        // the partner (lane 31 - l) filtered this row's points 8..15
+        float2 v[16];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) v[r] = make_float2(are[r], aim[r]);
+#pragma unroll
+        for (int m = 0; m < 8; ++m)
+            v[15 - m] = make_float2(__shfl_xor_sync(0xffffffffu, are[8 + m], 31),
+                                    __shfl_xor_sync(0xffffffffu, aim[8 + m], 31));
+        // pass 0 -> B0
+        dft16(v);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) B0[fpad(16 * tf + r)] = v[r];
+        if (tid == 0) bulk_wait_read_all();                     // tile stores done reading the tile
+        __syncthreads();                                         // (1) B0 written, staging slot s read
+        if (tid == 0 && b + kTmemStage < b1)
+            issue_sb_tma(a, b + kTmemStage, need, stage + s * N, &bars[s]);
+        // outputs of the previous frame while pass 1 of this one runs
+        if (jp >= 0) gather(jp);
+        {
+            const int k = tf & 15;
+#pragma unroll
+            for (int r = 0; r < 16; ++r) v[r] = B0[fpad(tf + r * NT)];
+#pragma unroll
+            for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], w1[r - 1]);
+            dft16(v);
+            const int base = (tf >> 4) * 256 + k;
+#pragma unroll
+            for (int r = 0; r < 16; ++r) B1[fpad(base + r * 16)] = v[r];
+        }
+        const bool close_prev = jp >= 0 && closes_group(jp);
+        if (close_prev && tile_by_tma(jp)) fence_proxy_async_smem();
+        if (tid == 0) {
+            bulk_wait_read_all();                                // B2 read by its row store
+            *s_ok = (j + 1 < jb) ? (mbar_wait(&bars[(b + 1) % kTmemStage], stage_parity(b + 1), a.status) ? 1 : 0) : 1;
+        }
+        __syncthreads();                                         // (2) B1 written, gathers done
+        if (close_prev) flush_group(jp);
+        {
+#pragma unroll
+            for (int r = 0; r < 16; ++r) v[r] = B1[fpad(tf + r * NT)];
+#pragma unroll
+            for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], w2[r - 1]);
+            dft16(v);                                            // v[r] = bin tf + 256 r
+        }
+        if (a.full && !bulk) {
+            float2* row = a.full + (a.frame_offset + j) * a.full_ld;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) row[tf + i * NT] = v[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) B2[tf + i * NT] = v[i];
+        fence_proxy_async_smem();
+        jp = j;
+        ok = *s_ok != 0;
+    }
+    if (ok && jp >= 0) {
+        if (tid == 0) bulk_wait_read_all();                     // tile stores done reading the tile
+        __syncthreads();                                         // spectrum of the last frame in B2
+        gather(jp);
+        if (closes_group(jp)) {
+            if (tile_by_tma(jp)) fence_proxy_async_smem();
+            __syncthreads();
+            flush_group(jp);
+        }
+    }
+    if (tid == 0) bulk_wait_all();
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        umma::fence_after_sync();
+        umma::dealloc(*tmem_holder, 512);
+    }
+}
+
 // -------------------------------------------------------------- DIRECT
 template <int LOG2N>
 __global__ void __launch_bounds__(1024, 1) pfb_direct_kernel(const PfbArgs a) {
@@ -628,6 +933,39 @@ cudaError_t launch_tmem(PfbArgs a, int n_sms, int max_smem, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+cudaError_t launch_tmem_sym(PfbArgs a, int n_sms, int max_smem, cudaStream_t st) {
+    a.nb_smem = (a.n_tones > 0 && a.n_tones <= kTonesPerThread * kRingThreads &&
+                 sym_layout(a.n_tones).total <= static_cast<size_t>(max_smem))
+                    ? a.n_tones : 0;
+    const size_t smem = sym_layout(a.nb_smem).total;
+    if (smem > static_cast<size_t>(max_smem)) return cudaErrorInvalidConfiguration;
+    const int64_t shift = a.frame_offset & (kToneGroup - 1);
+    const int64_t grid = std::min<int64_t>(a.F, n_sms);
+    a.iters_per_cta = ((a.F + shift + grid - 1) / grid + kToneGroup - 1) / kToneGroup * kToneGroup;
+    const int64_t grid2 = (a.F + shift + a.iters_per_cta - 1) / a.iters_per_cta;
+    a.full_bulk = (a.full != nullptr && (reinterpret_cast<uintptr_t>(a.full) % 16) == 0 &&
+                   (a.full_ld % 2) == 0) ? 1 : 0;
+    CUtensorMap tm;
+    std::memset(&tm, 0, sizeof tm);
+    a.tones_tma = 0;
+    auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tmap_encode_tiled_fn());
+    if (a.nb_smem > 0 && enc && (reinterpret_cast<uintptr_t>(a.tones) % 16) == 0 && (a.tones_ld % 2) == 0 &&
+        a.frame_offset + a.F < (int64_t(1) << 31)) {
+        cuuint64_t dims[2] = {static_cast<cuuint64_t>(a.frame_offset + a.F), static_cast<cuuint64_t>(a.n_tones)};
+        cuuint64_t strides[1] = {static_cast<cuuint64_t>(a.tones_ld) * 8};
+        cuuint32_t box[2] = {kToneGroup, kToneBox};
+        cuuint32_t estr[2] = {1, 1};
+        if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, a.tones, dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+            a.tones_tma = 1;
+    }
+    cudaError_t e = cudaFuncSetAttribute(pfb_tmem_sym_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    pfb_tmem_sym_kernel<<<static_cast<unsigned>(grid2), kRingThreads, smem, st>>>(a, tm);
+    return cudaGetLastError();
+}
+
 template <int LOG2N>
 cudaError_t dispatch_ring_T(PfbArgs a, int tk, int n_sms, int max_smem, int la, cudaStream_t st) {
     switch (tk) {
@@ -670,6 +1008,7 @@ cudaError_t pfb_launch(const PfbLaunch& L, cudaStream_t st) {
     a.use_tma = aligned ? 1 : 0;
     const int lg = L.log2n;
     if (lg == 12 && a.use_tma && L.variant != 1) {
+        if (L.taps_kernel == 8 && L.sym_taps && L.variant != 2) return launch_tmem_sym(a, L.n_sms, L.max_smem, st);
         if (L.taps_kernel == 4) return launch_tmem<4>(a, L.n_sms, L.max_smem, st);
         if (L.taps_kernel == 8) return launch_tmem<8>(a, L.n_sms, L.max_smem, st);
     }

@@ -45,7 +45,9 @@ struct PfbLaunch {
     int n_sms;
     int max_smem;
     int lookahead;      // ring super-blocks fetched ahead (0 = as many as fit, <= 3)
-    int variant;        // 0 = best available, 1 = shared-memory int16 ring only
+    int variant;        // 0 = best available, 1 = shared-memory int16 ring only,
+                        // 2 = no symmetric-tap TMEM kernel
+    int sym_taps;       // kernel taps exactly symmetric (h[j] == h[T*N - 1 - j])
     int hop;            // samples between frames (N: critically sampled)
     int64_t a0;         // absolute sample index of the virtual stream's first sample
 };
@@ -192,6 +194,7 @@ cudaError_t carry_update(const int16_t* old_carry, int64_t cl, const int16_t* bu
 struct rfr_plan {
     int mode = 0;
     int32_t N = 0, T = 0, Tk = 0, log2n = 0;   // PFB (Tk: kernel taps, zero-padded)
+    bool sym_taps = false;                     // PFB kernel taps exactly symmetric (Tk == T)
     bool gen = false;                          // PFB through the any-N kernels
     rfr::GenPlan gplan;
     int32_t L = 0, D = 0, Lpad = 0;            // demod
