@@ -400,8 +400,12 @@ void rfr_batch_destroy(rfr_batch* batch);
  * rfr_batch_push -- one step: plan i pushes bufs[i] (device, n_samples[i]
  * samples) into outs[i] exactly as rfr_push_into would (bit-identical
  * results, stream state kept per plan), but all plans' kernels run
- * concurrently from ONE CUDA-graph launch into `stream`.  The executable
- * graph is kept and updated in place on the next step.  outs[i].frames is set.
+ * concurrently from ONE CUDA-graph launch into `stream`.  Inside it, the
+ * tensor-core GEMMs of every three-product demodulation plan run as one
+ * persistent kernel over all those plans' tiles (one launch per tone-tile
+ * width and per 16 plans), the other kernels on one graph branch per plan.
+ * The executable graph is kept and updated in place on the next step.
+ * outs[i].frames is set.
  * Every push is checked before anything is enqueued (RFR_E_INVALID /
  * RFR_E_SHORT leave all plans unchanged).  Scratch growth happens before the
  * graph is built.
@@ -417,8 +421,10 @@ const char* rfr_batch_last_error(const rfr_batch* batch);
 /*
  * rfr_plan_autotune -- time the plan's result-neutral launch choices (PFB:
  * ring look-ahead of 1..3 super-blocks; demodulation: GEMM tile raster
- * groups) on a push of n_samples and keep the fastest.  Outputs stay
- * bit-identical whatever is chosen.  With use_cache != 0 the choice is read
+ * groups and, for the three-product form, the tile shape: 128 frames x 128
+ * or 64 tones) on a push of n_samples and keep the fastest (Sec. III: the
+ * host runtime tunes the GPU kernels).  Outputs stay bit-identical whatever
+ * is chosen.  With use_cache != 0 the choice is read
  * from / written to the JSON file named by RFR_TUNE_CACHE (default
  * ./rfr_tune_cache.json), keyed by plan shape, push size and GPU.  The
  * stream state is left unchanged.  *best_ms (may be NULL) receives the time
@@ -427,6 +433,13 @@ const char* rfr_batch_last_error(const rfr_batch* batch);
 rfr_status rfr_plan_autotune(rfr_plan* plan, int64_t n_samples, int32_t use_cache, double* best_ms);
 rfr_status rfr_plan_get_tune(const rfr_plan* plan, int32_t* pfb_lookahead, int32_t* demod_raster,
                              int32_t* tuned);
+/* Tones per GEMM tile of a three-product demodulation plan (128 or 64, as
+ * tuned; 128 by default); 0 for other plans.  Setting it is result-neutral
+ * (the autotuner chooses it; set it by hand only to pin a choice).
+ * Errors: RFR_E_INVALID (not a three-product demodulation plan, or a width
+ * other than 64 or 128). */
+rfr_status rfr_plan_get_tone_tile(const rfr_plan* plan, int32_t* tones_per_tile);
+rfr_status rfr_plan_set_tone_tile(rfr_plan* plan, int32_t tones_per_tile);
 
 /* ---------------------------------------------------------------- serving */
 typedef struct rfr_server rfr_server;

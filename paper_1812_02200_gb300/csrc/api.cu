@@ -219,8 +219,12 @@ rfr_status ensure_scratch(rfr_plan* p, int64_t n) {
 }
 
 // Core of every push: enqueue the frames of [carry | buf] into `out`.
+// defer_gemm (batched steps): a three-product demodulation plan leaves its
+// GEMM to the caller's persistent launch, described in *defer_gemm
+// (n_tiles = 0 when the plan has nothing to launch or is another form).
 rfr_status push_core(rfr_plan* p, const int16_t* iq, int64_t n, const rfr_output* o,
-                     int64_t* frames_out, cudaStream_t st) {
+                     int64_t* frames_out, cudaStream_t st, rfr::DemodGemmJob* defer_gemm) {
+    if (defer_gemm) defer_gemm->n_tiles = 0;
     if (n < 0 || (n > 0 && iq == nullptr)) return fail(p, RFR_E_INVALID, "bad input buffer");
     const int64_t lv = p->cl + n;
     const int64_t F = frames_for_len(p, lv);
@@ -322,7 +326,9 @@ rfr_status push_core(rfr_plan* p, const int16_t* iq, int64_t n, const rfr_output
                     L.xs_hi = p->d_xs3;
                     L.xs_lo = nullptr;
                     L.xs_rows = p->xs3_rows_cap;
-                    RFR_CUDA(p, rfr::demod3_launch(L, st));
+                    L.tone_tile = p->tune.demod_bt;
+                    if (defer_gemm) RFR_CUDA(p, rfr::demod3_prepare(L, st, defer_gemm));
+                    else RFR_CUDA(p, rfr::demod3_launch(L, st));
                 } else {
                     RFR_CUDA(p, rfr::demod_launch(L, st));
                 }

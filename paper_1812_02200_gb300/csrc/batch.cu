@@ -2,15 +2,19 @@
 // launch autotuner.
 //
 // rfr_batch_push enqueues one push per plan.  Each plan's kernels go on its
-// own branch (fork/join with events), the whole step is captured into a CUDA
-// graph, and the graph is launched into the caller's stream as ONE launch.
+// own branch (fork/join with events), except the demodulation GEMMs of the
+// three-product plans: those of all plans run as ONE persistent kernel launch
+// over every plan's tiles (demod3_gemm), after the plans' pre-GEMM kernels.
+// The whole step is captured into a CUDA graph and launched into the caller's
+// stream as ONE graph launch.
 // The executable graph is kept and updated in place (cudaGraphExecUpdate) on
 // the next step, so steady-state steps re-instantiate nothing.  Allocation
 // (scratch growth) happens before capture, never inside it.
 //
 // rfr_plan_autotune times the launch choices that never change results
-// (bit-identical outputs) -- the PFB ring look-ahead and the GEMM tile raster
-// -- on a buffer of the caller's size, keeps the fastest in the plan and in a
+// (bit-identical outputs) -- the PFB ring look-ahead, and the demodulation
+// GEMM's tile raster and tone-tile width (128 or 64 tones per tile) -- on a
+// buffer of the caller's size, keeps the fastest in the plan and in a
 // JSON cache file (RFR_TUNE_CACHE, default ./rfr_tune_cache.json) keyed by
 // the plan shape and the GPU, so later plans of the same shape load it.
 #include <cuda_runtime.h>
@@ -34,8 +38,11 @@ struct rfr_batch {
     std::vector<rfr_plan*> plans;
     std::vector<cudaStream_t> branches;
     std::vector<cudaEvent_t> ev_join;
+    std::vector<rfr::DemodGemmJob> jobs;   // deferred three-product GEMMs, one per plan
     cudaStream_t origin = nullptr;
+    cudaStream_t gemm_stream = nullptr;    // the persistent GEMM launch of the step
     cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_gemm = nullptr;
     cudaGraphExec_t exec = nullptr;
     int64_t steps = 0, updates = 0, instantiations = 0;
     std::string last_error;
@@ -54,7 +61,9 @@ void batch_destroy(rfr_batch* b) {
     for (auto s : b->branches) cudaStreamDestroy(s);
     for (auto e : b->ev_join) cudaEventDestroy(e);
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_gemm) cudaEventDestroy(b->ev_gemm);
     if (b->origin) cudaStreamDestroy(b->origin);
+    if (b->gemm_stream) cudaStreamDestroy(b->gemm_stream);
     delete b;
 }
 
@@ -78,30 +87,39 @@ std::string tune_key(const rfr_plan* p, int64_t n) {
     return k.str();
 }
 
-// Minimal line-oriented JSON map: {"key": [pfb_lookahead, demod_raster], ...}
-std::map<std::string, std::pair<int, int>> tune_load() {
-    std::map<std::string, std::pair<int, int>> m;
+// Minimal line-oriented JSON map:
+//   {"key": [pfb_lookahead, demod_raster, demod_tone_tile], ...}
+// (entries with two numbers have the default tone tile, 128)
+struct TuneEntry {
+    int lookahead = 0, raster = 1, bt = 128;
+};
+std::map<std::string, TuneEntry> tune_load() {
+    std::map<std::string, TuneEntry> m;
     std::ifstream f(tune_path());
     std::string line;
     while (std::getline(f, line)) {
         const size_t q0 = line.find('"'), q1 = line.find('"', q0 + 1);
         const size_t b0 = line.find('[', q1 == std::string::npos ? 0 : q1);
         if (q0 == std::string::npos || q1 == std::string::npos || b0 == std::string::npos) continue;
-        int a = 0, c = 1;
-        if (std::sscanf(line.c_str() + b0, "[%d, %d]", &a, &c) == 2) m[line.substr(q0 + 1, q1 - q0 - 1)] = {a, c};
+        TuneEntry t;
+        const int got = std::sscanf(line.c_str() + b0, "[%d, %d, %d]", &t.lookahead, &t.raster, &t.bt);
+        if (got >= 2) {
+            if (got == 2 || (t.bt != 64 && t.bt != 128)) t.bt = 128;
+            m[line.substr(q0 + 1, q1 - q0 - 1)] = t;
+        }
     }
     return m;
 }
 
-void tune_store(const std::map<std::string, std::pair<int, int>>& m) {
+void tune_store(const std::map<std::string, TuneEntry>& m) {
     const std::string path = tune_path(), tmp = path + ".tmp";
     {
         std::ofstream f(tmp);
         f << "{\n";
         size_t i = 0;
         for (const auto& kv : m) {
-            f << "  \"" << kv.first << "\": [" << kv.second.first << ", " << kv.second.second << "]"
-              << (++i < m.size() ? "," : "") << "\n";
+            f << "  \"" << kv.first << "\": [" << kv.second.lookahead << ", " << kv.second.raster << ", "
+              << kv.second.bt << "]" << (++i < m.size() ? "," : "") << "\n";
         }
         f << "}\n";
     }
@@ -126,7 +144,10 @@ rfr_status rfr_batch_create(rfr_batch** out, rfr_plan* const* plans, int32_t n) 
     const int nb = std::min(n, 32);
     b->branches.resize(nb, nullptr);
     b->ev_join.resize(n, nullptr);
+    b->jobs.resize(n);
     bool ok = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&b->gemm_stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->ev_gemm, cudaEventDisableTiming) == cudaSuccess &&
               cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess;
     for (auto& s : b->branches) ok = ok && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess;
     for (auto& e : b->ev_join) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
@@ -162,16 +183,34 @@ rfr_status rfr_batch_push(rfr_batch* b, const int16_t* const* bufs, const int64_
         return batch_fail(b, RFR_E_CUDA, "begin capture");
     rfr_status err = RFR_OK;
     cudaEventRecord(b->ev_fork, b->origin);
+    cudaStreamWaitEvent(b->gemm_stream, b->ev_fork, 0);
+    std::vector<const rfr::DemodGemmJob*> gemms;
     for (int i = 0; i < n && err == RFR_OK; ++i) {
         cudaStream_t br = b->branches[i % b->branches.size()];
         cudaStreamWaitEvent(br, b->ev_fork, 0);
         int64_t F = 0;
-        err = rfr::push_core(b->plans[i], bufs[i], n_samples[i], &outs[i], &F, br);
+        err = rfr::push_core(b->plans[i], bufs[i], n_samples[i], &outs[i], &F, br, &b->jobs[i]);
         outs[i].frames = F;
         if (err != RFR_OK) b->last_error = "push " + std::to_string(i) + ": " + b->plans[i]->last_error;
         cudaEventRecord(b->ev_join[i], br);
-        cudaStreamWaitEvent(b->origin, b->ev_join[i], 0);
+        if (b->jobs[i].n_tiles > 0) {
+            // the plan's GEMM waits for its pre-GEMM kernels
+            cudaStreamWaitEvent(b->gemm_stream, b->ev_join[i], 0);
+            gemms.push_back(&b->jobs[i]);
+        } else {
+            cudaStreamWaitEvent(b->origin, b->ev_join[i], 0);
+        }
     }
+    if (err == RFR_OK && !gemms.empty()) {
+        const cudaError_t ge = rfr::demod3_gemm(gemms.data(), static_cast<int>(gemms.size()), b->plans[0]->n_sms,
+                                                b->gemm_stream);
+        if (ge != cudaSuccess) {
+            err = RFR_E_CUDA;
+            b->last_error = std::string("batched GEMM launch: ") + cudaGetErrorString(ge);
+        }
+    }
+    cudaEventRecord(b->ev_gemm, b->gemm_stream);
+    cudaStreamWaitEvent(b->origin, b->ev_gemm, 0);
     cudaGraph_t graph = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(b->origin, &graph);
     if (err != RFR_OK) {
@@ -230,19 +269,23 @@ rfr_status rfr_plan_autotune(rfr_plan* p, int64_t n_samples, int32_t use_cache, 
         auto m = tune_load();
         auto it = m.find(key);
         if (it != m.end()) {
-            p->tune.pfb_lookahead = it->second.first;
-            p->tune.demod_raster = it->second.second;
+            p->tune.pfb_lookahead = it->second.lookahead;
+            p->tune.demod_raster = it->second.raster;
+            p->tune.demod_bt = it->second.bt;
             p->tune.tuned = true;
             if (best_ms) *best_ms = -1.0;
             return RFR_OK;
         }
     }
     // candidates (all give bit-identical results)
-    std::vector<std::pair<int, int>> cand;
+    std::vector<TuneEntry> cand;
     if (p->mode == RFR_MODE_PFB) {
-        for (int la : {1, 2, 3}) cand.push_back({la, 1});
+        for (int la : {1, 2, 3}) cand.push_back({la, 1, 128});
     } else {
-        for (int r : {1, 8, 19, 38}) cand.push_back({0, r});
+        for (int bt : {128, 64}) {
+            if (bt == 64 && p->demod_products != 3) continue;     // the tone tile is a three-product choice
+            for (int r : {1, 8, 19, 38}) cand.push_back({0, r, bt});
+        }
     }
     // scratch buffers: zero input, outputs sized for the push
     const int64_t F = rfr::frames_for_samples(p, n_samples) + 1;
@@ -282,11 +325,12 @@ rfr_status rfr_plan_autotune(rfr_plan* p, int64_t n_samples, int32_t use_cache, 
     o.tones_cap = F;
     const rfr::TuneConfig keep = p->tune;
     double best = 1e30;
-    std::pair<int, int> best_c = cand.front();
+    TuneEntry best_c = cand.front();
     rfr_status rs = rfr::ensure_scratch(p, n_samples);
     for (size_t c = 0; c < cand.size() && rs == RFR_OK; ++c) {
-        p->tune.pfb_lookahead = cand[c].first;
-        p->tune.demod_raster = cand[c].second;
+        p->tune.pfb_lookahead = cand[c].lookahead;
+        p->tune.demod_raster = cand[c].raster;
+        p->tune.demod_bt = cand[c].bt;
         float ms_best = 1e30f;
         for (int rep = 0; rep < 4 && rs == RFR_OK; ++rep) {
             p->samples = s_samples;
@@ -322,8 +366,9 @@ rfr_status rfr_plan_autotune(rfr_plan* p, int64_t n_samples, int32_t use_cache, 
         p->tune = keep;
         return rs;
     }
-    p->tune.pfb_lookahead = best_c.first;
-    p->tune.demod_raster = best_c.second;
+    p->tune.pfb_lookahead = best_c.lookahead;
+    p->tune.demod_raster = best_c.raster;
+    p->tune.demod_bt = best_c.bt;
     p->tune.tuned = true;
     if (best_ms) *best_ms = best;
     if (use_cache) {
@@ -332,6 +377,19 @@ rfr_status rfr_plan_autotune(rfr_plan* p, int64_t n_samples, int32_t use_cache, 
         m[key] = best_c;
         tune_store(m);
     }
+    return RFR_OK;
+}
+
+rfr_status rfr_plan_set_tone_tile(rfr_plan* p, int32_t tones_per_tile) {
+    if (!p || p->mode != RFR_MODE_DEMOD || p->demod_products != 3 || (tones_per_tile != 64 && tones_per_tile != 128))
+        return RFR_E_INVALID;
+    p->tune.demod_bt = tones_per_tile;
+    return RFR_OK;
+}
+
+rfr_status rfr_plan_get_tone_tile(const rfr_plan* p, int32_t* tones_per_tile) {
+    if (!p || !tones_per_tile) return RFR_E_INVALID;
+    *tones_per_tile = p->mode == RFR_MODE_DEMOD && p->demod_products == 3 ? p->tune.demod_bt : 0;
     return RFR_OK;
 }
 

@@ -39,6 +39,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 #include <mutex>
 
 #include "dev_common.cuh"
@@ -367,29 +368,54 @@ demod_gemm_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constan
 // hi/lo as above ((xr+xi)/2 has at most 17 significant bits, exact as hi+lo);
 // each product again takes the three MMAs hi.hi + hi.lo + lo.hi.
 //
-// Tile: 128 frames x 128 tones, K-blocks of 64 complex taps (one plane per
-// TMA stage: A hi, lo 128x64 and B hi, lo 128x64, 64 KB; three stages).  The
-// three products of an accumulation chunk run one after the other, each into
-// one of four 128-column TMEM slots taken in rotation, so the epilogue drains
-// a slot while the MMAs fill the others and every slot is drained three
-// product phases before it is reused.  Sixteen epilogue warps (four per TMEM
-// lane quadrant, 32 tones each) drain a slot with one 32-column load each,
-// adding 2 P1 to both sums, P2 to the imaginary and -P3 to the real sum.
-constexpr int G3_BT = 128;                                 // tones per tile
+// Tile: 128 frames x BT tones (BT = 128 or 64, the tone-tile width chosen by
+// the plan's autotuner), K-blocks of 64 complex taps (one plane per TMA
+// stage: A hi, lo 128x64 and B hi, lo BTx64).  The three products of an
+// accumulation chunk run one after the other, each into one of four BT-column
+// TMEM slots taken in rotation, so the epilogue drains a slot while the MMAs
+// fill the others and every slot is drained three product phases before it
+// is reused.  Sixteen epilogue warps (four per TMEM lane quadrant, BT/4 tones
+// each) drain a slot with one load each, adding 2 P1 to both sums, P2 to the
+// imaginary and -P3 to the real sum.
+//
+// The kernel is persistent over a list of plans: one launch runs the tiles
+// of every demodulation stream of a batched step (or of one push), each CTA
+// striding over the global tile index; a tile's plan is found from the
+// plans' first-tile offsets.  Each output element is accumulated in the same
+// order whatever the tile width or the plans sharing the launch.
 constexpr int G3_BK = 64;                                  // complex taps per K-block
 constexpr uint32_t G3_A_BYTES = BM * G3_BK * 2;
-constexpr uint32_t G3_B_BYTES = G3_BT * G3_BK * 2;
-constexpr uint32_t G3_STAGE_BYTES = 2 * G3_A_BYTES + 2 * G3_B_BYTES;
-constexpr int G3_STAGES = 3;
 constexpr int G3_SLOTS = 4;
-constexpr size_t G3_SMEM = 1024 + G3_STAGES * G3_STAGE_BYTES + 256;
-constexpr int G3_EPI_WARPS = 16;          // 4 lane quadrants x 4 groups of 32 tones
+constexpr int G3_EPI_WARPS = 16;          // 4 lane quadrants x 4 tone groups
 constexpr int G3_THREADS = (G3_EPI_WARPS + 2) * 32;
+template <int BT> struct G3Cfg {
+    static constexpr uint32_t B_BYTES = BT * G3_BK * 2;
+    static constexpr uint32_t STAGE_BYTES = 2 * G3_A_BYTES + 2 * B_BYTES;
+    static constexpr int STAGES = BT == 128 ? 3 : 4;
+    static constexpr size_t SMEM = 1024 + STAGES * STAGE_BYTES + 256;
+    static constexpr uint32_t TMEM_COLS = G3_SLOTS * BT;   // 512 or 256
+    static constexpr int TPG = BT / 4;                     // tones per epilogue warp
+};
 
-struct G3Maps {
+struct G3Plan {
     CUtensorMap a[6];   // (x sum/2, xr, xi) x (hi, lo): [rows][D] fp16, Toeplitz view
     CUtensorMap b[6];   // (cr, ci - cr, cr + ci) x (hi, lo): [ntp][Lpad] fp16, K-major
+    GemmArgs g;
+    int tile0;          // first global tile of this plan
 };
+constexpr int kG3MaxPlans = 16;
+struct G3Batch {
+    int n_plans, total_tiles;
+    G3Plan p[kG3MaxPlans];
+};
+static_assert(sizeof(G3Batch) <= 32000, "kernel parameter space");
+static_assert(sizeof(G3Plan) <= kDemodJobBytes, "job storage");
+
+__device__ __forceinline__ int g3_plan_of(const G3Batch& bt, int tile) {
+    int pi = 0;
+    while (pi + 1 < bt.n_plans && tile >= bt.p[pi + 1].tile0) ++pi;
+    return pi;
+}
 
 __global__ void build_taps3_kernel(const double* __restrict__ h, const uint64_t* __restrict__ words,
                                    int n_tones, int ntp, int L, int Lpad, double scale,
@@ -433,21 +459,26 @@ __global__ void presplit3_kernel(const uint32_t* __restrict__ carry, int64_t cl,
     }
 }
 
+template <int BT>
 __global__ void __launch_bounds__(G3_THREADS, 1)
-demod3m_gemm_kernel(const __grid_constant__ G3Maps mp, const GemmArgs g) {
+demod3m_gemm_kernel(const __grid_constant__ G3Batch bt) {
+    using Cfg = G3Cfg<BT>;
+    constexpr int STAGES = Cfg::STAGES;
+    constexpr uint32_t STAGE_BYTES = Cfg::STAGE_BYTES, B_BYTES = Cfg::B_BYTES;
     extern __shared__ unsigned char smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     unsigned char* smem = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + G3_STAGES * G3_STAGE_BYTES);
-    uint64_t* empty = full + G3_STAGES;
-    uint64_t* sfull = empty + G3_STAGES;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* sfull = empty + STAGES;
     uint64_t* sempty = sfull + G3_SLOTS;
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(sempty + G3_SLOTS);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+    int* const status0 = bt.p[0].g.status;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < G3_STAGES; ++s) {
+        for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
@@ -459,21 +490,21 @@ demod3m_gemm_kernel(const __grid_constant__ G3Maps mp, const GemmArgs g) {
         fence_mbar_init();
     }
     if (warp == G3_EPI_WARPS + 1) {
-        umma::alloc(tmem_holder, TMEM_COLS);
+        umma::alloc(tmem_holder, Cfg::TMEM_COLS);
         umma::relinquish();
     }
-    if (warp == G3_EPI_WARPS && lane == 0) {
+    if (warp == G3_EPI_WARPS && lane < bt.n_plans) {
         for (int i = 0; i < 6; ++i) {
-            tma_prefetch_desc(&mp.a[i]);
-            tma_prefetch_desc(&mp.b[i]);
+            tma_prefetch_desc(&bt.p[lane].a[i]);
+            tma_prefetch_desc(&bt.p[lane].b[i]);
         }
     }
     umma::fence_before_sync();
     __syncthreads();
     umma::fence_after_sync();
     const uint32_t tmem = *tmem_holder;
-    const int n_tiles = g.n_mt * g.n_nt;
-    constexpr uint32_t IDESC = umma::idesc_f16_f32(BM, G3_BT);
+    const int n_tiles = bt.total_tiles;
+    constexpr uint32_t IDESC = umma::idesc_f16_f32(BM, BT);
 
     if (warp == G3_EPI_WARPS) {
         // ------------------------------------------------ TMA producer
@@ -481,37 +512,39 @@ demod3m_gemm_kernel(const __grid_constant__ G3Maps mp, const GemmArgs g) {
             uint32_t it = 0;
             bool stop = false;
             for (int tile = blockIdx.x; tile < n_tiles && !stop; tile += gridDim.x) {
+                const int pi = g3_plan_of(bt, tile);
+                const G3Plan& P = bt.p[pi];
                 int tm, tn;
-                tile_coords(g, tile, tm, tn);
-                const int m0 = tm * BM, n0 = tn * G3_BT;
-                for (int kb0 = 0; kb0 < g.KB && !stop; kb0 += g.kchunk) {
-                    const int kb1 = min(kb0 + g.kchunk, g.KB);
+                tile_coords(P.g, tile - P.tile0, tm, tn);
+                const int m0 = tm * BM, n0 = tn * BT;
+                for (int kb0 = 0; kb0 < P.g.KB && !stop; kb0 += P.g.kchunk) {
+                    const int kb1 = min(kb0 + P.g.kchunk, P.g.KB);
                     for (int q = 0; q < 3 && !stop; ++q) {
                         for (int kb = kb0; kb < kb1; ++kb, ++it) {
-                            const int s = it % G3_STAGES;
-                            const uint32_t ph = (it / G3_STAGES) & 1;
-                            if (*abort_flag || !mbar_wait(&empty[s], ph ^ 1, g.status)) {
+                            const int s = it % STAGES;
+                            const uint32_t ph = (it / STAGES) & 1;
+                            if (*abort_flag || !mbar_wait(&empty[s], ph ^ 1, status0)) {
                                 *abort_flag = 1;
                                 stop = true;
                                 break;
                             }
-                            unsigned char* st = smem + s * G3_STAGE_BYTES;
-                            mbar_arrive_expect_tx(&full[s], G3_STAGE_BYTES);
+                            unsigned char* st = smem + s * STAGE_BYTES;
+                            mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
                             const int kt = kb * G3_BK;
-                            const int c0 = kt % g.two_d, c1 = m0 + kt / g.two_d;
-                            tma_load_2d(st, &mp.a[2 * q], c0, c1, &full[s]);
-                            tma_load_2d(st + G3_A_BYTES, &mp.a[2 * q + 1], c0, c1, &full[s]);
-                            tma_load_2d(st + 2 * G3_A_BYTES, &mp.b[2 * q], kt, n0, &full[s]);
-                            tma_load_2d(st + 2 * G3_A_BYTES + G3_B_BYTES, &mp.b[2 * q + 1], kt, n0, &full[s]);
+                            const int c0 = kt % P.g.two_d, c1 = m0 + kt / P.g.two_d;
+                            tma_load_2d(st, &P.a[2 * q], c0, c1, &full[s]);
+                            tma_load_2d(st + G3_A_BYTES, &P.a[2 * q + 1], c0, c1, &full[s]);
+                            tma_load_2d(st + 2 * G3_A_BYTES, &P.b[2 * q], kt, n0, &full[s]);
+                            tma_load_2d(st + 2 * G3_A_BYTES + B_BYTES, &P.b[2 * q + 1], kt, n0, &full[s]);
                         }
                     }
                 }
             }
             // wait for the copies still in flight before leaving
-            for (uint32_t k = 0; k < G3_STAGES && it > 0; ++k) {
+            for (uint32_t k = 0; k < static_cast<uint32_t>(STAGES) && it > 0; ++k) {
                 const uint32_t j = it - 1 - k;
                 if (static_cast<int32_t>(j) < 0) break;
-                mbar_wait(&full[j % G3_STAGES], (j / G3_STAGES) & 1, g.status);
+                mbar_wait(&full[j % STAGES], (j / STAGES) & 1, status0);
             }
         }
     } else if (warp == G3_EPI_WARPS + 1) {
@@ -520,29 +553,30 @@ demod3m_gemm_kernel(const __grid_constant__ G3Maps mp, const GemmArgs g) {
             uint32_t it = 0, phase = 0;
             bool stop = false;
             for (int tile = blockIdx.x; tile < n_tiles && !stop; tile += gridDim.x) {
+                const GemmArgs& g = bt.p[g3_plan_of(bt, tile)].g;
                 for (int kb0 = 0; kb0 < g.KB && !stop; kb0 += g.kchunk) {
                     const int kb1 = min(kb0 + g.kchunk, g.KB);
                     for (int q = 0; q < 3 && !stop; ++q, ++phase) {
                         const uint32_t slot = phase % G3_SLOTS, use = phase / G3_SLOTS;
-                        if (*abort_flag || !mbar_wait(&sempty[slot], (use & 1) ^ 1, g.status)) {
+                        if (*abort_flag || !mbar_wait(&sempty[slot], (use & 1) ^ 1, status0)) {
                             *abort_flag = 1;
                             stop = true;
                             break;
                         }
                         umma::fence_after_sync();
-                        const uint32_t d_tmem = tmem + slot * G3_BT;
+                        const uint32_t d_tmem = tmem + slot * BT;
                         for (int kb = kb0; kb < kb1; ++kb, ++it) {
-                            const int s = it % G3_STAGES;
-                            const uint32_t ph = (it / G3_STAGES) & 1;
-                            if (!mbar_wait(&full[s], ph, g.status)) {
+                            const int s = it % STAGES;
+                            const uint32_t ph = (it / STAGES) & 1;
+                            if (!mbar_wait(&full[s], ph, status0)) {
                                 *abort_flag = 1;
                                 stop = true;
                                 break;
                             }
                             umma::fence_after_sync();
-                            const uint32_t sa = smem_u32(smem + s * G3_STAGE_BYTES);
+                            const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
                             const uint32_t ah = sa, al = sa + G3_A_BYTES;
-                            const uint32_t bh = sa + 2 * G3_A_BYTES, bl = bh + G3_B_BYTES;
+                            const uint32_t bh = sa + 2 * G3_A_BYTES, bl = bh + B_BYTES;
 #pragma unroll
                             for (int k = 0; k < G3_BK / 16; ++k) {
                                 const uint32_t off = k * 32;
@@ -561,56 +595,65 @@ demod3m_gemm_kernel(const __grid_constant__ G3Maps mp, const GemmArgs g) {
         __syncwarp();
     } else {
         // ------------------------------------------------ epilogue (16 warps)
-        const int qd = warp & 3, grp = warp >> 2;          // lane quadrant, 32-tone group
+        constexpr int TPG = Cfg::TPG;
+        const int qd = warp & 3, grp = warp >> 2;          // lane quadrant, tone group
         const int row = qd * 32 + lane;
         uint32_t phase = 0;
         bool ok = true;
         for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+            const G3Plan& P = bt.p[g3_plan_of(bt, tile)];
+            const GemmArgs& g = P.g;
             int mt, tn;
-            tile_coords(g, tile, mt, tn);
-            const int m0 = mt * BM, n0 = tn * G3_BT;
-            float re[32], im[32];
+            tile_coords(g, tile - P.tile0, mt, tn);
+            const int m0 = mt * BM, n0 = tn * BT;
+            float re[TPG], im[TPG];
 #pragma unroll
-            for (int i = 0; i < 32; ++i) re[i] = im[i] = 0.f;
+            for (int i = 0; i < TPG; ++i) re[i] = im[i] = 0.f;
             for (int kb0 = 0; kb0 < g.KB && ok; kb0 += g.kchunk) {
                 for (int q = 0; q < 3; ++q, ++phase) {
                     const uint32_t slot = phase % G3_SLOTS, use = phase / G3_SLOTS;
-                    if (*abort_flag || !mbar_wait(&sfull[slot], use & 1, g.status)) {
+                    if (*abort_flag || !mbar_wait(&sfull[slot], use & 1, status0)) {
                         *abort_flag = 1;
                         ok = false;
                         break;
                     }
                     umma::fence_after_sync();
-                    uint32_t r[32];
-                    umma::ld_32x32b_x32(tmem + (static_cast<uint32_t>(qd * 32) << 16) + slot * G3_BT + grp * 32, r);
-                    umma::wait_ld();
+                    uint32_t r[TPG];
+                    const uint32_t ta = tmem + (static_cast<uint32_t>(qd * 32) << 16) + slot * BT + grp * TPG;
+                    if constexpr (TPG == 32) {
+                        umma::ld_32x32b_x32(ta, r);
+                        umma::wait_ld();
+                    } else {
+                        umma::ld_32x32b_x16(ta, r);
+                        umma::wait_ld_regs(r);
+                    }
                     umma::fence_before_sync();
                     mbar_arrive(&sempty[slot]);
                     if (q == 0) {
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) {
+                        for (int i = 0; i < TPG; ++i) {
                             const float v = 2.f * __uint_as_float(r[i]);
                             re[i] += v;
                             im[i] += v;
                         }
                     } else if (q == 1) {
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) im[i] += __uint_as_float(r[i]);
+                        for (int i = 0; i < TPG; ++i) im[i] += __uint_as_float(r[i]);
                     } else {
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) re[i] -= __uint_as_float(r[i]);
+                        for (int i = 0; i < TPG; ++i) re[i] -= __uint_as_float(r[i]);
                     }
                 }
             }
             if (!ok) break;
             const int64_t k = static_cast<int64_t>(m0) + row;
             if (k < g.F) {
-                const int tb = n0 + grp * 32;
+                const int tb = n0 + grp * TPG;
                 const int64_t K = g.F0 + k;
                 const int64_t arow = K / BM - g.F0 / BM;
                 const int si = static_cast<int>(K % BM);
 #pragma unroll
-                for (int tl = 0; tl < 32; ++tl) {
+                for (int tl = 0; tl < TPG; ++tl) {
                     const int t = tb + tl;
                     if (t < g.n_tones) {
                         const float2 an = __ldg(g.anchors + arow * g.ntp + t);
@@ -627,7 +670,7 @@ demod3m_gemm_kernel(const __grid_constant__ G3Maps mp, const GemmArgs g) {
     __syncthreads();
     if (warp == G3_EPI_WARPS + 1) {
         umma::fence_after_sync();
-        umma::dealloc(tmem, TMEM_COLS);
+        umma::dealloc(tmem, Cfg::TMEM_COLS);
     }
 }
 
@@ -737,13 +780,16 @@ cudaError_t demod3_build_taps(const double* d_h, const uint64_t* d_words, int n_
     return cudaGetLastError();
 }
 
-cudaError_t demod3_launch(const DemodLaunch& L, cudaStream_t st) {
+cudaError_t demod3_prepare(const DemodLaunch& L, cudaStream_t st, DemodGemmJob* job) {
+    job->n_tiles = 0;
+    job->bt = L.tone_tile == 64 ? 64 : 128;
     if (L.F <= 0) return cudaSuccess;
-    if (L.D % G3_BK != 0 || L.Lpad % G3_BK != 0 || L.ntp % G3_BT != 0) return cudaErrorInvalidValue;
+    if (L.D % G3_BK != 0 || L.Lpad % G3_BK != 0 || L.ntp % 128 != 0) return cudaErrorInvalidValue;
     const int64_t rows = static_cast<int64_t>(demod3_xs_rows(L.F, L.Lpad, L.D));
     if (rows > L.xs_rows) return cudaErrorInvalidValue;
+    const int bt = job->bt;
     const int n_mt = static_cast<int>((L.F + BM - 1) / BM);
-    const int n_nt = L.ntp / G3_BT;
+    const int n_nt = (L.n_tones + bt - 1) / bt;       // tiles past the last tone are skipped
     const int n_anch = demod_anchor_rows(L.F0, L.F);
     float2* anchors = static_cast<float2*>(L.rot);
     float2* steps = anchors + static_cast<int64_t>(n_anch) * L.ntp;
@@ -755,15 +801,16 @@ cudaError_t demod3_launch(const DemodLaunch& L, cudaStream_t st) {
     presplit3_kernel<<<grid_for(total, L.n_sms), 256, 0, st>>>(
         reinterpret_cast<const uint32_t*>(L.carry), L.cl, reinterpret_cast<const uint32_t*>(L.buf), L.cl + L.n,
         total, xp);
-    G3Maps mp;
+    G3Plan* P = reinterpret_cast<G3Plan*>(job->bytes);
+    std::memset(P, 0, sizeof(G3Plan));
     const __half* bp = static_cast<const __half*>(L.b_hi);
     const int64_t bplane = static_cast<int64_t>(L.ntp) * L.Lpad;
     for (int i = 0; i < 6; ++i) {
-        if (!make_map(&mp.a[i], xp + i * total, static_cast<uint64_t>(L.D), static_cast<uint64_t>(rows), BM) ||
-            !make_map(&mp.b[i], bp + i * bplane, static_cast<uint64_t>(L.Lpad), static_cast<uint64_t>(L.ntp), G3_BT))
+        if (!make_map(&P->a[i], xp + i * total, static_cast<uint64_t>(L.D), static_cast<uint64_t>(rows), BM) ||
+            !make_map(&P->b[i], bp + i * bplane, static_cast<uint64_t>(L.Lpad), static_cast<uint64_t>(L.ntp), bt))
             return cudaErrorInvalidValue;
     }
-    GemmArgs g{};
+    GemmArgs& g = P->g;
     g.raster = L.raster_group;
     g.F = L.F;
     g.F0 = L.F0;
@@ -781,12 +828,54 @@ cudaError_t demod3_launch(const DemodLaunch& L, cudaStream_t st) {
     g.ld = L.tones_ld;
     g.fo = L.frame_offset;
     g.status = L.status;
-    cudaError_t e = cudaFuncSetAttribute(demod3m_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(G3_SMEM));
-    if (e != cudaSuccess) return e;
-    const int grid = std::min(n_mt * n_nt, L.n_sms);
-    demod3m_gemm_kernel<<<grid, G3_THREADS, G3_SMEM, st>>>(mp, g);
+    job->n_tiles = n_mt * n_nt;
     return cudaGetLastError();
+}
+
+namespace {
+template <int BT>
+cudaError_t g3_run(const G3Batch& b, int n_sms, cudaStream_t st) {
+    using Cfg = G3Cfg<BT>;
+    cudaError_t e = cudaFuncSetAttribute(demod3m_gemm_kernel<BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(Cfg::SMEM));
+    if (e != cudaSuccess) return e;
+    const int grid = std::max(1, std::min(b.total_tiles, n_sms));
+    demod3m_gemm_kernel<BT><<<grid, G3_THREADS, Cfg::SMEM, st>>>(b);
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t demod3_gemm(const DemodGemmJob* const* jobs, int n, int n_sms, cudaStream_t st) {
+    // one persistent launch per group of up to kG3MaxPlans jobs of the same tile width
+    for (int bt : {128, 64}) {
+        G3Batch b;
+        b.n_plans = 0;
+        b.total_tiles = 0;
+        for (int i = 0; i <= n; ++i) {
+            const bool flush = i == n || b.n_plans == kG3MaxPlans;
+            if (flush && b.n_plans > 0) {
+                const cudaError_t e = bt == 128 ? g3_run<128>(b, n_sms, st) : g3_run<64>(b, n_sms, st);
+                if (e != cudaSuccess) return e;
+                b.n_plans = 0;
+                b.total_tiles = 0;
+            }
+            if (i == n) break;
+            if (jobs[i]->bt != bt || jobs[i]->n_tiles <= 0) continue;
+            std::memcpy(&b.p[b.n_plans], jobs[i]->bytes, sizeof(G3Plan));
+            b.p[b.n_plans].tile0 = b.total_tiles;
+            b.total_tiles += jobs[i]->n_tiles;
+            ++b.n_plans;
+        }
+    }
+    return cudaSuccess;
+}
+
+cudaError_t demod3_launch(const DemodLaunch& L, cudaStream_t st) {
+    DemodGemmJob job;
+    cudaError_t e = demod3_prepare(L, st, &job);
+    if (e != cudaSuccess || job.n_tiles <= 0) return e;
+    const DemodGemmJob* jp = &job;
+    return demod3_gemm(&jp, 1, L.n_sms, st);
 }
 
 }  // namespace rfr

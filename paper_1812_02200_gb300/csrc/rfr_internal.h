@@ -130,6 +130,15 @@ struct DemodLaunch {
     int n_sms;
     int kchunk;                 // k-blocks per TMEM accumulation chunk
     int raster_group;           // tile order: groups of this many 128-frame tiles sweep all tones
+    int tone_tile;              // three-product GEMM: tones per tile, 128 or 64 (0 = 128)
+};
+// The three-product GEMM of one push, described for a persistent launch that
+// may cover several plans (opaque record of demod.cu).
+constexpr int kDemodJobBytes = 2048;
+struct DemodGemmJob {
+    alignas(128) unsigned char bytes[kDemodJobBytes];
+    int bt = 128;               // tone-tile width
+    int n_tiles = 0;            // 0: nothing to launch
 };
 cudaError_t demod_build_taps(const double* d_h, const uint64_t* d_words, int n_tones, int ntp,
                              int L, int Lpad, int e, void* b_hi, void* b_lo, cudaStream_t st);
@@ -141,6 +150,12 @@ size_t demod_xs_rows(int64_t F, int Lpad, int D);
 cudaError_t demod3_build_taps(const double* d_h, const uint64_t* d_words, int n_tones, int ntp, int L, int Lpad,
                               int e, void* planes, cudaStream_t st);
 cudaError_t demod3_launch(const DemodLaunch& L, cudaStream_t st);
+// the per-push kernels before the GEMM (rotation tables, pre-split), and the
+// GEMM's description in *job
+cudaError_t demod3_prepare(const DemodLaunch& L, cudaStream_t st, DemodGemmJob* job);
+// persistent GEMM launch(es) over the jobs' tiles (one per tone-tile width
+// and per 16 plans)
+cudaError_t demod3_gemm(const DemodGemmJob* const* jobs, int n, int n_sms, cudaStream_t st);
 size_t demod3_xs_rows(int64_t F, int Lpad, int D);
 int demod_anchor_rows(int64_t F0, int64_t F);
 
@@ -181,6 +196,7 @@ void plain_release(void* scratch, void* fft_plan);
 struct TuneConfig {
     int pfb_lookahead = 0;      // 0 = as many ring super-blocks as shared memory allows
     int demod_raster = 1;       // 1 = tones fastest across the whole grid
+    int demod_bt = 128;         // three-product GEMM: tones per tile (128 or 64)
     bool tuned = false;
 };
 
@@ -279,7 +295,7 @@ namespace rfr {
 // Enqueue one push of [carry | iq] into `o` on `st` (no allocation when the
 // scratch is already large enough; see ensure_scratch).
 rfr_status push_core(rfr_plan* p, const int16_t* iq, int64_t n, const rfr_output* o,
-                     int64_t* frames_out, cudaStream_t st);
+                     int64_t* frames_out, cudaStream_t st, DemodGemmJob* defer_gemm = nullptr);
 // Grow the plan's per-push scratch for a push of n samples (may allocate and
 // synchronise the device; never call it during stream capture).
 rfr_status ensure_scratch(rfr_plan* p, int64_t n);

@@ -113,6 +113,8 @@ _SIGS = {
     "rfr_demod_noalloc": (C.c_int, [_P, C.c_int64, _P, C.c_int32, C.c_int32, _P, C.c_int32, _P, C.c_int64, _P]),
     "rfr_demod_noalloc_status": (C.c_int, [_P, C.POINTER(C.c_int32)]),
     "rfr_plan_inject_device_status": (C.c_int, [_P, C.c_int32]),
+    "rfr_plan_get_tone_tile": (C.c_int, [_P, C.POINTER(C.c_int32)]),
+    "rfr_plan_set_tone_tile": (C.c_int, [_P, C.c_int32]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -342,6 +344,11 @@ class Plan:
         n = 0 if history is None else history.shape[0]
         self._check(_lib.rfr_plan_seek(self._h, int(start_sample), _ptr(history), n), "seek")
 
+    def set_tone_tile(self, tones_per_tile: int):
+        """Three-product demodulation: tones per GEMM tile (128 or 64);
+        result-neutral, normally chosen by autotune()."""
+        self._check(_lib.rfr_plan_set_tone_tile(self._h, int(tones_per_tile)), "set_tone_tile")
+
     def inject_device_status(self, status: int):
         """Write the plan's device status word as a timed-out kernel would
         (1), or clear it (0): host-side failure injection for tests."""
@@ -356,7 +363,9 @@ class Plan:
     def tune(self) -> dict:
         a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
         self._check(_lib.rfr_plan_get_tune(self._h, C.byref(a), C.byref(b), C.byref(c)), "tune")
-        return {"pfb_lookahead": a.value, "demod_raster": b.value, "tuned": bool(c.value)}
+        t = C.c_int32()
+        self._check(_lib.rfr_plan_get_tone_tile(self._h, C.byref(t)), "tone tile")
+        return {"pfb_lookahead": a.value, "demod_raster": b.value, "tone_tile": t.value, "tuned": bool(c.value)}
 
     def state_export(self) -> bytes:
         n = C.c_size_t()

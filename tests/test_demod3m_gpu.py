@@ -147,3 +147,64 @@ def test_demod3m_switching_forms(lib):
     with pytest.raises(lib.RfrError) as e:
         q.set_demod_products(3)
     assert e.value.status == -7
+
+
+@pytest.mark.parametrize("L,D,nt", [(1024, 512, 20), (1000, 512, 130), (4096, 2048, 300), (1024, 2048, 70)])
+def test_tone_tile_64_equals_128_and_oracle(lib, L, D, nt):
+    """The tile shape is a launch choice: 64 tones per tile (tiles past the
+    last tone skipped) gives, bit for bit, the frames of 128 tones per tile,
+    and both match the oracle."""
+    case = siggen.demod_case(D * 120 + 77, nt, seed=5100 + L + nt)
+    a = _plan3(lib, L, D, case["words"], "hann", 1e-3)
+    b = _plan3(lib, L, D, case["words"], "hann", 1e-3)
+    b.set_tone_tile(64)
+    assert a.tune()["tone_tile"] == 128 and b.tune()["tone_tile"] == 64
+    ga = _run(a, case["x"], nt)
+    gb = _run(b, case["x"], nt)
+    assert np.array_equal(ga, gb)
+    ref = oracle.demod(case["x"], L, D, oracle.lowpass("hann", L, 1e-3), case["words"])
+    assert rel_rows(gb, ref).max() < TOL
+    with pytest.raises(lib.RfrError):
+        a.set_tone_tile(96)
+
+
+def test_persistent_gemm_over_many_plans(lib):
+    """A batched step with 19 demodulation plans (more than one persistent
+    launch holds, both tile widths) and two PFB plans: every stream's frames
+    equal the same stream pushed alone."""
+    rng = np.random.default_rng(12)
+    specs = []
+    for i in range(19):
+        L = int(rng.choice([256, 1024, 1000]))
+        D = int(rng.choice([64, 512, 448]))
+        specs.append(("demod", L, D, int(rng.integers(1, 300)), 64 if i % 3 == 0 else 128))
+    specs += [("pfb", 1024, 8, 16, 0), ("pfb", 4096, 8, 24, 0)]
+    plans_b, plans_a, xs, outs_b, outs_a = [], [], [], [], []
+    for i, (kind, a1, a2, nt, bt) in enumerate(specs):
+        if kind == "demod":
+            c = siggen.demod_case(a2 * int(rng.integers(30, 80)) + int(rng.integers(0, a2)), nt, seed=6000 + i)
+            mk = lambda: _plan3(lib, a1, a2, c["words"], "hann", 1e-3)
+        else:
+            c = siggen.pfb_case(a1 * 60 + 11, a1, nt, seed=6000 + i)
+            mk = lambda: lib.Plan(a1, a2, window="hann", words=c["words"], full=False)
+        pb, pa = mk(), mk()
+        if kind == "demod":
+            pb.set_tone_tile(bt)
+            pa.set_tone_tile(bt)
+        x = torch.from_numpy(c["x"]).to(DEV)
+        F = pa.frames_for(x.shape[0])
+        plans_b.append(pb)
+        plans_a.append(pa)
+        xs.append(x)
+        outs_b.append(torch.zeros((nt, F), dtype=torch.complex64, device=DEV))
+        outs_a.append(torch.zeros((nt, F), dtype=torch.complex64, device=DEV))
+    batch = lib.Batch(plans_b)
+    half = [x.shape[0] // 2 for x in xs]
+    got = batch.push([x[:h] for x, h in zip(xs, half)], None, outs_b)
+    batch.push([x[h:] for x, h in zip(xs, half)], None, outs_b, got)
+    for p, x, o in zip(plans_a, xs, outs_a):
+        p.push_into(x, tones=o)
+    torch.cuda.synchronize()
+    for i, (ob, oa) in enumerate(zip(outs_b, outs_a)):
+        assert torch.equal(ob, oa), i
+    batch.close()
