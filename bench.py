@@ -974,7 +974,7 @@ def run_ours(args, ws, rank, local):
     value = aggregate_rate(ws, args.steps, samples_step, ms_max)
     kernel_ms = ms / args.steps          # fused kernel + the tiny carry-update kernel
     achieved = samples_step * BYTES_PER_SAMPLE / (kernel_ms * 1e-3) / 1e9
-    traffic = profile_traffic("pfb_tmem_kernel_c2.md", PFB_SOURCES)
+    traffic = profile_traffic("pfb_tmem_sym_kernel_c2.md", PFB_SOURCES)
 
     # -- plain FP32 GPU form on the same input (FP32 FIR + cuFFT + gather)
     plain = None
@@ -1056,10 +1056,10 @@ def run_ours(args, ws, rank, local):
         "rel_err_full_rms": None if full_err is None else full_err["rms_norm_max"],
         "full_spectrum_error": full_err,
         "gpu_launches": 2 * args.steps,
-        "gpu_launches_note": "fused PFB kernel + carry-update kernel per step",
+        "gpu_launches_note": "fused PFB kernel (pfb_tmem_sym_kernel) + carry-update kernel per step",
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": traffic,
-                     "kernel": "pfb_tmem_kernel<8> (N=4096 TMA-fed, FP32 delay line in TMEM)",
+                     "kernel": "pfb_tmem_sym_kernel (N=4096 T=8, symmetric taps, TMA-fed, FP32 delay line in TMEM)",
                      "bytes_per_sample": BYTES_PER_SAMPLE,
                      "peak_kind": f"{peak_kind} (STREAM copy)"},
         "plain_fp32": plain,
