@@ -421,8 +421,9 @@ const char* rfr_batch_last_error(const rfr_batch* batch);
 /*
  * rfr_plan_autotune -- time the plan's result-neutral launch choices (PFB:
  * ring look-ahead of 1..3 super-blocks; demodulation: GEMM tile raster
- * groups and, for the three-product form, the tile shape: 128 frames x 128
- * or 64 tones) on a push of n_samples and keep the fastest (Sec. III: the
+ * groups and, for the three-product form, the tile shape (128 frames x 128
+ * or 64 tones) and whether the FP16 split of the stream is fused into the
+ * GEMM) on a push of n_samples and keep the fastest (Sec. III: the
  * host runtime tunes the GPU kernels).  Outputs stay bit-identical whatever
  * is chosen.  With use_cache != 0 the choice is read
  * from / written to the JSON file named by RFR_TUNE_CACHE (default
@@ -440,6 +441,16 @@ rfr_status rfr_plan_get_tune(const rfr_plan* plan, int32_t* pfb_lookahead, int32
  * other than 64 or 128). */
 rfr_status rfr_plan_get_tone_tile(const rfr_plan* plan, int32_t* tones_per_tile);
 rfr_status rfr_plan_set_tone_tile(rfr_plan* plan, int32_t tones_per_tile);
+
+/* Three-product demodulation: on = 1 fuses the FP16 hi/lo split of the int16
+ * stream (the GEMM's A operand) into the GEMM's producer warps, which read
+ * the stream and write the swizzled operand tiles themselves, instead of a
+ * separate kernel writing six FP16 planes (12 bytes per sample) to device
+ * memory for the GEMM to load (Sec. III.B's mix and filter as one kernel).
+ * Result-neutral (bit-identical planes); the autotuner times both forms.
+ * Errors: RFR_E_INVALID (not a three-product demodulation plan, on not 0/1). */
+rfr_status rfr_plan_set_fused_presplit(rfr_plan* plan, int32_t on);
+rfr_status rfr_plan_get_fused_presplit(const rfr_plan* plan, int32_t* on);
 
 /* ---------------------------------------------------------------- serving */
 typedef struct rfr_server rfr_server;

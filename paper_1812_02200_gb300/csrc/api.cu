@@ -327,6 +327,7 @@ rfr_status push_core(rfr_plan* p, const int16_t* iq, int64_t n, const rfr_output
                     L.xs_lo = nullptr;
                     L.xs_rows = p->xs3_rows_cap;
                     L.tone_tile = p->tune.demod_bt;
+                    L.fused_presplit = p->tune.demod_fused;
                     if (defer_gemm) RFR_CUDA(p, rfr::demod3_prepare(L, st, defer_gemm));
                     else RFR_CUDA(p, rfr::demod3_launch(L, st));
                 } else {

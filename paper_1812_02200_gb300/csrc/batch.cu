@@ -88,10 +88,10 @@ std::string tune_key(const rfr_plan* p, int64_t n) {
 }
 
 // Minimal line-oriented JSON map:
-//   {"key": [pfb_lookahead, demod_raster, demod_tone_tile], ...}
-// (entries with two numbers have the default tone tile, 128)
+//   {"key": [pfb_lookahead, demod_raster, demod_tone_tile, demod_fused], ...}
+// (missing trailing numbers take their defaults: tone tile 128, not fused)
 struct TuneEntry {
-    int lookahead = 0, raster = 1, bt = 128;
+    int lookahead = 0, raster = 1, bt = 128, fused = 0;
 };
 std::map<std::string, TuneEntry> tune_load() {
     std::map<std::string, TuneEntry> m;
@@ -102,9 +102,10 @@ std::map<std::string, TuneEntry> tune_load() {
         const size_t b0 = line.find('[', q1 == std::string::npos ? 0 : q1);
         if (q0 == std::string::npos || q1 == std::string::npos || b0 == std::string::npos) continue;
         TuneEntry t;
-        const int got = std::sscanf(line.c_str() + b0, "[%d, %d, %d]", &t.lookahead, &t.raster, &t.bt);
+        const int got = std::sscanf(line.c_str() + b0, "[%d, %d, %d, %d]", &t.lookahead, &t.raster, &t.bt, &t.fused);
         if (got >= 2) {
             if (got == 2 || (t.bt != 64 && t.bt != 128)) t.bt = 128;
+            if (got < 4 || (t.fused != 0 && t.fused != 1)) t.fused = 0;
             m[line.substr(q0 + 1, q1 - q0 - 1)] = t;
         }
     }
@@ -119,7 +120,7 @@ void tune_store(const std::map<std::string, TuneEntry>& m) {
         size_t i = 0;
         for (const auto& kv : m) {
             f << "  \"" << kv.first << "\": [" << kv.second.lookahead << ", " << kv.second.raster << ", "
-              << kv.second.bt << "]" << (++i < m.size() ? "," : "") << "\n";
+              << kv.second.bt << ", " << kv.second.fused << "]" << (++i < m.size() ? "," : "") << "\n";
         }
         f << "}\n";
     }
@@ -272,6 +273,7 @@ rfr_status rfr_plan_autotune(rfr_plan* p, int64_t n_samples, int32_t use_cache, 
             p->tune.pfb_lookahead = it->second.lookahead;
             p->tune.demod_raster = it->second.raster;
             p->tune.demod_bt = it->second.bt;
+            p->tune.demod_fused = it->second.fused;
             p->tune.tuned = true;
             if (best_ms) *best_ms = -1.0;
             return RFR_OK;
@@ -282,10 +284,12 @@ rfr_status rfr_plan_autotune(rfr_plan* p, int64_t n_samples, int32_t use_cache, 
     if (p->mode == RFR_MODE_PFB) {
         for (int la : {1, 2, 3}) cand.push_back({la, 1, 128});
     } else {
-        for (int bt : {128, 64}) {
-            if (bt == 64 && p->demod_products != 3) continue;     // the tone tile is a three-product choice
-            for (int r : {1, 8, 19, 38}) cand.push_back({0, r, bt});
-        }
+        for (int fused : {0, 1})
+            for (int bt : {128, 64}) {
+                // the tone tile and the fused pre-split are three-product choices
+                if ((bt == 64 || fused) && p->demod_products != 3) continue;
+                for (int r : {1, 8, 19, 38}) cand.push_back({0, r, bt, fused});
+            }
     }
     // scratch buffers: zero input, outputs sized for the push
     const int64_t F = rfr::frames_for_samples(p, n_samples) + 1;
@@ -331,6 +335,7 @@ rfr_status rfr_plan_autotune(rfr_plan* p, int64_t n_samples, int32_t use_cache, 
         p->tune.pfb_lookahead = cand[c].lookahead;
         p->tune.demod_raster = cand[c].raster;
         p->tune.demod_bt = cand[c].bt;
+        p->tune.demod_fused = cand[c].fused;
         float ms_best = 1e30f;
         for (int rep = 0; rep < 4 && rs == RFR_OK; ++rep) {
             p->samples = s_samples;
@@ -369,6 +374,7 @@ rfr_status rfr_plan_autotune(rfr_plan* p, int64_t n_samples, int32_t use_cache, 
     p->tune.pfb_lookahead = best_c.lookahead;
     p->tune.demod_raster = best_c.raster;
     p->tune.demod_bt = best_c.bt;
+    p->tune.demod_fused = best_c.fused;
     p->tune.tuned = true;
     if (best_ms) *best_ms = best;
     if (use_cache) {
@@ -384,6 +390,18 @@ rfr_status rfr_plan_set_tone_tile(rfr_plan* p, int32_t tones_per_tile) {
     if (!p || p->mode != RFR_MODE_DEMOD || p->demod_products != 3 || (tones_per_tile != 64 && tones_per_tile != 128))
         return RFR_E_INVALID;
     p->tune.demod_bt = tones_per_tile;
+    return RFR_OK;
+}
+
+rfr_status rfr_plan_set_fused_presplit(rfr_plan* p, int32_t on) {
+    if (!p || p->mode != RFR_MODE_DEMOD || p->demod_products != 3 || (on != 0 && on != 1)) return RFR_E_INVALID;
+    p->tune.demod_fused = on;
+    return RFR_OK;
+}
+
+rfr_status rfr_plan_get_fused_presplit(const rfr_plan* p, int32_t* on) {
+    if (!p || !on) return RFR_E_INVALID;
+    *on = p->mode == RFR_MODE_DEMOD && p->demod_products == 3 ? p->tune.demod_fused : 0;
     return RFR_OK;
 }
 

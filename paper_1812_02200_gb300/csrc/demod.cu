@@ -378,6 +378,14 @@ demod_gemm_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constan
 // each) drain a slot with one load each, adding 2 P1 to both sums, P2 to the
 // imaginary and -P3 to the real sum.
 //
+// Fused pre-split (FUSED): instead of TMA loads of the six pre-split source
+// planes (written to HBM by presplit3_kernel, 12 bytes per sample), two
+// producer warps read the int16 stream view [carry | buffer] and write each
+// stage's A hi/lo tiles themselves, in the 128-byte swizzled layout the TMA
+// would produce, with the same FP32 -> FP16 hi/lo rounding as the pre-split
+// kernel (bit-identical planes, so bit-identical results); only the B tiles
+// arrive by TMA.  A launch choice the autotuner times.
+//
 // The kernel is persistent over a list of plans: one launch runs the tiles
 // of every demodulation stream of a batched step (or of one push), each CTA
 // striding over the global tile index; a tile's plan is found from the
@@ -388,6 +396,8 @@ constexpr uint32_t G3_A_BYTES = BM * G3_BK * 2;
 constexpr int G3_SLOTS = 4;
 constexpr int G3_EPI_WARPS = 16;          // 4 lane quadrants x 4 tone groups
 constexpr int G3_THREADS = (G3_EPI_WARPS + 2) * 32;
+constexpr int G3_FUSED_PRODUCERS = 2;                       // producer warps of the fused form
+constexpr int G3_THREADS_FUSED = (G3_EPI_WARPS + G3_FUSED_PRODUCERS + 1) * 32;
 template <int BT> struct G3Cfg {
     static constexpr uint32_t B_BYTES = BT * G3_BK * 2;
     static constexpr uint32_t STAGE_BYTES = 2 * G3_A_BYTES + 2 * B_BYTES;
@@ -398,10 +408,16 @@ template <int BT> struct G3Cfg {
 };
 
 struct G3Plan {
-    CUtensorMap a[6];   // (x sum/2, xr, xi) x (hi, lo): [rows][D] fp16, Toeplitz view
+    CUtensorMap a[6];   // (x sum/2, xr, xi) x (hi, lo): [rows][D] fp16, Toeplitz view (unused when fused)
     CUtensorMap b[6];   // (cr, ci - cr, cr + ci) x (hi, lo): [ntp][Lpad] fp16, K-major
     GemmArgs g;
     int tile0;          // first global tile of this plan
+    // fused form: the int16 stream view v[s] = s < cl ? carry[s] : buf[s - cl]
+    // for s < lv (0 beyond); vec: the buffer part may be read 16 bytes at a time
+    const uint32_t* carry;
+    const uint32_t* buf;
+    int64_t cl, lv;
+    int vec;
 };
 constexpr int kG3MaxPlans = 16;
 struct G3Batch {
@@ -459,8 +475,49 @@ __global__ void presplit3_kernel(const uint32_t* __restrict__ carry, int64_t cl,
     }
 }
 
-template <int BT>
-__global__ void __launch_bounds__(G3_THREADS, 1)
+// One row (frame m) of a stage's A hi/lo tiles in the fused form: view
+// samples s0 .. s0+63 -> plane q ((xr+xi)/2, xr or xi) -> FP16 hi/lo, eight
+// samples (one 16-byte chunk) at a time, chunk c of row i stored at
+// i*128 + ((c ^ (i & 7)) << 4) (the 128-byte swizzle).
+__device__ __forceinline__ void g3_fill_row(const G3Plan& P, int q, int64_t s0, unsigned char* ahi,
+                                            unsigned char* alo, int i) {
+    const bool in_buf = P.vec && s0 >= P.cl && s0 + G3_BK <= P.lv;
+    const uint32_t* bp = P.buf + (s0 - P.cl);
+#pragma unroll 2
+    for (int c = 0; c < G3_BK / 8; ++c) {
+        uint32_t w[8];
+        if (in_buf) {
+            const uint4 u0 = __ldg(reinterpret_cast<const uint4*>(bp + c * 8));
+            const uint4 u1 = __ldg(reinterpret_cast<const uint4*>(bp + c * 8 + 4));
+            w[0] = u0.x; w[1] = u0.y; w[2] = u0.z; w[3] = u0.w;
+            w[4] = u1.x; w[5] = u1.y; w[6] = u1.z; w[7] = u1.w;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int64_t sv = s0 + c * 8 + e;
+                w[e] = sv < P.lv ? (sv < P.cl ? __ldg(P.carry + sv) : __ldg(P.buf + (sv - P.cl))) : 0u;
+            }
+        }
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+            const float2 f0 = iq_to_f2(w[e]), f1 = iq_to_f2(w[e + 1]);
+            const float v0 = q == 0 ? 0.5f * (f0.x + f0.y) : (q == 1 ? f0.x : f0.y);   // exact in FP32
+            const float v1 = q == 0 ? 0.5f * (f1.x + f1.y) : (q == 1 ? f1.x : f1.y);
+            const __half h0 = __float2half_rn(v0), h1 = __float2half_rn(v1);
+            const __half l0 = __float2half_rn(v0 - __half2float(h0));
+            const __half l1 = __float2half_rn(v1 - __half2float(h1));
+            hi[e / 2] = static_cast<uint32_t>(__half_as_ushort(h0)) | (static_cast<uint32_t>(__half_as_ushort(h1)) << 16);
+            lo[e / 2] = static_cast<uint32_t>(__half_as_ushort(l0)) | (static_cast<uint32_t>(__half_as_ushort(l1)) << 16);
+        }
+        const uint32_t off = static_cast<uint32_t>(i) * 128u + (static_cast<uint32_t>(c ^ (i & 7)) << 4);
+        *reinterpret_cast<uint4*>(ahi + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4*>(alo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    }
+}
+
+template <int BT, bool FUSED>
+__global__ void __launch_bounds__(FUSED ? G3_THREADS_FUSED : G3_THREADS, 1)
 demod3m_gemm_kernel(const __grid_constant__ G3Batch bt) {
     using Cfg = G3Cfg<BT>;
     constexpr int STAGES = Cfg::STAGES;
@@ -475,11 +532,13 @@ demod3m_gemm_kernel(const __grid_constant__ G3Batch bt) {
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(sempty + G3_SLOTS);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
     int* const status0 = bt.p[0].g.status;
+    constexpr int PROD_WARP = G3_EPI_WARPS;                                  // first producer warp
+    constexpr int MMA_WARP = G3_EPI_WARPS + (FUSED ? G3_FUSED_PRODUCERS : 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
-            mbar_init(&full[s], 1);
+            mbar_init(&full[s], FUSED ? G3_FUSED_PRODUCERS * 32 : 1);
             mbar_init(&empty[s], 1);
         }
         for (int b = 0; b < G3_SLOTS; ++b) {
@@ -489,13 +548,13 @@ demod3m_gemm_kernel(const __grid_constant__ G3Batch bt) {
         *abort_flag = 0;
         fence_mbar_init();
     }
-    if (warp == G3_EPI_WARPS + 1) {
+    if (warp == MMA_WARP) {
         umma::alloc(tmem_holder, Cfg::TMEM_COLS);
         umma::relinquish();
     }
-    if (warp == G3_EPI_WARPS && lane < bt.n_plans) {
+    if (warp == PROD_WARP && lane < bt.n_plans) {
         for (int i = 0; i < 6; ++i) {
-            tma_prefetch_desc(&bt.p[lane].a[i]);
+            if (!FUSED) tma_prefetch_desc(&bt.p[lane].a[i]);
             tma_prefetch_desc(&bt.p[lane].b[i]);
         }
     }
@@ -506,7 +565,54 @@ demod3m_gemm_kernel(const __grid_constant__ G3Batch bt) {
     const int n_tiles = bt.total_tiles;
     constexpr uint32_t IDESC = umma::idesc_f16_f32(BM, BT);
 
-    if (warp == G3_EPI_WARPS) {
+    if (FUSED && warp >= PROD_WARP && warp < MMA_WARP) {
+        // ------------------------------------------------ fused producers
+        const int pt = threadIdx.x - PROD_WARP * 32;                         // 0 .. 63
+        uint32_t it = 0;
+        bool stop = false;
+        for (int tile = blockIdx.x; tile < n_tiles && !stop; tile += gridDim.x) {
+            const int pi = g3_plan_of(bt, tile);
+            const G3Plan& P = bt.p[pi];
+            int tm, tn;
+            tile_coords(P.g, tile - P.tile0, tm, tn);
+            const int m0 = tm * BM, n0 = tn * BT;
+            const int64_t D = P.g.two_d;
+            for (int kb0 = 0; kb0 < P.g.KB && !stop; kb0 += P.g.kchunk) {
+                const int kb1 = min(kb0 + P.g.kchunk, P.g.KB);
+                for (int q = 0; q < 3 && !stop; ++q) {
+                    for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                        const int s = it % STAGES;
+                        const uint32_t ph = (it / STAGES) & 1;
+                        if (*abort_flag || !mbar_wait(&empty[s], ph ^ 1, status0)) {
+                            *abort_flag = 1;
+                            stop = true;
+                            break;
+                        }
+                        unsigned char* st = smem + s * STAGE_BYTES;
+                        const int kt = kb * G3_BK;
+                        if (pt == 0) {
+                            mbar_expect_tx(&full[s], 2 * B_BYTES);
+                            tma_load_2d(st + 2 * G3_A_BYTES, &P.b[2 * q], kt, n0, &full[s]);
+                            tma_load_2d(st + 2 * G3_A_BYTES + B_BYTES, &P.b[2 * q + 1], kt, n0, &full[s]);
+                        }
+#pragma unroll 1
+                        for (int i = pt; i < BM; i += G3_FUSED_PRODUCERS * 32)
+                            g3_fill_row(P, q, (static_cast<int64_t>(m0) + i) * D + kt, st, st + G3_A_BYTES, i);
+                        fence_proxy_async_smem();                 // the MMAs read the tiles through the async proxy
+                        mbar_arrive(&full[s]);
+                    }
+                }
+            }
+        }
+        // the B copies still in flight complete before the CTA exits
+        if (pt == 0) {
+            for (uint32_t k = 0; k < static_cast<uint32_t>(STAGES) && it > 0; ++k) {
+                const uint32_t j = it - 1 - k;
+                if (static_cast<int32_t>(j) < 0) break;
+                mbar_wait(&full[j % STAGES], (j / STAGES) & 1, status0);
+            }
+        }
+    } else if (!FUSED && warp == PROD_WARP) {
         // ------------------------------------------------ TMA producer
         if (lane == 0) {
             uint32_t it = 0;
@@ -547,7 +653,7 @@ demod3m_gemm_kernel(const __grid_constant__ G3Batch bt) {
                 mbar_wait(&full[j % STAGES], (j / STAGES) & 1, status0);
             }
         }
-    } else if (warp == G3_EPI_WARPS + 1) {
+    } else if (warp == MMA_WARP) {
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
             uint32_t it = 0, phase = 0;
@@ -593,7 +699,7 @@ demod3m_gemm_kernel(const __grid_constant__ G3Batch bt) {
             }
         }
         __syncwarp();
-    } else {
+    } else if (warp < G3_EPI_WARPS) {
         // ------------------------------------------------ epilogue (16 warps)
         constexpr int TPG = Cfg::TPG;
         const int qd = warp & 3, grp = warp >> 2;          // lane quadrant, tone group
@@ -668,7 +774,7 @@ demod3m_gemm_kernel(const __grid_constant__ G3Batch bt) {
     }
     umma::fence_before_sync();
     __syncthreads();
-    if (warp == G3_EPI_WARPS + 1) {
+    if (warp == MMA_WARP) {
         umma::fence_after_sync();
         umma::dealloc(tmem, Cfg::TMEM_COLS);
     }
@@ -783,10 +889,11 @@ cudaError_t demod3_build_taps(const double* d_h, const uint64_t* d_words, int n_
 cudaError_t demod3_prepare(const DemodLaunch& L, cudaStream_t st, DemodGemmJob* job) {
     job->n_tiles = 0;
     job->bt = L.tone_tile == 64 ? 64 : 128;
+    job->fused = L.fused_presplit ? 1 : 0;
     if (L.F <= 0) return cudaSuccess;
     if (L.D % G3_BK != 0 || L.Lpad % G3_BK != 0 || L.ntp % 128 != 0) return cudaErrorInvalidValue;
     const int64_t rows = static_cast<int64_t>(demod3_xs_rows(L.F, L.Lpad, L.D));
-    if (rows > L.xs_rows) return cudaErrorInvalidValue;
+    if (!job->fused && rows > L.xs_rows) return cudaErrorInvalidValue;
     const int bt = job->bt;
     const int n_mt = static_cast<int>((L.F + BM - 1) / BM);
     const int n_nt = (L.n_tones + bt - 1) / bt;       // tiles past the last tone are skipped
@@ -796,17 +903,27 @@ cudaError_t demod3_prepare(const DemodLaunch& L, cudaStream_t st, DemodGemmJob* 
     const int64_t nrot = static_cast<int64_t>(n_anch) * L.ntp + static_cast<int64_t>(L.ntp) * BM;
     rot_kernel<<<grid_for(nrot, L.n_sms), 256, 0, st>>>(L.words, L.n_tones, L.ntp, L.F0 / BM, L.L, L.D, n_anch,
                                                          anchors, steps);
-    const int64_t total = rows * L.D;
-    __half* xp = static_cast<__half*>(L.xs_hi);
-    presplit3_kernel<<<grid_for(total, L.n_sms), 256, 0, st>>>(
-        reinterpret_cast<const uint32_t*>(L.carry), L.cl, reinterpret_cast<const uint32_t*>(L.buf), L.cl + L.n,
-        total, xp);
     G3Plan* P = reinterpret_cast<G3Plan*>(job->bytes);
     std::memset(P, 0, sizeof(G3Plan));
     const __half* bp = static_cast<const __half*>(L.b_hi);
     const int64_t bplane = static_cast<int64_t>(L.ntp) * L.Lpad;
+    const int64_t total = rows * L.D;
+    __half* xp = static_cast<__half*>(L.xs_hi);
+    if (job->fused) {
+        // the GEMM's producers read the stream view themselves
+        P->carry = reinterpret_cast<const uint32_t*>(L.carry);
+        P->buf = reinterpret_cast<const uint32_t*>(L.buf);
+        P->cl = L.cl;
+        P->lv = L.cl + L.n;
+        P->vec = (reinterpret_cast<uintptr_t>(L.buf) % 16 == 0) && ((L.cl % 4) + 4) % 4 == 0 ? 1 : 0;
+    } else {
+        presplit3_kernel<<<grid_for(total, L.n_sms), 256, 0, st>>>(
+            reinterpret_cast<const uint32_t*>(L.carry), L.cl, reinterpret_cast<const uint32_t*>(L.buf), L.cl + L.n,
+            total, xp);
+    }
     for (int i = 0; i < 6; ++i) {
-        if (!make_map(&P->a[i], xp + i * total, static_cast<uint64_t>(L.D), static_cast<uint64_t>(rows), BM) ||
+        if ((!job->fused &&
+             !make_map(&P->a[i], xp + i * total, static_cast<uint64_t>(L.D), static_cast<uint64_t>(rows), BM)) ||
             !make_map(&P->b[i], bp + i * bplane, static_cast<uint64_t>(L.Lpad), static_cast<uint64_t>(L.ntp), bt))
             return cudaErrorInvalidValue;
     }
@@ -833,34 +950,38 @@ cudaError_t demod3_prepare(const DemodLaunch& L, cudaStream_t st, DemodGemmJob* 
 }
 
 namespace {
-template <int BT>
+template <int BT, bool FUSED>
 cudaError_t g3_run(const G3Batch& b, int n_sms, cudaStream_t st) {
     using Cfg = G3Cfg<BT>;
-    cudaError_t e = cudaFuncSetAttribute(demod3m_gemm_kernel<BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(demod3m_gemm_kernel<BT, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(Cfg::SMEM));
     if (e != cudaSuccess) return e;
     const int grid = std::max(1, std::min(b.total_tiles, n_sms));
-    demod3m_gemm_kernel<BT><<<grid, G3_THREADS, Cfg::SMEM, st>>>(b);
+    demod3m_gemm_kernel<BT, FUSED><<<grid, FUSED ? G3_THREADS_FUSED : G3_THREADS, Cfg::SMEM, st>>>(b);
     return cudaGetLastError();
 }
 }  // namespace
 
 cudaError_t demod3_gemm(const DemodGemmJob* const* jobs, int n, int n_sms, cudaStream_t st) {
-    // one persistent launch per group of up to kG3MaxPlans jobs of the same tile width
-    for (int bt : {128, 64}) {
+    // one persistent launch per group of up to kG3MaxPlans jobs of the same
+    // tile width and producer form
+    for (int variant = 0; variant < 4; ++variant) {
+        const int bt = variant & 1 ? 64 : 128;
+        const int fused = variant >> 1;
         G3Batch b;
         b.n_plans = 0;
         b.total_tiles = 0;
         for (int i = 0; i <= n; ++i) {
             const bool flush = i == n || b.n_plans == kG3MaxPlans;
             if (flush && b.n_plans > 0) {
-                const cudaError_t e = bt == 128 ? g3_run<128>(b, n_sms, st) : g3_run<64>(b, n_sms, st);
+                const cudaError_t e = bt == 128 ? (fused ? g3_run<128, true>(b, n_sms, st) : g3_run<128, false>(b, n_sms, st))
+                                                : (fused ? g3_run<64, true>(b, n_sms, st) : g3_run<64, false>(b, n_sms, st));
                 if (e != cudaSuccess) return e;
                 b.n_plans = 0;
                 b.total_tiles = 0;
             }
             if (i == n) break;
-            if (jobs[i]->bt != bt || jobs[i]->n_tiles <= 0) continue;
+            if (jobs[i]->bt != bt || jobs[i]->fused != fused || jobs[i]->n_tiles <= 0) continue;
             std::memcpy(&b.p[b.n_plans], jobs[i]->bytes, sizeof(G3Plan));
             b.p[b.n_plans].tile0 = b.total_tiles;
             b.total_tiles += jobs[i]->n_tiles;

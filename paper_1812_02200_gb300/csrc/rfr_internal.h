@@ -131,6 +131,7 @@ struct DemodLaunch {
     int kchunk;                 // k-blocks per TMEM accumulation chunk
     int raster_group;           // tile order: groups of this many 128-frame tiles sweep all tones
     int tone_tile;              // three-product GEMM: tones per tile, 128 or 64 (0 = 128)
+    int fused_presplit;         // three-product GEMM: producers convert the int16 stream themselves
 };
 // The three-product GEMM of one push, described for a persistent launch that
 // may cover several plans (opaque record of demod.cu).
@@ -138,6 +139,7 @@ constexpr int kDemodJobBytes = 2048;
 struct DemodGemmJob {
     alignas(128) unsigned char bytes[kDemodJobBytes];
     int bt = 128;               // tone-tile width
+    int fused = 0;              // pre-split fused into the GEMM's producers
     int n_tiles = 0;            // 0: nothing to launch
 };
 cudaError_t demod_build_taps(const double* d_h, const uint64_t* d_words, int n_tones, int ntp,
@@ -197,6 +199,7 @@ struct TuneConfig {
     int pfb_lookahead = 0;      // 0 = as many ring super-blocks as shared memory allows
     int demod_raster = 1;       // 1 = tones fastest across the whole grid
     int demod_bt = 128;         // three-product GEMM: tones per tile (128 or 64)
+    int demod_fused = 0;        // three-product GEMM: pre-split fused into its producers (0/1)
     bool tuned = false;
 };
 

@@ -115,6 +115,8 @@ _SIGS = {
     "rfr_plan_inject_device_status": (C.c_int, [_P, C.c_int32]),
     "rfr_plan_get_tone_tile": (C.c_int, [_P, C.POINTER(C.c_int32)]),
     "rfr_plan_set_tone_tile": (C.c_int, [_P, C.c_int32]),
+    "rfr_plan_set_fused_presplit": (C.c_int, [_P, C.c_int32]),
+    "rfr_plan_get_fused_presplit": (C.c_int, [_P, C.POINTER(C.c_int32)]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -349,6 +351,12 @@ class Plan:
         result-neutral, normally chosen by autotune()."""
         self._check(_lib.rfr_plan_set_tone_tile(self._h, int(tones_per_tile)), "set_tone_tile")
 
+    def set_fused_presplit(self, on: bool):
+        """Three-product demodulation: the FP16 split of the stream inside the
+        GEMM's producers (True) or as its own kernel (False); result-neutral,
+        normally chosen by autotune()."""
+        self._check(_lib.rfr_plan_set_fused_presplit(self._h, 1 if on else 0), "set_fused_presplit")
+
     def inject_device_status(self, status: int):
         """Write the plan's device status word as a timed-out kernel would
         (1), or clear it (0): host-side failure injection for tests."""
@@ -363,9 +371,11 @@ class Plan:
     def tune(self) -> dict:
         a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
         self._check(_lib.rfr_plan_get_tune(self._h, C.byref(a), C.byref(b), C.byref(c)), "tune")
-        t = C.c_int32()
+        t, f = C.c_int32(), C.c_int32()
         self._check(_lib.rfr_plan_get_tone_tile(self._h, C.byref(t)), "tone tile")
-        return {"pfb_lookahead": a.value, "demod_raster": b.value, "tone_tile": t.value, "tuned": bool(c.value)}
+        self._check(_lib.rfr_plan_get_fused_presplit(self._h, C.byref(f)), "fused pre-split")
+        return {"pfb_lookahead": a.value, "demod_raster": b.value, "tone_tile": t.value,
+                "fused_presplit": f.value, "tuned": bool(c.value)}
 
     def state_export(self) -> bytes:
         n = C.c_size_t()

@@ -208,3 +208,93 @@ def test_persistent_gemm_over_many_plans(lib):
     for i, (ob, oa) in enumerate(zip(outs_b, outs_a)):
         assert torch.equal(ob, oa), i
     batch.close()
+
+
+FUSED_SHAPES = [
+    # L, D, tones, window, cutoff, bt
+    (1024, 512, 40, "hann", 1e-3, 128),
+    (1000, 512, 130, "hann", 2e-3, 64),       # L not a multiple of 64
+    (4096, 2048, 160, "blackman", 2e-4, 128),
+    (1024, 2048, 50, "hamming", 1e-3, 128),   # L < D: the view skips D - L samples
+    (3000, 448, 300, "hann", 1e-3, 64),
+    (256, 64, 8, "blackman", 0.01, 128),
+]
+
+
+@pytest.mark.parametrize("L,D,nt,win,fc,bt", FUSED_SHAPES)
+def test_fused_presplit_equals_two_kernels_and_oracle(lib, L, D, nt, win, fc, bt):
+    """The FP16 split of the stream done by the GEMM's producer warps gives,
+    bit for bit, the frames of the separate pre-split kernel: one push of a
+    ragged buffer, then a stream pushed in odd-sized pieces (carry lengths and
+    buffer addresses that are not multiples of 4 samples / 16 bytes take the
+    per-sample path)."""
+    case = siggen.demod_case(D * 90 + 37, nt, seed=7100 + L + nt)
+    a = _plan3(lib, L, D, case["words"], win, fc)
+    b = _plan3(lib, L, D, case["words"], win, fc)
+    a.set_tone_tile(bt)
+    b.set_tone_tile(bt)
+    b.set_fused_presplit(True)
+    assert b.tune()["fused_presplit"] == 1 and a.tune()["fused_presplit"] == 0
+    ga = _run(a, case["x"], nt)
+    gb = _run(b, case["x"], nt)
+    assert np.array_equal(ga, gb)
+    ref = oracle.demod(case["x"], L, D, oracle.lowpass(win, L, fc), case["words"])
+    assert rel_rows(gb, ref).max() < TOL
+    # streamed in odd pieces through the fused form = one push
+    c = _plan3(lib, L, D, case["words"], win, fc)
+    c.set_tone_tile(bt)
+    c.set_fused_presplit(True)
+    x = torch.from_numpy(case["x"]).to(DEV)
+    F = ga.shape[1]
+    out = torch.zeros((nt, F), dtype=torch.complex64, device=DEV)
+    rng = np.random.default_rng(L + D)
+    pos, off = 0, 0
+    while pos < x.shape[0]:
+        cnt = min(int(rng.integers(1, 7 * D)), x.shape[0] - pos)
+        off += c.push_into(x[pos:pos + cnt], tones=out, frame_offset=off)
+        pos += cnt
+    torch.cuda.synchronize()
+    assert off == F
+    assert np.array_equal(out.cpu().numpy(), ga)
+
+
+def test_fused_presplit_far_origin_and_batch(lib):
+    """The fused form at an absolute origin past 2^40 against the oracle, and
+    in a batched step beside plans of the other forms (one persistent launch
+    per form) equal to the streams alone."""
+    L, D, nt = 2048, 512, 70
+    halo = L - D
+    S = (2 ** 40 + D - 1) // D * D + 3 * D
+    case = siggen.demod_case(halo + D * 100 + 9, nt, seed=7301)
+    p = _plan3(lib, L, D, case["words"], "blackman", 1e-3)
+    p.set_fused_presplit(True)
+    x = torch.from_numpy(case["x"]).to(DEV)
+    p.seek(S, x[:halo])
+    F = p.frames_for(x.shape[0] - halo)
+    out = torch.zeros((nt, F), dtype=torch.complex64, device=DEV)
+    assert p.push_into(x[halo:], tones=out) == F
+    torch.cuda.synchronize()
+    h64, _ = p.taps_table()
+    ref = oracle.demod(case["x"], L, D, h64, case["words"], S // D, S // D + F, m0=S - halo)
+    assert rel_rows(out.cpu().numpy(), ref).max() < TOL
+    # batch: fused/unfused x tile widths
+    plans_b, plans_a, xs, ob, oa = [], [], [], [], []
+    for i, (fused, bt) in enumerate([(1, 128), (0, 128), (1, 64), (0, 64), (1, 128)]):
+        c = siggen.demod_case(D * 70 + 11 * i, 30 + 40 * i, seed=7400 + i)
+        for lst in (plans_b, plans_a):
+            q = _plan3(lib, 1024, D, c["words"], "hann", 1e-3)
+            q.set_fused_presplit(bool(fused))
+            q.set_tone_tile(bt)
+            lst.append(q)
+        xs.append(torch.from_numpy(c["x"]).to(DEV))
+        Fi = plans_a[-1].frames_for(xs[-1].shape[0])
+        ob.append(torch.zeros((30 + 40 * i, Fi), dtype=torch.complex64, device=DEV))
+        oa.append(torch.zeros((30 + 40 * i, Fi), dtype=torch.complex64, device=DEV))
+    batch = lib.Batch(plans_b)
+    batch.push(xs, None, ob)
+    for q, xx, o in zip(plans_a, xs, oa):
+        q.push_into(xx, tones=o)
+    torch.cuda.synchronize()
+    for i, (u, v) in enumerate(zip(ob, oa)):
+        assert torch.equal(u, v), i
+    batch.close()
