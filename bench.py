@@ -412,6 +412,25 @@ def run_demod(args, dev, stream, rank):
                                 "MMAs (2.25x the algorithmic flops on the tensor pipe); push time "
                                 "includes the rotation, pre-split and carry kernels",
                         "peak_kind": f"{peak_kind} dense bf16 (fp16 has the same nominal rate)"}}
+    # -- the same three-product GEMM with the FP16 split fused into its
+    # producer warps (no pre-split kernel; each A tile converted once per tone
+    # tile and product)
+    pf = rfr.Plan(0, DEMOD_L, window="blackman", cutoff=DEMOD_FC, words=c["words"], decimation=DEMOD_D)
+    pf.set_tone_tile(plan.tune()["tone_tile"] or 128)
+    pf.set_fused_presplit(True)
+    pf.push_into(x, tones=out, stream=stream)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(2):
+        pf.push_into(x, tones=out, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    msf = e0.elapsed_time(e1) / 2
+    res["fused_presplit"] = {"value": samples / (msf * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": msf,
+                             "note": "pre-split fused into two producer warps of the GEMM: no 12 B/sample "
+                                     "pass through HBM, but every A tile is converted once per tone tile and "
+                                     "product (48 times per sample at 2048 tones)"}
+    pf.close()
     # -- the four-product (real-embedding) form of the same contraction
     p4 = rfr.Plan(0, DEMOD_L, window="blackman", cutoff=DEMOD_FC, words=c["words"], decimation=DEMOD_D)
     p4.set_demod_products(4)

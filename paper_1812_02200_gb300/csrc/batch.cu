@@ -284,10 +284,15 @@ rfr_status rfr_plan_autotune(rfr_plan* p, int64_t n_samples, int32_t use_cache, 
     if (p->mode == RFR_MODE_PFB) {
         for (int la : {1, 2, 3}) cand.push_back({la, 1, 128});
     } else {
+        // the fused pre-split converts each A tile once per tone tile and
+        // product (3 x tone tiles times per sample): timed only for plans of
+        // at most two 128-tone tiles, where that stays cheap
+        const bool try_fused = p->demod_products == 3 && p->words.size() <= 256;
         for (int fused : {0, 1})
             for (int bt : {128, 64}) {
                 // the tone tile and the fused pre-split are three-product choices
                 if ((bt == 64 || fused) && p->demod_products != 3) continue;
+                if (fused && !try_fused) continue;
                 for (int r : {1, 8, 19, 38}) cand.push_back({0, r, bt, fused});
             }
     }

@@ -661,6 +661,73 @@ __global__ void __launch_bounds__(kFirThreads) gen_fir_kernel(const GenArgs a) {
     }
 }
 
+// The FIR ahead of pass A for hop == N (every frame shifted alike): a thread
+// takes kMfPts points of kMfFrames consecutive frames.  Frame f + g reads
+// input blocks g .. g + T - 1 (block r = samples base + r*N + pos), so the
+// kMfFrames + T - 1 blocks are loaded and converted once and each feeds the
+// frames that use it, in tap order t = r - g = 0 .. T-1 from zero (the same
+// sums as gen_fir_kernel, bit for bit); the taps are loaded once for all the
+// thread's frames.
+constexpr int kMfPts = 4, kMfFrames = 4;
+template <int TC>
+__global__ void __launch_bounds__(kFirThreads) gen_fir_frames_kernel(const GenArgs a) {
+    constexpr int G = kMfFrames, P = kMfPts, R = G + TC - 1;
+    const int64_t f0 = static_cast<int64_t>(blockIdx.y) * G;            // first frame (of this launch)
+    const int gn = static_cast<int>(a.F - f0 < G ? a.F - f0 : G);       // frames of this row that exist
+    const int64_t base = (a.k0 + f0) * a.hop;
+    const int N = a.N, sh = a.sh_fixed;
+    const int qb = static_cast<int>(blockIdx.x) * (kFirThreads * P) + static_cast<int>(threadIdx.x);
+    int pos[P];
+    float hv[TC][P];
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+        const int q = qb + j * kFirThreads;
+        pos[j] = q < N ? (q >= sh ? q - sh : q - sh + N) : 0;
+#pragma unroll
+        for (int t = 0; t < TC; ++t) hv[t][j] = __ldg(a.h + (t * N + pos[j]));
+    }
+    float ar[G][P], ai[G][P];
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+#pragma unroll
+        for (int j = 0; j < P; ++j) ar[g][j] = ai[g][j] = 0.f;
+    const bool fast = base >= a.cl;
+    const uint32_t* xp = a.buf + (base - a.cl);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (r >= gn + TC - 1) break;                                    // blocks past the last frame
+        float2 x[P];
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+            const int64_t o = static_cast<int64_t>(r) * N + pos[j];
+            uint32_t w;
+            if (fast) w = __ldg(xp + o);
+            else w = base + o < a.cl ? __ldg(a.carry + (base + o)) : __ldg(a.buf + (base + o - a.cl));
+            x[j] = iq_to_f2(w);
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const int t = r - g;
+            if (t < 0 || t >= TC) continue;
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+                ar[g][j] = fmaf(hv[t][j], x[j].x, ar[g][j]);
+                ai[g][j] = fmaf(hv[t][j], x[j].y, ai[g][j]);
+            }
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        if (g >= gn) break;
+        float2* vrow = a.v + (f0 + g) * N;
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+            const int q = qb + j * kFirThreads;
+            if (q < N) vrow[q] = make_float2(ar[g][j], ai[g][j]);
+        }
+    }
+}
+
 template <int TH>
 __global__ void __launch_bounds__(TH, GenCfg<TH>::kMinBlocks)
     gen_pass_a_kernel(const GenArgs a, const __grid_constant__ CUtensorMap tmv) {
@@ -1046,12 +1113,20 @@ cudaError_t gen_run(GenArgs a, const PfbLaunch& L, const GenPlan& g, cudaStream_
         if (a.vtma) {
             const dim3 fg(static_cast<unsigned>((g.N + kFirThreads * kFirPts - 1) / (kFirThreads * kFirPts)),
                           static_cast<unsigned>(a.F));
-            switch (a.T) {
-            case 1: gen_fir_kernel<1><<<fg, kFirThreads, 0, st>>>(a); break;
-            case 2: gen_fir_kernel<2><<<fg, kFirThreads, 0, st>>>(a); break;
-            case 3: gen_fir_kernel<3><<<fg, kFirThreads, 0, st>>>(a); break;
-            case 4: gen_fir_kernel<4><<<fg, kFirThreads, 0, st>>>(a); break;
-            case 8: gen_fir_kernel<8><<<fg, kFirThreads, 0, st>>>(a); break;
+            // hop == N: blocks shared by consecutive frames are read once
+            const dim3 fm(static_cast<unsigned>((g.N + kFirThreads * kMfPts - 1) / (kFirThreads * kMfPts)),
+                          static_cast<unsigned>((a.F + kMfFrames - 1) / kMfFrames));
+            const bool frames = a.sh_fixed >= 0 && a.hop == g.N;
+            switch (frames ? a.T : -a.T) {
+            case 2: gen_fir_frames_kernel<2><<<fm, kFirThreads, 0, st>>>(a); break;
+            case 3: gen_fir_frames_kernel<3><<<fm, kFirThreads, 0, st>>>(a); break;
+            case 4: gen_fir_frames_kernel<4><<<fm, kFirThreads, 0, st>>>(a); break;
+            case 8: gen_fir_frames_kernel<8><<<fm, kFirThreads, 0, st>>>(a); break;
+            case 1: case -1: gen_fir_kernel<1><<<fg, kFirThreads, 0, st>>>(a); break;
+            case -2: gen_fir_kernel<2><<<fg, kFirThreads, 0, st>>>(a); break;
+            case -3: gen_fir_kernel<3><<<fg, kFirThreads, 0, st>>>(a); break;
+            case -4: gen_fir_kernel<4><<<fg, kFirThreads, 0, st>>>(a); break;
+            case -8: gen_fir_kernel<8><<<fg, kFirThreads, 0, st>>>(a); break;
             default: gen_fir_kernel<0><<<fg, kFirThreads, 0, st>>>(a); break;
             }
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
