@@ -693,18 +693,23 @@ __global__ void __launch_bounds__(kFirThreads) gen_fir_frames_kernel(const GenAr
         for (int j = 0; j < P; ++j) ar[g][j] = ai[g][j] = 0.f;
     const bool fast = base >= a.cl;
     const uint32_t* xp = a.buf + (base - a.cl);
+    // every block's loads issued before the first use (blocks past the last
+    // frame of the row read as zero and feed no existing frame)
+    uint32_t w[R][P];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        if (r >= gn + TC - 1) break;                                    // blocks past the last frame
-        float2 x[P];
+    for (int r = 0; r < R; ++r)
 #pragma unroll
         for (int j = 0; j < P; ++j) {
             const int64_t o = static_cast<int64_t>(r) * N + pos[j];
-            uint32_t w;
-            if (fast) w = __ldg(xp + o);
-            else w = base + o < a.cl ? __ldg(a.carry + (base + o)) : __ldg(a.buf + (base + o - a.cl));
-            x[j] = iq_to_f2(w);
+            if (r >= gn + TC - 1) w[r][j] = 0u;
+            else if (fast) w[r][j] = __ldg(xp + o);
+            else w[r][j] = base + o < a.cl ? __ldg(a.carry + (base + o)) : __ldg(a.buf + (base + o - a.cl));
         }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        float2 x[P];
+#pragma unroll
+        for (int j = 0; j < P; ++j) x[j] = iq_to_f2(w[r][j]);
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             const int t = r - g;
