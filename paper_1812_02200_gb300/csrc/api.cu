@@ -196,6 +196,76 @@ rfr_status ensure_demod_scratch(rfr_plan* p, int64_t F, int64_t F0, cudaStream_t
     return RFR_OK;
 }
 
+// Oversampled N = 4096 PFB as phase passes.  With hop H = N/R, frame
+// j = R*i + k of the push starts at view sample i*N + k*H, so the frames of
+// phase k are the critically sampled PFB of the view shifted by k*H samples
+// (one fused-kernel launch), written to full rows fo + k + R*i (row pitch
+// R*ld) and tone columns fo + k + R*i (column stride R).  The channel phase
+// of the absolute time origin is exp(-2*pi*i*c*s/N) with s = (a0 + k*H) mod N
+// a multiple of H, i.e. (-i)^(c*m) with m = s/H (R = 4) or (-1)^(c*m)
+// (R = 2): an exact swap/negation of each bin, applied by the kernel.  A
+// push that is not 16-byte aligned (or whose carry is not a multiple of 4
+// samples) first copies [carry | buffer] into one aligned scratch view.
+rfr_status phase_passes(rfr_plan* p, const rfr::PfbLaunch& L0, const rfr_output* o, int64_t lv, int64_t F,
+                        cudaStream_t st) {
+    const int R = p->phase_R;
+    const int64_t H = p->H, N = p->N;
+    const int16_t* vcarry = L0.carry;
+    const int16_t* vbuf = L0.buf;
+    int64_t vcl = L0.cl;
+    const bool aligned = (reinterpret_cast<uintptr_t>(L0.buf) % 16 == 0) && (L0.cl % 4 == 0) &&
+                         (reinterpret_cast<uintptr_t>(L0.carry) % 16 == 0);
+    if (!aligned) {
+        if (lv > p->view_cap) {
+            const rfr_status rs = refuse_growth_in_capture(p, st);
+            if (rs != RFR_OK) return rs;
+            cudaDeviceSynchronize();
+            dev_free(p->d_view);
+            p->d_view = nullptr;
+            p->view_cap = 0;
+            RFR_CUDA(p, dev_alloc(&p->d_view, static_cast<size_t>(lv) * 4));
+            p->view_cap = lv;
+        }
+        RFR_CUDA(p, rfr::carry_update(L0.carry, L0.cl, L0.buf, L0.n, 0, lv, p->d_view, st));
+        vcarry = p->d_view;
+        vbuf = p->d_view;
+        vcl = 0;
+    }
+    for (int k = 0; k < R; ++k) {
+        const int64_t Fk = (F - k + R - 1) / R;           // frames R*i + k < F
+        if (Fk <= 0) continue;
+        const int64_t off = k * H;
+        rfr::PfbLaunch L = L0;
+        if (off < vcl) {
+            L.carry = vcarry + 2 * off;
+            L.cl = vcl - off;
+            L.buf = vbuf;
+        } else {
+            L.carry = vcarry;
+            L.cl = 0;
+            L.buf = vbuf + 2 * (off - vcl);
+        }
+        L.n = (lv - off) - L.cl;
+        L.F = Fk;
+        L.frame_offset = 0;
+        L.hop = static_cast<int>(N);
+        if (L0.full) {
+            L.full = static_cast<float2*>(L0.full) + (o->frame_offset + k) * o->full_ld;
+            L.full_ld = R * o->full_ld;
+        }
+        if (L0.tones) {
+            L.tones = static_cast<float2*>(L0.tones) + o->frame_offset + k;
+            L.tone_cs = R;
+        }
+        const int64_t s = ((L0.a0 + off) % N + N) % N;     // a multiple of H
+        const int m = static_cast<int>(s / H);
+        L.rot = R == 4 ? m : 2 * m;
+        L.a0 = L0.a0 + off;
+        RFR_CUDA(p, rfr::pfb_launch(L, st));
+    }
+    return RFR_OK;
+}
+
 }  // namespace
 
 namespace rfr {
@@ -214,6 +284,17 @@ rfr_status ensure_scratch(rfr_plan* p, int64_t n) {
     // later pushes of up to n samples never allocate (nor synchronise)
     const int64_t F = frames_for_len(p, std::max<int64_t>(p->cl, p->W - 1) + n);
     if (p->mode == RFR_MODE_PFB && p->gen && F > 0) RFR_CUDA(p, rfr::gen_plan_reserve(&p->gplan, F));
+    if (p->mode == RFR_MODE_PFB && p->phase_R > 1) {
+        const int64_t lv = std::max<int64_t>(p->cl, p->W - 1) + n;
+        if (lv > p->view_cap) {
+            cudaDeviceSynchronize();
+            dev_free(p->d_view);
+            p->d_view = nullptr;
+            p->view_cap = 0;
+            RFR_CUDA(p, dev_alloc(&p->d_view, static_cast<size_t>(lv) * 4));
+            p->view_cap = lv;
+        }
+    }
     if (p->mode == RFR_MODE_DEMOD && F > 0 && !p->words.empty()) return ensure_demod_scratch(p, F, -1, nullptr);
     return RFR_OK;
 }
@@ -266,7 +347,12 @@ rfr_status push_core(rfr_plan* p, const int16_t* iq, int64_t n, const rfr_output
                 else if (p->gplan.z_frames < 1)
                     return fail(p, RFR_E_INVALID, "reserve scratch (a push outside capture) before capturing");
             }
-            RFR_CUDA(p, p->gen ? rfr::gen_pfb_launch(L, p->gplan, st) : rfr::pfb_launch(L, st));
+            if (p->phase_R > 1) {
+                rfr_status rs = phase_passes(p, L, o, lv, F, st);
+                if (rs != RFR_OK) return rs;
+            } else {
+                RFR_CUDA(p, p->gen ? rfr::gen_pfb_launch(L, p->gplan, st) : rfr::pfb_launch(L, st));
+            }
         } else if (p->mode == RFR_MODE_CHIRP) {
             rfr::ChirpLaunch L{};
             L.carry = carry;
@@ -376,7 +462,7 @@ void destroy(rfr_plan* p) {
                     static_cast<void*>(p->d_words), static_cast<void*>(p->d_rates), static_cast<void*>(p->d_h32), p->d_c32, p->d_bhi, p->d_blo,
                     static_cast<void*>(p->d_status), static_cast<void*>(p->d_carry[0]),
                     static_cast<void*>(p->d_carry[1]), p->d_xs_hi, p->d_xs_lo, p->d_rot, p->d_qfull, p->d_b3, p->d_xs3,
-                    p->d_qtones})
+                    p->d_qtones, static_cast<void*>(p->d_view)})
         dev_free(q);
     for (int i = 0; i < rfr_plan::kStageBufs; ++i) {
         dev_free(p->d_stage_in[i]);
@@ -472,7 +558,14 @@ rfr_status rfr_plan_create(rfr_plan** out, int32_t channels, int32_t taps, const
         // powers of two from 16 to 16384, critically sampled: the fused
         // single-CTA kernels; every other N = 2^a 3^b 5^c 7^d up to 2^24 and
         // every hop < N (oversampled): the mixed-radix kernels
-        p->gen = !pow2 || channels < 16 || channels > 16384 || decimation != channels;
+        // N = 4096, T = 8 with hop N/2 or N/4: the oversampled frames are
+        // N/hop interleaved critically sampled PFBs of the stream shifted by
+        // k*hop (k < N/hop), each rotated by an exact quarter-turn power per
+        // bin (the channel phase of the absolute time origin), so they run on
+        // the symmetric-tap fused kernel as phase passes
+        const bool phase = pow2 && channels == 4096 && taps == 8 && (decimation == 2048 || decimation == 1024);
+        p->gen = !phase && (!pow2 || channels < 16 || channels > 16384 || decimation != channels);
+        p->phase_R = phase ? channels / decimation : 1;
         if (p->gen && !rfr::gen_supported(channels)) return bad(RFR_E_UNSUPPORTED);
         if (p->gen) {
             p->Tk = taps;

@@ -67,6 +67,8 @@ struct PfbArgs {
     int nb_smem;             // TMEM variant: tones staged in smem (0 or n_tones)
     int full_bulk;           // TMEM variant: full rows written by one TMA bulk store each
     int* status;
+    int tone_cs;             // symmetric-tap kernel: tone columns of consecutive frames this far apart
+    int rot;                 // symmetric-tap kernel: bin c multiplied by (-i)^((c * rot) mod 4)
     int64_t q_lo, q_hi;      // iteration range
     int64_t iters_per_cta;
     int ring_sb;             // RING: super-blocks in the ring
@@ -660,7 +662,7 @@ __global__ void __launch_bounds__(kRingThreads, 1)
             for (int k = 0; k < kTonesPerThread; ++k)
                 if (bk[k] >= 0) tile[(tid + k * NT) * kToneGroup + q] = tv[k];
         } else if (a.n_tones > 0) {
-            float2* col = a.tones + a.frame_offset + j;
+            float2* col = a.tones + (a.frame_offset + j) * a.tone_cs;
             for (int t = tid; t < a.n_tones; t += NT) col[t * a.tones_ld] = B2[__ldg(a.bins + t)];
         }
     };
@@ -687,10 +689,10 @@ __global__ void __launch_bounds__(kRingThreads, 1)
             // frames j - q .. j of the group that this CTA produced
             const int q0 = static_cast<int>(max_i64(0, ja - (j - q)));
             const int nq = q + 1 - q0;
-            float2* base = a.tones + a.frame_offset + (j - q);
+            float2* base = a.tones + (a.frame_offset + (j - q)) * a.tone_cs;
             for (int it = tid; it < nq * nb_smem; it += NT) {
                 const int t = it / nq, qq = q0 + (it - t * nq);
-                base[static_cast<int64_t>(t) * a.tones_ld + qq] = tile[t * kToneGroup + qq];
+                base[static_cast<int64_t>(t) * a.tones_ld + static_cast<int64_t>(qq) * a.tone_cs] = tile[t * kToneGroup + qq];
             }
         }
     };
@@ -773,6 +775,15 @@ __global__ void __launch_bounds__(kRingThreads, 1)
 #pragma unroll
             for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], w2[r - 1]);
             dft16(v);                                            // v[r] = bin tf + 256 r
+        }
+        if (a.rot) {
+            // (-i)^((c * rot) mod 4) for c = tf + 256 r: the same power for all r (exact)
+            const int e = (tf * a.rot) & 3;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const float2 u = v[i];
+                v[i] = e == 1 ? make_float2(u.y, -u.x) : e == 2 ? make_float2(-u.x, -u.y) : e == 3 ? make_float2(-u.y, u.x) : u;
+            }
         }
         if (a.full && !bulk) {
             float2* row = a.full + (a.frame_offset + j) * a.full_ld;
@@ -949,8 +960,8 @@ cudaError_t launch_tmem_sym(PfbArgs a, int n_sms, int max_smem, cudaStream_t st)
     std::memset(&tm, 0, sizeof tm);
     a.tones_tma = 0;
     auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tmap_encode_tiled_fn());
-    if (a.nb_smem > 0 && enc && (reinterpret_cast<uintptr_t>(a.tones) % 16) == 0 && (a.tones_ld % 2) == 0 &&
-        a.frame_offset + a.F < (int64_t(1) << 31)) {
+    if (a.nb_smem > 0 && enc && a.tone_cs == 1 && (reinterpret_cast<uintptr_t>(a.tones) % 16) == 0 &&
+        (a.tones_ld % 2) == 0 && a.frame_offset + a.F < (int64_t(1) << 31)) {
         cuuint64_t dims[2] = {static_cast<cuuint64_t>(a.frame_offset + a.F), static_cast<cuuint64_t>(a.n_tones)};
         cuuint64_t strides[1] = {static_cast<cuuint64_t>(a.tones_ld) * 8};
         cuuint32_t box[2] = {kToneGroup, kToneBox};
@@ -1002,11 +1013,18 @@ cudaError_t pfb_launch(const PfbLaunch& L, cudaStream_t st) {
     a.tones_ld = L.tones_ld;
     a.frame_offset = L.frame_offset;
     a.status = L.status;
+    a.tone_cs = L.tone_cs > 0 ? L.tone_cs : 1;
+    a.rot = L.rot & 3;
     if (a.F <= 0) return cudaSuccess;
     const bool aligned = (reinterpret_cast<uintptr_t>(L.buf) % 16 == 0) && (L.cl % 4 == 0) &&
                          (reinterpret_cast<uintptr_t>(L.carry) % 16 == 0);
     a.use_tma = aligned ? 1 : 0;
     const int lg = L.log2n;
+    if (a.tone_cs != 1 || a.rot != 0) {
+        // phase passes of an oversampled plan: only the symmetric-tap kernel has them
+        if (lg != 12 || !a.use_tma || L.taps_kernel != 8 || !L.sym_taps) return cudaErrorInvalidValue;
+        return launch_tmem_sym(a, L.n_sms, L.max_smem, st);
+    }
     if (lg == 12 && a.use_tma && L.variant != 1) {
         if (L.taps_kernel == 8 && L.sym_taps && L.variant != 2) return launch_tmem_sym(a, L.n_sms, L.max_smem, st);
         if (L.taps_kernel == 4) return launch_tmem<4>(a, L.n_sms, L.max_smem, st);

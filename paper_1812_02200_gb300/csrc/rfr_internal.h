@@ -48,6 +48,8 @@ struct PfbLaunch {
     int variant;        // 0 = best available, 1 = shared-memory int16 ring only,
                         // 2 = no symmetric-tap TMEM kernel
     int sym_taps;       // kernel taps exactly symmetric (h[j] == h[T*N - 1 - j])
+    int tone_cs;        // tone columns of consecutive frames this far apart (0/1: adjacent)
+    int rot;            // bin c multiplied by (-i)^((c * rot) mod 4) (phase passes)
     int hop;            // samples between frames (N: critically sampled)
     int64_t a0;         // absolute sample index of the virtual stream's first sample
 };
@@ -214,6 +216,10 @@ struct rfr_plan {
     int mode = 0;
     int32_t N = 0, T = 0, Tk = 0, log2n = 0;   // PFB (Tk: kernel taps, zero-padded)
     bool sym_taps = false;                     // PFB kernel taps exactly symmetric (Tk == T)
+    int phase_R = 1;                           // oversampled N = 4096 PFB: hop = N / phase_R, run as
+                                               // phase_R critically sampled passes (see push_core)
+    int16_t* d_view = nullptr;                 // phase passes: contiguous copy of [carry | buffer]
+    int64_t view_cap = 0;                      //   when the push is not 16-byte aligned (samples)
     bool gen = false;                          // PFB through the any-N kernels
     rfr::GenPlan gplan;
     int32_t L = 0, D = 0, Lpad = 0;            // demod
