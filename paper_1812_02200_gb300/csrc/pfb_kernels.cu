@@ -538,9 +538,13 @@ __host__ __device__ __forceinline__ SymLayout sym_layout(int nb) {
     return L;
 }
 
+template <bool PHASE>
 __global__ void __launch_bounds__(kRingThreads, 1)
     pfb_tmem_sym_kernel(const PfbArgs a, const __grid_constant__ CUtensorMap tm_tones) {
     constexpr int N = 4096, NT = 256, T = 8;
+    // PHASE: a phase pass of an oversampled plan (tone columns a.tone_cs
+    // apart, bins turned by (-i)^(c * a.rot)); otherwise adjacent columns, no turn
+    const int64_t tcs = PHASE ? a.tone_cs : 1;
     extern __shared__ __align__(1024) unsigned char smem[];
     const int nb_smem = a.nb_smem;
     const SymLayout lay = sym_layout(nb_smem);
@@ -662,7 +666,7 @@ __global__ void __launch_bounds__(kRingThreads, 1)
             for (int k = 0; k < kTonesPerThread; ++k)
                 if (bk[k] >= 0) tile[(tid + k * NT) * kToneGroup + q] = tv[k];
         } else if (a.n_tones > 0) {
-            float2* col = a.tones + (a.frame_offset + j) * a.tone_cs;
+            float2* col = a.tones + (a.frame_offset + j) * tcs;
             for (int t = tid; t < a.n_tones; t += NT) col[t * a.tones_ld] = B2[__ldg(a.bins + t)];
         }
     };
@@ -689,10 +693,10 @@ __global__ void __launch_bounds__(kRingThreads, 1)
             // frames j - q .. j of the group that this CTA produced
             const int q0 = static_cast<int>(max_i64(0, ja - (j - q)));
             const int nq = q + 1 - q0;
-            float2* base = a.tones + (a.frame_offset + (j - q)) * a.tone_cs;
+            float2* base = a.tones + (a.frame_offset + (j - q)) * tcs;
             for (int it = tid; it < nq * nb_smem; it += NT) {
                 const int t = it / nq, qq = q0 + (it - t * nq);
-                base[static_cast<int64_t>(t) * a.tones_ld + static_cast<int64_t>(qq) * a.tone_cs] = tile[t * kToneGroup + qq];
+                base[static_cast<int64_t>(t) * a.tones_ld + qq * tcs] = tile[t * kToneGroup + qq];
             }
         }
     };
@@ -776,7 +780,7 @@ __global__ void __launch_bounds__(kRingThreads, 1)
             for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], w2[r - 1]);
             dft16(v);                                            // v[r] = bin tf + 256 r
         }
-        if (a.rot) {
+        if (PHASE && a.rot) {
             // (-i)^((c * rot) mod 4) for c = tf + 256 r: the same power for all r (exact)
             const int e = (tf * a.rot) & 3;
 #pragma unroll
@@ -971,9 +975,11 @@ cudaError_t launch_tmem_sym(PfbArgs a, int n_sms, int max_smem, cudaStream_t st)
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
             a.tones_tma = 1;
     }
-    cudaError_t e = cudaFuncSetAttribute(pfb_tmem_sym_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const bool phase = a.tone_cs != 1 || a.rot != 0;
+    auto k = phase ? pfb_tmem_sym_kernel<true> : pfb_tmem_sym_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    pfb_tmem_sym_kernel<<<static_cast<unsigned>(grid2), kRingThreads, smem, st>>>(a, tm);
+    k<<<static_cast<unsigned>(grid2), kRingThreads, smem, st>>>(a, tm);
     return cudaGetLastError();
 }
 
