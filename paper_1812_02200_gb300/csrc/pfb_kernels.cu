@@ -604,10 +604,11 @@ __global__ void __launch_bounds__(kRingThreads, 1)
     // int16 block b (staging slot s) -> FP32 -> the thread's TMEM columns of
     // slot b mod 8: points (tf, q) then the mirror points (255-tf, 15-m), as
     // planar pairs (re_q, re_q+1, im_q, im_q+1)
-    auto convert = [&](int64_t b, int s, uint32_t (&xr)[32]) {
+    auto ingest = [&](int64_t b, int s) {
         // the phase completed already (thread 0 saw it before the last
         // barrier); each thread's own wait makes the copy visible to it
         mbar_wait(&bars[s], static_cast<uint32_t>(((b - b0) / kTmemStage) & 1), a.status);
+        uint32_t xr[32];
         const uint32_t* sg = stage + s * N;
 #pragma unroll
         for (int q = 0; q < 16; q += 2) {
@@ -620,10 +621,6 @@ __global__ void __launch_bounds__(kRingThreads, 1)
             xr[2 * q + 2] = __float_as_uint(f0.y);
             xr[2 * q + 3] = __float_as_uint(f1.y);
         }
-    };
-    auto ingest = [&](int64_t b, int s) {
-        uint32_t xr[32];
-        convert(b, s, xr);
         umma::st_32x32b_x32(tbase + 32u * static_cast<uint32_t>(b % kTmemSlots), xr);
         umma::wait_st();
     };
@@ -707,57 +704,37 @@ __global__ void __launch_bounds__(kRingThreads, 1)
     for (int64_t j = ja; ok && j < jb; ++j) {
         const int64_t b = j + T - 1;                             // the block that completes frame j
         const int s = static_cast<int>(b % kTmemStage);
-        // polyphase FIR, taps in order t = 0..T-1: taps 0..T-2 from the
-        // delay line in TMEM (slot halves: own points, then mirror points,
-        // the next load in flight during the FMAs); the newest block (tap
-        // T-1) straight from its conversion, then stored for later frames
+        ingest(b, s);
+        // polyphase FIR, taps in order t = 0..T-1 (slot halves: own points,
+        // then mirror points, the next load in flight during the FMAs)
         float are[16], aim[16];
 #pragma unroll
         for (int r = 0; r < 16; ++r) are[r] = aim[r] = 0.f;
-        umma::wait_st();                                         // the previous frame's block is in TMEM
-        {
-            uint32_t xa[16], xb[16];
-            umma::ld_32x32b_x16(tbase + 32u * static_cast<uint32_t>(j % kTmemSlots), xa);
-            umma::wait_ld_regs(xa);
+        uint32_t xa[16], xb[16];
+        umma::ld_32x32b_x16(tbase + 32u * static_cast<uint32_t>(j % kTmemSlots), xa);
+        umma::wait_ld_regs(xa);
 #pragma unroll
-            for (int t = 0; t < T - 1; ++t) {
-                const uint32_t col = tbase + 32u * static_cast<uint32_t>((j + t) % kTmemSlots);
-                umma::ld_32x32b_x16(col + 16u, xb);
-#pragma unroll
-                for (int q = 0; q < 8; q += 2) {
-                    ffma2(are[q], are[q + 1], H[t][q], H[t][q + 1], __uint_as_float(xa[2 * q]),
-                          __uint_as_float(xa[2 * q + 1]));
-                    ffma2(aim[q], aim[q + 1], H[t][q], H[t][q + 1], __uint_as_float(xa[2 * q + 2]),
-                          __uint_as_float(xa[2 * q + 3]));
-                }
-                umma::wait_ld_regs(xb);
-                if (t + 2 < T)
-                    umma::ld_32x32b_x16(tbase + 32u * static_cast<uint32_t>((j + t + 1) % kTmemSlots), xa);
-#pragma unroll
-                for (int m = 0; m < 8; m += 2) {
-                    ffma2(are[8 + m], are[9 + m], H[T - 1 - t][m], H[T - 1 - t][m + 1], __uint_as_float(xb[2 * m]),
-                          __uint_as_float(xb[2 * m + 1]));
-                    ffma2(aim[8 + m], aim[9 + m], H[T - 1 - t][m], H[T - 1 - t][m + 1],
-                          __uint_as_float(xb[2 * m + 2]), __uint_as_float(xb[2 * m + 3]));
-                }
-                if (t + 2 < T) umma::wait_ld_regs(xa);
-            }
-        }
-        {
-            uint32_t xr[32];
-            convert(b, s, xr);
+        for (int t = 0; t < T; ++t) {
+            const uint32_t col = tbase + 32u * static_cast<uint32_t>((j + t) % kTmemSlots);
+            umma::ld_32x32b_x16(col + 16u, xb);
 #pragma unroll
             for (int q = 0; q < 8; q += 2) {
-                ffma2(are[q], are[q + 1], H[T - 1][q], H[T - 1][q + 1], __uint_as_float(xr[2 * q]),
-                      __uint_as_float(xr[2 * q + 1]));
-                ffma2(aim[q], aim[q + 1], H[T - 1][q], H[T - 1][q + 1], __uint_as_float(xr[2 * q + 2]),
-                      __uint_as_float(xr[2 * q + 3]));
-                ffma2(are[8 + q], are[9 + q], H[0][q], H[0][q + 1], __uint_as_float(xr[16 + 2 * q]),
-                      __uint_as_float(xr[17 + 2 * q]));
-                ffma2(aim[8 + q], aim[9 + q], H[0][q], H[0][q + 1], __uint_as_float(xr[18 + 2 * q]),
-                      __uint_as_float(xr[19 + 2 * q]));
+                ffma2(are[q], are[q + 1], H[t][q], H[t][q + 1], __uint_as_float(xa[2 * q]),
+                      __uint_as_float(xa[2 * q + 1]));
+                ffma2(aim[q], aim[q + 1], H[t][q], H[t][q + 1], __uint_as_float(xa[2 * q + 2]),
+                      __uint_as_float(xa[2 * q + 3]));
             }
-            umma::st_32x32b_x32(tbase + 32u * static_cast<uint32_t>(b % kTmemSlots), xr);
+            umma::wait_ld_regs(xb);
+            if (t + 1 < T)
+                umma::ld_32x32b_x16(tbase + 32u * static_cast<uint32_t>((j + t + 1) % kTmemSlots), xa);
+#pragma unroll
+            for (int m = 0; m < 8; m += 2) {
+                ffma2(are[8 + m], are[9 + m], H[T - 1 - t][m], H[T - 1 - t][m + 1], __uint_as_float(xb[2 * m]),
+                      __uint_as_float(xb[2 * m + 1]));
+                ffma2(aim[8 + m], aim[9 + m], H[T - 1 - t][m], H[T - 1 - t][m + 1],
+                      __uint_as_float(xb[2 * m + 2]), __uint_as_float(xb[2 * m + 3]));
+            }
+            if (t + 1 < T) umma::wait_ld_regs(xa);
         }
         // the partner (lane 31 - l) filtered this row's points 8..15
         float2 v[16];
@@ -834,7 +811,6 @@ __global__ void __launch_bounds__(kRingThreads, 1)
         }
     }
     if (tid == 0) bulk_wait_all();
-    umma::wait_st();                                             // the last block's TMEM store
     umma::fence_before_sync();
     __syncthreads();
     if (warp == 0) {
