@@ -370,13 +370,15 @@ demod_gemm_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constan
 //
 // Tile: 128 frames x BT tones (BT = 128 or 64, the tone-tile width chosen by
 // the plan's autotuner), K-blocks of 64 complex taps (one plane per TMA
-// stage: A hi, lo 128x64 and B hi, lo BTx64).  The three products of an
-// accumulation chunk run one after the other, each into one of four BT-column
-// TMEM slots taken in rotation, so the epilogue drains a slot while the MMAs
-// fill the others and every slot is drained three product phases before it
-// is reused.  Sixteen epilogue warps (four per TMEM lane quadrant, BT/4 tones
-// each) drain a slot with one load each, adding 2 P1 to both sums, P2 to the
-// imaginary and -P3 to the real sum.
+// stage: A hi, lo 128x64 and B hi, lo BTx64, B lo right after B hi).  Per 16
+// taps two MMAs: A hi times [B hi | B lo] as one N = 2 BT product (the hi.hi
+// and hi.lo terms side by side in TMEM), then A lo times B hi (N = BT) added
+// onto the hi.hi half.  The three products of an accumulation chunk run one
+// after the other, each into a 2 BT-column TMEM slot taken in rotation (two
+// slots for BT = 128, four for 64), so the epilogue drains a slot while the
+// MMAs fill the next.  Sixteen epilogue warps (four per TMEM lane quadrant,
+// BT/4 tones each) drain a slot by adding its two halves, then add 2 P1 to
+// both sums, P2 to the imaginary and -P3 to the real sum.
 //
 // Fused pre-split (FUSED): instead of TMA loads of the six pre-split source
 // planes (written to HBM by presplit3_kernel, 12 bytes per sample), two
@@ -393,7 +395,7 @@ demod_gemm_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constan
 // order whatever the tile width or the plans sharing the launch.
 constexpr int G3_BK = 64;                                  // complex taps per K-block
 constexpr uint32_t G3_A_BYTES = BM * G3_BK * 2;
-constexpr int G3_SLOTS = 4;
+constexpr int G3_SLOTS_MAX = 4;
 constexpr int G3_EPI_WARPS = 16;          // 4 lane quadrants x 4 tone groups
 constexpr int G3_THREADS = (G3_EPI_WARPS + 2) * 32;
 constexpr int G3_FUSED_PRODUCERS = 2;                       // producer warps of the fused form
@@ -403,7 +405,11 @@ template <int BT> struct G3Cfg {
     static constexpr uint32_t STAGE_BYTES = 2 * G3_A_BYTES + 2 * B_BYTES;
     static constexpr int STAGES = BT == 128 ? 3 : 4;
     static constexpr size_t SMEM = 1024 + STAGES * STAGE_BYTES + 256;
-    static constexpr uint32_t TMEM_COLS = G3_SLOTS * BT;   // 512 or 256
+    // a slot holds one product's accumulator as two BT-column halves:
+    // [0, BT) collects hi.hi + lo.hi, [BT, 2 BT) hi.lo (see the MMA issuer)
+    static constexpr int SLOTS = BT == 128 ? 2 : 4;
+    static constexpr uint32_t SLOT_COLS = 2 * BT;
+    static constexpr uint32_t TMEM_COLS = SLOTS * SLOT_COLS;   // 512
     static constexpr int TPG = BT / 4;                     // tones per epilogue warp
 };
 
@@ -528,8 +534,9 @@ demod3m_gemm_kernel(const __grid_constant__ G3Batch bt) {
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
     uint64_t* empty = full + STAGES;
     uint64_t* sfull = empty + STAGES;
-    uint64_t* sempty = sfull + G3_SLOTS;
-    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(sempty + G3_SLOTS);
+    uint64_t* sempty = sfull + G3_SLOTS_MAX;
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(sempty + G3_SLOTS_MAX);
+    constexpr int SLOTS = Cfg::SLOTS;
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
     int* const status0 = bt.p[0].g.status;
     constexpr int PROD_WARP = G3_EPI_WARPS;                                  // first producer warp
@@ -541,7 +548,7 @@ demod3m_gemm_kernel(const __grid_constant__ G3Batch bt) {
             mbar_init(&full[s], FUSED ? G3_FUSED_PRODUCERS * 32 : 1);
             mbar_init(&empty[s], 1);
         }
-        for (int b = 0; b < G3_SLOTS; ++b) {
+        for (int b = 0; b < SLOTS; ++b) {
             mbar_init(&sfull[b], 1);
             mbar_init(&sempty[b], G3_EPI_WARPS * 32);
         }
@@ -564,6 +571,7 @@ demod3m_gemm_kernel(const __grid_constant__ G3Batch bt) {
     const uint32_t tmem = *tmem_holder;
     const int n_tiles = bt.total_tiles;
     constexpr uint32_t IDESC = umma::idesc_f16_f32(BM, BT);
+    constexpr uint32_t IDESC_W = umma::idesc_f16_f32(BM, 2 * BT);
 
     if (FUSED && warp >= PROD_WARP && warp < MMA_WARP) {
         // ------------------------------------------------ fused producers
@@ -663,14 +671,14 @@ demod3m_gemm_kernel(const __grid_constant__ G3Batch bt) {
                 for (int kb0 = 0; kb0 < g.KB && !stop; kb0 += g.kchunk) {
                     const int kb1 = min(kb0 + g.kchunk, g.KB);
                     for (int q = 0; q < 3 && !stop; ++q, ++phase) {
-                        const uint32_t slot = phase % G3_SLOTS, use = phase / G3_SLOTS;
+                        const uint32_t slot = phase % SLOTS, use = phase / SLOTS;
                         if (*abort_flag || !mbar_wait(&sempty[slot], (use & 1) ^ 1, status0)) {
                             *abort_flag = 1;
                             stop = true;
                             break;
                         }
                         umma::fence_after_sync();
-                        const uint32_t d_tmem = tmem + slot * BT;
+                        const uint32_t d_tmem = tmem + slot * Cfg::SLOT_COLS;
                         for (int kb = kb0; kb < kb1; ++kb, ++it) {
                             const int s = it % STAGES;
                             const uint32_t ph = (it / STAGES) & 1;
@@ -687,8 +695,8 @@ demod3m_gemm_kernel(const __grid_constant__ G3Batch bt) {
                             for (int k = 0; k < G3_BK / 16; ++k) {
                                 const uint32_t off = k * 32;
                                 const uint32_t acc = (kb > kb0 || k > 0) ? 1u : 0u;
-                                umma::mma_f16(d_tmem, umma::desc_k_sw128(ah + off), umma::desc_k_sw128(bh + off), IDESC, acc);
-                                umma::mma_f16(d_tmem, umma::desc_k_sw128(ah + off), umma::desc_k_sw128(bl + off), IDESC, 1u);
+                                // hi.hi | hi.lo over 2 BT columns (B lo follows B hi), then lo.hi
+                                umma::mma_f16(d_tmem, umma::desc_k_sw128(ah + off), umma::desc_k_sw128(bh + off), IDESC_W, acc);
                                 umma::mma_f16(d_tmem, umma::desc_k_sw128(al + off), umma::desc_k_sw128(bh + off), IDESC, 1u);
                             }
                             umma::commit(&empty[s]);
@@ -717,38 +725,42 @@ demod3m_gemm_kernel(const __grid_constant__ G3Batch bt) {
             for (int i = 0; i < TPG; ++i) re[i] = im[i] = 0.f;
             for (int kb0 = 0; kb0 < g.KB && ok; kb0 += g.kchunk) {
                 for (int q = 0; q < 3; ++q, ++phase) {
-                    const uint32_t slot = phase % G3_SLOTS, use = phase / G3_SLOTS;
+                    const uint32_t slot = phase % SLOTS, use = phase / SLOTS;
                     if (*abort_flag || !mbar_wait(&sfull[slot], use & 1, status0)) {
                         *abort_flag = 1;
                         ok = false;
                         break;
                     }
                     umma::fence_after_sync();
-                    uint32_t r[TPG];
-                    const uint32_t ta = tmem + (static_cast<uint32_t>(qd * 32) << 16) + slot * BT + grp * TPG;
-                    if constexpr (TPG == 32) {
-                        umma::ld_32x32b_x32(ta, r);
-                        umma::wait_ld();
-                    } else {
-                        umma::ld_32x32b_x16(ta, r);
-                        umma::wait_ld_regs(r);
+                    const uint32_t ta = tmem + (static_cast<uint32_t>(qd * 32) << 16) + slot * Cfg::SLOT_COLS + grp * TPG;
+                    // the product = (hi.hi + lo.hi) + hi.lo, 16 tones at a time
+#pragma unroll
+                    for (int h = 0; h < TPG; h += 16) {
+                        uint32_t r0[16], r1[16];
+                        umma::ld_32x32b_x16(ta + h, r0);
+                        umma::ld_32x32b_x16(ta + BT + h, r1);
+                        umma::wait_ld_regs(r0);
+                        umma::wait_ld_regs(r1);
+                        float pv[16];
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) pv[i] = __uint_as_float(r0[i]) + __uint_as_float(r1[i]);
+                        if (q == 0) {
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) {
+                                const float v = 2.f * pv[i];
+                                re[h + i] += v;
+                                im[h + i] += v;
+                            }
+                        } else if (q == 1) {
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) im[h + i] += pv[i];
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) re[h + i] -= pv[i];
+                        }
                     }
                     umma::fence_before_sync();
                     mbar_arrive(&sempty[slot]);
-                    if (q == 0) {
-#pragma unroll
-                        for (int i = 0; i < TPG; ++i) {
-                            const float v = 2.f * __uint_as_float(r[i]);
-                            re[i] += v;
-                            im[i] += v;
-                        }
-                    } else if (q == 1) {
-#pragma unroll
-                        for (int i = 0; i < TPG; ++i) im[i] += __uint_as_float(r[i]);
-                    } else {
-#pragma unroll
-                        for (int i = 0; i < TPG; ++i) re[i] -= __uint_as_float(r[i]);
-                    }
                 }
             }
             if (!ok) break;
