@@ -412,6 +412,25 @@ def run_demod(args, dev, stream, rank):
                                 "MMAs (2.25x the algorithmic flops on the tensor pipe); push time "
                                 "includes the rotation, pre-split and carry kernels",
                         "peak_kind": f"{peak_kind} dense bf16 (fp16 has the same nominal rate)"}}
+    # -- the other cluster form of the same GEMM (two-CTA clusters sharing
+    # the frame tiles by multicast, or one CTA per tile), same tile and raster
+    tn = plan.tune()
+    pp = rfr.Plan(0, DEMOD_L, window="blackman", cutoff=DEMOD_FC, words=c["words"], decimation=DEMOD_D)
+    pp.set_tone_tile(tn["tone_tile"] or 128)
+    pp.set_demod_pair(not tn["pair"])
+    pp.push_into(x, tones=out, stream=stream)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(k):
+        pp.push_into(x, tones=out, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    msp = e0.elapsed_time(e1) / k
+    res["single_cta" if tn["pair"] else "pair_clusters"] = {
+        "value": samples / (msp * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": msp,
+        "note": "the same GEMM with one CTA per tile" if tn["pair"] else
+                "the same GEMM in two-CTA clusters sharing each frame tile by TMA multicast"}
+    pp.close()
     # -- the same three-product GEMM with the FP16 split fused into its
     # producer warps (no pre-split kernel; each A tile converted once per tone
     # tile and product)
@@ -473,6 +492,24 @@ def run_demod(args, dev, stream, rank):
                              "form": "FP32 CUDA-core tiled kernel over the Toeplitz view",
                              "rel_err_max_checked_tones": plain_rel,
                              "speedup_of_tensor_path": pms / ms}
+        # the library GEMM form: cublasCgemm (pedantic FP32) on the materialised Toeplitz matrix
+        plan.plain_oneshot(x, tones=out, stream=stream, form=rfr.PLAIN_CGEMM)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        plan.plain_oneshot(x, tones=out, stream=stream, form=rfr.PLAIN_CGEMM)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        gms = e0.elapsed_time(e1)
+        cg_rel = None
+        if rank == 0 and not args.no_check:
+            got = np.concatenate([out[sel, a:b].cpu().numpy() for a, b in fr], axis=1)
+            cg_rel = float(np.max(np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)))
+        res["plain_fp32_cgemm"] = {"value": samples / (gms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": gms,
+                                   "form": "cublasCgemm, pedantic FP32, on the Toeplitz matrix materialised "
+                                           "in 512 MiB frame chunks, then the rotation kernel",
+                                   "fp32_tflops": flops / (gms * 1e-3) / 1e12,
+                                   "rel_err_max_checked_tones": cg_rel,
+                                   "speedup_of_tensor_path": gms / ms}
     if rank == 0 and not args.no_cpu:
         # FP64 oracle on a bounded sample: all 2048 tones over 32 frames
         import oracle
@@ -637,8 +674,10 @@ def run_large_n(args, dev, stream, x, words):
     """PFB beyond the fused kernels (Sec. III.A): Fig. 3's N = 10^5 and the
     section's largest, 10^7, with A_v = T = 4 and a Hamming window (four-step
     two-pass form), and the workload's N = 4096, T = 8 Kaiser(9) oversampled
-    4x (hop 1024, the mixed-radix one-pass form); each on the workload's
-    2^28-sample stream, full spectrum + its 1000 tones."""
+    4x (hop 1024, the mixed-radix one-pass form); and the batched workload's
+    power-of-two shapes whose FP32 delay line does not fit one SM's tensor
+    memory (N = 16384 T = 8, N = 4096 T = 16, N = 16384 T = 16, Kaiser(9));
+    each on the workload's 2^28-sample stream, full spectrum + its 1000 tones."""
     import torch
 
     from paper_1812_02200_gb300 import rfr
@@ -646,7 +685,8 @@ def run_large_n(args, dev, stream, x, words):
     out = []
     n = x.shape[0]
     for N, T, win, hop, reps in ((100000, 4, "hamming", 100000, 5), (10 ** 7, 4, "hamming", 10 ** 7, 3),
-                                 (4096, 8, "kaiser", 1024, 3)):
+                                 (4096, 8, "kaiser", 1024, 3), (16384, 8, "kaiser", 16384, 3),
+                                 (4096, 16, "kaiser", 4096, 3), (16384, 16, "kaiser", 16384, 3)):
         plan = rfr.Plan(N, T, window=win, beta=BETA if win == "kaiser" else 0.0, words=words, full=True,
                         tones=True, decimation=hop)
         F = plan.frames_for(n)

@@ -382,6 +382,24 @@ rfr_status rfr_plan_get_bins(const rfr_plan* plan, int32_t* bins, int32_t* count
 rfr_status rfr_plain_oneshot(rfr_plan* plan, const int16_t* iq, int64_t n_samples,
                              rfr_output* out, void* stream);
 
+/*
+ * rfr_plain_oneshot_form -- rfr_plain_oneshot with the comparison form named:
+ *   RFR_PLAIN_DEFAULT  the forms above;
+ *   RFR_PLAIN_CGEMM    demodulation plans only: the mix + filter of Sec. III.B
+ *                      as the library matrix product the paper names for it,
+ *                      cublasCgemm in pedantic FP32 (no TF32, no emulation) of
+ *                      the Toeplitz matrix X[k][n] = x[(k+1)D - L + n],
+ *                      materialised on the device in frame chunks of at most
+ *                      512 MiB, by the modulated taps C_t[n]; then the rotation
+ *                      exp(-i*phi_t((k+1)D - L)) into [tone][frame].
+ * Same arguments, output layout and zero history as rfr_plain_oneshot.
+ * Errors: RFR_E_INVALID (unknown form), RFR_E_UNSUPPORTED (Cgemm form on a
+ * PFB or chirp plan), RFR_E_SHORT, RFR_E_CUDA (a cuBLAS failure included).
+ */
+enum { RFR_PLAIN_DEFAULT = 0, RFR_PLAIN_CGEMM = 1 };
+rfr_status rfr_plain_oneshot_form(rfr_plan* plan, int32_t form, const int16_t* iq, int64_t n_samples,
+                                  rfr_output* out, void* stream);
+
 /* ------------------------------------------------------------------ batch */
 typedef struct rfr_batch rfr_batch;
 
@@ -451,6 +469,20 @@ rfr_status rfr_plan_set_tone_tile(rfr_plan* plan, int32_t tones_per_tile);
  * Errors: RFR_E_INVALID (not a three-product demodulation plan, on not 0/1). */
 rfr_status rfr_plan_set_fused_presplit(rfr_plan* plan, int32_t on);
 rfr_status rfr_plan_get_fused_presplit(const rfr_plan* plan, int32_t* on);
+
+/* Three-product demodulation: on = 1 runs the GEMM in clusters of two CTAs
+ * on two SMs that take the two tone tiles of one frame tile; the frames'
+ * operand tiles (the Toeplitz view of the stream, Sec. III.B) are the same
+ * for both, so each CTA loads half of every such tile and TMA multicasts it
+ * into both CTAs' shared memory, a quarter less operand traffic from L2 per
+ * CTA.  Default 0 (one CTA per tile; the cluster form measured about 3 %
+ * slower on the 2048-tone workload, the two CTAs running in lock step).
+ * Applies to the separate pre-split form only (get reports 0 while the
+ * fused pre-split is on).  Result-neutral (the same MMAs in the same
+ * order); the autotuner times both forms.
+ * Errors: RFR_E_INVALID (not a three-product demodulation plan, on not 0/1). */
+rfr_status rfr_plan_set_demod_pair(rfr_plan* plan, int32_t on);
+rfr_status rfr_plan_get_demod_pair(const rfr_plan* plan, int32_t* on);
 
 /* ---------------------------------------------------------------- serving */
 typedef struct rfr_server rfr_server;

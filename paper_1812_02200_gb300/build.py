@@ -67,7 +67,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:
         lib64 = os.path.join(_cuda_home(), "lib64")
         cmd = (["nvcc"] + ARCH + ["-shared", "-o", LIB + ".tmp"] + objs +
-               ["-L" + lib64, "-lcufft", "-Xlinker", "-rpath," + lib64])
+               ["-L" + lib64, "-lcufft", "-lcublas", "-Xlinker", "-rpath," + lib64])
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

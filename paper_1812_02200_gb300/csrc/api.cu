@@ -414,6 +414,7 @@ rfr_status push_core(rfr_plan* p, const int16_t* iq, int64_t n, const rfr_output
                     L.xs_rows = p->xs3_rows_cap;
                     L.tone_tile = p->tune.demod_bt;
                     L.fused_presplit = p->tune.demod_fused;
+                    L.pair = p->tune.demod_pair;
                     if (defer_gemm) RFR_CUDA(p, rfr::demod3_prepare(L, st, defer_gemm));
                     else RFR_CUDA(p, rfr::demod3_launch(L, st));
                 } else {
@@ -475,7 +476,7 @@ void destroy(rfr_plan* p) {
         dev_free(p->d_tgroup[g]);
         if (p->tgroup_ev[g]) cudaEventDestroy(p->tgroup_ev[g]);
     }
-    rfr::plain_release(p->plain_scratch, p->plain_fft);
+    rfr::plain_release(p->plain_scratch, p->plain_fft, p->plain_blas);
     rfr::gen_plan_free(&p->gplan);
     delete p;
 }
@@ -1117,9 +1118,17 @@ rfr_status rfr_plan_get_bins(const rfr_plan* p, int32_t* bins, int32_t* count) {
 }
 
 rfr_status rfr_plain_oneshot(rfr_plan* p, const int16_t* iq, int64_t n, rfr_output* out, void* stream) {
+    return rfr_plain_oneshot_form(p, RFR_PLAIN_DEFAULT, iq, n, out, stream);
+}
+
+rfr_status rfr_plain_oneshot_form(rfr_plan* p, int32_t form, const int16_t* iq, int64_t n, rfr_output* out,
+                                  void* stream) {
     rfr::TraceRange tr("rfr_plain_oneshot");
     if (!p || !out || n < 0 || (n > 0 && !iq)) return RFR_E_INVALID;
+    if (form != RFR_PLAIN_DEFAULT && form != RFR_PLAIN_CGEMM) return fail(p, RFR_E_INVALID, "unknown plain form");
     if (p->mode == RFR_MODE_CHIRP) return fail(p, RFR_E_UNSUPPORTED, "no plain form for chirp plans");
+    if (form == RFR_PLAIN_CGEMM && p->mode != RFR_MODE_DEMOD)
+        return fail(p, RFR_E_UNSUPPORTED, "the Cgemm form is a demodulation form");
     if (p->mode == RFR_MODE_PFB && p->H != p->N)
         return fail(p, RFR_E_UNSUPPORTED, "the plain form is critically sampled only");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1143,8 +1152,12 @@ rfr_status rfr_plain_oneshot(rfr_plan* p, const int16_t* iq, int64_t n, rfr_outp
                 RFR_CUDA(p, dev_alloc(&p->d_c32, static_cast<size_t>(nt) * p->L * 8));
                 RFR_CUDA(p, rfr::plain_demod_taps(p->d_h32, p->d_words, nt, p->L, p->d_c32, st));
             }
-            RFR_CUDA(p, rfr::plain_demod(iq, n, p->L, p->D, p->d_c32, p->d_words, nt,
-                                         static_cast<char*>(out->tones) + out->frame_offset * 8, out->tones_ld, st));
+            char* t0 = static_cast<char*>(out->tones) + out->frame_offset * 8;
+            if (form == RFR_PLAIN_CGEMM)
+                RFR_CUDA(p, rfr::plain_demod_cgemm(iq, n, p->L, p->D, p->d_c32, p->d_words, nt, t0, out->tones_ld,
+                                                   &p->plain_scratch, &p->plain_scratch_bytes, &p->plain_blas, st));
+            else
+                RFR_CUDA(p, rfr::plain_demod(iq, n, p->L, p->D, p->d_c32, p->d_words, nt, t0, out->tones_ld, st));
         }
     }
     out->frames = F;

@@ -91,7 +91,7 @@ std::string tune_key(const rfr_plan* p, int64_t n) {
 //   {"key": [pfb_lookahead, demod_raster, demod_tone_tile, demod_fused], ...}
 // (missing trailing numbers take their defaults: tone tile 128, not fused)
 struct TuneEntry {
-    int lookahead = 0, raster = 1, bt = 128, fused = 0;
+    int lookahead = 0, raster = 1, bt = 128, fused = 0, pair = 0;
 };
 std::map<std::string, TuneEntry> tune_load() {
     std::map<std::string, TuneEntry> m;
@@ -102,10 +102,12 @@ std::map<std::string, TuneEntry> tune_load() {
         const size_t b0 = line.find('[', q1 == std::string::npos ? 0 : q1);
         if (q0 == std::string::npos || q1 == std::string::npos || b0 == std::string::npos) continue;
         TuneEntry t;
-        const int got = std::sscanf(line.c_str() + b0, "[%d, %d, %d, %d]", &t.lookahead, &t.raster, &t.bt, &t.fused);
+        const int got = std::sscanf(line.c_str() + b0, "[%d, %d, %d, %d, %d]", &t.lookahead, &t.raster, &t.bt,
+                                    &t.fused, &t.pair);
         if (got >= 2) {
             if (got == 2 || (t.bt != 64 && t.bt != 128)) t.bt = 128;
             if (got < 4 || (t.fused != 0 && t.fused != 1)) t.fused = 0;
+            if (got < 5 || (t.pair != 0 && t.pair != 1) || t.fused) t.pair = 0;
             m[line.substr(q0 + 1, q1 - q0 - 1)] = t;
         }
     }
@@ -120,7 +122,8 @@ void tune_store(const std::map<std::string, TuneEntry>& m) {
         size_t i = 0;
         for (const auto& kv : m) {
             f << "  \"" << kv.first << "\": [" << kv.second.lookahead << ", " << kv.second.raster << ", "
-              << kv.second.bt << ", " << kv.second.fused << "]" << (++i < m.size() ? "," : "") << "\n";
+              << kv.second.bt << ", " << kv.second.fused << ", " << kv.second.pair << "]"
+              << (++i < m.size() ? "," : "") << "\n";
         }
         f << "}\n";
     }
@@ -274,6 +277,7 @@ rfr_status rfr_plan_autotune(rfr_plan* p, int64_t n_samples, int32_t use_cache, 
             p->tune.demod_raster = it->second.raster;
             p->tune.demod_bt = it->second.bt;
             p->tune.demod_fused = it->second.fused;
+            p->tune.demod_pair = it->second.pair;
             p->tune.tuned = true;
             if (best_ms) *best_ms = -1.0;
             return RFR_OK;
@@ -289,12 +293,14 @@ rfr_status rfr_plan_autotune(rfr_plan* p, int64_t n_samples, int32_t use_cache, 
         // at most two 128-tone tiles, where that stays cheap
         const bool try_fused = p->demod_products == 3 && p->words.size() <= 256;
         for (int fused : {0, 1})
-            for (int bt : {128, 64}) {
-                // the tone tile and the fused pre-split are three-product choices
-                if ((bt == 64 || fused) && p->demod_products != 3) continue;
-                if (fused && !try_fused) continue;
-                for (int r : {1, 8, 19, 38}) cand.push_back({0, r, bt, fused});
-            }
+            for (int pair : {1, 0})
+                for (int bt : {128, 64}) {
+                    // tone tile, fused pre-split and clusters are three-product choices;
+                    // the cluster form loads A by TMA, so it excludes the fused pre-split
+                    if ((bt == 64 || fused || pair) && p->demod_products != 3) continue;
+                    if (fused && (!try_fused || pair)) continue;
+                    for (int r : {1, 8, 19, 38}) cand.push_back({0, r, bt, fused, pair});
+                }
     }
     // scratch buffers: zero input, outputs sized for the push
     const int64_t F = rfr::frames_for_samples(p, n_samples) + 1;
@@ -341,6 +347,7 @@ rfr_status rfr_plan_autotune(rfr_plan* p, int64_t n_samples, int32_t use_cache, 
         p->tune.demod_raster = cand[c].raster;
         p->tune.demod_bt = cand[c].bt;
         p->tune.demod_fused = cand[c].fused;
+        p->tune.demod_pair = cand[c].pair;
         float ms_best = 1e30f;
         for (int rep = 0; rep < 4 && rs == RFR_OK; ++rep) {
             p->samples = s_samples;
@@ -380,6 +387,7 @@ rfr_status rfr_plan_autotune(rfr_plan* p, int64_t n_samples, int32_t use_cache, 
     p->tune.demod_raster = best_c.raster;
     p->tune.demod_bt = best_c.bt;
     p->tune.demod_fused = best_c.fused;
+    p->tune.demod_pair = best_c.pair;
     p->tune.tuned = true;
     if (best_ms) *best_ms = best;
     if (use_cache) {
@@ -407,6 +415,18 @@ rfr_status rfr_plan_set_fused_presplit(rfr_plan* p, int32_t on) {
 rfr_status rfr_plan_get_fused_presplit(const rfr_plan* p, int32_t* on) {
     if (!p || !on) return RFR_E_INVALID;
     *on = p->mode == RFR_MODE_DEMOD && p->demod_products == 3 ? p->tune.demod_fused : 0;
+    return RFR_OK;
+}
+
+rfr_status rfr_plan_set_demod_pair(rfr_plan* p, int32_t on) {
+    if (!p || p->mode != RFR_MODE_DEMOD || p->demod_products != 3 || (on != 0 && on != 1)) return RFR_E_INVALID;
+    p->tune.demod_pair = on;
+    return RFR_OK;
+}
+
+rfr_status rfr_plan_get_demod_pair(const rfr_plan* p, int32_t* on) {
+    if (!p || !on) return RFR_E_INVALID;
+    *on = p->mode == RFR_MODE_DEMOD && p->demod_products == 3 && !p->tune.demod_fused ? p->tune.demod_pair : 0;
     return RFR_OK;
 }
 

@@ -177,19 +177,22 @@ struct GemmArgs {
 
 // Tile index -> (M tile, N tile): groups of g.raster M tiles are swept
 // N-tile-major, so concurrently running CTAs share the same tap slices in L2.
-__device__ __forceinline__ void tile_coords(const GemmArgs& g, int tile, int& mt, int& nt) {
-    const int r = g.raster > 1 ? g.raster : 1;
+__device__ __forceinline__ void tile_coords_of(int raster, int n_mt, int n_nt, int tile, int& mt, int& nt) {
+    const int r = raster > 1 ? raster : 1;
     if (r == 1) {
-        mt = tile / g.n_nt;
-        nt = tile % g.n_nt;
+        mt = tile / n_nt;
+        nt = tile % n_nt;
         return;
     }
-    const int per_group = r * g.n_nt;
+    const int per_group = r * n_nt;
     const int grp = tile / per_group, in = tile % per_group;
     const int m_base = grp * r;
-    const int rows = min(r, g.n_mt - m_base);
+    const int rows = min(r, n_mt - m_base);
     nt = in / rows;
     mt = m_base + in % rows;
+}
+__device__ __forceinline__ void tile_coords(const GemmArgs& g, int tile, int& mt, int& nt) {
+    tile_coords_of(g.raster, g.n_mt, g.n_nt, tile, mt, nt);
 }
 
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
@@ -395,6 +398,7 @@ demod_gemm_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constan
 // order whatever the tile width or the plans sharing the launch.
 constexpr int G3_BK = 64;                                  // complex taps per K-block
 constexpr uint32_t G3_A_BYTES = BM * G3_BK * 2;
+constexpr uint32_t G3_A_HALF = G3_A_BYTES / 2;              // 64 rows: one CTA's share in the pair form
 constexpr int G3_SLOTS_MAX = 4;
 constexpr int G3_EPI_WARPS = 16;          // 4 lane quadrants x 4 tone groups
 constexpr int G3_THREADS = (G3_EPI_WARPS + 2) * 32;
@@ -437,6 +441,21 @@ __device__ __forceinline__ int g3_plan_of(const G3Batch& bt, int tile) {
     int pi = 0;
     while (pi + 1 < bt.n_plans && tile >= bt.p[pi + 1].tile0) ++pi;
     return pi;
+}
+
+// Tile (frame tile mt, tone tile nt) of work item `tile` of a plan.  In the
+// pair form a work item is a frame tile and a pair of tone tiles 2j, 2j + 1,
+// the CTA of cluster rank r taking tone tile 2j + r (past the plan's last
+// tone tile when its count is odd: the taps there are read as zeros and
+// no output is stored).
+template <bool PAIR>
+__device__ __forceinline__ void g3_coords(const GemmArgs& g, int tile, int rank, int& mt, int& nt) {
+    if (PAIR) {
+        tile_coords_of(g.raster, g.n_mt, (g.n_nt + 1) >> 1, tile, mt, nt);
+        nt = 2 * nt + rank;
+    } else {
+        tile_coords(g, tile, mt, nt);
+    }
 }
 
 __global__ void build_taps3_kernel(const double* __restrict__ h, const uint64_t* __restrict__ words,
@@ -522,9 +541,16 @@ __device__ __forceinline__ void g3_fill_row(const G3Plan& P, int q, int64_t s0, 
     }
 }
 
-template <int BT, bool FUSED>
+// PAIR: launched in clusters of two CTAs that take the two tone tiles of a
+// work item; they need the same A tiles, so each CTA loads 64 rows of every
+// A tile and multicasts them into both CTAs' stage buffers.  A stage of a
+// CTA is then refilled only when both CTAs' MMAs have consumed it (its empty
+// barrier takes one commit from each), and the two CTAs meet at cluster
+// barriers after initialising their mbarriers and before leaving.
+template <int BT, bool FUSED, bool PAIR>
 __global__ void __launch_bounds__(FUSED ? G3_THREADS_FUSED : G3_THREADS, 1)
 demod3m_gemm_kernel(const __grid_constant__ G3Batch bt) {
+    static_assert(!(FUSED && PAIR), "the pair form loads its A tiles by TMA");
     using Cfg = G3Cfg<BT>;
     constexpr int STAGES = Cfg::STAGES;
     constexpr uint32_t STAGE_BYTES = Cfg::STAGE_BYTES, B_BYTES = Cfg::B_BYTES;
@@ -543,10 +569,13 @@ demod3m_gemm_kernel(const __grid_constant__ G3Batch bt) {
     constexpr int MMA_WARP = G3_EPI_WARPS + (FUSED ? G3_FUSED_PRODUCERS : 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rank = PAIR ? static_cast<int>(cluster_ctarank()) : 0;
+    const int cta0 = PAIR ? static_cast<int>(blockIdx.x >> 1) : static_cast<int>(blockIdx.x);
+    const int ncta = PAIR ? static_cast<int>(gridDim.x >> 1) : static_cast<int>(gridDim.x);
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], FUSED ? G3_FUSED_PRODUCERS * 32 : 1);
-            mbar_init(&empty[s], 1);
+            mbar_init(&empty[s], PAIR ? 2 : 1);
         }
         for (int b = 0; b < SLOTS; ++b) {
             mbar_init(&sfull[b], 1);
@@ -567,6 +596,7 @@ demod3m_gemm_kernel(const __grid_constant__ G3Batch bt) {
     }
     umma::fence_before_sync();
     __syncthreads();
+    if (PAIR) cluster_sync();          // both CTAs' barriers exist before any multicast
     umma::fence_after_sync();
     const uint32_t tmem = *tmem_holder;
     const int n_tiles = bt.total_tiles;
@@ -578,11 +608,11 @@ demod3m_gemm_kernel(const __grid_constant__ G3Batch bt) {
         const int pt = threadIdx.x - PROD_WARP * 32;                         // 0 .. 63
         uint32_t it = 0;
         bool stop = false;
-        for (int tile = blockIdx.x; tile < n_tiles && !stop; tile += gridDim.x) {
+        for (int tile = cta0; tile < n_tiles && !stop; tile += ncta) {
             const int pi = g3_plan_of(bt, tile);
             const G3Plan& P = bt.p[pi];
             int tm, tn;
-            tile_coords(P.g, tile - P.tile0, tm, tn);
+            g3_coords<PAIR>(P.g, tile - P.tile0, rank, tm, tn);
             const int m0 = tm * BM, n0 = tn * BT;
             const int64_t D = P.g.two_d;
             for (int kb0 = 0; kb0 < P.g.KB && !stop; kb0 += P.g.kchunk) {
@@ -625,11 +655,11 @@ demod3m_gemm_kernel(const __grid_constant__ G3Batch bt) {
         if (lane == 0) {
             uint32_t it = 0;
             bool stop = false;
-            for (int tile = blockIdx.x; tile < n_tiles && !stop; tile += gridDim.x) {
+            for (int tile = cta0; tile < n_tiles && !stop; tile += ncta) {
                 const int pi = g3_plan_of(bt, tile);
                 const G3Plan& P = bt.p[pi];
                 int tm, tn;
-                tile_coords(P.g, tile - P.tile0, tm, tn);
+                g3_coords<PAIR>(P.g, tile - P.tile0, rank, tm, tn);
                 const int m0 = tm * BM, n0 = tn * BT;
                 for (int kb0 = 0; kb0 < P.g.KB && !stop; kb0 += P.g.kchunk) {
                     const int kb1 = min(kb0 + P.g.kchunk, P.g.KB);
@@ -646,8 +676,16 @@ demod3m_gemm_kernel(const __grid_constant__ G3Batch bt) {
                             mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
                             const int kt = kb * G3_BK;
                             const int c0 = kt % P.g.two_d, c1 = m0 + kt / P.g.two_d;
-                            tma_load_2d(st, &P.a[2 * q], c0, c1, &full[s]);
-                            tma_load_2d(st + G3_A_BYTES, &P.a[2 * q + 1], c0, c1, &full[s]);
+                            if (PAIR) {
+                                // rows 64 r .. 64 r + 63 of both A planes, into both CTAs (64-row boxes)
+                                const uint32_t ho = static_cast<uint32_t>(rank) * G3_A_HALF;
+                                const int r1 = c1 + rank * (BM / 2);
+                                tma_load_2d_mc(st + ho, &P.a[2 * q], c0, r1, &full[s], 0x3);
+                                tma_load_2d_mc(st + G3_A_BYTES + ho, &P.a[2 * q + 1], c0, r1, &full[s], 0x3);
+                            } else {
+                                tma_load_2d(st, &P.a[2 * q], c0, c1, &full[s]);
+                                tma_load_2d(st + G3_A_BYTES, &P.a[2 * q + 1], c0, c1, &full[s]);
+                            }
                             tma_load_2d(st + 2 * G3_A_BYTES, &P.b[2 * q], kt, n0, &full[s]);
                             tma_load_2d(st + 2 * G3_A_BYTES + B_BYTES, &P.b[2 * q + 1], kt, n0, &full[s]);
                         }
@@ -660,13 +698,20 @@ demod3m_gemm_kernel(const __grid_constant__ G3Batch bt) {
                 if (static_cast<int32_t>(j) < 0) break;
                 mbar_wait(&full[j % STAGES], (j / STAGES) & 1, status0);
             }
+            // pair form: and for both CTAs' last commits to this CTA's empty
+            // barriers, so that nothing arrives here after the CTA has left
+            for (uint32_t k = 0; PAIR && k < static_cast<uint32_t>(STAGES) && it > 0; ++k) {
+                const uint32_t j = it - 1 - k;
+                if (static_cast<int32_t>(j) < 0) break;
+                mbar_wait(&empty[j % STAGES], (j / STAGES) & 1, status0);
+            }
         }
     } else if (warp == MMA_WARP) {
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
             uint32_t it = 0, phase = 0;
             bool stop = false;
-            for (int tile = blockIdx.x; tile < n_tiles && !stop; tile += gridDim.x) {
+            for (int tile = cta0; tile < n_tiles && !stop; tile += ncta) {
                 const GemmArgs& g = bt.p[g3_plan_of(bt, tile)].g;
                 for (int kb0 = 0; kb0 < g.KB && !stop; kb0 += g.kchunk) {
                     const int kb1 = min(kb0 + g.kchunk, g.KB);
@@ -699,7 +744,10 @@ demod3m_gemm_kernel(const __grid_constant__ G3Batch bt) {
                                 umma::mma_f16(d_tmem, umma::desc_k_sw128(ah + off), umma::desc_k_sw128(bh + off), IDESC_W, acc);
                                 umma::mma_f16(d_tmem, umma::desc_k_sw128(al + off), umma::desc_k_sw128(bh + off), IDESC, 1u);
                             }
-                            umma::commit(&empty[s]);
+                            if (PAIR)
+                                umma::commit_mc(&empty[s], 0x3);      // frees the stage in both CTAs
+                            else
+                                umma::commit(&empty[s]);
                         }
                         umma::commit(&sfull[slot]);
                     }
@@ -714,11 +762,11 @@ demod3m_gemm_kernel(const __grid_constant__ G3Batch bt) {
         const int row = qd * 32 + lane;
         uint32_t phase = 0;
         bool ok = true;
-        for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+        for (int tile = cta0; tile < n_tiles && ok; tile += ncta) {
             const G3Plan& P = bt.p[g3_plan_of(bt, tile)];
             const GemmArgs& g = P.g;
             int mt, tn;
-            tile_coords(g, tile - P.tile0, mt, tn);
+            g3_coords<PAIR>(g, tile - P.tile0, rank, mt, tn);
             const int m0 = mt * BM, n0 = tn * BT;
             float re[TPG], im[TPG];
 #pragma unroll
@@ -786,6 +834,7 @@ demod3m_gemm_kernel(const __grid_constant__ G3Batch bt) {
     }
     umma::fence_before_sync();
     __syncthreads();
+    if (PAIR) cluster_sync();          // neither CTA leaves while the other may still signal it
     if (warp == MMA_WARP) {
         umma::fence_after_sync();
         umma::dealloc(tmem, Cfg::TMEM_COLS);
@@ -902,6 +951,7 @@ cudaError_t demod3_prepare(const DemodLaunch& L, cudaStream_t st, DemodGemmJob* 
     job->n_tiles = 0;
     job->bt = L.tone_tile == 64 ? 64 : 128;
     job->fused = L.fused_presplit ? 1 : 0;
+    job->pair = (L.pair && !job->fused) ? 1 : 0;
     if (L.F <= 0) return cudaSuccess;
     if (L.D % G3_BK != 0 || L.Lpad % G3_BK != 0 || L.ntp % 128 != 0) return cudaErrorInvalidValue;
     const int64_t rows = static_cast<int64_t>(demod3_xs_rows(L.F, L.Lpad, L.D));
@@ -934,8 +984,8 @@ cudaError_t demod3_prepare(const DemodLaunch& L, cudaStream_t st, DemodGemmJob* 
             total, xp);
     }
     for (int i = 0; i < 6; ++i) {
-        if ((!job->fused &&
-             !make_map(&P->a[i], xp + i * total, static_cast<uint64_t>(L.D), static_cast<uint64_t>(rows), BM)) ||
+        if ((!job->fused && !make_map(&P->a[i], xp + i * total, static_cast<uint64_t>(L.D),
+                                      static_cast<uint64_t>(rows), job->pair ? BM / 2 : BM)) ||
             !make_map(&P->b[i], bp + i * bplane, static_cast<uint64_t>(L.Lpad), static_cast<uint64_t>(L.ntp), bt))
             return cudaErrorInvalidValue;
     }
@@ -957,43 +1007,82 @@ cudaError_t demod3_prepare(const DemodLaunch& L, cudaStream_t st, DemodGemmJob* 
     g.ld = L.tones_ld;
     g.fo = L.frame_offset;
     g.status = L.status;
-    job->n_tiles = n_mt * n_nt;
+    job->n_tiles = n_mt * (job->pair ? (n_nt + 1) / 2 : n_nt);
     return cudaGetLastError();
 }
 
 namespace {
-template <int BT, bool FUSED>
+template <int BT, bool FUSED, bool PAIR>
 cudaError_t g3_run(const G3Batch& b, int n_sms, cudaStream_t st) {
     using Cfg = G3Cfg<BT>;
-    cudaError_t e = cudaFuncSetAttribute(demod3m_gemm_kernel<BT, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(Cfg::SMEM));
+    auto kern = demod3m_gemm_kernel<BT, FUSED, PAIR>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(Cfg::SMEM));
     if (e != cudaSuccess) return e;
-    const int grid = std::max(1, std::min(b.total_tiles, n_sms));
-    demod3m_gemm_kernel<BT, FUSED><<<grid, FUSED ? G3_THREADS_FUSED : G3_THREADS, Cfg::SMEM, st>>>(b);
+    const int threads = FUSED ? G3_THREADS_FUSED : G3_THREADS;
+    if (!PAIR) {
+        const int grid = std::max(1, std::min(b.total_tiles, n_sms));
+        kern<<<grid, threads, Cfg::SMEM, st>>>(b);
+        return cudaGetLastError();
+    }
+    // clusters of two CTAs: as many as can be resident at once (one CTA per SM)
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(threads, 1, 1);
+    cfg.dynamicSmemBytes = Cfg::SMEM;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    static int max_clusters[2] = {0, 0};          // per tile width, queried once
+    int& mc = max_clusters[BT == 128 ? 0 : 1];
+    if (mc <= 0) {
+        cfg.gridDim = dim3(static_cast<unsigned>(2 * (n_sms / 2)), 1, 1);
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess || n <= 0) {
+            cudaGetLastError();
+            n = n_sms / 2;
+        }
+        mc = n;
+    }
+    const int clusters = std::max(1, std::min(b.total_tiles, mc));
+    cfg.gridDim = dim3(static_cast<unsigned>(2 * clusters), 1, 1);
+    e = cudaLaunchKernelEx(&cfg, kern, b);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 }  // namespace
 
 cudaError_t demod3_gemm(const DemodGemmJob* const* jobs, int n, int n_sms, cudaStream_t st) {
     // one persistent launch per group of up to kG3MaxPlans jobs of the same
-    // tile width and producer form
-    for (int variant = 0; variant < 4; ++variant) {
+    // tile width, producer form and cluster form
+    for (int variant = 0; variant < 8; ++variant) {
         const int bt = variant & 1 ? 64 : 128;
-        const int fused = variant >> 1;
+        const int fused = (variant >> 1) & 1;
+        const int pair = variant >> 2;
+        if (fused && pair) continue;
         G3Batch b;
         b.n_plans = 0;
         b.total_tiles = 0;
         for (int i = 0; i <= n; ++i) {
             const bool flush = i == n || b.n_plans == kG3MaxPlans;
             if (flush && b.n_plans > 0) {
-                const cudaError_t e = bt == 128 ? (fused ? g3_run<128, true>(b, n_sms, st) : g3_run<128, false>(b, n_sms, st))
-                                                : (fused ? g3_run<64, true>(b, n_sms, st) : g3_run<64, false>(b, n_sms, st));
+                cudaError_t e;
+                if (pair)
+                    e = bt == 128 ? g3_run<128, false, true>(b, n_sms, st) : g3_run<64, false, true>(b, n_sms, st);
+                else if (fused)
+                    e = bt == 128 ? g3_run<128, true, false>(b, n_sms, st) : g3_run<64, true, false>(b, n_sms, st);
+                else
+                    e = bt == 128 ? g3_run<128, false, false>(b, n_sms, st) : g3_run<64, false, false>(b, n_sms, st);
                 if (e != cudaSuccess) return e;
                 b.n_plans = 0;
                 b.total_tiles = 0;
             }
             if (i == n) break;
-            if (jobs[i]->bt != bt || jobs[i]->fused != fused || jobs[i]->n_tiles <= 0) continue;
+            if (jobs[i]->bt != bt || jobs[i]->fused != fused || jobs[i]->pair != pair || jobs[i]->n_tiles <= 0)
+                continue;
             std::memcpy(&b.p[b.n_plans], jobs[i]->bytes, sizeof(G3Plan));
             b.p[b.n_plans].tile0 = b.total_tiles;
             b.total_tiles += jobs[i]->n_tiles;

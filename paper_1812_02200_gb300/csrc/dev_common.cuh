@@ -91,6 +91,26 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int32_t
         " [%0], [%1, {%2, %3}], [%4];"
         ::"r"(smem_u32(dst)), "l"(tmap), "r"(c0), "r"(c1), "r"(smem_u32(bar)) : "memory");
 }
+// The same copy multicast to the CTAs of the cluster named in cta_mask: the
+// box lands at dst's offset in each of them and completes bytes on the
+// mbarrier at bar's offset in each of them.
+__device__ __forceinline__ void tma_load_2d_mc(void* dst, const void* tmap, int32_t c0, int32_t c1,
+                                               uint64_t* bar, uint16_t cta_mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
+        " [%0], [%1, {%2, %3}], [%4], %5;"
+        ::"r"(smem_u32(dst)), "l"(tmap), "r"(c0), "r"(c1), "r"(smem_u32(bar)), "h"(cta_mask) : "memory");
+}
+// Rank of this CTA in its cluster, and a barrier over every thread of the
+// cluster (release / acquire at cluster scope).
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 // 1-D bulk copy shared -> global (bulk async-group completion).
 // dst, src 16-byte aligned; bytes a multiple of 16.
 __device__ __forceinline__ void tma_bulk_s2g(void* dst, const void* src, uint32_t bytes) {

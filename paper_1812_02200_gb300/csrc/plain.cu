@@ -3,8 +3,12 @@
 //          cuFFT C2C transform (the library route of Sec. III.A), and a gather
 //          kernel for the tone bins;
 //   demod: an FP32 CUDA-core kernel over the Toeplitz view of the stream with
-//          FP32 modulated taps (mix + filter + decimate of Sec. III.B).
+//          FP32 modulated taps (mix + filter + decimate of Sec. III.B), or
+//          cublasCgemm in pedantic FP32 (no TF32, no emulation) on the Toeplitz
+//          matrix materialised in frame chunks (the library GEMM the paper
+//          names for the same product).
 // One-shot with zero history (frame k uses samples (k+1)*hop - W .. (k+1)*hop - 1).
+#include <cublas_v2.h>
 #include <cufft.h>
 
 #include <algorithm>
@@ -111,9 +115,10 @@ cudaError_t plain_pfb(const int16_t* iq, int64_t n, int N, int T, const float* h
     return cudaGetLastError();
 }
 
-void plain_release(void* scratch, void* fft_plan) {
+void plain_release(void* scratch, void* fft_plan, void* blas) {
     if (scratch) cudaFree(scratch);
     if (fft_plan) cufftDestroy(static_cast<cufftHandle>(reinterpret_cast<uintptr_t>(fft_plan)));
+    if (blas) cublasDestroy(static_cast<cublasHandle_t>(blas));
 }
 
 }  // namespace rfr
@@ -221,6 +226,85 @@ cudaError_t plain_demod(const int16_t* iq, int64_t n, int L, int D, const void* 
     plain_demod_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<const uint32_t*>(iq), n, L, D,
                                              static_cast<const float2*>(c32), words, n_tones, F,
                                              static_cast<float2*>(tones), tones_ld);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------- demod (cublasCgemm, FP32)
+namespace {
+
+// X[r][n] = x[(k0 + r + 1) * D - L + n] as complex FP32, zero outside the buffer
+// (frame k0 + r of the Toeplitz matrix; rows of L contiguous values).
+__global__ void toeplitz_rows_kernel(const uint32_t* __restrict__ x, int64_t n_samples, int L, int D,
+                                     int64_t k0, int64_t rows, float2* __restrict__ X) {
+    const int64_t total = rows * L;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t r = i / L;
+        const int64_t m = (k0 + r + 1) * D - L + (i - r * L);
+        X[i] = (m >= 0 && m < n_samples) ? iq_to_f2(x[m]) : make_float2(0.f, 0.f);
+    }
+}
+
+// out[t][k] *= exp(-i * phi_t(b_k)), b_k = (k + 1) * D - L, phase in uint64.
+__global__ void rotate_rows_kernel(float2* __restrict__ out, int64_t ld, int64_t F, int L, int D,
+                                   const uint64_t* __restrict__ words, int n_tones) {
+    const int64_t total = F * n_tones;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int t = static_cast<int>(i / F);
+        const int64_t k = i - static_cast<int64_t>(t) * F;
+        const uint64_t ph = words[t] * static_cast<uint64_t>((k + 1) * D - L);
+        float s, c;
+        sincospif(static_cast<float>(static_cast<int32_t>(ph >> 32)) * 0x1p-31f, &s, &c);
+        float2* o = out + static_cast<int64_t>(t) * ld + k;
+        *o = cmul(*o, make_float2(c, -s));
+    }
+}
+
+}  // namespace
+
+cudaError_t plain_demod_cgemm(const int16_t* iq, int64_t n, int L, int D, const void* c32, const uint64_t* words,
+                              int n_tones, void* tones, int64_t tones_ld, void** scratch, size_t* scratch_bytes,
+                              void** blas, cudaStream_t st) {
+    const int64_t F = n / D;
+    if (F <= 0 || n_tones <= 0) return cudaSuccess;
+    // frame chunk: the materialised rows take at most 512 MiB
+    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(F, (int64_t{512} << 20) / (int64_t{8} * L)));
+    const size_t need = static_cast<size_t>(chunk) * L * 8;
+    if (*scratch_bytes < need) {
+        if (*scratch) cudaFree(*scratch);
+        *scratch = nullptr;
+        *scratch_bytes = 0;
+        cudaError_t e = cudaMalloc(scratch, need);
+        if (e != cudaSuccess) return e;
+        *scratch_bytes = need;
+    }
+    if (!*blas) {
+        cublasHandle_t h;
+        if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+        if (cublasSetMathMode(h, CUBLAS_PEDANTIC_MATH) != CUBLAS_STATUS_SUCCESS) {
+            cublasDestroy(h);
+            return cudaErrorUnknown;
+        }
+        *blas = h;
+    }
+    cublasHandle_t h = static_cast<cublasHandle_t>(*blas);
+    if (cublasSetStream(h, st) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+    float2* X = static_cast<float2*>(*scratch);
+    float2* out = static_cast<float2*>(tones);
+    const cuComplex one = make_cuComplex(1.f, 0.f), zero = make_cuComplex(0.f, 0.f);
+    for (int64_t k0 = 0; k0 < F; k0 += chunk) {
+        const int64_t rows = std::min(chunk, F - k0);
+        toeplitz_rows_kernel<<<grid_for(rows * L), 256, 0, st>>>(reinterpret_cast<const uint32_t*>(iq), n, L, D,
+                                                                  k0, rows, X);
+        // column-major: Out (rows x tones, ld tones_ld) = X^T (rows x L) * C (L x tones); X and C
+        // are row-major [rows][L] and [tone][L], i.e. column-major L x rows and L x tones.
+        if (cublasCgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, static_cast<int>(rows), n_tones, L, &one,
+                        reinterpret_cast<const cuComplex*>(X), L, static_cast<const cuComplex*>(c32), L, &zero,
+                        reinterpret_cast<cuComplex*>(out + k0), static_cast<int>(tones_ld)) != CUBLAS_STATUS_SUCCESS)
+            return cudaErrorUnknown;
+    }
+    rotate_rows_kernel<<<grid_for(F * n_tones), 256, 0, st>>>(out, tones_ld, F, L, D, words, n_tones);
     return cudaGetLastError();
 }
 

@@ -134,6 +134,7 @@ struct DemodLaunch {
     int raster_group;           // tile order: groups of this many 128-frame tiles sweep all tones
     int tone_tile;              // three-product GEMM: tones per tile, 128 or 64 (0 = 128)
     int fused_presplit;         // three-product GEMM: producers convert the int16 stream themselves
+    int pair;                   // three-product GEMM: clusters of two CTAs sharing A tiles by multicast
 };
 // The three-product GEMM of one push, described for a persistent launch that
 // may cover several plans (opaque record of demod.cu).
@@ -142,6 +143,7 @@ struct DemodGemmJob {
     alignas(128) unsigned char bytes[kDemodJobBytes];
     int bt = 128;               // tone-tile width
     int fused = 0;              // pre-split fused into the GEMM's producers
+    int pair = 0;               // two-CTA clusters (n_tiles then counts tone-tile pairs)
     int n_tiles = 0;            // 0: nothing to launch
 };
 cudaError_t demod_build_taps(const double* d_h, const uint64_t* d_words, int n_tones, int ntp,
@@ -193,7 +195,10 @@ cudaError_t plain_demod_taps(const float* h32, const uint64_t* words, int n_tone
 cudaError_t plain_demod(const int16_t* iq, int64_t n, int L, int D, const void* c32,
                         const uint64_t* words, int n_tones, void* tones, int64_t tones_ld,
                         cudaStream_t st);
-void plain_release(void* scratch, void* fft_plan);
+cudaError_t plain_demod_cgemm(const int16_t* iq, int64_t n, int L, int D, const void* c32,
+                              const uint64_t* words, int n_tones, void* tones, int64_t tones_ld,
+                              void** scratch, size_t* scratch_bytes, void** blas, cudaStream_t st);
+void plain_release(void* scratch, void* fft_plan, void* blas);
 
 // ------------------------------------------------------------- tuning
 // Launch choices that never change results (bit-identical outputs).
@@ -202,6 +207,7 @@ struct TuneConfig {
     int demod_raster = 1;       // 1 = tones fastest across the whole grid
     int demod_bt = 128;         // three-product GEMM: tones per tile (128 or 64)
     int demod_fused = 0;        // three-product GEMM: pre-split fused into its producers (0/1)
+    int demod_pair = 0;         // three-product GEMM: two-CTA clusters sharing A tiles (0/1)
     bool tuned = false;
 };
 
@@ -295,6 +301,7 @@ struct rfr_plan {
     size_t plain_scratch_bytes = 0;
     void* plain_fft = nullptr;
     int64_t plain_fft_batch = 0;
+    void* plain_blas = nullptr;    // cuBLAS handle of the Cgemm form
 
     rfr::TuneConfig tune;
     std::string last_error;

@@ -25,6 +25,7 @@ if not os.path.exists(LIB_PATH):
 _lib = C.CDLL(LIB_PATH)
 
 OK, E_INVALID, E_NOMEM, E_CUDA, E_TIMEOUT, E_SHORT, E_BUSY, E_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
+PLAIN_DEFAULT, PLAIN_CGEMM = 0, 1
 WIN = {"rect": 0, "hann": 1, "hamming": 2, "blackman": 3, "kaiser": 4}
 OUT_FULL, OUT_TONES = 1, 2
 MODE_PFB, MODE_DEMOD = 1, 2
@@ -80,6 +81,7 @@ _SIGS = {
     "rfr_plan_get_taps": (C.c_int, [_P, _P, _P, C.POINTER(C.c_int64)]),
     "rfr_plan_get_bins": (C.c_int, [_P, _P, C.POINTER(C.c_int32)]),
     "rfr_plain_oneshot": (C.c_int, [_P, _P, C.c_int64, C.POINTER(Output), _P]),
+    "rfr_plain_oneshot_form": (C.c_int, [_P, C.c_int32, _P, C.c_int64, C.POINTER(Output), _P]),
     "rfr_freq_to_word": (C.c_uint64, [C.c_double, C.c_double]),
     "rfr_word_to_bin": (C.c_int32, [C.c_uint64, C.c_int32]),
     "rfr_status_string": (C.c_char_p, [C.c_int]),
@@ -117,6 +119,8 @@ _SIGS = {
     "rfr_plan_set_tone_tile": (C.c_int, [_P, C.c_int32]),
     "rfr_plan_set_fused_presplit": (C.c_int, [_P, C.c_int32]),
     "rfr_plan_get_fused_presplit": (C.c_int, [_P, C.POINTER(C.c_int32)]),
+    "rfr_plan_set_demod_pair": (C.c_int, [_P, C.c_int32]),
+    "rfr_plan_get_demod_pair": (C.c_int, [_P, C.POINTER(C.c_int32)]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -323,10 +327,15 @@ class Plan:
         self._check(_lib.rfr_process_host(self._h, _ptr(x), x.shape[0], C.byref(o)), "process_host")
         return o.frames
 
-    def plain_oneshot(self, x, full=None, tones=None, stream=None) -> int:
+    def plain_oneshot(self, x, full=None, tones=None, stream=None, form: int = 0) -> int:
+        """The plain FP32 comparison form; form PLAIN_CGEMM (demodulation
+        only) runs cublasCgemm on the materialised Toeplitz matrix."""
         o = self._out(full, tones, 0)
-        self._check(_lib.rfr_plain_oneshot(self._h, _ptr(x), x.shape[0], C.byref(o),
-                                           _stream_ptr(stream)), "plain_oneshot")
+        if form == PLAIN_DEFAULT:
+            st = _lib.rfr_plain_oneshot(self._h, _ptr(x), x.shape[0], C.byref(o), _stream_ptr(stream))
+        else:
+            st = _lib.rfr_plain_oneshot_form(self._h, form, _ptr(x), x.shape[0], C.byref(o), _stream_ptr(stream))
+        self._check(st, "plain_oneshot")
         return o.frames
 
     def reset(self):
@@ -357,6 +366,12 @@ class Plan:
         normally chosen by autotune()."""
         self._check(_lib.rfr_plan_set_fused_presplit(self._h, 1 if on else 0), "set_fused_presplit")
 
+    def set_demod_pair(self, on: bool):
+        """Three-product demodulation: the GEMM in clusters of two CTAs that
+        share each frame tile by TMA multicast (True) or one CTA per tile
+        (False, the default); result-neutral, normally chosen by autotune()."""
+        self._check(_lib.rfr_plan_set_demod_pair(self._h, 1 if on else 0), "set_demod_pair")
+
     def inject_device_status(self, status: int):
         """Write the plan's device status word as a timed-out kernel would
         (1), or clear it (0): host-side failure injection for tests."""
@@ -371,11 +386,12 @@ class Plan:
     def tune(self) -> dict:
         a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
         self._check(_lib.rfr_plan_get_tune(self._h, C.byref(a), C.byref(b), C.byref(c)), "tune")
-        t, f = C.c_int32(), C.c_int32()
+        t, f, pr = C.c_int32(), C.c_int32(), C.c_int32()
         self._check(_lib.rfr_plan_get_tone_tile(self._h, C.byref(t)), "tone tile")
         self._check(_lib.rfr_plan_get_fused_presplit(self._h, C.byref(f)), "fused pre-split")
+        self._check(_lib.rfr_plan_get_demod_pair(self._h, C.byref(pr)), "pair")
         return {"pfb_lookahead": a.value, "demod_raster": b.value, "tone_tile": t.value,
-                "fused_presplit": f.value, "tuned": bool(c.value)}
+                "fused_presplit": f.value, "pair": pr.value, "tuned": bool(c.value)}
 
     def state_export(self) -> bytes:
         n = C.c_size_t()

@@ -298,3 +298,75 @@ def test_fused_presplit_far_origin_and_batch(lib):
     for i, (u, v) in enumerate(zip(ob, oa)):
         assert torch.equal(u, v), i
     batch.close()
+
+
+PAIR_SHAPES = [
+    # L, D, tones, frames, tones per tile: odd and even tone-tile counts, ragged frame tiles
+    (1024, 512, 20, 130, 128),     # one tone tile: the pair's second CTA works on zero taps
+    (1000, 512, 130, 140, 128),    # two tiles, L not a multiple of 64
+    (3000, 448, 300, 90, 128),     # three tiles
+    (4096, 2048, 160, 129, 64),    # three 64-tone tiles, the workload's filter
+    (1024, 2048, 50, 160, 64),     # L < D
+    (256, 64, 8, 300, 128),
+]
+
+
+@pytest.mark.parametrize("L,D,nt,frames,bt", PAIR_SHAPES)
+def test_pair_form_equals_single_cta_and_oracle(lib, L, D, nt, frames, bt):
+    """Two-CTA clusters sharing each frame tile's operand tiles by TMA
+    multicast give, bit for bit, the frames of one CTA per tile (the same
+    MMAs in the same order), and match the oracle."""
+    case = siggen.demod_case(frames * D + D // 5, nt, seed=7700 + L + nt + bt)
+    a = _plan3(lib, L, D, case["words"], "hann", 1e-3)
+    b = _plan3(lib, L, D, case["words"], "hann", 1e-3)
+    for p in (a, b):
+        p.set_tone_tile(bt)
+    a.set_demod_pair(False)
+    b.set_demod_pair(True)
+    assert a.tune()["pair"] == 0 and b.tune()["pair"] == 1
+    ga = _run(a, case["x"], nt)
+    gb = _run(b, case["x"], nt)
+    assert np.isfinite(gb).all()
+    assert np.array_equal(ga, gb)
+    ref = oracle.demod(case["x"], L, D, oracle.lowpass("hann", L, 1e-3), case["words"])
+    e = rel_rows(gb, ref)
+    print(f"pair form L={L} D={D} tones={nt} bt={bt}: bit-identical to one CTA per tile, max rel err {e.max():.3e}")
+    assert e.max() < TOL
+    # the fused pre-split has no pair form
+    b.set_fused_presplit(True)
+    assert b.tune()["pair"] == 0
+
+
+def test_pair_form_in_batches_with_the_other_forms(lib):
+    """A batched step mixing pair, single-CTA and fused plans of both tile
+    widths (one persistent launch per form): every stream equals the same
+    stream pushed alone in the single-CTA form."""
+    D = 512
+    forms = [(1, 0, 128), (0, 0, 128), (1, 0, 64), (0, 1, 128), (1, 0, 128), (0, 0, 64), (1, 0, 64)]
+    plans_b, plans_a, xs, ob, oa = [], [], [], [], []
+    for i, (pair, fused, bt) in enumerate(forms):
+        nt = 25 + 61 * i
+        c = siggen.demod_case(D * (60 + 7 * i) + 13 * i, nt, seed=7800 + i)
+        q = _plan3(lib, 1024, D, c["words"], "hann", 1e-3)
+        q.set_tone_tile(bt)
+        q.set_demod_pair(bool(pair))
+        q.set_fused_presplit(bool(fused))
+        plans_b.append(q)
+        r = _plan3(lib, 1024, D, c["words"], "hann", 1e-3)
+        r.set_tone_tile(bt)
+        r.set_demod_pair(False)
+        plans_a.append(r)
+        xs.append(torch.from_numpy(c["x"]).to(DEV))
+        F = r.frames_for(xs[-1].shape[0])
+        ob.append(torch.zeros((nt, F), dtype=torch.complex64, device=DEV))
+        oa.append(torch.zeros((nt, F), dtype=torch.complex64, device=DEV))
+    batch = lib.Batch(plans_b)
+    half = [x.shape[0] // 2 for x in xs]
+    got = batch.push([x[:h] for x, h in zip(xs, half)], None, ob)
+    batch.push([x[h:] for x, h in zip(xs, half)], None, ob, got)
+    for q, xx, o in zip(plans_a, xs, oa):
+        q.push_into(xx, tones=o)
+    torch.cuda.synchronize()
+    for i, (u, v) in enumerate(zip(ob, oa)):
+        assert torch.equal(u, v), i
+    batch.close()

@@ -170,6 +170,59 @@ def test_demod_plain_fp32_form(lib):
     assert e.max() < 1e-3          # reported; the FP32 form is not held to 1e-5
 
 
+def test_demod_plain_cgemm_form(lib):
+    """The library-GEMM comparison form (cublasCgemm, pedantic FP32, on the
+    materialised Toeplitz matrix): the oracle on every tone of a small case
+    (L < D included), and on a stream long enough for two frame chunks of the
+    materialised matrix (65536 rows of L = 1024 fill its 512 MiB), compared
+    with the CUDA-core form on all frames and with the oracle on the frames
+    around the chunk boundary."""
+    for L, D, nt, frames, seed in [(1024, 512, 40, 200, 52), (1024, 2048, 25, 90, 53), (256, 64, 9, 301, 54)]:
+        case = siggen.demod_case(D * frames + 7, nt, seed=seed)
+        plan = _plan(lib, L, D, case["words"])
+        x = torch.from_numpy(case["x"]).to(DEV)
+        out = torch.full((nt, frames), float("nan"), dtype=torch.complex64, device=DEV)
+        assert plan.plain_oneshot(x, tones=out, form=lib.PLAIN_CGEMM) == frames
+        torch.cuda.synchronize()
+        h = oracle.lowpass("blackman", L, 40e3 / 200e6)
+        ref = oracle.demod(case["x"], L, D, h, case["words"])
+        e = rel_rows(out.cpu().numpy(), ref)
+        print(f"Cgemm form L={L} D={D}: max rel err {e.max():.3e}")
+        assert e.max() < 1e-4
+        plan.close()
+
+    L, D, nt = 1024, 32, 6
+    F = 65536 + 37
+    case = siggen.demod_case(F * D, nt, seed=55)
+    plan = _plan(lib, L, D, case["words"])
+    x = torch.from_numpy(case["x"]).to(DEV)
+    out = torch.zeros((nt, F), dtype=torch.complex64, device=DEV)
+    core = torch.zeros((nt, F), dtype=torch.complex64, device=DEV)
+    assert plan.plain_oneshot(x, tones=out, form=lib.PLAIN_CGEMM) == F
+    assert plan.plain_oneshot(x, tones=core) == F
+    torch.cuda.synchronize()
+    g, c = out.cpu().numpy(), core.cpu().numpy()
+    d = rel_rows(g, c)
+    print(f"Cgemm form over two chunks vs CUDA-core form: max rel diff {d.max():.3e}")
+    assert np.isfinite(g).all() and d.max() < 1e-4
+    h = oracle.lowpass("blackman", L, 40e3 / 200e6)
+    k0, k1 = 65536 - 24, 65536 + 24
+    ref = oracle.demod(case["x"], L, D, h, case["words"], k0, k1)
+    e = rel_rows(g[:, k0:k1], ref)
+    print(f"Cgemm form at the chunk boundary: max rel err {e.max():.3e}")
+    assert e.max() < 1e-4
+    with pytest.raises(lib.RfrError) as ei:
+        plan.plain_oneshot(x, tones=out, form=7)
+    assert ei.value.status == lib.E_INVALID
+    plan.close()
+    pfb = lib.Plan(64, 4, window="hann", words=np.array([1 << 58], np.uint64))
+    with pytest.raises(lib.RfrError) as ei:
+        pfb.plain_oneshot(torch.zeros((64 * 8, 2), dtype=torch.int16, device=DEV),
+                          tones=torch.zeros((1, 8), dtype=torch.complex64, device=DEV), form=lib.PLAIN_CGEMM)
+    assert ei.value.status == lib.E_UNSUPPORTED
+    pfb.close()
+
+
 def test_demod_invalid_plans(lib):
     w = np.array([12345], np.uint64)
     for L, D in [(0, 512), (16385, 512), (1024, 100), (1024, 16), (1024, 0)]:
