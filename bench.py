@@ -676,7 +676,8 @@ def run_large_n(args, dev, stream, x, words):
     two-pass form), and the workload's N = 4096, T = 8 Kaiser(9) oversampled
     4x (hop 1024, the mixed-radix one-pass form); and the batched workload's
     power-of-two shapes whose FP32 delay line does not fit one SM's tensor
-    memory (N = 16384 T = 8, N = 4096 T = 16, N = 16384 T = 16, Kaiser(9));
+    memory (N = 16384 and 8192 with T = 8, direct kernel and cluster kernel;
+    N = 4096 T = 16, N = 16384 T = 16, direct kernel; Kaiser(9));
     each on the workload's 2^28-sample stream, full spectrum + its 1000 tones."""
     import torch
 
@@ -686,6 +687,7 @@ def run_large_n(args, dev, stream, x, words):
     n = x.shape[0]
     for N, T, win, hop, reps in ((100000, 4, "hamming", 100000, 5), (10 ** 7, 4, "hamming", 10 ** 7, 3),
                                  (4096, 8, "kaiser", 1024, 3), (16384, 8, "kaiser", 16384, 3),
+                                 (8192, 8, "kaiser", 8192, 3),
                                  (4096, 16, "kaiser", 4096, 3), (16384, 16, "kaiser", 16384, 3)):
         plan = rfr.Plan(N, T, window=win, beta=BETA if win == "kaiser" else 0.0, words=words, full=True,
                         tones=True, decimation=hop)
@@ -710,6 +712,23 @@ def run_large_n(args, dev, stream, x, words):
                "value": n / (ms * 1e-3) / 1e6, "unit": UNIT, "ms": ms, "frames": F,
                "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                             "frac": gbs / hbm_peak, "bytes_per_sample": bps}}
+        if N in (8192, 16384) and T <= 8:
+            # the cluster kernel (clusters of N / 4096 CTAs) on the same stream
+            pc = rfr.Plan(N, T, window=win, beta=BETA if win == "kaiser" else 0.0, words=words, full=True,
+                          tones=True, decimation=hop)
+            pc.set_pfb_cluster(True)
+            pc.push_into(x, full, tones, stream=stream)
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            for _ in range(reps):
+                pc.push_into(x, full, tones, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            cms = e0.elapsed_time(e1) / reps
+            res["cluster_kernel"] = {"value": n / (cms * 1e-3) / 1e6, "unit": UNIT, "ms": cms,
+                                     "form": f"clusters of {N // 4096} CTAs, filtered slices exchanged through "
+                                             "distributed shared memory (the default is the direct kernel)"}
+            pc.close()
         if not args.no_plain and N <= 100000 and hop == N:
             # the plain FP32 form on the same stream: FP32 FIR kernel + cuFFT + gather
             plan.plain_oneshot(x, full, tones, stream=stream)

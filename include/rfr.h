@@ -484,6 +484,22 @@ rfr_status rfr_plan_get_fused_presplit(const rfr_plan* plan, int32_t* on);
 rfr_status rfr_plan_set_demod_pair(rfr_plan* plan, int32_t on);
 rfr_status rfr_plan_get_demod_pair(const rfr_plan* plan, int32_t* on);
 
+/* PFB plans of N = 8192 or 16384 channels with T <= 8 taps (Sec. III.A), whose
+ * FP32 delay line of N*T points exceeds one SM's tensor memory: on = 1 runs
+ * them on clusters of N/4096 CTAs on as many SMs, each holding a 4096-channel
+ * slice's delay line in tensor memory and taps in registers; the N-point
+ * FFT is split into a radix-(N/4096) step across the CTAs (filtered slices
+ * exchanged through distributed shared memory) and a 4096-point FFT per
+ * CTA, and the output rows are assembled the same way.  on = 0 (the
+ * default): the direct kernel (taps and samples through L1/L2), which
+ * measured faster (99 against 57 Gs/s at N = 16384, T = 8): with one frame
+ * in flight per CTA the cross-SM exchanges and cluster barriers of every
+ * frame cannot be hidden.  The two round differently (both within the
+ * oracle's tolerance), so choose before the first push; the autotuner times
+ * both.  Errors: RFR_E_INVALID (another plan shape, on not 0/1). */
+rfr_status rfr_plan_set_pfb_cluster(rfr_plan* plan, int32_t on);
+rfr_status rfr_plan_get_pfb_cluster(const rfr_plan* plan, int32_t* on);
+
 /* ---------------------------------------------------------------- serving */
 typedef struct rfr_server rfr_server;
 

@@ -338,6 +338,9 @@ rfr_status push_core(rfr_plan* p, const int16_t* iq, int64_t n, const rfr_output
             L.hop = static_cast<int>(p->H);
             L.a0 = p->samples - p->cl;
             L.sym_taps = p->sym_taps ? 1 : 0;
+            L.cluster = p->tune.pfb_cluster && p->d_tw_cl ? 1 : 0;
+            L.tw_cl = p->d_tw_cl;
+            L.tw_cl_count = p->tw_cl_count;
             if (p->gen && p->gplan.N1 > 1 && p->gplan.z_frames < std::min(F, p->gplan.z_cap_frames)) {
                 // grow the between-pass buffer, unless the stream is being
                 // captured (then the frames go through the buffer in batches)
@@ -459,7 +462,7 @@ rfr_status reset_state(rfr_plan* p) {
 void destroy(rfr_plan* p) {
     if (!p) return;
     cudaDeviceSynchronize();
-    for (void* q : {static_cast<void*>(p->d_h), p->d_tw, static_cast<void*>(p->d_bins),
+    for (void* q : {static_cast<void*>(p->d_h), p->d_tw, p->d_tw_cl, static_cast<void*>(p->d_bins),
                     static_cast<void*>(p->d_words), static_cast<void*>(p->d_rates), static_cast<void*>(p->d_h32), p->d_c32, p->d_bhi, p->d_blo,
                     static_cast<void*>(p->d_status), static_cast<void*>(p->d_carry[0]),
                     static_cast<void*>(p->d_carry[1]), p->d_xs_hi, p->d_xs_lo, p->d_rot, p->d_qfull, p->d_b3, p->d_xs3,
@@ -591,6 +594,20 @@ rfr_status rfr_plan_create(rfr_plan** out, int32_t channels, int32_t taps, const
         for (int s = 0; s < nt; ++s) p->bins[s] = rfr::word_to_bin(p->words[s], channels);
         std::vector<float> tw = p->gen ? std::vector<float>() : make_twiddles(p->log2n);
         p->tw_count = static_cast<int>(tw.size() / 2);
+        std::vector<float> tw_cl;
+        const int ccl = p->gen ? 0 : rfr::pfb_cluster_size(p->log2n, p->Tk);
+        if (ccl > 0) {
+            // the cluster kernel's table: the 4096-point FFT's twiddles, then
+            // W_N^(k2 p1) for k2 < C, p1 < 4096 (its cross-CTA step; FP64 -> FP32)
+            tw_cl = make_twiddles(12);
+            p->tw_cl_count = static_cast<int>(tw_cl.size() / 2);
+            for (int k2 = 0; k2 < ccl; ++k2)
+                for (int p1 = 0; p1 < 4096; ++p1) {
+                    const double ang = -2.0 * kPi * static_cast<double>(k2 * p1) / static_cast<double>(channels);
+                    tw_cl.push_back(static_cast<float>(std::cos(ang)));
+                    tw_cl.push_back(static_cast<float>(std::sin(ang)));
+                }
+        }
         p->W = static_cast<int64_t>(p->Tk) * channels;
         p->H = decimation;
         p->carry_cap = p->W;
@@ -609,6 +626,10 @@ rfr_status rfr_plan_create(rfr_plan** out, int32_t channels, int32_t taps, const
         cudaMemcpy(p->d_h, hk.data(), hk.size() * 4, cudaMemcpyHostToDevice);
         cudaMemcpy(p->d_h32, p->h32.data(), p->h32.size() * 4, cudaMemcpyHostToDevice);
         if (!tw.empty()) cudaMemcpy(p->d_tw, tw.data(), tw.size() * 4, cudaMemcpyHostToDevice);
+        if (!tw_cl.empty()) {
+            if ((e = dev_alloc(&p->d_tw_cl, tw_cl.size() * 4)) != cudaSuccess) return bad(cuda_fail(p, e, "plan alloc"));
+            cudaMemcpy(p->d_tw_cl, tw_cl.data(), tw_cl.size() * 4, cudaMemcpyHostToDevice);
+        }
         if (nt) cudaMemcpy(p->d_bins, p->bins.data(), nt * 4, cudaMemcpyHostToDevice);
     } else if (channels == 0) {
         // ----------------------------------------------------------- demod

@@ -91,7 +91,7 @@ std::string tune_key(const rfr_plan* p, int64_t n) {
 //   {"key": [pfb_lookahead, demod_raster, demod_tone_tile, demod_fused], ...}
 // (missing trailing numbers take their defaults: tone tile 128, not fused)
 struct TuneEntry {
-    int lookahead = 0, raster = 1, bt = 128, fused = 0, pair = 0;
+    int lookahead = 0, raster = 1, bt = 128, fused = 0, pair = 0, cluster = 0;
 };
 std::map<std::string, TuneEntry> tune_load() {
     std::map<std::string, TuneEntry> m;
@@ -102,12 +102,13 @@ std::map<std::string, TuneEntry> tune_load() {
         const size_t b0 = line.find('[', q1 == std::string::npos ? 0 : q1);
         if (q0 == std::string::npos || q1 == std::string::npos || b0 == std::string::npos) continue;
         TuneEntry t;
-        const int got = std::sscanf(line.c_str() + b0, "[%d, %d, %d, %d, %d]", &t.lookahead, &t.raster, &t.bt,
-                                    &t.fused, &t.pair);
+        const int got = std::sscanf(line.c_str() + b0, "[%d, %d, %d, %d, %d, %d]", &t.lookahead, &t.raster, &t.bt,
+                                    &t.fused, &t.pair, &t.cluster);
         if (got >= 2) {
             if (got == 2 || (t.bt != 64 && t.bt != 128)) t.bt = 128;
             if (got < 4 || (t.fused != 0 && t.fused != 1)) t.fused = 0;
             if (got < 5 || (t.pair != 0 && t.pair != 1) || t.fused) t.pair = 0;
+            if (got < 6 || (t.cluster != 0 && t.cluster != 1)) t.cluster = 0;
             m[line.substr(q0 + 1, q1 - q0 - 1)] = t;
         }
     }
@@ -122,7 +123,7 @@ void tune_store(const std::map<std::string, TuneEntry>& m) {
         size_t i = 0;
         for (const auto& kv : m) {
             f << "  \"" << kv.first << "\": [" << kv.second.lookahead << ", " << kv.second.raster << ", "
-              << kv.second.bt << ", " << kv.second.fused << ", " << kv.second.pair << "]"
+              << kv.second.bt << ", " << kv.second.fused << ", " << kv.second.pair << ", " << kv.second.cluster << "]"
               << (++i < m.size() ? "," : "") << "\n";
         }
         f << "}\n";
@@ -278,6 +279,7 @@ rfr_status rfr_plan_autotune(rfr_plan* p, int64_t n_samples, int32_t use_cache, 
             p->tune.demod_bt = it->second.bt;
             p->tune.demod_fused = it->second.fused;
             p->tune.demod_pair = it->second.pair;
+            p->tune.pfb_cluster = p->d_tw_cl ? it->second.cluster : 0;
             p->tune.tuned = true;
             if (best_ms) *best_ms = -1.0;
             return RFR_OK;
@@ -287,6 +289,8 @@ rfr_status rfr_plan_autotune(rfr_plan* p, int64_t n_samples, int32_t use_cache, 
     std::vector<TuneEntry> cand;
     if (p->mode == RFR_MODE_PFB) {
         for (int la : {1, 2, 3}) cand.push_back({la, 1, 128});
+        // N = 8192, 16384 with T <= 8: the cluster kernel beside the direct one
+        if (p->d_tw_cl) cand.push_back({0, 1, 128, 0, 0, 1});
     } else {
         // the fused pre-split converts each A tile once per tone tile and
         // product (3 x tone tiles times per sample): timed only for plans of
@@ -348,6 +352,7 @@ rfr_status rfr_plan_autotune(rfr_plan* p, int64_t n_samples, int32_t use_cache, 
         p->tune.demod_bt = cand[c].bt;
         p->tune.demod_fused = cand[c].fused;
         p->tune.demod_pair = cand[c].pair;
+        p->tune.pfb_cluster = cand[c].cluster;
         float ms_best = 1e30f;
         for (int rep = 0; rep < 4 && rs == RFR_OK; ++rep) {
             p->samples = s_samples;
@@ -388,6 +393,7 @@ rfr_status rfr_plan_autotune(rfr_plan* p, int64_t n_samples, int32_t use_cache, 
     p->tune.demod_bt = best_c.bt;
     p->tune.demod_fused = best_c.fused;
     p->tune.demod_pair = best_c.pair;
+    p->tune.pfb_cluster = best_c.cluster;
     p->tune.tuned = true;
     if (best_ms) *best_ms = best;
     if (use_cache) {
@@ -427,6 +433,18 @@ rfr_status rfr_plan_set_demod_pair(rfr_plan* p, int32_t on) {
 rfr_status rfr_plan_get_demod_pair(const rfr_plan* p, int32_t* on) {
     if (!p || !on) return RFR_E_INVALID;
     *on = p->mode == RFR_MODE_DEMOD && p->demod_products == 3 && !p->tune.demod_fused ? p->tune.demod_pair : 0;
+    return RFR_OK;
+}
+
+rfr_status rfr_plan_set_pfb_cluster(rfr_plan* p, int32_t on) {
+    if (!p || p->mode != RFR_MODE_PFB || !p->d_tw_cl || (on != 0 && on != 1)) return RFR_E_INVALID;
+    p->tune.pfb_cluster = on;
+    return RFR_OK;
+}
+
+rfr_status rfr_plan_get_pfb_cluster(const rfr_plan* p, int32_t* on) {
+    if (!p || !on) return RFR_E_INVALID;
+    *on = p->mode == RFR_MODE_PFB && p->d_tw_cl ? p->tune.pfb_cluster : 0;
     return RFR_OK;
 }
 

@@ -819,6 +819,338 @@ __global__ void __launch_bounds__(kRingThreads, 1)
     }
 }
 
+// ------------------------------------------------- CLUSTER (N = 8192, 16384)
+// N = C * 4096 channels (C = 2 or 4), T <= 8 taps: the FP32 delay line of
+// N * T points exceeds one SM's tensor memory, so a cluster of C CTAs on C
+// SMs shares every frame.  CTA c (its rank in the cluster) owns channels
+// [4096 c, 4096 c + 4096): their staging, delay line in TMEM and taps in
+// registers, exactly as the one-SM kernel above.  The N-point DFT of the
+// filtered frame v is split as p = 4096 c + p1, k = k2 + C k1:
+//   y[k2 + C k1] = sum_p1 W_4096^(k1 p1) * W_N^(k2 p1) * sum_c W_C^(k2 c) v[4096 c + p1],
+// so after the FIR each CTA puts its slice in shared memory (E), the
+// cluster meets (S1), CTA k2 forms u[p1] = W_N^(k2 p1) sum_c W_C^(k2 c) E_c[p1]
+// from the C slices (distributed shared memory reads; W_C^m is an exact
+// quarter-turn power or a sign), runs the 4096-point FFT of the one-SM
+// kernel on u and leaves bins k2 + C k1 in its buffer P; the cluster meets
+// again (S2) and CTA c assembles output bins [4096 c, 4096 c + 4096) from
+// the C buffers into one contiguous row piece (one TMA bulk store) and
+// gathers its share of the tones (a contiguous range of tone rows, whole
+// 256-row boxes) the same way.  Waits on the staging ring are bounded; a
+// CTA whose wait gave up keeps taking part in every cluster barrier (with
+// no further copies) so that no peer is left waiting.  A plan choice
+// (rfr_plan_set_pfb_cluster), not the default: with one frame in flight per
+// CTA the exchanges and the two cluster barriers of every frame stay
+// exposed, and the direct kernel measured faster.
+constexpr int kClusterTonesPerCta = kTonesPerThread * kRingThreads;
+struct ClusterLayout {
+    size_t xb, tw, bins, tile, bars, total;
+};
+__host__ __device__ __forceinline__ ClusterLayout cluster_layout(int tw_count, int nb) {
+    ClusterLayout L{};
+    L.xb = static_cast<size_t>(kTmemStage) * 4096 * 4;
+    L.tw = L.xb + static_cast<size_t>(3) * (4096 + 256) * 8;             // P / Q pair and E
+    size_t o = L.tw + static_cast<size_t>(((tw_count + 1) & ~1) + 16) * 8;  // + W_N^(k2 256 r), r < 16
+    L.bins = o;
+    o = (o + static_cast<size_t>(nb) * 4 + 1023) / 1024 * 1024;
+    L.tile = o;
+    o += static_cast<size_t>((nb + kToneBox - 1) / kToneBox * kToneBox) * kToneGroup * 8;
+    L.bars = o;
+    L.total = o + kTmemStage * 8 + 16;
+    return L;
+}
+
+// Address of `p` (this CTA's shared memory) in cluster CTA `rank`.
+__device__ __forceinline__ uint32_t dsmem_map(const void* p, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ float2 dsmem_ld_f2(uint32_t addr) {
+    float2 v;
+    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr) : "memory");
+    return v;
+}
+// z * (-i)^m, exact
+__device__ __forceinline__ float2 quarter_turn(float2 z, int m) {
+    switch (m & 3) {
+    case 0: return z;
+    case 1: return make_float2(z.y, -z.x);
+    case 2: return make_float2(-z.x, -z.y);
+    default: return make_float2(-z.y, z.x);
+    }
+}
+
+// a.tw: the 4096-point FFT twiddles (a.tw_count entries), then W_N^(k2 p1)
+// at a.tw + a.tw_count + k2 * 4096 + p1.  a.nb_smem: tones per CTA (a
+// multiple of kToneBox, or 0: tones gathered per frame without the tile).
+template <int C, int T>
+__global__ void __launch_bounds__(kRingThreads, 1)
+    pfb_cluster_kernel(const PfbArgs a, const __grid_constant__ CUtensorMap tm_tones) {
+    constexpr int NB = 4096, NT = 256, N = C * NB;
+    static_assert(C == 2 || C == 4, "cluster of 2 or 4 CTAs");
+    static_assert(T <= kTmemSlots, "delay line fits in TMEM");
+    constexpr int XS = NB + NB / 16;                              // padded buffer length
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int ntc = a.nb_smem;                                    // tone rows per CTA
+    const ClusterLayout lay = cluster_layout(a.tw_count, ntc);
+    uint32_t* stage = reinterpret_cast<uint32_t*>(smem);
+    float2* const xb0 = reinterpret_cast<float2*>(smem + lay.xb);
+    float2* const xb1 = xb0 + XS;
+    float2* const E = xb1 + XS;
+    float2* tw = reinterpret_cast<float2*>(smem + lay.tw);
+    int32_t* sbins = reinterpret_cast<int32_t*>(smem + lay.bins);
+    float2* tile = reinterpret_cast<float2*>(smem + lay.tile);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + lay.bars);
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + kTmemStage);
+
+    const int tid = threadIdx.x, warp = tid >> 5, tf = tid;
+    const int rank = static_cast<int>(cluster_ctarank());
+    const int64_t cid = blockIdx.x / C;
+    // frames [ja, jb) of this cluster (the same for its C CTAs), whole tone
+    // groups of output frames as in the one-SM kernel
+    const int64_t shift = a.frame_offset & (kToneGroup - 1);
+    const int64_t ja = max_i64(0, cid * a.iters_per_cta - shift);
+    const int64_t jb = min_i64(a.F, (cid + 1) * a.iters_per_cta - shift);
+    if (ja >= jb) return;                                         // the whole cluster returns
+    const int64_t b0 = ja, b1 = jb + T - 1;
+    const int64_t need = (a.F + T - 1) * static_cast<int64_t>(N);
+    // this CTA's tone rows [t0, t1)
+    const int t0 = ntc > 0 ? min(a.n_tones, rank * ntc) : (a.n_tones * rank) / C;
+    const int t1 = ntc > 0 ? min(a.n_tones, t0 + ntc) : (a.n_tones * (rank + 1)) / C;
+
+    if (warp == 0) {
+        umma::alloc(tmem_holder, 512);
+        umma::relinquish();
+    }
+    if (tid == 0) {
+        for (int s = 0; s < kTmemStage; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    for (int i = tid; i < a.tw_count; i += blockDim.x) tw[i] = __ldg(a.tw + i);
+    // cross twiddles W_N^(rank p1), p1 = tf + 256 r, as W_N^(rank tf) (a
+    // register) times W_N^(rank 256 r) (16 values in shared memory)
+    float2* const xtw_r = tw + ((a.tw_count + 1) & ~1);
+    if (tid < 16) xtw_r[tid] = __ldg(a.tw + a.tw_count + rank * NB + tid * NT);
+    const float2 xtw_t = __ldg(a.tw + a.tw_count + rank * NB + tf);
+    if (ntc > 0)
+        for (int i = tid; i < t1 - t0; i += blockDim.x) sbins[i] = __ldg(a.bins + t0 + i);
+    float hr[T][16];
+#pragma unroll
+    for (int t = 0; t < T; ++t)
+#pragma unroll
+        for (int r = 0; r < 16; ++r) hr[t][r] = __ldg(a.h + t * N + rank * NB + tf + r * NT);
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    cluster_sync();                                               // every peer is running
+    const uint32_t tbase = *tmem_holder + (static_cast<uint32_t>(32 * (warp & 3)) << 16) +
+                           static_cast<uint32_t>(256 * (warp >> 2));
+    const bool tma = a.use_tma != 0;
+    if (tma && tid == 0)
+        for (int64_t b = b0; b < min_i64(b0 + kTmemStage, b1); ++b)
+            issue_sb_tma(a, b * C + rank, need, stage + (b % kTmemStage) * NB, &bars[b % kTmemStage]);
+
+    bool ok = true;
+    for (int64_t b = b0; b < b1; ++b) {
+        const int s = static_cast<int>(b % kTmemStage);
+        if (tma) {
+            if (ok && !mbar_wait(&bars[s], static_cast<uint32_t>(((b - b0) / kTmemStage) & 1), a.status)) ok = false;
+        } else {
+            copy_sb_threads(a, b * C + rank, need, stage + s * NB);
+            __syncthreads();
+        }
+        uint32_t xr[32];
+#pragma unroll
+        for (int r = 0; r < 16; r += 2) {
+            const float2 f0 = iq_to_f2(stage[s * NB + tf + r * NT]);
+            const float2 f1 = iq_to_f2(stage[s * NB + tf + (r + 1) * NT]);
+            xr[2 * r] = __float_as_uint(f0.x);
+            xr[2 * r + 1] = __float_as_uint(f1.x);
+            xr[2 * r + 2] = __float_as_uint(f0.y);
+            xr[2 * r + 3] = __float_as_uint(f1.y);
+        }
+        umma::st_32x32b_x32(tbase + 32u * static_cast<uint32_t>(b % kTmemSlots), xr);
+        umma::wait_st();
+        const int64_t j = b - (T - 1);
+        if (j < ja) {                                             // uniform across the cluster
+            __syncthreads();                                      // staging slot s fully read
+            if (tma && ok && tid == 0 && b + kTmemStage < b1)
+                issue_sb_tma(a, (b + kTmemStage) * C + rank, need, stage + s * NB, &bars[s]);
+            continue;
+        }
+        // FIR of this CTA's 4096 channels (taps t = 0..T-1 in order)
+        float are[16], aim[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) are[r] = aim[r] = 0.f;
+        uint32_t xa[16], xb[16];
+        umma::ld_32x32b_x16(tbase + 32u * static_cast<uint32_t>(j % kTmemSlots), xa);
+        umma::wait_ld_regs(xa);
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const uint32_t col = tbase + 32u * static_cast<uint32_t>((j + t) % kTmemSlots);
+            umma::ld_32x32b_x16(col + 16u, xb);
+#pragma unroll
+            for (int r = 0; r < 8; r += 2) {
+                ffma2(are[r], are[r + 1], hr[t][r], hr[t][r + 1], __uint_as_float(xa[2 * r]),
+                      __uint_as_float(xa[2 * r + 1]));
+                ffma2(aim[r], aim[r + 1], hr[t][r], hr[t][r + 1], __uint_as_float(xa[2 * r + 2]),
+                      __uint_as_float(xa[2 * r + 3]));
+            }
+            umma::wait_ld_regs(xb);
+            if (t + 1 < T)
+                umma::ld_32x32b_x16(tbase + 32u * static_cast<uint32_t>((j + t + 1) % kTmemSlots), xa);
+#pragma unroll
+            for (int r = 8; r < 16; r += 2) {
+                ffma2(are[r], are[r + 1], hr[t][r], hr[t][r + 1], __uint_as_float(xb[2 * r - 16]),
+                      __uint_as_float(xb[2 * r - 15]));
+                ffma2(aim[r], aim[r + 1], hr[t][r], hr[t][r + 1], __uint_as_float(xb[2 * r - 14]),
+                      __uint_as_float(xb[2 * r - 13]));
+            }
+            if (t + 1 < T) umma::wait_ld_regs(xa);
+        }
+#pragma unroll
+        for (int r = 0; r < 16; ++r) E[fpad(tf + r * NT)] = make_float2(are[r], aim[r]);
+        // the previous frame's row piece (in this frame's P) and tone tile
+        // have been read by their bulk stores before either is written again
+        if (tid == 0) bulk_wait_read_all();
+        cluster_sync();                                           // (S1) every slice in E; staging read
+        if (tma && ok && tid == 0 && b + kTmemStage < b1)
+            issue_sb_tma(a, (b + kTmemStage) * C + rank, need, stage + s * NB, &bars[s]);
+        // u[p1] = W_N^(rank p1) * sum_c W_C^(rank c) E_c[p1], p1 = tf + 256 r
+        // (the cross twiddles of k2 = rank follow the FFT twiddles in a.tw)
+        float2 v[16];
+        {
+            uint32_t e_at[C];                                     // E of each cluster CTA
+#pragma unroll
+            for (int c = 0; c < C; ++c) e_at[c] = dsmem_map(E, static_cast<uint32_t>(c)) + static_cast<uint32_t>(fpad(tf)) * 8u;
+            // remote loads issued in groups of 16 before their first use, so
+            // their latencies overlap
+            constexpr int RG = 16 / C;                            // points per group
+#pragma unroll
+            for (int r0 = 0; r0 < 16; r0 += RG) {
+                float2 e[RG][C];
+#pragma unroll
+                for (int rr = 0; rr < RG; ++rr)
+#pragma unroll
+                    for (int c = 0; c < C; ++c)
+                        e[rr][c] = dsmem_ld_f2(e_at[c] + static_cast<uint32_t>((r0 + rr) * (NT + NT / 16)) * 8u);
+#pragma unroll
+                for (int rr = 0; rr < RG; ++rr) {
+                    float2 acc = e[rr][0];
+#pragma unroll
+                    for (int c = 1; c < C; ++c) acc = cadd(acc, quarter_turn(e[rr][c], (rank * c * (4 / C)) & 3));
+                    v[r0 + rr] = rank == 0 ? acc : cmul(acc, cmul(xtw_t, xtw_r[r0 + rr]));
+                }
+            }
+        }
+        // 4096-point FFT of u, as the one-SM kernel: pass 0 -> P, 1 P -> Q, 2 Q -> registers
+        float2* const P = (j & 1) ? xb1 : xb0;
+        float2* const Q = (j & 1) ? xb0 : xb1;
+        dft16(v);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) P[fpad(16 * tf + r)] = v[r];
+        __syncthreads();                                          // (A)
+        {
+            const int k = tf & 15;
+#pragma unroll
+            for (int r = 0; r < 16; ++r) v[r] = P[fpad(tf + r * NT)];
+#pragma unroll
+            for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], tw[(r - 1) * 16 + k]);
+            dft16(v);
+            const int base = (tf >> 4) * 256 + k;
+#pragma unroll
+            for (int r = 0; r < 16; ++r) Q[fpad(base + r * 16)] = v[r];
+        }
+        __syncthreads();                                          // (B)
+        {
+#pragma unroll
+            for (int r = 0; r < 16; ++r) v[r] = Q[fpad(tf + r * NT)];
+#pragma unroll
+            for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], tw[240 + (r - 1) * 256 + tf]);
+            dft16(v);                                             // v[r] = Y_rank[k1], k1 = tf + 256 r
+        }
+#pragma unroll
+        for (int r = 0; r < 16; ++r) P[fpad(tf + r * NT)] = v[r];
+        cluster_sync();                                           // (S2) every Y_c in its P
+        // output bins k = 4096 rank + i, i = tf + 256 r: k2 = tf % C, k1 = k / C
+        const uint32_t p_k2 = dsmem_map(P, static_cast<uint32_t>(tf % C));
+        const bool bulk = a.full_bulk != 0;
+        if (a.full) {
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                const int k1 = (NB / C) * rank + (NT / C) * r + tf / C;
+                v[r] = dsmem_ld_f2(p_k2 + static_cast<uint32_t>(fpad(k1)) * 8u);
+            }
+            if (bulk) {
+#pragma unroll
+                for (int r = 0; r < 16; ++r) Q[tf + r * NT] = v[r];
+                fence_proxy_async_smem();
+            } else {
+                float2* row = a.full + (a.frame_offset + j) * a.full_ld + rank * NB;
+#pragma unroll
+                for (int r = 0; r < 16; ++r) row[tf + r * NT] = v[r];
+            }
+        }
+        // this CTA's tones t0 .. t1 - 1
+        const int q = static_cast<int>((a.frame_offset + j) & (kToneGroup - 1));
+        if (ntc > 0) {
+            float2 tv[kTonesPerThread];
+            int tb[kTonesPerThread];
+#pragma unroll
+            for (int k = 0; k < kTonesPerThread; ++k) {
+                const int i = tid + k * NT;
+                tb[k] = i < t1 - t0 ? sbins[i] : -1;
+            }
+#pragma unroll
+            for (int k = 0; k < kTonesPerThread; ++k)
+                if (tb[k] >= 0)
+                    tv[k] = dsmem_ld_f2(dsmem_map(P, static_cast<uint32_t>(tb[k] % C)) +
+                                        static_cast<uint32_t>(fpad(tb[k] / C)) * 8u);
+#pragma unroll
+            for (int k = 0; k < kTonesPerThread; ++k)
+                if (tb[k] >= 0) tile[(tid + k * NT) * kToneGroup + q] = tv[k];
+        } else {
+            float2* col = a.tones + a.frame_offset + j;
+            for (int t = t0 + tid; t < t1; t += NT) {
+                const int bin = __ldg(a.bins + t);
+                col[static_cast<int64_t>(t) * a.tones_ld] =
+                    dsmem_ld_f2(dsmem_map(P, static_cast<uint32_t>(bin % C)) + static_cast<uint32_t>(fpad(bin / C)) * 8u);
+            }
+        }
+        const bool group_end = ntc > 0 && t1 > t0 && (q == kToneGroup - 1 || j == jb - 1);
+        const bool gtma = group_end && a.tones_tma && q == kToneGroup - 1 && j - q >= ja;
+        if (gtma) fence_proxy_async_smem();
+        __syncthreads();                                          // (C) row piece and tile written
+        if (tid == 0) {
+            if (a.full && bulk)
+                tma_bulk_s2g(a.full + (a.frame_offset + j) * a.full_ld + rank * NB, Q, NB * 8);
+            if (gtma) {
+                const int32_t x0 = static_cast<int32_t>(a.frame_offset + j - q);
+                for (int r0 = 0; r0 < t1 - t0; r0 += kToneBox)
+                    tma_store_2d(&tm_tones, x0, t0 + r0, tile + static_cast<size_t>(r0) * kToneGroup);
+            }
+            bulk_commit();
+        }
+        if (group_end && !gtma) {
+            const int q0 = static_cast<int>(max_i64(0, ja - (j - q)));
+            const int nq = q + 1 - q0;
+            float2* base = a.tones + a.frame_offset + (j - q);
+            for (int it = tid; it < nq * (t1 - t0); it += NT) {
+                const int t = it / nq, qq = q0 + (it - t * nq);
+                base[static_cast<int64_t>(t0 + t) * a.tones_ld + qq] = tile[t * kToneGroup + qq];
+            }
+        }
+    }
+    if (tid == 0) bulk_wait_all();
+    umma::fence_before_sync();
+    __syncthreads();
+    cluster_sync();                                               // no peer reads this CTA's buffers any more
+    if (warp == 0) {
+        umma::fence_after_sync();
+        umma::dealloc(*tmem_holder, 512);
+    }
+}
+
 // -------------------------------------------------------------- DIRECT
 template <int LOG2N>
 __global__ void __launch_bounds__(1024, 1) pfb_direct_kernel(const PfbArgs a) {
@@ -983,6 +1315,71 @@ cudaError_t launch_tmem_sym(PfbArgs a, int n_sms, int max_smem, cudaStream_t st)
     return cudaGetLastError();
 }
 
+template <int C, int T>
+cudaError_t launch_cluster(PfbArgs a, int n_sms, int max_smem, cudaStream_t st) {
+    // tone rows per CTA: whole 256-row boxes, so no CTA's tone stores reach
+    // another CTA's rows
+    int ntc = 0;
+    if (a.n_tones > 0) {
+        ntc = ((a.n_tones + C - 1) / C + kToneBox - 1) / kToneBox * kToneBox;
+        if (ntc > kClusterTonesPerCta || cluster_layout(a.tw_count, ntc).total > static_cast<size_t>(max_smem)) ntc = 0;
+    }
+    a.nb_smem = ntc;
+    const size_t smem = cluster_layout(a.tw_count, ntc).total;
+    if (smem > static_cast<size_t>(max_smem)) return cudaErrorInvalidConfiguration;
+    auto k = pfb_cluster_kernel<C, T>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(kRingThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    static int max_clusters[2][2] = {{0, 0}, {0, 0}};             // [C == 4][T == 8], queried once
+    int& mc = max_clusters[C == 4 ? 1 : 0][T == 8 ? 1 : 0];
+    if (mc <= 0) {
+        cfg.gridDim = dim3(static_cast<unsigned>(C * (n_sms / C)), 1, 1);
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) != cudaSuccess || n <= 0) {
+            cudaGetLastError();
+            n = n_sms / C;
+        }
+        mc = n;
+    }
+    // whole tone groups of output frames per cluster, as the one-SM kernel
+    const int64_t shift = a.frame_offset & (kToneGroup - 1);
+    const int64_t ncl = std::max<int64_t>(1, std::min<int64_t>(a.F, mc));
+    a.iters_per_cta = ((a.F + shift + ncl - 1) / ncl + kToneGroup - 1) / kToneGroup * kToneGroup;
+    const int64_t ncl2 = (a.F + shift + a.iters_per_cta - 1) / a.iters_per_cta;
+    a.full_bulk = (a.full != nullptr && (reinterpret_cast<uintptr_t>(a.full) % 16) == 0 &&
+                   (a.full_ld % 2) == 0) ? 1 : 0;
+    CUtensorMap tm;
+    std::memset(&tm, 0, sizeof tm);
+    a.tones_tma = 0;
+    auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tmap_encode_tiled_fn());
+    if (ntc > 0 && enc && (reinterpret_cast<uintptr_t>(a.tones) % 16) == 0 && (a.tones_ld % 2) == 0 &&
+        a.frame_offset + a.F < (int64_t(1) << 31)) {
+        cuuint64_t dims[2] = {static_cast<cuuint64_t>(a.frame_offset + a.F), static_cast<cuuint64_t>(a.n_tones)};
+        cuuint64_t strides[1] = {static_cast<cuuint64_t>(a.tones_ld) * 8};
+        cuuint32_t box[2] = {kToneGroup, kToneBox};
+        cuuint32_t estr[2] = {1, 1};
+        if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, a.tones, dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+            a.tones_tma = 1;
+    }
+    cfg.gridDim = dim3(static_cast<unsigned>(C * ncl2), 1, 1);
+    e = cudaLaunchKernelEx(&cfg, k, a, tm);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
 template <int LOG2N>
 cudaError_t dispatch_ring_T(PfbArgs a, int tk, int n_sms, int max_smem, int la, cudaStream_t st) {
     switch (tk) {
@@ -995,8 +1392,9 @@ cudaError_t dispatch_ring_T(PfbArgs a, int tk, int n_sms, int max_smem, int la, 
 }  // namespace
 
 bool pfb_uses_ring(int log2n, int taps) { return log2n >= 4 && log2n <= 12 && taps <= 8; }
+int pfb_cluster_size(int log2n, int taps) { return (log2n == 13 || log2n == 14) && taps <= 8 ? 1 << (log2n - 12) : 0; }
 int pfb_kernel_taps(int log2n, int taps) {
-    if (pfb_uses_ring(log2n, taps)) return taps <= 4 ? 4 : 8;
+    if (pfb_uses_ring(log2n, taps) || pfb_cluster_size(log2n, taps) > 0) return taps <= 4 ? 4 : 8;
     return taps;
 }
 
@@ -1026,6 +1424,17 @@ cudaError_t pfb_launch(const PfbLaunch& L, cudaStream_t st) {
                          (reinterpret_cast<uintptr_t>(L.carry) % 16 == 0);
     a.use_tma = aligned ? 1 : 0;
     const int lg = L.log2n;
+    if (L.cluster && pfb_cluster_size(lg, L.taps_kernel) > 0) {
+        // N = 8192 or 16384, T <= 8 on the cluster kernel (when the plan
+        // chose it), aligned or not
+        if (a.tone_cs != 1 || a.rot != 0 || !L.tw_cl) return cudaErrorInvalidValue;
+        a.tw = reinterpret_cast<const float2*>(L.tw_cl);
+        a.tw_count = L.tw_cl_count;
+        if (lg == 13) return L.taps_kernel == 4 ? launch_cluster<2, 4>(a, L.n_sms, L.max_smem, st)
+                                                : launch_cluster<2, 8>(a, L.n_sms, L.max_smem, st);
+        return L.taps_kernel == 4 ? launch_cluster<4, 4>(a, L.n_sms, L.max_smem, st)
+                                  : launch_cluster<4, 8>(a, L.n_sms, L.max_smem, st);
+    }
     if (a.tone_cs != 1 || a.rot != 0) {
         // phase passes of an oversampled plan: only the symmetric-tap kernel has them
         if (lg != 12 || !a.use_tma || L.taps_kernel != 8 || !L.sym_taps) return cudaErrorInvalidValue;

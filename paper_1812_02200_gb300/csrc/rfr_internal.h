@@ -52,6 +52,9 @@ struct PfbLaunch {
     int rot;            // bin c multiplied by (-i)^((c * rot) mod 4) (phase passes)
     int hop;            // samples between frames (N: critically sampled)
     int64_t a0;         // absolute sample index of the virtual stream's first sample
+    int cluster;        // N = 8192, 16384 (T <= 8): the cluster kernel instead of the direct one
+    const void* tw_cl;  // its twiddles: the 4096-point FFT's, then W_N^(k2 p1)
+    int tw_cl_count;    // entries of the 4096-point FFT part
 };
 bool pfb_uses_ring(int log2n, int taps);
 // cuTensorMapEncodeTiled (PFN_cuTensorMapEncodeTiled_v12000) or nullptr
@@ -99,6 +102,8 @@ cudaError_t gen_plan_reserve(GenPlan* g, int64_t frames);
 cudaError_t gen_plan_set_tones(GenPlan* g, const int32_t* bins, int n_tones);
 void gen_plan_free(GenPlan* g);
 int pfb_kernel_taps(int log2n, int taps);
+// CTAs per cluster of the cluster PFB kernel (N = 8192, 16384 with T <= 8), else 0.
+int pfb_cluster_size(int log2n, int taps);
 cudaError_t pfb_launch(const PfbLaunch& L, cudaStream_t st);
 cudaError_t gen_pfb_launch(const PfbLaunch& L, const GenPlan& g, cudaStream_t st);
 
@@ -208,6 +213,7 @@ struct TuneConfig {
     int demod_bt = 128;         // three-product GEMM: tones per tile (128 or 64)
     int demod_fused = 0;        // three-product GEMM: pre-split fused into its producers (0/1)
     int demod_pair = 0;         // three-product GEMM: two-CTA clusters sharing A tiles (0/1)
+    int pfb_cluster = 0;        // PFB N = 8192, 16384 with T <= 8: cluster kernel (1) or direct (0)
     bool tuned = false;
 };
 
@@ -241,6 +247,8 @@ struct rfr_plan {
     // device tables
     float* d_h = nullptr;          // PFB kernel taps [Tk*N] (zero-padded oldest taps)
     void* d_tw = nullptr;          // FFT twiddles
+    void* d_tw_cl = nullptr;       // cluster PFB kernel's twiddles (N = 8192, 16384 with T <= 8)
+    int tw_cl_count = 0;
     int tw_count = 0;
     int32_t* d_bins = nullptr;
     uint64_t* d_words = nullptr;

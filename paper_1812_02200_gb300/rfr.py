@@ -121,6 +121,8 @@ _SIGS = {
     "rfr_plan_get_fused_presplit": (C.c_int, [_P, C.POINTER(C.c_int32)]),
     "rfr_plan_set_demod_pair": (C.c_int, [_P, C.c_int32]),
     "rfr_plan_get_demod_pair": (C.c_int, [_P, C.POINTER(C.c_int32)]),
+    "rfr_plan_set_pfb_cluster": (C.c_int, [_P, C.c_int32]),
+    "rfr_plan_get_pfb_cluster": (C.c_int, [_P, C.POINTER(C.c_int32)]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -372,6 +374,11 @@ class Plan:
         (False, the default); result-neutral, normally chosen by autotune()."""
         self._check(_lib.rfr_plan_set_demod_pair(self._h, 1 if on else 0), "set_demod_pair")
 
+    def set_pfb_cluster(self, on: bool):
+        """PFB N = 8192 or 16384 with T <= 8: the cluster kernel (True) or the
+        direct kernel (False, the default); set before the first push."""
+        self._check(_lib.rfr_plan_set_pfb_cluster(self._h, 1 if on else 0), "set_pfb_cluster")
+
     def inject_device_status(self, status: int):
         """Write the plan's device status word as a timed-out kernel would
         (1), or clear it (0): host-side failure injection for tests."""
@@ -386,12 +393,13 @@ class Plan:
     def tune(self) -> dict:
         a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
         self._check(_lib.rfr_plan_get_tune(self._h, C.byref(a), C.byref(b), C.byref(c)), "tune")
-        t, f, pr = C.c_int32(), C.c_int32(), C.c_int32()
+        t, f, pr, cl = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
         self._check(_lib.rfr_plan_get_tone_tile(self._h, C.byref(t)), "tone tile")
         self._check(_lib.rfr_plan_get_fused_presplit(self._h, C.byref(f)), "fused pre-split")
         self._check(_lib.rfr_plan_get_demod_pair(self._h, C.byref(pr)), "pair")
+        self._check(_lib.rfr_plan_get_pfb_cluster(self._h, C.byref(cl)), "cluster")
         return {"pfb_lookahead": a.value, "demod_raster": b.value, "tone_tile": t.value,
-                "fused_presplit": f.value, "pair": pr.value, "tuned": bool(c.value)}
+                "fused_presplit": f.value, "pair": pr.value, "pfb_cluster": cl.value, "tuned": bool(c.value)}
 
     def state_export(self) -> bytes:
         n = C.c_size_t()

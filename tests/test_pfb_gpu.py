@@ -77,7 +77,8 @@ CASES = [
     (4096, 12, "kaiser", 9.0, 60),    # DIRECT variant (T > 8)
     (1024, 16, "hann", 0.0, 80),      # DIRECT variant
     (8192, 4, "hann", 0.0, 40),       # DIRECT variant (N > 4096)
-    (16384, 2, "kaiser", 9.0, 30),    # DIRECT variant, largest N
+    (16384, 2, "kaiser", 9.0, 30),    # DIRECT variant, taps padded to 4
+    (16384, 12, "kaiser", 9.0, 20),   # DIRECT variant, largest N, T > 8
 ]
 
 
@@ -101,17 +102,23 @@ def test_pfb_parity_shapes(lib, N, T, win, beta, frames):
     assert fe["strict_tone_max"] < TOL and fe["strict_noise_max"] < STRICT_NOISE_BOUND
 
 
-@pytest.mark.parametrize("N,T", [(64, 4), (4096, 8), (1024, 16)])
-def test_streamed_equals_one_shot_bit_exact(lib, N, T):
+@pytest.mark.parametrize("N,T,cluster", [(64, 4, 0), (4096, 8, 0), (1024, 16, 0), (8192, 8, 0), (16384, 3, 0),
+                                         (8192, 8, 1), (16384, 3, 1)])
+def test_streamed_equals_one_shot_bit_exact(lib, N, T, cluster):
     """Random splits (aligned and odd sizes, some shorter than a frame) give
-    bit-identical frames to one push of the whole stream."""
+    bit-identical frames to one push of the whole stream (for N = 8192 and
+    16384 on the direct and on the cluster kernel)."""
     rng = np.random.default_rng(N + T)
     frames = 120 if N <= 1024 else 60
     case = siggen.pfb_case(N * frames + 5, N, 8, seed=77 + N)
     x = torch.from_numpy(case["x"]).to(DEV)
     one = _plan(lib, N, T, "hann", 0.0, case["words"])
-    f1, t1 = _run_gpu(one, case["x"], 8, N)
     st = _plan(lib, N, T, "hann", 0.0, case["words"])
+    if cluster:
+        one.set_pfb_cluster(True)
+        st.set_pfb_cluster(True)
+        assert st.tune()["pfb_cluster"] == 1
+    f1, t1 = _run_gpu(one, case["x"], 8, N)
     F = f1.shape[0]
     fo = torch.zeros((F, N), dtype=torch.complex64, device=DEV)
     to = torch.zeros((8, F), dtype=torch.complex64, device=DEV)
@@ -323,3 +330,95 @@ def test_many_tones_and_offsets(lib, n_tones, frame_offset):
     assert rel_rows(got_t, ref["tones"]).max() < TOL
     assert np.array_equal(got_t, fo[frame_offset:].cpu().numpy()[:, plan.bins()].T)
     assert not to[:, :frame_offset].abs().any() and not to[:, frame_offset + F:].abs().any()
+
+
+# N, T, window, beta, frames, tones, outputs (full, tones)
+CLUSTER_CASES = [
+    (16384, 8, "kaiser", 9.0, 24, 1000, (True, True)),    # the batched workload's largest plan
+    (16384, 4, "hann", 0.0, 30, 100, (True, True)),       # tones on the first CTA only
+    (8192, 8, "blackman", 0.0, 40, 700, (True, True)),    # two tone boxes per CTA
+    (8192, 5, "hamming", 0.0, 37, 3000, (False, True)),   # 1536 tone rows per CTA: per-frame tone stores
+    (16384, 7, "kaiser", 9.0, 21, 3000, (True, False)),   # full spectrum only
+]
+
+
+@pytest.mark.parametrize("N,T,win,beta,frames,nt,outs", CLUSTER_CASES)
+def test_cluster_pfb_parity(lib, N, T, win, beta, frames, nt, outs):
+    """N = 8192 and 16384 with T <= 8 on the cluster kernel (clusters of
+    N / 4096 CTAs that split the channels, exchange the filtered slices for
+    the cross-CTA step of the FFT and assemble the output rows through
+    distributed shared memory): full spectrum and tones against the oracle,
+    with ragged input (a residue that makes no frame); the direct kernel's
+    frames agree with them to FP32 rounding."""
+    full_on, tones_on = outs
+    case = siggen.pfb_case(N * frames + N // 5 + 3, N, nt, seed=8800 + N + T + nt,
+                           amp=(200.0, 1500.0), sigma=8.0)
+    plan = _plan(lib, N, T, win, beta, case["words"], full=full_on, tones=tones_on)
+    assert plan.tune()["pfb_cluster"] == 0
+    plan.set_pfb_cluster(True)
+    full, tones = _run_gpu(plan, case["x"], nt if tones_on else 0, N, full=full_on)
+    direct = _plan(lib, N, T, win, beta, case["words"], full=full_on, tones=tones_on)
+    dfull, dtones = _run_gpu(direct, case["x"], nt if tones_on else 0, N, full=full_on)
+    if tones_on:
+        assert rel_rows(tones, dtones).max() < 1e-5
+    if full_on:
+        assert rel_channels_vs_rms(full, dfull).max() < 1e-5
+    ref = oracle.pfb(case["x"], N, T, _oracle_taps(N, T, win, beta), bins=plan.bins())
+    msg = f"cluster N={N} T={T} tones={nt}:"
+    if tones_on:
+        assert np.isfinite(tones).all()
+        e_t = rel_rows(tones, ref["tones"])
+        msg += f" tones {e_t.max():.3e}"
+        assert e_t.max() < TOL, e_t.max()
+    if full_on:
+        assert full.shape[0] == frames and np.isfinite(full).all()
+        e_f = rel_channels_vs_rms(full, ref["full"])
+        fe = full_spectrum_errors(full, ref["full"], plan.bins())
+        msg += (f", full (max(own, RMS)) {e_f.max():.3e}, strict tone channels {fe['strict_tone_max']:.3e}, "
+                f"strict noise-only {fe['strict_noise_max']:.3e}")
+        assert e_f.max() < TOL, e_f.max()
+        assert fe["strict_tone_max"] < TOL and fe["strict_noise_max"] < STRICT_NOISE_BOUND
+    print(msg)
+
+
+def test_cluster_pfb_frame_offsets_and_partial_tone_groups(lib):
+    """Cluster kernel: pushes that start at output frame offsets that are not multiples of
+    the 4-frame tone group (partial groups leave by plain stores), into
+    output buffers with a row pitch larger than N: the same frames as one
+    push into a tight buffer."""
+    N, T, nt = 16384, 8, 600
+    case = siggen.pfb_case(N * 45, N, nt, seed=8901)
+    x = torch.from_numpy(case["x"]).to(DEV)
+    one = _plan(lib, N, T, "kaiser", 9.0, case["words"])
+    one.set_pfb_cluster(True)
+    f1, t1 = _run_gpu(one, case["x"], nt, N)
+    F = f1.shape[0]
+    st = _plan(lib, N, T, "kaiser", 9.0, case["words"])
+    st.set_pfb_cluster(True)
+    fo = torch.zeros((F + 3, N + 8), dtype=torch.complex64, device=DEV)
+    to = torch.zeros((nt, F + 5), dtype=torch.complex64, device=DEV)
+    off = 1
+    for a, b in [(0, N * 9), (N * 9, N * 22 + 100), (N * 22 + 100, N * 45)]:
+        off += st.push_into(x[a:b], fo, to, frame_offset=off)
+    torch.cuda.synchronize()
+    assert off == F + 1
+    assert np.array_equal(fo.cpu().numpy()[1:F + 1, :N], f1)
+    assert np.array_equal(to.cpu().numpy()[:, 1:F + 1], t1)
+
+
+def test_cluster_pfb_choice_is_validated(lib):
+    words = np.array([1 << 58], np.uint64)
+    p = lib.Plan(4096, 8, window="hann", words=words)
+    with pytest.raises(lib.RfrError):
+        p.set_pfb_cluster(True)                 # one SM holds N = 4096, T = 8
+    assert p.tune()["pfb_cluster"] == 0
+    q = lib.Plan(16384, 16, window="hann", words=words)
+    with pytest.raises(lib.RfrError):
+        q.set_pfb_cluster(True)                 # T > 8: direct kernel only
+    r = lib.Plan(8192, 8, window="hann", words=words)
+    r.set_pfb_cluster(True)
+    assert r.tune()["pfb_cluster"] == 1
+    r.set_pfb_cluster(False)
+    assert r.tune()["pfb_cluster"] == 0
+    for x in (p, q, r):
+        x.close()
