@@ -305,21 +305,23 @@ rfr_status rfr_state_import(rfr_plan* plan, const void* host, size_t bytes);
  * differently), which needs D % 64 == 0 (RFR_E_UNSUPPORTED otherwise) and
  * builds its tap planes on the first switch (allocates, synchronises the
  * device).  Either switch resets the accumulation chunk to the form's
- * default (2 blocks: 64 taps in the four-product form, 128 in the three-
- * product form, which reaches the same accuracy).  Set it before the first
- * push of a stream.
+ * default (64 taps in the four-product form, 256 in the three-product
+ * form).  Set it before the first push of a stream.
  */
 rfr_status rfr_plan_set_demod_products(rfr_plan* plan, int32_t products);
 
 /*
  * rfr_plan_set_accum_chunk -- demodulation only: how many K blocks (32 taps
  * each in the four-product form, 64 in the three-product form; 1..64,
- * default 2) the tensor cores accumulate in TMEM before the epilogue
- * adds the partial sums into FP32 registers.  Longer chunks are slightly
- * faster and less accurate (the tensor cores' internal accumulation error
- * grows with the partial sums); the default keeps the weakest tones of the
- * 2048-tone workload near 2e-6 relative error.  Changes the results' rounding,
- * so set it before the first push.
+ * default 2 in the four-product form, 4 in the three-product form) the
+ * tensor cores accumulate in TMEM before the epilogue adds the partial sums
+ * into FP32 registers.  Longer chunks are faster (fewer TMEM reads by the
+ * epilogue, which compete with the MMAs) and less accurate (the tensor
+ * cores' internal accumulation error grows with the partial sums): on the
+ * weakest tones of the 2048-tone workload, 1.2e-6 / 1.9e-6 / 3.7e-6
+ * relative error at 2 / 4 / 8 blocks of the three-product form, which runs
+ * 16.7 / 18.2 / 19.1 Gs/s there.  Changes the results' rounding, so set it
+ * before the first push.
  */
 rfr_status rfr_plan_set_accum_chunk(rfr_plan* plan, int32_t k_blocks);
 

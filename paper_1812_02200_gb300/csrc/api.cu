@@ -1050,7 +1050,7 @@ rfr_status rfr_plan_set_demod_products(rfr_plan* p, int32_t products) {
         }
     }
     p->demod_products = 3;
-    p->accum_chunk = 2;
+    p->accum_chunk = 4;                // 256 taps per TMEM chunk
     return RFR_OK;
 }
 
