@@ -151,6 +151,34 @@ struct rfr_server {
 
 namespace {
 
+// Rows of row_bytes (a multiple of 8) from device memory src (pitch
+// src_pitch) to dst (pitch dst_pitch), 8 bytes per thread and step: dst may
+// be the device address of mapped pinned host memory, which the kernel
+// writes directly.  The tone rows of one request are as short as its frame
+// count (1-32 KB for the workload's buffers), and a 2-D copy-engine transfer
+// of rows that short runs far below the host link's rate.
+__global__ void copy_rows_kernel(char* __restrict__ dst, int64_t dst_pitch, const char* __restrict__ src,
+                                 int64_t src_pitch, int64_t row_bytes, int64_t rows) {
+    const int64_t words = row_bytes / 8;
+    const int64_t total = words * rows;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t r = i / words, c = i - r * words;
+        reinterpret_cast<uint64_t*>(dst + r * dst_pitch)[c] = reinterpret_cast<const uint64_t*>(src + r * src_pitch)[c];
+    }
+}
+
+// Device address of pinned host memory, or nullptr (pageable, or device memory).
+void* mapped_host(const void* p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+    return a.devicePointer;
+}
+
 bool host_pointer(const void* p) {
     cudaPointerAttributes a{};
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -234,9 +262,22 @@ void worker_loop(rfr_server* s) {
                     cudaMemcpy2DAsync(static_cast<char*>(o.full) + o.frame_offset * o.full_ld * 8, o.full_ld * 8,
                                       so.full, static_cast<size_t>(p->N) * 8, static_cast<size_t>(p->N) * 8, got,
                                       cudaMemcpyDefault, st);
-                if (want_tones)
-                    cudaMemcpy2DAsync(static_cast<char*>(o.tones) + o.frame_offset * 8, o.tones_ld * 8, so.tones,
-                                      so.tones_ld * 8, got * 8, nt, cudaMemcpyDefault, st);
+                if (want_tones) {
+                    char* dst = static_cast<char*>(o.tones) + o.frame_offset * 8;
+                    char* dmap = static_cast<char*>(mapped_host(o.tones));
+                    if (dmap) {
+                        // pinned host rows written by a kernel through the mapping
+                        const int64_t total = got * nt;
+                        const unsigned grid = static_cast<unsigned>(
+                            std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, static_cast<int64_t>(p->n_sms) * 8)));
+                        copy_rows_kernel<<<grid, 256, 0, st>>>(dmap + o.frame_offset * 8, o.tones_ld * 8,
+                                                               static_cast<const char*>(so.tones), so.tones_ld * 8,
+                                                               got * 8, nt);
+                    } else {
+                        cudaMemcpy2DAsync(dst, o.tones_ld * 8, so.tones, so.tones_ld * 8, got * 8, nt,
+                                          cudaMemcpyDefault, st);
+                    }
+                }
             }
             if (rs != RFR_OK) {
                 s->error = rs;
