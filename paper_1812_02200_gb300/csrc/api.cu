@@ -74,6 +74,30 @@ std::vector<float> make_twiddles(int log2n) {
     return t;
 }
 
+// ------------------------------------------------- phase-pass tone rows
+// Output frame f = R m + k of tone t comes from column m of pass k's dense
+// row.  Grid rows are tones; a thread takes column m of the R pass rows
+// (coalesced loads across the warp) and writes output frames R m .. R m + R - 1.
+__global__ void interleave_tones_kernel(const float2* __restrict__ src, int64_t src_ld, int R, int n_tones,
+                                        int64_t F, float2* __restrict__ out, int64_t ld) {
+    const int64_t M = (F + R - 1) / R;
+    const int64_t pass = static_cast<int64_t>(n_tones) * src_ld;
+    for (int t = blockIdx.y; t < n_tones; t += gridDim.y) {
+        const float2* s = src + static_cast<int64_t>(t) * src_ld;
+        float2* o = out + static_cast<int64_t>(t) * ld;
+        for (int64_t m = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; m < M;
+             m += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+            float2 v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (k < R) v[k] = s[k * pass + m];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (k < R && m * R + k < F) o[m * R + k] = v[k];
+        }
+    }
+}
+
 // -------------------------------------------------------------- carry copy
 __global__ void carry_update_kernel(const uint32_t* __restrict__ old_carry, int64_t cl,
                                     const uint32_t* __restrict__ buf, int64_t from, int64_t count,
@@ -206,6 +230,28 @@ rfr_status ensure_demod_scratch(rfr_plan* p, int64_t F, int64_t F0, cudaStream_t
 // (R = 2): an exact swap/negation of each bin, applied by the kernel.  A
 // push that is not 16-byte aligned (or whose carry is not a multiple of 4
 // samples) first copies [carry | buffer] into one aligned scratch view.
+// Rows for the tones of every phase pass of a push of F frames: R x tones
+// rows of ceil(F / R) frames, rounded up to an even count (the tone tile's
+// TMA stores need 16-byte row pitches).  Grows outside stream capture only.
+cudaError_t ensure_pass_tones(rfr_plan* p, int64_t F, cudaStream_t st) {
+    const int nt = static_cast<int>(p->words.size());
+    if (nt == 0 || !(p->out_flags & RFR_OUT_TONES)) return cudaSuccess;
+    const int64_t need = ((F + p->phase_R - 1) / p->phase_R + 1) & ~int64_t(1);
+    if (need <= p->ptones_cap) return cudaSuccess;
+    if (st) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(st, &cs);
+        if (cs != cudaStreamCaptureStatusNone) return cudaErrorStreamCaptureUnsupported;
+    }
+    cudaDeviceSynchronize();
+    dev_free(p->d_ptones);
+    p->d_ptones = nullptr;
+    p->ptones_cap = 0;
+    const cudaError_t e = dev_alloc(&p->d_ptones, static_cast<size_t>(p->phase_R) * nt * need * 8);
+    if (e == cudaSuccess) p->ptones_cap = need;
+    return e;
+}
+
 rfr_status phase_passes(rfr_plan* p, const rfr::PfbLaunch& L0, const rfr_output* o, int64_t lv, int64_t F,
                         cudaStream_t st) {
     const int R = p->phase_R;
@@ -231,6 +277,17 @@ rfr_status phase_passes(rfr_plan* p, const rfr::PfbLaunch& L0, const rfr_output*
         vbuf = p->d_view;
         vcl = 0;
     }
+    // each pass writes its tones as dense rows [k][tone][i] through the tone
+    // tile's TMA stores; one kernel then interleaves them into [tone][frame]
+    // (written at a column stride of R, each 32-byte sector of a tone row
+    // would be filled by R launches, partially each time)
+    const int nt = static_cast<int>(p->words.size());
+    if (L0.tones) {
+        const cudaError_t e = ensure_pass_tones(p, F, st);
+        if (e == cudaErrorStreamCaptureUnsupported)
+            return fail(p, RFR_E_INVALID, "push inside stream capture would grow the plan's scratch; push that size once before capturing");
+        RFR_CUDA(p, e);
+    }
     for (int k = 0; k < R; ++k) {
         const int64_t Fk = (F - k + R - 1) / R;           // frames R*i + k < F
         if (Fk <= 0) continue;
@@ -254,8 +311,9 @@ rfr_status phase_passes(rfr_plan* p, const rfr::PfbLaunch& L0, const rfr_output*
             L.full_ld = R * o->full_ld;
         }
         if (L0.tones) {
-            L.tones = static_cast<float2*>(L0.tones) + o->frame_offset + k;
-            L.tone_cs = R;
+            L.tones = static_cast<float2*>(p->d_ptones) + static_cast<int64_t>(k) * nt * p->ptones_cap;
+            L.tones_ld = p->ptones_cap;
+            L.tone_cs = 1;
         }
         const int64_t s = ((L0.a0 + off) % N + N) % N;     // a multiple of H
         const int m = static_cast<int>(s / H);
@@ -263,6 +321,9 @@ rfr_status phase_passes(rfr_plan* p, const rfr::PfbLaunch& L0, const rfr_output*
         L.a0 = L0.a0 + off;
         RFR_CUDA(p, rfr::pfb_launch(L, st));
     }
+    if (L0.tones)
+        RFR_CUDA(p, rfr::interleave_tones(p->d_ptones, p->ptones_cap, R, nt, F,
+                                          static_cast<float2*>(L0.tones) + o->frame_offset, o->tones_ld, st));
     return RFR_OK;
 }
 
@@ -294,6 +355,7 @@ rfr_status ensure_scratch(rfr_plan* p, int64_t n) {
             RFR_CUDA(p, dev_alloc(&p->d_view, static_cast<size_t>(lv) * 4));
             p->view_cap = lv;
         }
+        RFR_CUDA(p, ensure_pass_tones(p, F, nullptr));
     }
     if (p->mode == RFR_MODE_DEMOD && F > 0 && !p->words.empty()) return ensure_demod_scratch(p, F, -1, nullptr);
     return RFR_OK;
@@ -466,7 +528,7 @@ void destroy(rfr_plan* p) {
                     static_cast<void*>(p->d_words), static_cast<void*>(p->d_rates), static_cast<void*>(p->d_h32), p->d_c32, p->d_bhi, p->d_blo,
                     static_cast<void*>(p->d_status), static_cast<void*>(p->d_carry[0]),
                     static_cast<void*>(p->d_carry[1]), p->d_xs_hi, p->d_xs_lo, p->d_rot, p->d_qfull, p->d_b3, p->d_xs3,
-                    p->d_qtones, static_cast<void*>(p->d_view)})
+                    p->d_qtones, static_cast<void*>(p->d_view), p->d_ptones})
         dev_free(q);
     for (int i = 0; i < rfr_plan::kStageBufs; ++i) {
         dev_free(p->d_stage_in[i]);
@@ -496,6 +558,18 @@ cudaError_t carry_update(const int16_t* old_carry, int64_t cl, const int16_t* bu
     carry_update_kernel<<<static_cast<unsigned>(blocks), threads, 0, st>>>(
         reinterpret_cast<const uint32_t*>(old_carry), cl, reinterpret_cast<const uint32_t*>(buf),
         from, count, reinterpret_cast<uint32_t*>(new_carry));
+    return cudaGetLastError();
+}
+
+cudaError_t interleave_tones(const void* src, int64_t src_ld, int R, int n_tones, int64_t F, void* out,
+                             int64_t ld, cudaStream_t st) {
+    if (F <= 0 || n_tones <= 0) return cudaSuccess;
+    if (R < 1 || R > 4) return cudaErrorInvalidValue;
+    const int64_t M = (F + R - 1) / R;
+    const dim3 grid(static_cast<unsigned>(std::min<int64_t>((M + 255) / 256, 65535)),
+                    static_cast<unsigned>(std::min(n_tones, 65535)));
+    interleave_tones_kernel<<<grid, 256, 0, st>>>(static_cast<const float2*>(src), src_ld, R, n_tones, F,
+                                                  static_cast<float2*>(out), ld);
     return cudaGetLastError();
 }
 }  // namespace rfr

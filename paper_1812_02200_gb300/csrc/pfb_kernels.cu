@@ -781,12 +781,19 @@ __global__ void __launch_bounds__(kRingThreads, 1)
             dft16(v);                                            // v[r] = bin tf + 256 r
         }
         if (PHASE && a.rot) {
-            // (-i)^((c * rot) mod 4) for c = tf + 256 r: the same power for all r (exact)
+            // (-i)^e, e = (c * rot) mod 4 for c = tf + 256 r: the same power for
+            // all r, and it differs between the lanes of a warp, so it is applied
+            // without branches: odd e swaps re and im, then sign bits are flipped
+            // (e = 1: (im, -re); 2: (-re, -im); 3: (-im, re)); exact
             const int e = (tf * a.rot) & 3;
+            const bool sw = (e & 1) != 0;
+            const uint32_t m_re = (e == 2 || e == 3) ? 0x80000000u : 0u;
+            const uint32_t m_im = (e == 1 || e == 2) ? 0x80000000u : 0u;
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
                 const float2 u = v[i];
-                v[i] = e == 1 ? make_float2(u.y, -u.x) : e == 2 ? make_float2(-u.x, -u.y) : e == 3 ? make_float2(-u.y, u.x) : u;
+                const float re = sw ? u.y : u.x, im = sw ? u.x : u.y;
+                v[i] = make_float2(__uint_as_float(__float_as_uint(re) ^ m_re), __uint_as_float(__float_as_uint(im) ^ m_im));
             }
         }
         if (a.full && !bulk) {

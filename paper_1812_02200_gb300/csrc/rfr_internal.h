@@ -220,6 +220,10 @@ struct TuneConfig {
 // ------------------------------------------------------------- state
 cudaError_t carry_update(const int16_t* old_carry, int64_t cl, const int16_t* buf, int64_t n,
                          int64_t from, int64_t count, int16_t* new_carry, cudaStream_t st);
+// out[t * ld + R m + k] = src[(k * n_tones + t) * src_ld + m] for R m + k < F:
+// the R phase passes' tone rows interleaved into [tone][frame].
+cudaError_t interleave_tones(const void* src, int64_t src_ld, int R, int n_tones, int64_t F, void* out,
+                             int64_t ld, cudaStream_t st);
 
 }  // namespace rfr
 
@@ -232,6 +236,8 @@ struct rfr_plan {
                                                // phase_R critically sampled passes (see push_core)
     int16_t* d_view = nullptr;                 // phase passes: contiguous copy of [carry | buffer]
     int64_t view_cap = 0;                      //   when the push is not 16-byte aligned (samples)
+    void* d_ptones = nullptr;                  // phase passes: each pass's tones [pass][tone][frame]
+    int64_t ptones_cap = 0;                    //   frames per pass row
     bool gen = false;                          // PFB through the any-N kernels
     rfr::GenPlan gplan;
     int32_t L = 0, D = 0, Lpad = 0;            // demod

@@ -288,3 +288,24 @@ def test_oversampled_4096_phase_passes(lib, hop):
     assert ft is None and np.array_equal(tt, tones)
     fonly, _ = _run(mk(tones=False), case["x"], 0, N)
     assert np.array_equal(fonly, full)
+
+
+def test_oversampled_phase_passes_many_tones(lib):
+    """Hop N/2 with 1500 tones (more than the fused kernel's tone tile holds:
+    each pass stores its tones per frame into its dense rows), pushed at an
+    odd output frame offset: the tones equal the full spectrum's bin columns
+    and the oracle."""
+    N, T, hop, nt = 4096, 8, 2048, 1500
+    case = siggen.pfb_case(hop * 70 + N * T + 5, N, nt, seed=8123, amp=(200.0, 1500.0))
+    plan = lib.Plan(N, T, window="kaiser", beta=9.0, words=case["words"], decimation=hop, full=True, tones=True)
+    x = torch.from_numpy(case["x"]).to(DEV)
+    F = plan.frames_for(x.shape[0])
+    fo = torch.zeros((F + 3, N), dtype=torch.complex64, device=DEV)
+    to = torch.zeros((nt, F + 3), dtype=torch.complex64, device=DEV)
+    assert plan.push_into(x, fo, to, frame_offset=3) == F
+    torch.cuda.synchronize()
+    full, tones = fo.cpu().numpy()[3:], to.cpu().numpy()[:, 3:]
+    assert np.array_equal(tones, full[:, plan.bins()].T)
+    sel = np.linspace(0, nt - 1, 12).astype(int)
+    ref = oracle.pfb_hop(case["x"], N, T, hop, _taps(N, T, "kaiser", 9.0), k_end=F, bins=plan.bins()[sel])
+    assert rel_rows(tones[sel], ref["tones"]).max() < TOL
