@@ -30,7 +30,7 @@ def _origin(base, hop, k):
 
 @pytest.mark.parametrize("base", ORIGIN_BASES)
 @pytest.mark.parametrize("L,D,nt,products", [(1024, 512, 48, 3), (1024, 512, 48, 4), (256, 512, 20, 3),
-                                             (4096, 2048, 64, 3)])
+                                             (4096, 2048, 64, 3), (1024, 512, 300, "3-cluster")])
 def test_demod_far_origin_matches_oracle(lib, base, L, D, nt, products):
     S = _origin(base, D, 3)
     halo = max(L - D, 0)
@@ -39,6 +39,8 @@ def test_demod_far_origin_matches_oracle(lib, base, L, D, nt, products):
     plan = lib.Plan(0, L, window="blackman", cutoff=1e-3, words=c["words"], decimation=D)
     if products == 4:
         plan.set_demod_products(4)
+    elif products == "3-cluster":
+        plan.set_demod_pair(True)                       # two-CTA clusters, three tone tiles
     x = torch.from_numpy(c["x"]).to(DEV)
     plan.seek(S, x[:halo] if halo else None)
     info = plan.info()
@@ -147,3 +149,32 @@ def test_tx_far_origin_matches_oracle(lib, base):
     amb = ~unique
     assert ((got[amb] == np.floor(v[amb])) | (got[amb] == np.ceil(v[amb]))).all()
     tx.close()
+
+
+@pytest.mark.parametrize("base", [2 ** 40, 2 ** 62])
+def test_cluster_pfb_far_origin_matches_oracle(lib, base):
+    """N = 16384, T = 8 on the cluster kernel, seeked past 2^40 and 2^62 with
+    its history: frames against the oracle at the same absolute origin."""
+    N, T, nt = 16384, 8, 40
+    S = _origin(base, N, 2)
+    halo = (T - 1) * N
+    n_push = N * 12 + 321
+    c = siggen.pfb_case(halo + n_push, N, nt, seed=base % 983, amp=(200.0, 1500.0))
+    plan = lib.Plan(N, T, window="kaiser", beta=9.0, words=c["words"])
+    plan.set_pfb_cluster(True)
+    x = torch.from_numpy(c["x"]).to(DEV)
+    plan.seek(S, x[:halo])
+    F = plan.frames_for(n_push)
+    full = torch.zeros((F, N), dtype=torch.complex64, device=DEV)
+    tones = torch.zeros((nt, F), dtype=torch.complex64, device=DEV)
+    assert plan.push_into(x[halo:], full, tones) == F
+    torch.cuda.synchronize()
+    _, h32 = oracle.pfb_prototype(N, T, "kaiser", 9.0)
+    K0 = S // N
+    ref = oracle.pfb_hop(c["x"], N, T, N, h32.astype(np.float64), k_begin=K0, k_end=K0 + F,
+                         bins=plan.bins(), m0=S - halo)
+    e = rel_rows(tones.cpu().numpy(), ref["tones"])
+    print(f"cluster PFB origin 2^{int(np.log2(base))}+: max tone rel err {e.max():.3e}")
+    assert e.max() < TOL
+    assert np.array_equal(tones.cpu().numpy(), full.cpu().numpy()[:, plan.bins()].T)
+    plan.close()
