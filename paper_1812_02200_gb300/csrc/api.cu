@@ -345,7 +345,7 @@ rfr_status ensure_scratch(rfr_plan* p, int64_t n) {
     // later pushes of up to n samples never allocate (nor synchronise)
     const int64_t F = frames_for_len(p, std::max<int64_t>(p->cl, p->W - 1) + n);
     if (p->mode == RFR_MODE_PFB && p->gen && F > 0) RFR_CUDA(p, rfr::gen_plan_reserve(&p->gplan, F));
-    if (p->mode == RFR_MODE_PFB && p->phase_R > 1) {
+    if (p->mode == RFR_MODE_PFB && (p->phase_R > 1 || (!p->gen && rfr::pfb_split16(p->log2n, p->Tk)))) {
         const int64_t lv = std::max<int64_t>(p->cl, p->W - 1) + n;
         if (lv > p->view_cap) {
             cudaDeviceSynchronize();
@@ -355,7 +355,7 @@ rfr_status ensure_scratch(rfr_plan* p, int64_t n) {
             RFR_CUDA(p, dev_alloc(&p->d_view, static_cast<size_t>(lv) * 4));
             p->view_cap = lv;
         }
-        RFR_CUDA(p, ensure_pass_tones(p, F, nullptr));
+        if (p->phase_R > 1) RFR_CUDA(p, ensure_pass_tones(p, F, nullptr));
     }
     if (p->mode == RFR_MODE_DEMOD && F > 0 && !p->words.empty()) return ensure_demod_scratch(p, F, -1, nullptr);
     return RFR_OK;
@@ -415,6 +415,29 @@ rfr_status push_core(rfr_plan* p, const int16_t* iq, int64_t n, const rfr_output
             if (p->phase_R > 1) {
                 rfr_status rs = phase_passes(p, L, o, lv, F, st);
                 if (rs != RFR_OK) return rs;
+            } else if (!p->gen && rfr::pfb_split16(p->log2n, p->Tk)) {
+                // the two-pass 16-tap form needs a 16-byte aligned view: an
+                // unaligned push goes through a contiguous copy of it
+                const bool aligned = (reinterpret_cast<uintptr_t>(iq) % 16 == 0) && (p->cl % 4 == 0) &&
+                                     (reinterpret_cast<uintptr_t>(carry) % 16 == 0);
+                if (!aligned) {
+                    if (lv > p->view_cap) {
+                        const rfr_status rs = refuse_growth_in_capture(p, st);
+                        if (rs != RFR_OK) return rs;
+                        cudaDeviceSynchronize();
+                        dev_free(p->d_view);
+                        p->d_view = nullptr;
+                        p->view_cap = 0;
+                        RFR_CUDA(p, dev_alloc(&p->d_view, static_cast<size_t>(lv) * 4));
+                        p->view_cap = lv;
+                    }
+                    RFR_CUDA(p, rfr::carry_update(carry, p->cl, iq, n, 0, lv, p->d_view, st));
+                    L.carry = p->d_view;
+                    L.cl = 0;
+                    L.buf = p->d_view;
+                    L.n = lv;
+                }
+                RFR_CUDA(p, rfr::pfb_launch(L, st));
             } else {
                 RFR_CUDA(p, p->gen ? rfr::gen_pfb_launch(L, p->gplan, st) : rfr::pfb_launch(L, st));
             }

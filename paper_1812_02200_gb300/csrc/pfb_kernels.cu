@@ -69,6 +69,7 @@ struct PfbArgs {
     int* status;
     int tone_cs;             // symmetric-tap kernel: tone columns of consecutive frames this far apart
     int rot;                 // symmetric-tap kernel: bin c multiplied by (-i)^((c * rot) mod 4)
+    int accumulate;          // TMEM kernel: add the frames to the outputs instead of writing them
     int64_t q_lo, q_hi;      // iteration range
     int64_t iters_per_cta;
     int ring_sb;             // RING: super-blocks in the ring
@@ -434,7 +435,7 @@ __global__ void __launch_bounds__(kRingThreads, 1)
         if (a.full && !bulk) {
             float2* row = a.full + (a.frame_offset + j) * a.full_ld;
 #pragma unroll
-            for (int i = 0; i < 16; ++i) row[tf + i * NT] = v[i];
+            for (int i = 0; i < 16; ++i) row[tf + i * NT] = a.accumulate ? cadd(row[tf + i * NT], v[i]) : v[i];
         }
         if (bulk) {
 #pragma unroll
@@ -446,7 +447,10 @@ __global__ void __launch_bounds__(kRingThreads, 1)
         }
         __syncthreads();                                         // (C) spectrum in P; Q reads done
         if (bulk && tid == 0) {
-            tma_bulk_s2g(a.full + (a.frame_offset + j) * a.full_ld, P, N * 8);
+            if (a.accumulate)
+                tma_bulk_s2g_add_f32(a.full + (a.frame_offset + j) * a.full_ld, P, N * 8);
+            else
+                tma_bulk_s2g(a.full + (a.frame_offset + j) * a.full_ld, P, N * 8);
             bulk_commit();
         }
         if (nb_smem > 0) {
@@ -468,8 +472,13 @@ __global__ void __launch_bounds__(kRingThreads, 1)
                 if (gtma) {
                     if (tid == 0) {
                         const int32_t x0 = static_cast<int32_t>(a.frame_offset + j - q);
-                        for (int r0 = 0; r0 < nb_smem; r0 += kToneBox)
-                            tma_store_2d(&tm_tones, x0, r0, tile + static_cast<size_t>(r0) * kToneGroup);
+                        for (int r0 = 0; r0 < nb_smem; r0 += kToneBox) {
+                            // accumulate: the map views the rows as FP32 pairs
+                            if (a.accumulate)
+                                tma_reduce_add_2d(&tm_tones, 2 * x0, r0, tile + static_cast<size_t>(r0) * kToneGroup);
+                            else
+                                tma_store_2d(&tm_tones, x0, r0, tile + static_cast<size_t>(r0) * kToneGroup);
+                        }
                         bulk_commit();
                     }
                 } else {
@@ -479,7 +488,8 @@ __global__ void __launch_bounds__(kRingThreads, 1)
                     float2* base = a.tones + a.frame_offset + (j - q);
                     for (int it = tid; it < nq * nb_smem; it += NT) {
                         const int t = it / nq, qq = q0 + (it - t * nq);
-                        base[static_cast<int64_t>(t) * a.tones_ld + qq] = tile[t * kToneGroup + qq];
+                        float2& o = base[static_cast<int64_t>(t) * a.tones_ld + qq];
+                        o = a.accumulate ? cadd(o, tile[t * kToneGroup + qq]) : tile[t * kToneGroup + qq];
                     }
                 }
             }
@@ -487,7 +497,8 @@ __global__ void __launch_bounds__(kRingThreads, 1)
             float2* col = a.tones + a.frame_offset + j;
             for (int t = tid; t < a.n_tones; t += NT) {
                 const int bin = __ldg(a.bins + t);
-                col[t * a.tones_ld] = P[bulk ? bin : fpad(bin)];
+                const float2 tv = P[bulk ? bin : fpad(bin)];
+                col[t * a.tones_ld] = a.accumulate ? cadd(col[t * a.tones_ld], tv) : tv;
             }
         }
     }
@@ -1269,15 +1280,18 @@ cudaError_t launch_tmem(PfbArgs a, int n_sms, int max_smem, cudaStream_t st) {
     std::memset(&tm, 0, sizeof tm);
     a.tones_tma = 0;
     auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tmap_encode_tiled_fn());
+    // (adding into the tones: the rows as FP32 pairs, so that the tensor
+    // reduce adds component by component; coordinates in floats)
     if (a.nb_smem > 0 && enc && (reinterpret_cast<uintptr_t>(a.tones) % 16) == 0 && (a.tones_ld % 2) == 0 &&
-        a.frame_offset + a.F < (int64_t(1) << 31)) {
-        cuuint64_t dims[2] = {static_cast<cuuint64_t>(a.frame_offset + a.F), static_cast<cuuint64_t>(a.n_tones)};
+        a.frame_offset + a.F < (int64_t(1) << 30)) {
+        const int w = a.accumulate ? 2 : 1;
+        cuuint64_t dims[2] = {static_cast<cuuint64_t>(w * (a.frame_offset + a.F)), static_cast<cuuint64_t>(a.n_tones)};
         cuuint64_t strides[1] = {static_cast<cuuint64_t>(a.tones_ld) * 8};
-        cuuint32_t box[2] = {kToneGroup, kToneBox};
+        cuuint32_t box[2] = {static_cast<cuuint32_t>(w * kToneGroup), kToneBox};
         cuuint32_t estr[2] = {1, 1};
-        if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, a.tones, dims, strides, box, estr,
-                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
-                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+        if (enc(&tm, a.accumulate ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, a.tones,
+                dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
             a.tones_tma = 1;
     }
     auto k = pfb_tmem_kernel<T>;
@@ -1400,8 +1414,10 @@ cudaError_t dispatch_ring_T(PfbArgs a, int tk, int n_sms, int max_smem, int la, 
 
 bool pfb_uses_ring(int log2n, int taps) { return log2n >= 4 && log2n <= 12 && taps <= 8; }
 int pfb_cluster_size(int log2n, int taps) { return (log2n == 13 || log2n == 14) && taps <= 8 ? 1 << (log2n - 12) : 0; }
+bool pfb_split16(int log2n, int taps) { return log2n == 12 && taps == 16; }
 int pfb_kernel_taps(int log2n, int taps) {
     if (pfb_uses_ring(log2n, taps) || pfb_cluster_size(log2n, taps) > 0) return taps <= 4 ? 4 : 8;
+    if (log2n == 12 && taps > 8 && taps <= 16) return 16;     // two 8-tap passes (see pfb_launch)
     return taps;
 }
 
@@ -1441,6 +1457,33 @@ cudaError_t pfb_launch(const PfbLaunch& L, cudaStream_t st) {
                                                 : launch_cluster<2, 8>(a, L.n_sms, L.max_smem, st);
         return L.taps_kernel == 4 ? launch_cluster<4, 4>(a, L.n_sms, L.max_smem, st)
                                   : launch_cluster<4, 8>(a, L.n_sms, L.max_smem, st);
+    }
+    if (pfb_split16(lg, L.taps_kernel)) {
+        // N = 4096, T = 16 (9 .. 16 taps, zero-padded at the oldest end): the
+        // FIR is linear in the taps and so is the FFT, so a frame is the sum
+        // of two 8-tap PFB frames over the halves of its window: taps 0..7
+        // on the stream view as it is, taps 8..15 on the view 8N samples on;
+        // the second pass adds its rows (TMA bulk reduce-add) and tones into
+        // the first's.  The caller passes a 16-byte aligned view.
+        if (a.tone_cs != 1 || a.rot != 0 || !a.use_tma) return cudaErrorInvalidValue;
+        constexpr int64_t half = int64_t(8) * 4096;
+        PfbArgs a1 = a;
+        a1.T = 8;
+        cudaError_t e = launch_tmem<8>(a1, L.n_sms, L.max_smem, st);
+        if (e != cudaSuccess) return e;
+        PfbArgs a2 = a1;
+        a2.h = a.h + half;
+        if (a.cl >= half) {
+            a2.carry = a.carry + half;
+            a2.cl = a.cl - half;
+        } else {
+            a2.carry = a.carry;
+            a2.cl = 0;
+            a2.buf = a.buf + (half - a.cl);
+            a2.n = a.n - (half - a.cl);
+        }
+        a2.accumulate = 1;
+        return launch_tmem<8>(a2, L.n_sms, L.max_smem, st);
     }
     if (a.tone_cs != 1 || a.rot != 0) {
         // phase passes of an oversampled plan: only the symmetric-tap kernel has them

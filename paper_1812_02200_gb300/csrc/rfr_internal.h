@@ -104,6 +104,8 @@ void gen_plan_free(GenPlan* g);
 int pfb_kernel_taps(int log2n, int taps);
 // CTAs per cluster of the cluster PFB kernel (N = 8192, 16384 with T <= 8), else 0.
 int pfb_cluster_size(int log2n, int taps);
+// N = 4096 with 16 kernel taps: two 8-tap passes of the TMEM kernel (aligned view).
+bool pfb_split16(int log2n, int taps);
 cudaError_t pfb_launch(const PfbLaunch& L, cudaStream_t st);
 cudaError_t gen_pfb_launch(const PfbLaunch& L, const GenPlan& g, cudaStream_t st);
 

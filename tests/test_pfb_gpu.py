@@ -74,7 +74,8 @@ CASES = [
     (1024, 8, "kaiser", 9.0, 300),
     (2048, 2, "hann", 0.0, 300),
     (4096, 8, "kaiser", 9.0, 400),
-    (4096, 12, "kaiser", 9.0, 60),    # DIRECT variant (T > 8)
+    (4096, 12, "kaiser", 9.0, 60),    # two 8-tap TMEM passes (taps padded to 16)
+    (4096, 16, "hann", 0.0, 50),      # two 8-tap TMEM passes
     (1024, 16, "hann", 0.0, 80),      # DIRECT variant
     (8192, 4, "hann", 0.0, 40),       # DIRECT variant (N > 4096)
     (16384, 2, "kaiser", 9.0, 30),    # DIRECT variant, taps padded to 4
@@ -103,7 +104,7 @@ def test_pfb_parity_shapes(lib, N, T, win, beta, frames):
 
 
 @pytest.mark.parametrize("N,T,cluster", [(64, 4, 0), (4096, 8, 0), (1024, 16, 0), (8192, 8, 0), (16384, 3, 0),
-                                         (8192, 8, 1), (16384, 3, 1)])
+                                         (8192, 8, 1), (16384, 3, 1), (4096, 16, 0), (4096, 11, 0)])
 def test_streamed_equals_one_shot_bit_exact(lib, N, T, cluster):
     """Random splits (aligned and odd sizes, some shorter than a frame) give
     bit-identical frames to one push of the whole stream (for N = 8192 and
@@ -422,3 +423,28 @@ def test_cluster_pfb_choice_is_validated(lib):
     assert r.tune()["pfb_cluster"] == 0
     for x in (p, q, r):
         x.close()
+
+
+def test_two_pass_16_taps_outputs(lib):
+    """N = 4096, T = 16 as two 8-tap passes, the second adding into the
+    first's outputs: tones only, full only and both agree bit for bit, the
+    tones equal the spectrum's bin columns, and a push at an odd output
+    frame offset with a row pitch above N (the plain-store paths) equals the
+    tight push."""
+    N, T, nt = 4096, 16, 700
+    case = siggen.pfb_case(N * 60 + 9, N, nt, seed=9301)
+    x = torch.from_numpy(case["x"]).to(DEV)
+    both = _plan(lib, N, T, "kaiser", 9.0, case["words"])
+    f_b, t_b = _run_gpu(both, case["x"], nt, N)
+    assert np.array_equal(t_b, f_b[:, both.bins()].T)
+    _, t_t = _run_gpu(_plan(lib, N, T, "kaiser", 9.0, case["words"], full=False), case["x"], nt, N, full=False)
+    f_f, _ = _run_gpu(_plan(lib, N, T, "kaiser", 9.0, case["words"], tones=False), case["x"], 0, N)
+    assert np.array_equal(t_t, t_b) and np.array_equal(f_f, f_b)
+    F = f_b.shape[0]
+    p = _plan(lib, N, T, "kaiser", 9.0, case["words"])
+    fo = torch.zeros((F + 3, N + 1), dtype=torch.complex64, device=DEV)     # odd pitch: plain row stores
+    to = torch.zeros((nt, F + 5), dtype=torch.complex64, device=DEV)
+    assert p.push_into(x, fo, to, frame_offset=3) == F
+    torch.cuda.synchronize()
+    assert np.array_equal(fo.cpu().numpy()[3:F + 3, :N], f_b)
+    assert np.array_equal(to.cpu().numpy()[:, 3:F + 3], t_b)
