@@ -357,6 +357,86 @@ __device__ float2* gen_fft_to(float2* buf0, float2* buf1, const GenFft& f, int g
     return dst;
 }
 
+// Compiled-in transform shapes (the four-step passes of N = 10^5 and 10^7): the same stages, loads, twiddles and butterflies as gen_fft_to in
+// the same order (so the same results), with the length, the span, the
+// group count and every stride known at compile time, so the index
+// arithmetic folds into constants and immediate offsets.
+template <int R, int TH, int N, int GL2, int NS, bool OUT, typename Sink>
+__device__ __forceinline__ void fixed_stage(const float2* __restrict__ src, float2* __restrict__ dst,
+                                            const float2* __restrict__ tw, Sink& sink) {
+    constexpr int nb = (N / R) << GL2;
+    constexpr int iters = (nb + TH - 1) / TH;
+#pragma unroll
+    for (int i = 0; i < iters; ++i) {
+        const int u = static_cast<int>(threadIdx.x) + i * TH;
+        if (nb % TH != 0 && u >= nb) break;
+        const int g = u & ((1 << GL2) - 1), j = u >> GL2;
+        const int k = NS == 1 ? 0 : j % NS;
+        float2 v[R];
+        load_strided<R>(v, src, u, nb);                      // points (j + r*nR)*G + g
+        if constexpr (NS > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], __ldg(tw + (r - 1) * NS + k));
+        }
+        dft_any<R>(v);
+        const int base = (j - k) * R + k;
+        if constexpr (OUT) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) sink(((base + r * NS) << GL2) + g, v[r]);
+        } else {
+            store_strided<R>(v, dst, (base << GL2) + g, NS << GL2);
+        }
+    }
+    if constexpr (!OUT) __syncthreads();
+}
+
+template <int TH, int GL2, int N, int NS, int R, int... Rest>
+struct FixedFft {
+    // stages from src; returns the buffer the last stage did not read
+    template <typename Sink>
+    __device__ __forceinline__ static float2* run(float2* src, float2* dst, const float2* __restrict__ tw, Sink& sink) {
+        if constexpr (sizeof...(Rest) == 0) {
+            fixed_stage<R, TH, N, GL2, NS, true>(src, dst, tw, sink);
+            return dst;
+        } else {
+            fixed_stage<R, TH, N, GL2, NS, false>(src, dst, tw, sink);
+            return FixedFft<TH, GL2, N, NS * R, Rest...>::run(dst, src, tw + (NS > 1 ? (R - 1) * NS : 0), sink);
+        }
+    }
+};
+
+// The compiled-in shapes: {id, threads, log2 of the transforms per CTA,
+// length, radices}; ids 1.. as dispatched by fft_to below (a shape listed
+// here for one pass is only taken by the pass that dispatches it).
+struct FixedShape {
+    int id, th, gl2, n, nst, radix[4];
+};
+constexpr FixedShape kFixedShapes[] = {
+    {1, 256, 3, 400, 2, {25, 16, 0, 0}},     // N = 10^5, pass A
+    {2, 256, 4, 250, 2, {25, 10, 0, 0}},     // N = 10^5, pass B
+    {4, 512, 1, 3125, 3, {25, 25, 5, 0}},    // N = 10^7, pass A
+    {5, 512, 1, 3200, 3, {25, 16, 8, 0}},    // N = 10^7, pass B
+};
+
+// gen_fft_to, through a compiled-in shape when `fix` names one (pass A
+// dispatches its shape, pass B its own: more shapes in one kernel made its
+// register allocation worse, with spills)
+template <int TH, int PASS, typename Sink>
+__device__ __forceinline__ float2* fft_to(float2* buf0, float2* buf1, const GenFft& f, int gl2,
+                                          const float2* __restrict__ tw, int fix, Sink sink) {
+    const float2* t0 = tw + f.tw_off[0];
+    if constexpr (TH == 256 && PASS == 0) {
+        if (fix == 1) return FixedFft<TH, 3, 400, 1, 25, 16>::run(buf0, buf1, t0, sink);
+    } else if constexpr (TH == 256) {
+        if (fix == 2) return FixedFft<TH, 4, 250, 1, 25, 10>::run(buf0, buf1, t0, sink);
+    } else if constexpr (PASS == 0) {
+        if (fix == 4) return FixedFft<TH, 1, 3125, 1, 25, 25, 5>::run(buf0, buf1, t0, sink);
+    } else {
+        if (fix == 5) return FixedFft<TH, 1, 3200, 1, 25, 16, 8>::run(buf0, buf1, t0, sink);
+    }
+    return gen_fft_to<TH>(buf0, buf1, f, gl2, tw, sink);
+}
+
 struct GenArgs {
     const uint32_t* carry;
     int64_t cl;
@@ -392,6 +472,7 @@ struct GenArgs {
     // points apart in shared memory)
     float2* v;
     int vtma, vbox_rows, vboxes, vsstride;
+    int fixa, fixb;         // compiled-in shapes of pass A / B (kFixedShapes ids), 0: generic stages
 };
 
 // FIR of the points e = tid, tid + TH, ... < E of one frame into sm: point e
@@ -586,21 +667,23 @@ __global__ void __launch_bounds__(TH, GenCfg<TH>::kMinBlocks) gen_single_kernel(
 
 // The FIR of the two-pass form ahead of pass A: v[k][q] for the launch's
 // frames k and every FFT input index q (window position (q - s) mod N), into
-// V in natural order.  One CTA per (frame, kFirThreads * kFirPts points);
-// consecutive threads take consecutive points, so every load and store is
-// coalesced, and the small register footprint leaves many warps in flight.
+// V in natural order.  One CTA per (frame, kFirThreads * kFirPts points),
+// the frames of a point range consecutive in launch order (their windows
+// overlap, and the range's taps are shared); consecutive threads take
+// consecutive points, so every load and store is coalesced, and the small
+// register footprint leaves many warps in flight.
 // Taps are summed in the same order as fir_points (t = 0.. T-1 from zero).
 constexpr int kFirThreads = 256, kFirPts = 8;
 // TC > 0: T == TC known at compile time, so every load of a thread (2 TC
 // kFirPts) is issued before the first use; TC == 0: any T.
 template <int TC>
 __global__ void __launch_bounds__(kFirThreads) gen_fir_kernel(const GenArgs a) {
-    const int64_t kk = blockIdx.y;
+    const int64_t kk = blockIdx.x;
     const int64_t base = (a.k0 + kk) * a.hop;
     const int sh = frame_shift(a, base);
     const int N = a.N;
     const int T = TC > 0 ? TC : a.T;
-    const int qb = static_cast<int>(blockIdx.x) * (kFirThreads * kFirPts) + static_cast<int>(threadIdx.x);
+    const int qb = static_cast<int>(blockIdx.y) * (kFirThreads * kFirPts) + static_cast<int>(threadIdx.x);
     int pos[kFirPts];
     float ar[kFirPts], ai[kFirPts];
 #pragma unroll
@@ -672,11 +755,11 @@ constexpr int kMfPts = 4, kMfFrames = 4;
 template <int TC>
 __global__ void __launch_bounds__(kFirThreads) gen_fir_frames_kernel(const GenArgs a) {
     constexpr int G = kMfFrames, P = kMfPts, R = G + TC - 1;
-    const int64_t f0 = static_cast<int64_t>(blockIdx.y) * G;            // first frame (of this launch)
+    const int64_t f0 = static_cast<int64_t>(blockIdx.x) * G;            // first frame (of this launch)
     const int gn = static_cast<int>(a.F - f0 < G ? a.F - f0 : G);       // frames of this row that exist
     const int64_t base = (a.k0 + f0) * a.hop;
     const int N = a.N, sh = a.sh_fixed;
-    const int qb = static_cast<int>(blockIdx.x) * (kFirThreads * P) + static_cast<int>(threadIdx.x);
+    const int qb = static_cast<int>(blockIdx.y) * (kFirThreads * P) + static_cast<int>(threadIdx.x);
     int pos[P];
     float hv[TC][P];
 #pragma unroll
@@ -789,7 +872,7 @@ __global__ void __launch_bounds__(TH, GenCfg<TH>::kMinBlocks)
         __syncthreads();
         // the last stage multiplies by W_N^{p2*c1} and stores Z directly
         float2* zf = a.z + kk * a.N;
-        gen_fft_to<TH>(sm, sm1, a.fa, a.gla, a.tw_a, [=](int e, float2 v) {
+        fft_to<TH, 0>(sm, sm1, a.fa, a.gla, a.tw_a, a.fixa, [=](int e, float2 v) {
             const int g = e & (GA - 1), c1 = e >> gla, p2 = g0 + g;
             if (p2 < N2) {
                 const int m = p2 * c1;                       // < N1*N2 = N
@@ -848,7 +931,7 @@ __global__ void __launch_bounds__(TH, GenCfg<TH>::kMinBlocks) gen_pass_b_kernel(
         const bool keep = a.n_tones > 0;
         float2* const freebuf = (a.fb.nst & 1) ? sm1 : sm;
         const int glb = a.glb, N1 = a.N1;
-        gen_fft_to<TH>(sm, sm1, a.fb, a.glb, a.tw_b, [=](int e, float2 v) {
+        fft_to<TH, 1>(sm, sm1, a.fb, a.glb, a.tw_b, a.fixb, [=](int e, float2 v) {
             const int g = e & (GB - 1), c2 = e >> glb;
             if (row && c0 + g < N1) row[c0 + g + static_cast<int64_t>(N1) * c2] = v;
             if (keep) freebuf[gpad(e)] = v;
@@ -1116,11 +1199,14 @@ cudaError_t gen_run(GenArgs a, const PfbLaunch& L, const GenPlan& g, cudaStream_
         a.F = std::min<int64_t>(g.z_frames, L.F - k0);
         cudaError_t e;
         if (a.vtma) {
-            const dim3 fg(static_cast<unsigned>((g.N + kFirThreads * kFirPts - 1) / (kFirThreads * kFirPts)),
-                          static_cast<unsigned>(a.F));
-            // hop == N: blocks shared by consecutive frames are read once
-            const dim3 fm(static_cast<unsigned>((g.N + kFirThreads * kMfPts - 1) / (kFirThreads * kMfPts)),
-                          static_cast<unsigned>((a.F + kMfFrames - 1) / kMfFrames));
+            const dim3 fg(static_cast<unsigned>(a.F),
+                          static_cast<unsigned>((g.N + kFirThreads * kFirPts - 1) / (kFirThreads * kFirPts)));
+            // hop == N: blocks shared by consecutive frames are read once;
+            // the frame groups of a point range are consecutive CTAs, so the
+            // blocks two groups share and the range's taps are read from
+            // DRAM once (for N = 10^7 the taps alone are 160 MB)
+            const dim3 fm(static_cast<unsigned>((a.F + kMfFrames - 1) / kMfFrames),
+                          static_cast<unsigned>((g.N + kFirThreads * kMfPts - 1) / (kFirThreads * kMfPts)));
             const bool frames = a.sh_fixed >= 0 && a.hop == g.N;
             switch (frames ? a.T : -a.T) {
             case 2: gen_fir_frames_kernel<2><<<fm, kFirThreads, 0, st>>>(a); break;
@@ -1189,6 +1275,17 @@ cudaError_t gen_pfb_launch(const PfbLaunch& L, const GenPlan& g, cudaStream_t st
     a.tones = static_cast<float2*>(L.tones);
     a.tones_ld = L.tones_ld;
     a.fo = L.frame_offset;
+    auto fixed_id = [&](const GenFft& f, int gl2) {
+        for (const FixedShape& c : kFixedShapes) {
+            if (c.th != g.threads || c.gl2 != gl2 || c.n != f.n || c.nst != f.nst) continue;
+            bool same = true;
+            for (int s = 0; s < f.nst; ++s) same = same && c.radix[s] == f.radix[s];
+            if (same) return c.id;
+        }
+        return 0;
+    };
+    a.fixa = g.N1 > 1 ? fixed_id(g.fa, g.gla) : 0;
+    a.fixb = g.N1 > 1 ? fixed_id(g.fb, g.glb) : 0;
     return g.threads == 256 ? gen_run<256>(a, L, g, st) : gen_run<512>(a, L, g, st);
 }
 
