@@ -338,6 +338,23 @@ rfr_status push_check(rfr_plan* p, const int16_t* iq, int64_t n, const rfr_outpu
     return RFR_OK;
 }
 
+// The first-half FIR rows of the 16-tap N = 4096 form for F frames; growing
+// them is refused while `st` is being captured (st null: not capturing).
+rfr_status ensure_pre_rows(rfr_plan* p, int64_t F, cudaStream_t st) {
+    if (F <= p->pre_cap) return RFR_OK;
+    if (st) {
+        const rfr_status rs = refuse_growth_in_capture(p, st);
+        if (rs != RFR_OK) return rs;
+    }
+    cudaDeviceSynchronize();
+    dev_free(p->d_pre);
+    p->d_pre = nullptr;
+    p->pre_cap = 0;
+    RFR_CUDA(p, dev_alloc(&p->d_pre, static_cast<size_t>(F) * 4096 * 8));
+    p->pre_cap = F;
+    return RFR_OK;
+}
+
 rfr_status ensure_scratch(rfr_plan* p, int64_t n) {
     // the most frames a push of n samples can complete whatever the stream's
     // state (a carried residue adds up to hop - 1 samples: the carry holds at
@@ -356,6 +373,10 @@ rfr_status ensure_scratch(rfr_plan* p, int64_t n) {
             p->view_cap = lv;
         }
         if (p->phase_R > 1) RFR_CUDA(p, ensure_pass_tones(p, F, nullptr));
+        else {
+            const rfr_status rs = ensure_pre_rows(p, F, nullptr);
+            if (rs != RFR_OK) return rs;
+        }
     }
     if (p->mode == RFR_MODE_DEMOD && F > 0 && !p->words.empty()) return ensure_demod_scratch(p, F, -1, nullptr);
     return RFR_OK;
@@ -437,6 +458,10 @@ rfr_status push_core(rfr_plan* p, const int16_t* iq, int64_t n, const rfr_output
                     L.buf = p->d_view;
                     L.n = lv;
                 }
+                const rfr_status rs = ensure_pre_rows(p, F, st);
+                if (rs != RFR_OK) return rs;
+                L.pre = p->d_pre;
+                L.pre_cap = p->pre_cap;
                 RFR_CUDA(p, rfr::pfb_launch(L, st));
             } else {
                 RFR_CUDA(p, p->gen ? rfr::gen_pfb_launch(L, p->gplan, st) : rfr::pfb_launch(L, st));
@@ -551,7 +576,7 @@ void destroy(rfr_plan* p) {
                     static_cast<void*>(p->d_words), static_cast<void*>(p->d_rates), static_cast<void*>(p->d_h32), p->d_c32, p->d_bhi, p->d_blo,
                     static_cast<void*>(p->d_status), static_cast<void*>(p->d_carry[0]),
                     static_cast<void*>(p->d_carry[1]), p->d_xs_hi, p->d_xs_lo, p->d_rot, p->d_qfull, p->d_b3, p->d_xs3,
-                    p->d_qtones, static_cast<void*>(p->d_view), p->d_ptones})
+                    p->d_qtones, static_cast<void*>(p->d_view), p->d_ptones, p->d_pre})
         dev_free(q);
     for (int i = 0; i < rfr_plan::kStageBufs; ++i) {
         dev_free(p->d_stage_in[i]);

@@ -117,24 +117,12 @@ __device__ __forceinline__ void tma_bulk_s2g(void* dst, const void* src, uint32_
     asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
                  ::"l"(dst), "r"(smem_u32(src)), "r"(bytes) : "memory");
 }
-// As tma_bulk_s2g, adding the FP32 values to those in global memory
-// (element-wise add, bulk async-group completion).
-__device__ __forceinline__ void tma_bulk_s2g_add_f32(void* dst, const void* src, uint32_t bytes) {
-    asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;"
-                 ::"l"(dst), "r"(smem_u32(src)), "r"(bytes) : "memory");
-}
 // 2-D tiled tensor copy shared -> global (bulk async-group completion); the
 // box is the tensor map's, (c0, c1) its origin: c0 the innermost coordinate
 // in elements (c0 * element size a multiple of 16 bytes), c1 the row, both
 // >= 0.  Elements outside the tensor's extent are not written.
 __device__ __forceinline__ void tma_store_2d(const void* tmap, int32_t c0, int32_t c1, const void* src) {
     asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];"
-                 ::"l"(tmap), "r"(c0), "r"(c1), "r"(smem_u32(src)) : "memory");
-}
-// As tma_store_2d, adding the box to the tensor's values (the tensor map's
-// element type, here FP32) instead of writing it.
-__device__ __forceinline__ void tma_reduce_add_2d(const void* tmap, int32_t c0, int32_t c1, const void* src) {
-    asm volatile("cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2}], [%3];"
                  ::"l"(tmap), "r"(c0), "r"(c1), "r"(smem_u32(src)) : "memory");
 }
 __device__ __forceinline__ void bulk_commit() {

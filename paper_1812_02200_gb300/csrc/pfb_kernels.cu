@@ -69,7 +69,7 @@ struct PfbArgs {
     int* status;
     int tone_cs;             // symmetric-tap kernel: tone columns of consecutive frames this far apart
     int rot;                 // symmetric-tap kernel: bin c multiplied by (-i)^((c * rot) mod 4)
-    int accumulate;          // TMEM kernel: add the frames to the outputs instead of writing them
+    const float2* pre;       // TMEM kernel <T, true>: [F][4096] FIR partial sums the frames' FIR starts from
     int64_t q_lo, q_hi;      // iteration range
     int64_t iters_per_cta;
     int ring_sb;             // RING: super-blocks in the ring
@@ -277,7 +277,10 @@ __host__ __device__ __forceinline__ TmemLayout tmem_layout(int tw_count, int nb)
     return L;
 }
 
-template <int T>
+// PRE: each frame's FIR accumulators start from a.pre's row of the frame
+// (the first half of a 16-tap FIR, see fir8_pre_kernel) instead of zero;
+// the next frame's row is loaded while this frame's FFT runs.
+template <int T, bool PRE>
 __global__ void __launch_bounds__(kRingThreads, 1)
     pfb_tmem_kernel(const PfbArgs a, const __grid_constant__ CUtensorMap tm_tones) {
     constexpr int N = 4096, NT = 256;
@@ -331,6 +334,17 @@ __global__ void __launch_bounds__(kRingThreads, 1)
             issue_sb_tma(a, b, need, stage + (b % kTmemStage) * N, &bars[b % kTmemStage]);
 
     bool ok = true;
+    float are[16], aim[16];
+    bool pre_loaded = false;
+    auto load_pre = [&](int64_t jj) {
+        const float2* row = a.pre + jj * N + tf;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const float2 q = __ldg(row + r * NT);
+            are[r] = q.x;
+            aim[r] = q.y;
+        }
+    };
     for (int64_t b = b0; b < b1; ++b) {
         const int s = static_cast<int>(b % kTmemStage);
         if (!mbar_wait(&bars[s], static_cast<uint32_t>(((b - b0) / kTmemStage) & 1), a.status)) {
@@ -357,9 +371,13 @@ __global__ void __launch_bounds__(kRingThreads, 1)
                 issue_sb_tma(a, b + kTmemStage, need, stage + s * N, &bars[s]);
             continue;
         }
-        float are[16], aim[16];
+        if constexpr (PRE) {
+            if (!pre_loaded) load_pre(j);                        // the CTA's first frame
+            pre_loaded = false;
+        } else {
 #pragma unroll
-        for (int r = 0; r < 16; ++r) are[r] = aim[r] = 0.f;
+            for (int r = 0; r < 16; ++r) are[r] = aim[r] = 0.f;
+        }
         // taps in order t = 0..T-1; each slot read as two 16-column halves,
         // the next half's load in flight while this half's FMAs issue
         uint32_t xa[16], xb[16];
@@ -391,6 +409,12 @@ __global__ void __launch_bounds__(kRingThreads, 1)
         float2 v[16];
 #pragma unroll
         for (int r = 0; r < 16; ++r) v[r] = make_float2(are[r], aim[r]);
+        if constexpr (PRE) {
+            if (j + 1 < jb) {
+                load_pre(j + 1);
+                pre_loaded = true;
+            }
+        }
         // 4096-point Stockham FFT, 3 radix-16 passes (as fft_frame<12>):
         // pass 0 -> P, pass 1 P -> Q, pass 2 Q -> registers; spectrum -> P.
         float2* const P = (j & 1) ? xb1 : xb0;
@@ -435,7 +459,7 @@ __global__ void __launch_bounds__(kRingThreads, 1)
         if (a.full && !bulk) {
             float2* row = a.full + (a.frame_offset + j) * a.full_ld;
 #pragma unroll
-            for (int i = 0; i < 16; ++i) row[tf + i * NT] = a.accumulate ? cadd(row[tf + i * NT], v[i]) : v[i];
+            for (int i = 0; i < 16; ++i) row[tf + i * NT] = v[i];
         }
         if (bulk) {
 #pragma unroll
@@ -447,10 +471,7 @@ __global__ void __launch_bounds__(kRingThreads, 1)
         }
         __syncthreads();                                         // (C) spectrum in P; Q reads done
         if (bulk && tid == 0) {
-            if (a.accumulate)
-                tma_bulk_s2g_add_f32(a.full + (a.frame_offset + j) * a.full_ld, P, N * 8);
-            else
-                tma_bulk_s2g(a.full + (a.frame_offset + j) * a.full_ld, P, N * 8);
+            tma_bulk_s2g(a.full + (a.frame_offset + j) * a.full_ld, P, N * 8);
             bulk_commit();
         }
         if (nb_smem > 0) {
@@ -472,13 +493,8 @@ __global__ void __launch_bounds__(kRingThreads, 1)
                 if (gtma) {
                     if (tid == 0) {
                         const int32_t x0 = static_cast<int32_t>(a.frame_offset + j - q);
-                        for (int r0 = 0; r0 < nb_smem; r0 += kToneBox) {
-                            // accumulate: the map views the rows as FP32 pairs
-                            if (a.accumulate)
-                                tma_reduce_add_2d(&tm_tones, 2 * x0, r0, tile + static_cast<size_t>(r0) * kToneGroup);
-                            else
-                                tma_store_2d(&tm_tones, x0, r0, tile + static_cast<size_t>(r0) * kToneGroup);
-                        }
+                        for (int r0 = 0; r0 < nb_smem; r0 += kToneBox)
+                            tma_store_2d(&tm_tones, x0, r0, tile + static_cast<size_t>(r0) * kToneGroup);
                         bulk_commit();
                     }
                 } else {
@@ -488,8 +504,7 @@ __global__ void __launch_bounds__(kRingThreads, 1)
                     float2* base = a.tones + a.frame_offset + (j - q);
                     for (int it = tid; it < nq * nb_smem; it += NT) {
                         const int t = it / nq, qq = q0 + (it - t * nq);
-                        float2& o = base[static_cast<int64_t>(t) * a.tones_ld + qq];
-                        o = a.accumulate ? cadd(o, tile[t * kToneGroup + qq]) : tile[t * kToneGroup + qq];
+                        base[static_cast<int64_t>(t) * a.tones_ld + qq] = tile[t * kToneGroup + qq];
                     }
                 }
             }
@@ -497,8 +512,7 @@ __global__ void __launch_bounds__(kRingThreads, 1)
             float2* col = a.tones + a.frame_offset + j;
             for (int t = tid; t < a.n_tones; t += NT) {
                 const int bin = __ldg(a.bins + t);
-                const float2 tv = P[bulk ? bin : fpad(bin)];
-                col[t * a.tones_ld] = a.accumulate ? cadd(col[t * a.tones_ld], tv) : tv;
+                col[t * a.tones_ld] = P[bulk ? bin : fpad(bin)];
             }
         }
     }
@@ -1260,7 +1274,59 @@ cudaError_t launch_direct(PfbArgs a, int n_sms, int max_smem, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <int T>
+// The first half of a 16-tap frame's FIR for the two-pass 16-tap form
+// (N = 4096): pre[j][p] = sum_{t<8} h[t N + p] x[(j + t) N + p] over the
+// stream view [carry | buffer], FMAs in tap order from zero as in the TMEM
+// kernel's FIR (which then continues the same sums with taps 8..15).  A
+// thread takes kPrePts points of kPreFrames consecutive frames, whose
+// kPreFrames + 7 input blocks it loads and converts once; the frame groups
+// of a point range are consecutive CTAs (shared blocks come from DRAM once).
+constexpr int kPreThreads = 256, kPrePts = 4, kPreFrames = 4;
+__global__ void __launch_bounds__(kPreThreads) fir8_pre_kernel(const PfbArgs a, float2* __restrict__ pre) {
+    constexpr int N = 4096, TT = 8, G = kPreFrames, P = kPrePts, R = G + TT - 1;
+    const int64_t f0 = static_cast<int64_t>(blockIdx.x) * G;
+    const int gn = static_cast<int>(min_i64(a.F - f0, G));
+    const int qb = static_cast<int>(blockIdx.y) * (kPreThreads * P) + static_cast<int>(threadIdx.x);
+    float hv[TT][P];
+#pragma unroll
+    for (int t = 0; t < TT; ++t)
+#pragma unroll
+        for (int k = 0; k < P; ++k) hv[t][k] = __ldg(a.h + t * N + qb + k * kPreThreads);
+    const int64_t base = f0 * N + qb;
+    uint32_t w[R][P];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int k = 0; k < P; ++k)
+            w[r][k] = r < gn + TT - 1 ? vload(a, base + static_cast<int64_t>(r) * N + k * kPreThreads) : 0u;
+    float ar[G][P], ai[G][P];
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+#pragma unroll
+        for (int k = 0; k < P; ++k) ar[g][k] = ai[g][k] = 0.f;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+            const float2 x = iq_to_f2(w[r][k]);
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                const int t = r - g;
+                if (t < 0 || t >= TT) continue;
+                ar[g][k] = fmaf(hv[t][k], x.x, ar[g][k]);
+                ai[g][k] = fmaf(hv[t][k], x.y, ai[g][k]);
+            }
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        if (g >= gn) break;
+#pragma unroll
+        for (int k = 0; k < P; ++k) pre[(f0 + g) * N + qb + k * kPreThreads] = make_float2(ar[g][k], ai[g][k]);
+    }
+}
+
+template <int T, bool PRE = false>
 cudaError_t launch_tmem(PfbArgs a, int n_sms, int max_smem, cudaStream_t st) {
     a.nb_smem = (a.n_tones > 0 && a.n_tones <= kTonesPerThread * kRingThreads &&
                  tmem_layout(a.tw_count, a.n_tones).total <= static_cast<size_t>(max_smem))
@@ -1280,21 +1346,18 @@ cudaError_t launch_tmem(PfbArgs a, int n_sms, int max_smem, cudaStream_t st) {
     std::memset(&tm, 0, sizeof tm);
     a.tones_tma = 0;
     auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tmap_encode_tiled_fn());
-    // (adding into the tones: the rows as FP32 pairs, so that the tensor
-    // reduce adds component by component; coordinates in floats)
     if (a.nb_smem > 0 && enc && (reinterpret_cast<uintptr_t>(a.tones) % 16) == 0 && (a.tones_ld % 2) == 0 &&
-        a.frame_offset + a.F < (int64_t(1) << 30)) {
-        const int w = a.accumulate ? 2 : 1;
-        cuuint64_t dims[2] = {static_cast<cuuint64_t>(w * (a.frame_offset + a.F)), static_cast<cuuint64_t>(a.n_tones)};
+        a.frame_offset + a.F < (int64_t(1) << 31)) {
+        cuuint64_t dims[2] = {static_cast<cuuint64_t>(a.frame_offset + a.F), static_cast<cuuint64_t>(a.n_tones)};
         cuuint64_t strides[1] = {static_cast<cuuint64_t>(a.tones_ld) * 8};
-        cuuint32_t box[2] = {static_cast<cuuint32_t>(w * kToneGroup), kToneBox};
+        cuuint32_t box[2] = {kToneGroup, kToneBox};
         cuuint32_t estr[2] = {1, 1};
-        if (enc(&tm, a.accumulate ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, a.tones,
-                dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+        if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, a.tones, dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
             a.tones_tma = 1;
     }
-    auto k = pfb_tmem_kernel<T>;
+    auto k = pfb_tmem_kernel<T, PRE>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<static_cast<unsigned>(grid2), kRingThreads, smem, st>>>(a, tm);
@@ -1459,17 +1522,19 @@ cudaError_t pfb_launch(const PfbLaunch& L, cudaStream_t st) {
                                   : launch_cluster<4, 8>(a, L.n_sms, L.max_smem, st);
     }
     if (pfb_split16(lg, L.taps_kernel)) {
-        // N = 4096, T = 16 (9 .. 16 taps, zero-padded at the oldest end): the
-        // FIR is linear in the taps and so is the FFT, so a frame is the sum
-        // of two 8-tap PFB frames over the halves of its window: taps 0..7
-        // on the stream view as it is, taps 8..15 on the view 8N samples on;
-        // the second pass adds its rows (TMA bulk reduce-add) and tones into
-        // the first's.  The caller passes a 16-byte aligned view.
-        if (a.tone_cs != 1 || a.rot != 0 || !a.use_tma) return cudaErrorInvalidValue;
+        // N = 4096, T = 16 (9 .. 16 taps, zero-padded at the oldest end):
+        // the FIR of taps 0..7 over the window's first 8 blocks by
+        // fir8_pre_kernel into L.pre, then the TMEM kernel over the view 8N
+        // samples on with taps 8..15, its FIR sums starting from those rows
+        // (the same FMA chain as one 16-tap FIR).  The caller passes a
+        // 16-byte aligned view and L.pre for at least F frames.
+        if (a.tone_cs != 1 || a.rot != 0 || !a.use_tma || !L.pre || L.pre_cap < a.F) return cudaErrorInvalidValue;
         constexpr int64_t half = int64_t(8) * 4096;
         PfbArgs a1 = a;
         a1.T = 8;
-        cudaError_t e = launch_tmem<8>(a1, L.n_sms, L.max_smem, st);
+        const dim3 pg(static_cast<unsigned>((a.F + kPreFrames - 1) / kPreFrames), 4096 / (kPreThreads * kPrePts));
+        fir8_pre_kernel<<<pg, kPreThreads, 0, st>>>(a1, static_cast<float2*>(L.pre));
+        cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         PfbArgs a2 = a1;
         a2.h = a.h + half;
@@ -1482,8 +1547,8 @@ cudaError_t pfb_launch(const PfbLaunch& L, cudaStream_t st) {
             a2.buf = a.buf + (half - a.cl);
             a2.n = a.n - (half - a.cl);
         }
-        a2.accumulate = 1;
-        return launch_tmem<8>(a2, L.n_sms, L.max_smem, st);
+        a2.pre = static_cast<const float2*>(L.pre);
+        return launch_tmem<8, true>(a2, L.n_sms, L.max_smem, st);
     }
     if (a.tone_cs != 1 || a.rot != 0) {
         // phase passes of an oversampled plan: only the symmetric-tap kernel has them

@@ -74,8 +74,8 @@ CASES = [
     (1024, 8, "kaiser", 9.0, 300),
     (2048, 2, "hann", 0.0, 300),
     (4096, 8, "kaiser", 9.0, 400),
-    (4096, 12, "kaiser", 9.0, 60),    # two 8-tap TMEM passes (taps padded to 16)
-    (4096, 16, "hann", 0.0, 50),      # two 8-tap TMEM passes
+    (4096, 12, "kaiser", 9.0, 60),    # first-half FIR pass + TMEM kernel (taps padded to 16)
+    (4096, 16, "hann", 0.0, 50),      # first-half FIR pass + TMEM kernel
     (1024, 16, "hann", 0.0, 80),      # DIRECT variant
     (8192, 4, "hann", 0.0, 40),       # DIRECT variant (N > 4096)
     (16384, 2, "kaiser", 9.0, 30),    # DIRECT variant, taps padded to 4
@@ -426,11 +426,11 @@ def test_cluster_pfb_choice_is_validated(lib):
 
 
 def test_two_pass_16_taps_outputs(lib):
-    """N = 4096, T = 16 as two 8-tap passes, the second adding into the
-    first's outputs: tones only, full only and both agree bit for bit, the
-    tones equal the spectrum's bin columns, and a push at an odd output
-    frame offset with a row pitch above N (the plain-store paths) equals the
-    tight push."""
+    """N = 4096, T = 16 as a first-half FIR pass (taps 0..7) and the TMEM
+    kernel continuing those sums with taps 8..15: tones only, full only and
+    both agree bit for bit, the tones equal the spectrum's bin columns, and a
+    push at an odd output frame offset with a row pitch above N (the
+    plain-store paths) equals the tight push."""
     N, T, nt = 4096, 16, 700
     case = siggen.pfb_case(N * 60 + 9, N, nt, seed=9301)
     x = torch.from_numpy(case["x"]).to(DEV)
