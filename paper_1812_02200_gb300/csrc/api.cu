@@ -438,7 +438,10 @@ rfr_status push_core(rfr_plan* p, const int16_t* iq, int64_t n, const rfr_output
                 if (rs != RFR_OK) return rs;
             } else if (!p->gen && rfr::pfb_split16(p->log2n, p->Tk)) {
                 // the two-pass 16-tap form needs a 16-byte aligned view: an
-                // unaligned push goes through a contiguous copy of it
+                // unaligned push goes through a contiguous copy of it.  Scratch
+                // that has to grow is sized for a push of n samples after any
+                // carry (so that a later push of that size never grows it)
+                const int64_t lv_max = std::max<int64_t>(p->cl, p->W - 1) + n;
                 const bool aligned = (reinterpret_cast<uintptr_t>(iq) % 16 == 0) && (p->cl % 4 == 0) &&
                                      (reinterpret_cast<uintptr_t>(carry) % 16 == 0);
                 if (!aligned) {
@@ -449,8 +452,8 @@ rfr_status push_core(rfr_plan* p, const int16_t* iq, int64_t n, const rfr_output
                         dev_free(p->d_view);
                         p->d_view = nullptr;
                         p->view_cap = 0;
-                        RFR_CUDA(p, dev_alloc(&p->d_view, static_cast<size_t>(lv) * 4));
-                        p->view_cap = lv;
+                        RFR_CUDA(p, dev_alloc(&p->d_view, static_cast<size_t>(lv_max) * 4));
+                        p->view_cap = lv_max;
                     }
                     RFR_CUDA(p, rfr::carry_update(carry, p->cl, iq, n, 0, lv, p->d_view, st));
                     L.carry = p->d_view;
@@ -458,7 +461,7 @@ rfr_status push_core(rfr_plan* p, const int16_t* iq, int64_t n, const rfr_output
                     L.buf = p->d_view;
                     L.n = lv;
                 }
-                const rfr_status rs = ensure_pre_rows(p, F, st);
+                const rfr_status rs = ensure_pre_rows(p, F <= p->pre_cap ? F : frames_for_len(p, lv_max), st);
                 if (rs != RFR_OK) return rs;
                 L.pre = p->d_pre;
                 L.pre_cap = p->pre_cap;

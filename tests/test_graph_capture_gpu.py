@@ -86,3 +86,14 @@ def test_oversampled_pfb_push_in_capture(lib):
                                       torch.full(ts, float("nan"), dtype=torch.complex64, device=DEV)))
     _check_refused_then_captured(lib, mk, hop * 40 + N * T, hop * 200,
                                  lambda p, n: ((nt, p.frames_for(n)), (p.frames_for(n), N)))
+
+
+def test_16_tap_pfb_push_in_capture(lib):
+    """N = 4096 with 16 taps: the first-half FIR rows are plan scratch too."""
+    N, T, nt = 4096, 16, 30
+    case = siggen.pfb_case(N * 300, N, nt, seed=9103)
+    mk = _Maker(lambda: lib.Plan(N, T, window="kaiser", beta=9.0, words=case["words"]),
+                case, lambda ts, fs: (torch.full(fs, float("nan"), dtype=torch.complex64, device=DEV),
+                                      torch.full(ts, float("nan"), dtype=torch.complex64, device=DEV)))
+    _check_refused_then_captured(lib, mk, N * 56, N * 200,
+                                 lambda p, n: ((nt, p.frames_for(n)), (p.frames_for(n), N)))
