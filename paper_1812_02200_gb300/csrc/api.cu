@@ -338,8 +338,9 @@ rfr_status push_check(rfr_plan* p, const int16_t* iq, int64_t n, const rfr_outpu
     return RFR_OK;
 }
 
-// The first-half FIR rows of the 16-tap N = 4096 form for F frames; growing
-// them is refused while `st` is being captured (st null: not capturing).
+// The FIR pre-sum rows of F frames (PFB plans with rfr::pfb_pre_rows);
+// growing them is refused while `st` is being captured (st null: not
+// capturing).
 rfr_status ensure_pre_rows(rfr_plan* p, int64_t F, cudaStream_t st) {
     if (F <= p->pre_cap) return RFR_OK;
     if (st) {
@@ -350,7 +351,7 @@ rfr_status ensure_pre_rows(rfr_plan* p, int64_t F, cudaStream_t st) {
     dev_free(p->d_pre);
     p->d_pre = nullptr;
     p->pre_cap = 0;
-    RFR_CUDA(p, dev_alloc(&p->d_pre, static_cast<size_t>(F) * 4096 * 8));
+    RFR_CUDA(p, dev_alloc(&p->d_pre, static_cast<size_t>(F) * p->N * 8));
     p->pre_cap = F;
     return RFR_OK;
 }
@@ -373,10 +374,10 @@ rfr_status ensure_scratch(rfr_plan* p, int64_t n) {
             p->view_cap = lv;
         }
         if (p->phase_R > 1) RFR_CUDA(p, ensure_pass_tones(p, F, nullptr));
-        else {
-            const rfr_status rs = ensure_pre_rows(p, F, nullptr);
-            if (rs != RFR_OK) return rs;
-        }
+    }
+    if (p->mode == RFR_MODE_PFB && !p->gen && p->phase_R == 1 && rfr::pfb_pre_rows(p->log2n, p->Tk)) {
+        const rfr_status rs = ensure_pre_rows(p, F, nullptr);
+        if (rs != RFR_OK) return rs;
     }
     if (p->mode == RFR_MODE_DEMOD && F > 0 && !p->words.empty()) return ensure_demod_scratch(p, F, -1, nullptr);
     return RFR_OK;
@@ -467,6 +468,15 @@ rfr_status push_core(rfr_plan* p, const int16_t* iq, int64_t n, const rfr_output
                 L.pre_cap = p->pre_cap;
                 RFR_CUDA(p, rfr::pfb_launch(L, st));
             } else {
+                if (!p->gen && rfr::pfb_pre_rows(p->log2n, p->Tk) && !L.cluster) {
+                    // FIR pre-sum rows, sized for a push of n samples after any
+                    // carry when they grow
+                    const int64_t lv_max = std::max<int64_t>(p->cl, p->W - 1) + n;
+                    const rfr_status rs = ensure_pre_rows(p, F <= p->pre_cap ? F : frames_for_len(p, lv_max), st);
+                    if (rs != RFR_OK) return rs;
+                    L.pre = p->d_pre;
+                    L.pre_cap = p->pre_cap;
+                }
                 RFR_CUDA(p, p->gen ? rfr::gen_pfb_launch(L, p->gplan, st) : rfr::pfb_launch(L, st));
             }
         } else if (p->mode == RFR_MODE_CHIRP) {

@@ -278,7 +278,7 @@ __host__ __device__ __forceinline__ TmemLayout tmem_layout(int tw_count, int nb)
 }
 
 // PRE: each frame's FIR accumulators start from a.pre's row of the frame
-// (the first half of a 16-tap FIR, see fir8_pre_kernel) instead of zero;
+// (the first half of a 16-tap FIR, see fir_pre_kernel) instead of zero;
 // the next frame's row is loaded while this frame's FFT runs.
 template <int T, bool PRE>
 __global__ void __launch_bounds__(kRingThreads, 1)
@@ -1184,8 +1184,13 @@ __global__ void __launch_bounds__(kRingThreads, 1)
 }
 
 // -------------------------------------------------------------- DIRECT
-template <int LOG2N>
-__global__ void __launch_bounds__(1024, 1) pfb_direct_kernel(const PfbArgs a) {
+// PRE: the frames' FIR sums come from a.pre (fir_pre_kernel) instead of
+// the in-kernel FIR.  Launched with max(N/16, 256) threads; below N = 8192
+// four CTAs per SM with the in-kernel FIR (64 registers), two with PRE.
+template <int LOG2N, bool PRE>
+__global__ void __launch_bounds__(LOG2N >= 14 ? 1024 : (LOG2N == 13 ? 512 : 256),
+                                  LOG2N >= 13 ? 1 : (PRE ? 2 : 4))
+    pfb_direct_kernel(const PfbArgs a) {
     constexpr int N = 1 << LOG2N;
     constexpr int NT = N / 16;
     constexpr int FSTRIDE = N + N / 16;
@@ -1203,7 +1208,22 @@ __global__ void __launch_bounds__(1024, 1) pfb_direct_kernel(const PfbArgs a) {
         float2 v[16];
 #pragma unroll
         for (int r = 0; r < 16; ++r) v[r] = make_float2(0.f, 0.f);
-        if (valid) {
+        if (PRE && valid) {
+            // the frame's FIR sums, computed ahead by fir_pre_kernel (the
+            // same FMA chain as the loop below)
+            const float2* row = a.pre + j * N + tf;
+#pragma unroll
+            for (int r = 0; r < 16; ++r) v[r] = __ldg(row + r * NT);
+            // the next frame's rows on their way to L2 (one request per
+            // 128-byte line: 16 consecutive points; at N = 16384 it costs a
+            // few spilled registers and still measured 9 % faster)
+            const int64_t jn = j + static_cast<int64_t>(gridDim.x) * G;
+            if (jn < a.F && (tf & 15) == 0) {
+                const float2* nrow = a.pre + jn * N + tf;
+#pragma unroll
+                for (int r = 0; r < 16; ++r) prefetch_l2(nrow + r * NT);
+            }
+        } else if (!PRE && valid) {
             for (int t = 0; t < T; ++t) {
                 const int64_t base = (j + t) * N + tf;
 #pragma unroll
@@ -1265,7 +1285,10 @@ cudaError_t launch_direct(PfbArgs a, int n_sms, int max_smem, cudaStream_t st) {
     if (smem > static_cast<size_t>(max_smem)) return cudaErrorInvalidConfiguration;
     const int64_t n_iter = (a.F + G - 1) / G;
     int per_sm = 1;
-    auto k = pfb_direct_kernel<LOG2N>;
+    // pre-sum instances only for the shapes that take them (pfb_pre_rows)
+    constexpr bool kPre = LOG2N == 10 || LOG2N == 11 || LOG2N == 13 || LOG2N == 14;
+    if (a.pre && !kPre) return cudaErrorInvalidValue;
+    auto k = a.pre ? pfb_direct_kernel<LOG2N, kPre> : pfb_direct_kernel<LOG2N, false>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
@@ -1274,31 +1297,40 @@ cudaError_t launch_direct(PfbArgs a, int n_sms, int max_smem, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// The first half of a 16-tap frame's FIR for the two-pass 16-tap form
-// (N = 4096): pre[j][p] = sum_{t<8} h[t N + p] x[(j + t) N + p] over the
-// stream view [carry | buffer], FMAs in tap order from zero as in the TMEM
-// kernel's FIR (which then continues the same sums with taps 8..15).  A
-// thread takes kPrePts points of kPreFrames consecutive frames, whose
-// kPreFrames + 7 input blocks it loads and converts once; the frame groups
-// of a point range are consecutive CTAs (shared blocks come from DRAM once).
-constexpr int kPreThreads = 256, kPrePts = 4, kPreFrames = 4;
-__global__ void __launch_bounds__(kPreThreads) fir8_pre_kernel(const PfbArgs a, float2* __restrict__ pre) {
-    constexpr int N = 4096, TT = 8, G = kPreFrames, P = kPrePts, R = G + TT - 1;
+// FIR sums of the first T (<= TMAX) taps of every frame of the stream view
+// [carry | buffer] (N channels):
+//   pre[j][p] = sum_{t<T} h[t N + p] x[(j + t) N + p],
+// FMAs in tap order from zero, the order of the fused kernels' FIRs, which
+// continue these sums (the 16-tap N = 4096 form: taps 0..7 here, 8..15 in
+// the TMEM kernel) or take them whole (the direct kernel).  A thread takes
+// P points (kPreThreads apart) of kPreFrames consecutive frames and loads
+// and converts each of their kPreFrames + T - 1 input blocks once; the frame
+// groups of a point range are consecutive CTAs, so the blocks two groups
+// share and the range's taps come from DRAM once.
+constexpr int kPreThreads = 256, kPreFrames = 4;
+template <int TMAX, int P, int LOG2N, bool EXACT>
+__global__ void __launch_bounds__(kPreThreads) fir_pre_kernel(const PfbArgs a, int T_arg, float2* __restrict__ pre) {
+    constexpr int N = 1 << LOG2N, G = kPreFrames, R = G + TMAX - 1;
+    const int T = EXACT ? TMAX : T_arg;              // EXACT: T == TMAX, known at compile time
     const int64_t f0 = static_cast<int64_t>(blockIdx.x) * G;
     const int gn = static_cast<int>(min_i64(a.F - f0, G));
     const int qb = static_cast<int>(blockIdx.y) * (kPreThreads * P) + static_cast<int>(threadIdx.x);
-    float hv[TT][P];
+    float hv[TMAX][P];
 #pragma unroll
-    for (int t = 0; t < TT; ++t)
+    for (int t = 0; t < TMAX; ++t)
 #pragma unroll
-        for (int k = 0; k < P; ++k) hv[t][k] = __ldg(a.h + t * N + qb + k * kPreThreads);
+        for (int k = 0; k < P; ++k) {
+            const int q = qb + k * kPreThreads;
+            hv[t][k] = (t < T && q < N) ? __ldg(a.h + t * N + q) : 0.f;
+        }
     const int64_t base = f0 * N + qb;
     uint32_t w[R][P];
 #pragma unroll
     for (int r = 0; r < R; ++r)
 #pragma unroll
         for (int k = 0; k < P; ++k)
-            w[r][k] = r < gn + TT - 1 ? vload(a, base + static_cast<int64_t>(r) * N + k * kPreThreads) : 0u;
+            w[r][k] = (r < gn + T - 1 && qb + k * kPreThreads < N)
+                          ? vload(a, base + static_cast<int64_t>(r) * N + k * kPreThreads) : 0u;
     float ar[G][P], ai[G][P];
 #pragma unroll
     for (int g = 0; g < G; ++g)
@@ -1312,7 +1344,7 @@ __global__ void __launch_bounds__(kPreThreads) fir8_pre_kernel(const PfbArgs a, 
 #pragma unroll
             for (int g = 0; g < G; ++g) {
                 const int t = r - g;
-                if (t < 0 || t >= TT) continue;
+                if (t < 0 || t >= TMAX || t >= T) continue;
                 ar[g][k] = fmaf(hv[t][k], x.x, ar[g][k]);
                 ai[g][k] = fmaf(hv[t][k], x.y, ai[g][k]);
             }
@@ -1322,7 +1354,41 @@ __global__ void __launch_bounds__(kPreThreads) fir8_pre_kernel(const PfbArgs a, 
     for (int g = 0; g < G; ++g) {
         if (g >= gn) break;
 #pragma unroll
-        for (int k = 0; k < P; ++k) pre[(f0 + g) * N + qb + k * kPreThreads] = make_float2(ar[g][k], ai[g][k]);
+        for (int k = 0; k < P; ++k) {
+            const int q = qb + k * kPreThreads;
+            if (q < N) pre[(f0 + g) * N + q] = make_float2(ar[g][k], ai[g][k]);
+        }
+    }
+}
+
+// The pre-sum rows of the first T taps of a.F frames (2^lg channels) into
+// pre: instances for the shapes that take them (rfr::pfb_pre_rows).
+template <int TMAX, int P, int LOG2N>
+cudaError_t launch_pre_n(const PfbArgs& a, int T, float2* pre, cudaStream_t st) {
+    const dim3 g(static_cast<unsigned>((a.F + kPreFrames - 1) / kPreFrames),
+                 static_cast<unsigned>(((1 << LOG2N) + kPreThreads * P - 1) / (kPreThreads * P)));
+    if (T == TMAX)
+        fir_pre_kernel<TMAX, P, LOG2N, true><<<g, kPreThreads, 0, st>>>(a, T, pre);
+    else
+        fir_pre_kernel<TMAX, P, LOG2N, false><<<g, kPreThreads, 0, st>>>(a, T, pre);
+    return cudaGetLastError();
+}
+cudaError_t launch_pre(const PfbArgs& a, int lg, int T, float2* pre, cudaStream_t st) {
+    if (T < 1 || T > 16) return cudaErrorInvalidValue;
+    if (T <= 8) {
+        switch (lg) {
+        case 12: return launch_pre_n<8, 4, 12>(a, T, pre, st);
+        case 13: return launch_pre_n<8, 4, 13>(a, T, pre, st);
+        case 14: return launch_pre_n<8, 4, 14>(a, T, pre, st);
+        default: return cudaErrorInvalidValue;
+        }
+    }
+    switch (lg) {
+    case 10: return launch_pre_n<16, 2, 10>(a, T, pre, st);
+    case 11: return launch_pre_n<16, 2, 11>(a, T, pre, st);
+    case 13: return launch_pre_n<16, 2, 13>(a, T, pre, st);
+    case 14: return launch_pre_n<16, 2, 14>(a, T, pre, st);
+    default: return cudaErrorInvalidValue;
     }
 }
 
@@ -1478,6 +1544,17 @@ cudaError_t dispatch_ring_T(PfbArgs a, int tk, int n_sms, int max_smem, int la, 
 bool pfb_uses_ring(int log2n, int taps) { return log2n >= 4 && log2n <= 12 && taps <= 8; }
 int pfb_cluster_size(int log2n, int taps) { return (log2n == 13 || log2n == 14) && taps <= 8 ? 1 << (log2n - 12) : 0; }
 bool pfb_split16(int log2n, int taps) { return log2n == 12 && taps == 16; }
+// Where the direct kernel takes its FIR from a pre-sum pass (measured, 2^28
+// samples, full + tones): N = 8192 at every T (T = 8: 3.14 -> 2.22 ms),
+// N = 16384 from T = 8 on (2.73 -> 2.24 ms; T = 4 1.87 -> 2.14 ms, so not
+// there), N = 1024 and 2048 with T > 8 (T = 16: 5.39 -> 3.95 and 4.92 ->
+// 3.30 ms); N = 256 with T = 16 lost 7 %, so smaller N keep the in-kernel FIR.
+bool pfb_pre_rows(int log2n, int taps) {
+    if (pfb_split16(log2n, taps)) return true;
+    if (log2n == 13) return true;
+    if (log2n == 14) return taps > 4;
+    return log2n >= 10 && log2n <= 11 && taps > 8;
+}
 int pfb_kernel_taps(int log2n, int taps) {
     if (pfb_uses_ring(log2n, taps) || pfb_cluster_size(log2n, taps) > 0) return taps <= 4 ? 4 : 8;
     if (log2n == 12 && taps > 8 && taps <= 16) return 16;     // two 8-tap passes (see pfb_launch)
@@ -1524,7 +1601,7 @@ cudaError_t pfb_launch(const PfbLaunch& L, cudaStream_t st) {
     if (pfb_split16(lg, L.taps_kernel)) {
         // N = 4096, T = 16 (9 .. 16 taps, zero-padded at the oldest end):
         // the FIR of taps 0..7 over the window's first 8 blocks by
-        // fir8_pre_kernel into L.pre, then the TMEM kernel over the view 8N
+        // fir_pre_kernel into L.pre, then the TMEM kernel over the view 8N
         // samples on with taps 8..15, its FIR sums starting from those rows
         // (the same FMA chain as one 16-tap FIR).  The caller passes a
         // 16-byte aligned view and L.pre for at least F frames.
@@ -1532,9 +1609,7 @@ cudaError_t pfb_launch(const PfbLaunch& L, cudaStream_t st) {
         constexpr int64_t half = int64_t(8) * 4096;
         PfbArgs a1 = a;
         a1.T = 8;
-        const dim3 pg(static_cast<unsigned>((a.F + kPreFrames - 1) / kPreFrames), 4096 / (kPreThreads * kPrePts));
-        fir8_pre_kernel<<<pg, kPreThreads, 0, st>>>(a1, static_cast<float2*>(L.pre));
-        cudaError_t e = cudaGetLastError();
+        cudaError_t e = launch_pre(a1, 12, 8, static_cast<float2*>(L.pre), st);
         if (e != cudaSuccess) return e;
         PfbArgs a2 = a1;
         a2.h = a.h + half;
@@ -1573,6 +1648,14 @@ cudaError_t pfb_launch(const PfbLaunch& L, cudaStream_t st) {
         case 12: return dispatch_ring_T<12>(a, L.taps_kernel, L.n_sms, L.max_smem, L.lookahead, st);
         default: return cudaErrorInvalidValue;
         }
+    }
+    if (L.pre) {
+        // the FIR of all taps ahead, as its own DRAM-streaming pass (the
+        // direct kernel would re-read every tap and sample T times through L2)
+        if (L.pre_cap < a.F) return cudaErrorInvalidValue;
+        cudaError_t e = launch_pre(a, lg, L.taps_kernel, static_cast<float2*>(L.pre), st);
+        if (e != cudaSuccess) return e;
+        a.pre = static_cast<const float2*>(L.pre);
     }
     switch (lg) {
     case 4: return launch_direct<4>(a, L.n_sms, L.max_smem, st);

@@ -55,7 +55,7 @@ struct PfbLaunch {
     int cluster;        // N = 8192, 16384 (T <= 8): the cluster kernel instead of the direct one
     const void* tw_cl;  // its twiddles: the 4096-point FFT's, then W_N^(k2 p1)
     int tw_cl_count;    // entries of the 4096-point FFT part
-    void* pre;          // N = 4096 with 16 kernel taps: FIR partial-sum rows [pre_cap][4096] (float2)
+    void* pre;          // FIR pre-sum rows [pre_cap][N] (float2) of pfb_pre_rows plans, or null
     int64_t pre_cap;
 };
 bool pfb_uses_ring(int log2n, int taps);
@@ -109,6 +109,9 @@ int pfb_cluster_size(int log2n, int taps);
 // N = 4096 with 16 kernel taps: a first-half FIR pass, then the TMEM kernel
 // seeded with it (aligned view, PfbLaunch::pre for the frames).
 bool pfb_split16(int log2n, int taps);
+// PFB plans whose pushes take FIR pre-sum rows (PfbLaunch::pre): the 16-tap
+// N = 4096 form and the direct kernel's shapes (N = 8192, 16384; T > 8).
+bool pfb_pre_rows(int log2n, int taps);
 cudaError_t pfb_launch(const PfbLaunch& L, cudaStream_t st);
 cudaError_t gen_pfb_launch(const PfbLaunch& L, const GenPlan& g, cudaStream_t st);
 
@@ -243,8 +246,8 @@ struct rfr_plan {
     int64_t view_cap = 0;                      //   when the push is not 16-byte aligned (samples)
     void* d_ptones = nullptr;                  // phase passes: each pass's tones [pass][tone][frame]
     int64_t ptones_cap = 0;                    //   frames per pass row
-    void* d_pre = nullptr;                     // N = 4096 with 9..16 taps: first-half FIR rows
-    int64_t pre_cap = 0;                       //   [frame][4096] float2, frames
+    void* d_pre = nullptr;                     // FIR pre-sum rows (rfr::pfb_pre_rows plans)
+    int64_t pre_cap = 0;                       //   [frame][N] float2, frames
     bool gen = false;                          // PFB through the any-N kernels
     rfr::GenPlan gplan;
     int32_t L = 0, D = 0, Lpad = 0;            // demod
