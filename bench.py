@@ -676,8 +676,9 @@ def run_large_n(args, dev, stream, x, words):
     two-pass form), and the workload's N = 4096, T = 8 Kaiser(9) oversampled
     4x (hop 1024, the mixed-radix one-pass form); and the batched workload's
     power-of-two shapes whose FP32 delay line does not fit one SM's tensor
-    memory (N = 16384 and 8192 with T = 8, direct kernel and cluster kernel;
-    N = 4096 T = 16, N = 16384 T = 16, direct kernel; Kaiser(9));
+    memory (N = 16384 and 8192 with T = 8, direct kernel with its pre-sum
+    FIR pass, and cluster kernel; N = 4096 T = 16 (pre-sum pass + TMEM
+    kernel), N = 16384 T = 16 (pre-sum pass + direct kernel); Kaiser(9));
     each on the workload's 2^28-sample stream, full spectrum + its 1000 tones."""
     import torch
 

@@ -157,9 +157,13 @@ typedef struct {
  * graph; rfr_server_create sizes them for its largest buffer, so serving
  * never allocates).  Demodulation plans likewise allocate their per-push
  * scratch (the FP16 split of the stream and the rotation tables) on the first
- * push of a given size, which synchronises the device; inside a stream
- * capture such a push fails with RFR_E_INVALID instead, so push once at the
- * largest size outside capture first.
+ * push of a given size, and so do PFB plans that run their FIR as a separate
+ * pre-sum pass (N = 8192; N = 16384 with T > 4; N = 1024, 2048 and 4096 with
+ * T > 8: 8 bytes per channel and frame) or the oversampled phase passes; a
+ * push that grows scratch synchronises the device and sizes it for that many
+ * samples after any carry.  Inside a stream capture such a push fails with
+ * RFR_E_INVALID instead, so push once at the largest size outside capture
+ * first.
  * Errors: RFR_E_INVALID (parameters), RFR_E_NOMEM, RFR_E_CUDA.
  */
 rfr_status rfr_plan_create(rfr_plan** plan, int32_t channels, int32_t taps,
@@ -493,10 +497,11 @@ rfr_status rfr_plan_get_demod_pair(const rfr_plan* plan, int32_t* on);
  * FFT is split into a radix-(N/4096) step across the CTAs (filtered slices
  * exchanged through distributed shared memory) and a 4096-point FFT per
  * CTA, and the output rows are assembled the same way.  on = 0 (the
- * default): the direct kernel (taps and samples through L1/L2), which
- * measured faster (99 against 57 Gs/s at N = 16384, T = 8): with one frame
- * in flight per CTA the cross-SM exchanges and cluster barriers of every
- * frame cannot be hidden.  The two round differently (both within the
+ * default): the direct kernel (one CTA per frame, the FIR as a separate
+ * pre-sum pass for T > 4 at N = 16384 and any T at N = 8192, else through
+ * L1/L2), which measured faster (132 against 58 Gs/s at N = 16384, T = 8):
+ * with one frame in flight per CTA the cross-SM exchanges and cluster
+ * barriers of every frame cannot be hidden.  The two round differently (both within the
  * oracle's tolerance), so choose before the first push; the autotuner times
  * both.  Errors: RFR_E_INVALID (another plan shape, on not 0/1). */
 rfr_status rfr_plan_set_pfb_cluster(rfr_plan* plan, int32_t on);
