@@ -158,8 +158,8 @@ typedef struct {
  * never allocates).  Demodulation plans likewise allocate their per-push
  * scratch (the FP16 split of the stream and the rotation tables) on the first
  * push of a given size, and so do PFB plans that run their FIR as a separate
- * pre-sum pass (N = 8192; N = 16384 with T > 4; N = 1024, 2048 and 4096 with
- * T > 8: 8 bytes per channel and frame) or the oversampled phase passes; a
+ * pre-sum pass (N = 8192; N = 16384 with T > 4; N = 256 to 4096 with T > 8:
+ * 8 bytes per channel and frame) or the oversampled phase passes; a
  * push that grows scratch synchronises the device and sizes it for that many
  * samples after any carry.  Inside a stream capture such a push fails with
  * RFR_E_INVALID instead, so push once at the largest size outside capture

@@ -1286,7 +1286,7 @@ cudaError_t launch_direct(PfbArgs a, int n_sms, int max_smem, cudaStream_t st) {
     const int64_t n_iter = (a.F + G - 1) / G;
     int per_sm = 1;
     // pre-sum instances only for the shapes that take them (pfb_pre_rows)
-    constexpr bool kPre = LOG2N == 10 || LOG2N == 11 || LOG2N == 13 || LOG2N == 14;
+    constexpr bool kPre = (LOG2N >= 8 && LOG2N <= 11) || LOG2N == 13 || LOG2N == 14;
     if (a.pre && !kPre) return cudaErrorInvalidValue;
     auto k = a.pre ? pfb_direct_kernel<LOG2N, kPre> : pfb_direct_kernel<LOG2N, false>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1389,6 +1389,8 @@ cudaError_t launch_pre(const PfbArgs& a, int lg, int T, float2* pre, cudaStream_
     }
     // more taps: one point and eight frames per thread
     switch (lg) {
+    case 8: return launch_pre_n<16, 1, 8, 8>(a, T, pre, st);
+    case 9: return launch_pre_n<16, 1, 8, 9>(a, T, pre, st);
     case 10: return launch_pre_n<16, 1, 8, 10>(a, T, pre, st);
     case 11: return launch_pre_n<16, 1, 8, 11>(a, T, pre, st);
     case 13: return launch_pre_n<16, 1, 8, 13>(a, T, pre, st);
@@ -1550,15 +1552,16 @@ bool pfb_uses_ring(int log2n, int taps) { return log2n >= 4 && log2n <= 12 && ta
 int pfb_cluster_size(int log2n, int taps) { return (log2n == 13 || log2n == 14) && taps <= 8 ? 1 << (log2n - 12) : 0; }
 bool pfb_split16(int log2n, int taps) { return log2n == 12 && taps == 16; }
 // Where the direct kernel takes its FIR from a pre-sum pass (measured, 2^28
-// samples, full + tones): N = 8192 at every T (T = 8: 3.14 -> 2.22 ms),
-// N = 16384 from T = 8 on (2.73 -> 2.24 ms; T = 4 1.87 -> 2.14 ms, so not
-// there), N = 1024 and 2048 with T > 8 (T = 16: 5.39 -> 3.95 and 4.92 ->
-// 3.30 ms); N = 256 with T = 16 lost 7 %, so smaller N keep the in-kernel FIR.
+// samples, full + tones): N = 8192 at every T (T = 8: 3.14 -> 1.81 ms),
+// N = 16384 from T = 8 on (2.73 -> 1.85 ms; T = 4 1.87 -> 2.14 ms, so not
+// there), N = 256 .. 2048 with T > 8 (T = 16: N = 1024 5.39 -> 3.15 ms,
+// N = 256 with 64 tones 4.39 -> 1.61 ms).  Smaller N, or T <= 8 below
+// N = 4096, run on the shared-memory ring kernel.
 bool pfb_pre_rows(int log2n, int taps) {
     if (pfb_split16(log2n, taps)) return true;
     if (log2n == 13) return true;
     if (log2n == 14) return taps > 4;
-    return log2n >= 10 && log2n <= 11 && taps > 8;
+    return log2n >= 8 && log2n <= 11 && taps > 8;
 }
 int pfb_kernel_taps(int log2n, int taps) {
     if (pfb_uses_ring(log2n, taps) || pfb_cluster_size(log2n, taps) > 0) return taps <= 4 ? 4 : 8;

@@ -76,10 +76,13 @@ CASES = [
     (4096, 8, "kaiser", 9.0, 400),
     (4096, 12, "kaiser", 9.0, 60),    # first-half FIR pass + TMEM kernel (taps padded to 16)
     (4096, 16, "hann", 0.0, 50),      # first-half FIR pass + TMEM kernel
-    (1024, 16, "hann", 0.0, 80),      # DIRECT variant
-    (8192, 4, "hann", 0.0, 40),       # DIRECT variant (N > 4096)
-    (16384, 2, "kaiser", 9.0, 30),    # DIRECT variant, taps padded to 4
-    (16384, 12, "kaiser", 9.0, 20),   # DIRECT variant, largest N, T > 8
+    (1024, 16, "hann", 0.0, 80),      # DIRECT variant, FIR as a pre-sum pass
+    (256, 12, "kaiser", 9.0, 120),    # DIRECT variant, T > 8 at small N
+    (2048, 9, "hamming", 0.0, 60),    # DIRECT variant, pre-sum pass, odd T
+    (8192, 4, "hann", 0.0, 40),       # DIRECT variant (N > 4096), pre-sum pass
+    (8192, 8, "kaiser", 9.0, 30),     # DIRECT variant, pre-sum pass
+    (16384, 2, "kaiser", 9.0, 30),    # DIRECT variant, taps padded to 4, FIR in the kernel
+    (16384, 12, "kaiser", 9.0, 20),   # DIRECT variant, largest N, T > 8, pre-sum pass
 ]
 
 
