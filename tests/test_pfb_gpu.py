@@ -83,6 +83,8 @@ CASES = [
     (8192, 8, "kaiser", 9.0, 30),     # DIRECT variant, pre-sum pass
     (16384, 2, "kaiser", 9.0, 30),    # DIRECT variant, taps padded to 4, FIR in the kernel
     (16384, 12, "kaiser", 9.0, 20),   # DIRECT variant, largest N, T > 8, pre-sum pass
+    (16384, 8, "kaiser", 9.0, 20),    # DIRECT variant, pre-sum pass (the large-N default at T = 8)
+    (512, 16, "blackman", 0.0, 100),  # DIRECT variant, pre-sum pass, 16 taps
 ]
 
 
