@@ -1,6 +1,6 @@
-// pfb_kernels.cu -- the fused polyphase filter bank (Sec. III.A of
-// arXiv:1812.02200): int16 IQ -> FP32 polyphase FIR -> N-point FFT -> full
-// spectrum and/or tone-bin gather, in one kernel per push.
+// pfb_kernels.cu -- the polyphase filter bank of Sec. III.A of
+// arXiv:1812.02200 for power-of-two N: int16 IQ -> FP32 polyphase FIR ->
+// N-point FFT -> full spectrum and/or tone-bin gather.
 //
 // Stream view.  A push sees the virtual stream v = [carry | buffer]: `carry`
 // (plan-owned, device) holds the last W - N + r samples of the stream (zero
@@ -11,19 +11,26 @@
 //     y_j[c] = sum_p v_j[p] exp(-2*pi*i*c*p/N)
 // which is frame (F0 + j) of the stream, F0 the frames before this push.
 //
-// Three variants:
+// Kernels:
 //  TMEM   (N = 4096, T <= 8, 16-byte aligned pushes): the FP32 delay line in
 //         tensor memory, int16 blocks by 1-D TMA, spectrum rows by TMA bulk
-//         stores and tone groups by 2-D TMA tensor stores (see below).
+//         stores and tone groups by 2-D TMA tensor stores (see below); the
+//         symmetric-tap form (exactly symmetric taps, the plan default) pairs
+//         mirrored rows per lane pair and also runs the phase passes of
+//         oversampled plans; a seeded form continues FIR sums from pre-sum
+//         rows (N = 4096 with 9..16 taps: first-half pass + taps 8..15).
 //  RING   (N <= 4096, T <= 8 after padding): each CTA owns a contiguous run
 //         of "super-blocks" (4096 samples = G = 4096/N frames' worth of new
 //         samples).  A ring of super-blocks in shared memory is filled by
 //         1-D TMA bulk copies (cp.async.bulk + mbarrier complete_tx), P
 //         super-blocks ahead; each sample is read from HBM once.  The FIR
 //         taps of the thread's 16 branches live in registers.
-//  DIRECT (any other N <= 16384, T <= 16): no ring; the T samples of every
-//         branch are read from global memory (L2 serves the T-fold reuse)
-//         and the taps with __ldg.
+//  CLUSTER (N = 8192, 16384, T <= 8; a plan choice): N/4096 CTAs per frame
+//         sharing the FFT through distributed shared memory.
+//  DIRECT (any other N <= 16384, T <= 16): the in-CTA FFT per frame, its FIR
+//         either a separate DRAM-streaming pre-sum pass (fir_pre_kernel; N =
+//         8192, 16384 with T > 4, N = 256 .. 2048 with T > 8) or read from
+//         global memory inside the kernel (L2 serves the T-fold reuse).
 // RING and DIRECT run the in-CTA FFT of fft_dev.cuh (TMEM the same passes
 // written out for N = 4096); all write
 //   full[(frame_offset + j) * full_ld + c]      (natural bin order)
@@ -1565,7 +1572,7 @@ bool pfb_pre_rows(int log2n, int taps) {
 }
 int pfb_kernel_taps(int log2n, int taps) {
     if (pfb_uses_ring(log2n, taps) || pfb_cluster_size(log2n, taps) > 0) return taps <= 4 ? 4 : 8;
-    if (log2n == 12 && taps > 8 && taps <= 16) return 16;     // two 8-tap passes (see pfb_launch)
+    if (log2n == 12 && taps > 8 && taps <= 16) return 16;     // first-half pass + seeded TMEM kernel (pfb_launch)
     return taps;
 }
 
