@@ -132,8 +132,11 @@ typedef struct {
  *              uses N = 10^5, the section reports up to 10^7 bins).  N must have
  *              no prime factor above 7 (N = 2^a 3^b 5^c 7^d); any other N
  *              returns RFR_E_UNSUPPORTED.  Powers of two from 16 to 16384 run
- *              the fused single-CTA kernels, every other N the mixed-radix
- *              kernels (one pass up to 8192, a four-step two-pass form above).
+ *              the single-CTA-per-frame kernels (FIR, FFT and gather fused
+ *              where the delay line fits one SM; for N = 8192, 16384 or
+ *              T > 8 the FIR as a separate pre-sum pass first), every other
+ *              N the mixed-radix kernels (one pass up to 8192, a four-step
+ *              two-pass form above).
  *              0: direct demodulation.
  *   taps       PFB: T taps per channel, 1 <= T <= 16 (prototype length N*T).
  *              Demodulation: filter length L, 1 <= L <= 16384.
@@ -145,7 +148,8 @@ typedef struct {
  *              at sample (k+1)*H - 1, each channel keeping the phase of the
  *              absolute time origin, so channel c equals the demodulator's
  *              output for the bin-centred word; oversampled plans run the
- *              mixed-radix kernels).  Demodulation: D >= 1 and D a multiple
+ *              mixed-radix kernels, except N = 4096, T = 8 at H = N/2 or N/4,
+ *              which runs as exact phase passes of the fused kernel).  Demodulation: D >= 1 and D a multiple
  *              of 32 for the tensor-core path.
  *   out_flags  PFB: any non-empty combination of RFR_OUT_FULL, RFR_OUT_TONES
  *              (RFR_OUT_TONES needs count > 0).  Demodulation: RFR_OUT_TONES.
